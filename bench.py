@@ -1,0 +1,329 @@
+"""Throughput of the TWA hot path on B300: spin-trajectory-steps per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: N = 10^4 spins, alpha = 1, w = N Gamma / 2, Gamma = 1, dt = 2e-5,
+M = 1024 trajectories per GPU (weak scaling: rank r runs trajectories
+[r M, (r+1) M) of one ensemble), W and L held as BF16 hi+lo images, FP32 state,
+BF16X3 contractions on tcgen05. One step = one stochastic-Heun step of all M
+trajectories: noise, L.eta and W.s (predictor), W.s~ (corrector), moments.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
+the host cores instead, on a bounded trajectory sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2608_10075_b300.configs import LARGE_N1E4 as CFG  # noqa: E402
+
+METRIC = "spin-traj-steps/s at N=1e4 (mixed vs FP64 GPU, observables within 3 SE)"
+UNIT = "spin-traj-steps/s"
+WORKLOAD = ("TWA stochastic Heun, N=10000 alpha=1 w=5000 Gamma=1 dt=2e-5, M=1024 trajectories/GPU, "
+            "BF16X3 (hi+lo W, L) tcgen05 contractions, FP32 state")
+REF_SAMPLE_M = 16
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def recorded_traffic(kernel_file, summary):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (matching sha256 prefix); else None."""
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2608_10075_b300", "csrc", kernel_file)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    txt = open(path).read()
+    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if m_sha and m_b and m_sha.group(1) == sha:
+        return float(m_b.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def contraction_flops(N, M, terms_w=3, terms_l=2):
+    """Tensor-core FLOPs of one predictor and one corrector launch.
+
+    Predictor: W.s over all N^2 entries for 2M columns with `terms_w` products
+    (BF16X3: 3), plus L.eta over the N(N+1)/2 lower-triangular entries with
+    `terms_l` products (hi and lo of L against the BF16 noise). Corrector: W.s~.
+    """
+    cols = 2 * M
+    wflops = 2.0 * N * N * cols * terms_w
+    lflops = 2.0 * (N * (N + 1) / 2.0) * cols * terms_l
+    return wflops + lflops, wflops
+
+
+def cpu_oracle_rate(N, M_sample, steps, cfg):
+    """Time the FP64 CPU oracle (as it stands) on a trajectory sample."""
+    import numpy as np  # noqa: F401
+    from threadpoolctl import threadpool_info
+
+    from oracle.twa_oracle import TWAOracle
+    o = TWAOracle(N, cfg["alpha"], cfg["w"], cfg["Gamma"], cfg["dt"], 0, M_sample)
+    o.run(1)   # warm-up step (first-touch of buffers)
+    t0 = time.perf_counter()
+    o.run(steps)
+    el = time.perf_counter() - t0
+    threads = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    return N * M_sample * steps / el, el, threads
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    N = CFG["N"]
+    K, Wm = args.steps, args.warmup
+    from oracle.twa_oracle import TWAOracle
+    from threadpoolctl import threadpool_info
+    t_setup = time.perf_counter()
+    o = TWAOracle(N, CFG["alpha"], CFG["w"], CFG["Gamma"], CFG["dt"], 0, REF_SAMPLE_M)
+    t_setup = time.perf_counter() - t_setup
+    o.run(Wm)
+    t0 = time.perf_counter()
+    o.run(K)
+    el = time.perf_counter() - t0
+    threads = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    v = N * REF_SAMPLE_M * K / el
+    sample = "%d of the %d trajectories, all %d sites, %d timed steps (+%d warm-up); W, L set-up %.1f s untimed" % (
+        REF_SAMPLE_M, CFG["M"], N, K, Wm, t_setup)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": 1e3 * el / max(K, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("M=1024 trajectories/GPU", "M=%d-trajectory sample" % REF_SAMPLE_M)
+                       + " (FP64 CPU oracle)", "N": N, "M": REF_SAMPLE_M, "alpha": CFG["alpha"], "w": CFG["w"],
+                       "dt": CFG["dt"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2608_10075_b300 import twa
+
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    N, M = CFG["N"], CFG["M"]
+    K, Wm = args.steps, args.warmup
+    ctx = twa.TWA(N, CFG["alpha"], CFG["w"], CFG["Gamma"], CFG["dt"], seed=0, precision=CFG["precision"],
+                  window_start=0.0, stream=stream, traj_offset=rank * M)
+    ctx.run(M, 0)
+    ctx.run(M, Wm)
+    ctx.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- timed region: K steps, device-resident inputs ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.run(M, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ctx.sync()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * M * world * K / (ms * 1e-3)
+
+    # ---- per-kernel times on the launching stream (separate pass) ----
+    kp = min(K, 50)
+    ctx.profile(True)
+    ctx.run(M, kp)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    pred_ms = prof["predict"][0] / max(prof["predict"][1], 1)
+    corr_ms = prof["correct"][0] / max(prof["correct"][1], 1)
+    step_kernel_ms = sum(v[0] for v in prof.values()) / max(kp, 1)
+    terms_w = 3 if CFG["precision"] == "bf16x3" else 1
+    terms_l = 2 if CFG["precision"] == "bf16x3" else 1
+    pflops, cflops = contraction_flops(N, M, terms_w, terms_l)
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    dominant = "predict" if prof["predict"][0] >= prof["correct"][0] else "correct"
+    d_ms = pred_ms if dominant == "predict" else corr_ms
+    d_flops = pflops if dominant == "predict" else cflops
+    achieved = d_flops / (d_ms * 1e-3) / 1e12
+    traffic = recorded_traffic("twa_tc.cu", "tc_predict_n10000.md") if dominant == "predict" else None
+
+    # ---- end to end through the C ABI with host buffers ----
+    xs = [torch.empty((M, N), dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    ctx.get_state(out=tuple(x.numpy() for x in xs))
+    mom_bytes = 5 * 8 * M
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.set_state(*(x.numpy() for x in xs))          # host -> device, pinned
+    ctx.run(M, K)
+    mom = ctx.moments()                               # device -> host
+    obs = ctx.observables()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = N * M * world * K / t_e2e
+    h2d = 3 * 8 * M * N
+    d2h = mom_bytes + 160
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        steps_cpu = 3
+        v, el, threads = cpu_oracle_rate(N, REF_SAMPLE_M, steps_cpu, CFG)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d trajectories x %d sites x %d steps of the same workload (%.1f s); W, L set-up untimed"
+                         % (REF_SAMPLE_M, N, steps_cpu, el)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "M_per_gpu": M, "alpha": CFG["alpha"], "w": CFG["w"],
+                       "Gamma": CFG["Gamma"], "dt": CFG["dt"], "precision": CFG["precision"],
+                       "parallelism": "trajectory shards, no data-path collective" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: W and L BF16 hi+lo images 600 MB, state 0.9 GB"},
+            "roofline": {"bound": "tensor", "kernel": "k_tc<%s>" % dominant, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": "%s bf16_tflops_sustained" % peak_src,
+                         "kernel_ms": d_ms, "flops_per_launch": d_flops,
+                         "kernel_ms_per_step": {k: v[0] / max(kp, 1) for k, v in prof.items() if v[1]},
+                         "step_kernel_ms": step_kernel_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+                    "note": "set_state from pinned host FP64 buffers, K steps, moments and observables to host"},
+            "gpu_launches": 4 * K,
+            "clocks": clk,
+            "observables": {k: obs[k] for k in ("sigma_z", "SpSm", "g2", "w_tilde", "stability", "nonfinite")},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+            dist_mod.init_process_group("nccl")
+        else:
+            dist_mod.init_process_group("gloo")
+        dist = dist_mod
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

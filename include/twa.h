@@ -1,0 +1,207 @@
+/*
+ * twa.h - C ABI of libtwa, a single-GPU (sm_103a) engine for the dissipative
+ * truncated-Wigner (TWA) dynamics of N spins under collective cavity decay and
+ * a spatially correlated pump (arxiv 2608.10075).
+ *
+ * Model (Eq. 1, Eq. 2): collective decay at rate Gamma through S^- = sum_i
+ * sigma_i^-, pump matrix w_ij = w / (|i-j| + 1)^alpha on an open chain.
+ * Dynamics (Sec. S1, Eq. S1): every trajectory m carries classical spins
+ * s_i = (x_i, y_i, z_i), i < N, moved by
+ *     d x_i =  z_i B^x_i,   d y_i = z_i B^y_i,   d z_i = -(x_i B^x_i + y_i B^y_i),
+ *     B^a_i  = 1/2 (Gamma S^a - sum_j w_ij s^a_j) dt + sqrt(Gamma dt) xi^a
+ *              - sqrt(dt) (L eta^a)_i,           a = x, y,
+ * with S^a = sum_j s^a_j, one collective normal xi^a per trajectory and step
+ * (the noise <xi xi> = Gamma has no site index), eta^a iid normals per site,
+ * and L L^T = W. Integrator: stochastic Heun (Stratonovich), then every spin is
+ * rescaled to length sqrt(3). Initial state (Sec. S1, item 3): x, y = +-1,
+ * z = init_state. Observables (Sec. S1, items 5-6, main text): window and
+ * ensemble means of S^z, <S+S-> = A + S^z/2 and
+ * <S+S+S-S-> = A^2 + 2 A S^z - S^z/3 + (S^z)^2/2 - 4/3 A, with A = |S^x + i S^y|^2/4,
+ * and g2 = <S+S+S-S-> / <S+S->^2.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32
+ * bits, seed high 32 bits), counter = (trajectory m, step t, site i, stream).
+ * Stream 0 gives the pump noise (i < N) and the collective noise (i = N),
+ * stream 1 (t = 0) the initial signs. Results depend only on (parameters, seed,
+ * m, t), never on launch shapes, so runs can be continued or split by
+ * trajectory and reproduce one uninterrupted run.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 on success or a negative TWA_E* code; no exception crosses the
+ *    ABI. After an error, twa_last_error(ctx) holds a one-line message. The
+ *    context stays usable after TWA_EINVAL.
+ *  - The library owns every device buffer it allocates (cudaMalloc on the
+ *    current device at twa_init); twa_destroy frees them. Caller buffers are
+ *    only read or written during the call that receives them (device buffers:
+ *    in stream order on the context's stream).
+ *  - Work is enqueued on the stream given in twa_opts (NULL = the legacy
+ *    default stream). twa_run only enqueues; errors raised on the device
+ *    (non-finite spins, a timed-out wait) are reported by the next call that
+ *    synchronises: twa_sync, twa_observables, twa_get_state, twa_get_moments.
+ *  - State arrays are [M][N] row-major: element (m, i) at m*N + i.
+ */
+#ifndef TWA_H
+#define TWA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TWA_API __attribute__((visibility("default")))
+#else
+#define TWA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define TWA_OK            0
+#define TWA_EINVAL       -1  /* bad argument; nothing was changed            */
+#define TWA_ENOTPSD      -2  /* the pump matrix has a non-positive pivot     */
+#define TWA_ENOMEM       -3  /* device allocation failed                     */
+#define TWA_ECUDA        -4  /* a CUDA call failed (message names it)        */
+#define TWA_ETIMEOUT     -5  /* a device-side wait ran out of its time limit */
+#define TWA_ENONFINITE   -6  /* a spin component became NaN or Inf           */
+#define TWA_ESTATE       -7  /* call out of order (e.g. no trajectories yet) */
+#define TWA_EUNSUPPORTED -8  /* option not available for these parameters   */
+
+/* arithmetic of the per-step contractions W.S and L.eta */
+#define TWA_PREC_FP64    0   /* FP64 everywhere (SIMT DFMA)                              */
+#define TWA_PREC_BF16    1   /* tcgen05 BF16 x BF16 -> FP32, one term, FP32 state        */
+#define TWA_PREC_BF16X3  2   /* tcgen05 split hi+lo: hi*hi + hi*lo + lo*hi, FP32 state   */
+
+typedef struct twa_ctx twa_ctx;   /* opaque, owned by the library */
+
+typedef struct twa_opts {
+    int    precision;       /* TWA_PREC_*; default TWA_PREC_FP64                      */
+    int    init_state;      /* initial s^z: -1 ground (default) or +1 excited         */
+    double window_start;    /* t0: the state after step t is averaged when
+                               t > round(t0 / dt); default 0 (every step)             */
+    int    renormalize;     /* 1 (default): rescale every spin to sqrt(3) each step   */
+    int    clip_negative;   /* 0 (default): non-positive Cholesky pivot -> TWA_ENOTPSD;
+                               1: zero that column of L and carry on (reported)        */
+    void*  stream;          /* cudaStream_t for all work; NULL = default stream       */
+    int64_t traj_offset;    /* global index of trajectory 0 in the Philox counter
+                               (default 0): shards of one ensemble use disjoint
+                               offsets and reproduce the unsharded run exactly     */
+} twa_opts;
+
+/* kernel classes timed by twa_profile_read */
+#define TWA_PROF_NOISE     0   /* Philox normals of a step                      */
+#define TWA_PROF_PREDICT   1   /* W.s and L.eta contraction + Heun predictor    */
+#define TWA_PROF_CORRECT   2   /* W.s~ contraction + Heun corrector             */
+#define TWA_PROF_CLOSE     3   /* collective sums + window moments              */
+#define TWA_PROF_GEMM64    4   /* FP64 path: one SIMT contraction               */
+#define TWA_PROF_ELEM64    5   /* FP64 path: elementwise / reduction kernels    */
+#define TWA_PROF_KINDS     6
+
+typedef struct twa_obs {
+    /* ensemble means over trajectories of the per-trajectory window means, and
+       their standard errors (g2: block jackknife over min(32, M) blocks)       */
+    double Sz, Sz_se;           /* <S^z>                                        */
+    double sigma_z, sigma_z_se; /* <S^z> / N                                    */
+    double SpSm, SpSm_se;       /* <S+S->, normal ordered                       */
+    double G2num, G2num_se;     /* <S+S+S-S->, normal ordered                   */
+    double g2, g2_se;           /* <S+S+S-S-> / <S+S->^2                        */
+    int64_t M;                  /* trajectories                                 */
+    int64_t steps;              /* completed steps                              */
+    int64_t samples;            /* steps inside the averaging window            */
+    /* diagnostics of the pump matrix (Eq. 3 and below) and of the run          */
+    double w_max, w_min;        /* extreme eigenvalues of w_ij (Lanczos)        */
+    double w_tilde;             /* w_max / (Gamma N)                             */
+    double stability;           /* max(Gamma N, w_max) dt (the paper asks < 0.05) */
+    double min_pivot;           /* smallest Cholesky pivot L_ii^2               */
+    int64_t clipped;            /* columns of L zeroed by clip_negative         */
+    int64_t nonfinite;          /* spin components found non-finite             */
+} twa_obs;
+
+/* Fill *opts with the defaults listed above. Returns TWA_EINVAL if opts is NULL. */
+TWA_API int twa_opts_default(twa_opts* opts);
+
+/* Create a context for N sites (Eq. 2 pump with exponent alpha >= 0 or +INF,
+ * prefactor w >= 0), collective decay Gamma >= 0, step dt > 0, Philox seed.
+ * Builds W in FP64 on the device and factors it (L L^T = W, lower triangular;
+ * alpha = 0: the exact rank-one factor L[:,0] = sqrt(w); alpha = +INF: sqrt(w) I),
+ * and computes the spectrum diagnostics. For the BF16 modes it also stores the
+ * BF16 hi/lo images of W and L. On success *out owns all device memory.
+ * Errors: TWA_EINVAL (bad numbers, N < 1, NULL out), TWA_ENOTPSD (a pivot
+ * <= 0 without clip_negative), TWA_ENOMEM, TWA_ECUDA. */
+TWA_API int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma,
+             double dt, uint64_t seed, const twa_opts* opts);
+
+/* Advance trajectories 0..M-1 by `steps` stochastic-Heun steps of Eq. S1.
+ * The first call fixes M (>= 1) and samples the discrete-Wigner initial state;
+ * later calls must pass the same M and continue the same noise stream (the
+ * step counter persists). Enqueue only. Errors: TWA_EINVAL (M changed, M < 1,
+ * steps < 0), TWA_ENOMEM, TWA_ECUDA. */
+TWA_API int twa_run(twa_ctx* ctx, int64_t M, int64_t steps);
+
+/* Wait for the context's stream and report device-side errors:
+ * TWA_ENONFINITE, TWA_ETIMEOUT, TWA_ECUDA. */
+TWA_API int twa_sync(twa_ctx* ctx);
+
+/* Reduce the per-trajectory window sums to the observables above (FP64 on the
+ * device) and copy them into the caller's host struct *out. Synchronises.
+ * Errors: TWA_ESTATE (no trajectories or no window sample yet), plus those of
+ * twa_sync. */
+TWA_API int twa_observables(twa_ctx* ctx, twa_obs* out);
+
+/* Copy the current spins into caller buffers of M*N doubles each, layout
+ * [M][N]; `on_device` = 1 for device pointers, 0 for host pointers.
+ * Synchronises. Errors: TWA_ESTATE (no trajectories yet), TWA_EINVAL. */
+TWA_API int twa_get_state(twa_ctx* ctx, double* sx, double* sy, double* sz, int on_device);
+
+/* Replace the spins of all M trajectories (fixing M if no run happened yet)
+ * from caller buffers of M*N doubles each, layout [M][N]. Values are used as
+ * given (no renormalisation); the step counter and window sums are kept.
+ * Errors: TWA_EINVAL (NULL pointer, M < 1 or M differs from the fixed M). */
+TWA_API int twa_set_state(twa_ctx* ctx, int64_t M, const double* sx, const double* sy,
+                  const double* sz, int on_device);
+
+/* Copy the per-trajectory window means, M*5 doubles [M][5] in the order
+ * S^z, A, A^2, A S^z, (S^z)^2 (symmetric-ordered classical moments, Sec. S1
+ * item 5), to a host (on_device = 0) or device buffer. Synchronises.
+ * Errors: TWA_ESTATE (no trajectories or no window sample yet). */
+TWA_API int twa_get_moments(twa_ctx* ctx, double* out, int on_device);
+
+/* Pump-field contraction of Eq. S1, P[k][i] = sum_j w_ij s[k][j], for K
+ * caller vectors s (device, [K][N] doubles) into P (device, [K][N] doubles),
+ * computed with the context's precision path (FP64, or the BF16 images of W
+ * and an hi/lo split of s with FP32 accumulation). Enqueued on the context's
+ * stream. Errors: TWA_EINVAL (NULL, K < 1). */
+TWA_API int twa_field(twa_ctx* ctx, const double* s, double* P, int64_t K);
+
+/* Ensemble reduction alone: observables and standard errors (the same FP64
+ * device reduction twa_observables uses) of M caller-supplied per-trajectory
+ * window means, `means` a host array [M][5] in the twa_get_moments order. Used
+ * to merge the shards of an ensemble run on several devices. Fills the first
+ * block of *out (Sz .. g2_se, M, samples = 1); diagnostics are zero.
+ * Errors: TWA_EINVAL (NULL, M < 1), TWA_ENOMEM, TWA_ECUDA. */
+TWA_API int twa_reduce_moments(const double* means, int64_t M, int64_t N, twa_obs* out);
+
+/* Start (enable = 1) or stop (0) timing every kernel the context launches with
+ * a pair of CUDA events recorded on its stream around the launch. Recording
+ * adds no synchronisation. Errors: TWA_EINVAL. */
+TWA_API int twa_profile(twa_ctx* ctx, int enable);
+
+/* Synchronise, then return per kernel class (TWA_PROF_*) the summed event time
+ * in ms and the number of launches since profiling started, and clear the
+ * record. Both arrays hold TWA_PROF_KINDS entries (either may be NULL). */
+TWA_API int twa_profile_read(twa_ctx* ctx, double* ms, int64_t* launches);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * twa_init when ctx is NULL). Never NULL. */
+TWA_API const char* twa_last_error(const twa_ctx* ctx);
+
+/* Free the context and all device memory it owns. NULL is allowed. */
+TWA_API void twa_destroy(twa_ctx* ctx);
+
+/* Library version string. */
+TWA_API const char* twa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TWA_H */

@@ -1,0 +1,381 @@
+// C-ABI entry points of libtwa (declared and documented in include/twa.h).
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "twa_internal.cuh"
+
+namespace {
+thread_local std::string g_init_error;
+constexpr int64_t MAX_N = 60000;          // W and L in FP64 take 2 N^2 8 B (57.6 GB at the limit)
+constexpr int64_t MAX_COUNTER = 0xFFFFFFFFll;
+
+bool use_tc(const twa_ctx* c) { return c->opts.precision != TWA_PREC_FP64; }
+}  // namespace
+
+namespace twa {
+
+int set_error(twa_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+int cuda_check(twa_ctx* c, cudaError_t e, const char* what) {
+    return set_error(c, TWA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace twa
+
+using twa::set_error;
+
+namespace {
+
+__global__ void k_window_means(const double* mom, const int64_t* cnt, double* out, int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) out[e] = mom[e] / (double)(*cnt);
+}
+
+int free_run_buffers(twa_ctx* c) {
+    twa::f64_free(c);
+    if (c->tc) twa::tc_free_run(c);
+    if (c->mom) cudaFree(c->mom);
+    c->mom = nullptr;
+    return TWA_OK;
+}
+
+// Fix M, allocate the trajectory buffers and zero the window sums.
+int fix_M(twa_ctx* c, int64_t M) {
+    c->M = M;
+    if (cudaMalloc(&c->mom, sizeof(double) * 5 * M) != cudaSuccess) {
+        c->M = 0;
+        return set_error(c, TWA_ENOMEM, "cudaMalloc window sums");
+    }
+    TWA_CUDA(c, cudaMemsetAsync(c->mom, 0, sizeof(double) * 5 * M, c->stream));
+    int rc = use_tc(c) ? twa::tc_alloc(c) : twa::f64_alloc(c);
+    if (rc) {
+        free_run_buffers(c);
+        c->M = 0;
+    }
+    return rc;
+}
+
+int check_device_flags(twa_ctx* c) {
+    unsigned long long fl[twa::FLAG_COUNT];
+    TWA_CUDA(c, cudaStreamSynchronize(c->stream));
+    TWA_CUDA(c, cudaMemcpy(fl, c->d_flags, sizeof(fl), cudaMemcpyDeviceToHost));
+    if (fl[twa::FLAG_TIMEOUT])
+        return set_error(c, TWA_ETIMEOUT,
+                         "a device-side wait ran out of its time limit (" + std::to_string(fl[twa::FLAG_TIMEOUT]) +
+                             " waits)");
+    if (fl[twa::FLAG_NONFINITE])
+        return set_error(c, TWA_ENONFINITE,
+                         std::to_string(fl[twa::FLAG_NONFINITE]) + " spin updates produced NaN/Inf");
+    return TWA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* twa_version(void) { return "libtwa 0.1 (sm_103a)"; }
+
+int twa_opts_default(twa_opts* o) {
+    if (!o) return TWA_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->precision = TWA_PREC_FP64;
+    o->init_state = -1;
+    o->window_start = 0.0;
+    o->renormalize = 1;
+    o->clip_negative = 0;
+    o->stream = nullptr;
+    return TWA_OK;
+}
+
+int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, double dt, uint64_t seed,
+             const twa_opts* opts) {
+    if (!out) return set_error(nullptr, TWA_EINVAL, "twa_init: out is NULL");
+    *out = nullptr;
+    twa_opts o;
+    twa_opts_default(&o);
+    if (opts) o = *opts;
+    if (N < 1 || N > MAX_N) return set_error(nullptr, TWA_EINVAL, "twa_init: N must be in [1, 60000]");
+    if (!(alpha >= 0.0)) return set_error(nullptr, TWA_EINVAL, "twa_init: alpha must be >= 0 (or +INF)");
+    if (!(w >= 0.0) || isinf(w)) return set_error(nullptr, TWA_EINVAL, "twa_init: w must be finite and >= 0");
+    if (!(Gamma >= 0.0) || isinf(Gamma)) return set_error(nullptr, TWA_EINVAL, "twa_init: Gamma must be finite and >= 0");
+    if (!(dt > 0.0) || isinf(dt)) return set_error(nullptr, TWA_EINVAL, "twa_init: dt must be finite and > 0");
+    if (o.precision < TWA_PREC_FP64 || o.precision > TWA_PREC_BF16X3)
+        return set_error(nullptr, TWA_EINVAL, "twa_init: unknown precision");
+    if (o.init_state != -1 && o.init_state != 1) return set_error(nullptr, TWA_EINVAL, "twa_init: init_state must be +-1");
+    if (!(o.window_start >= 0.0) || isinf(o.window_start))
+        return set_error(nullptr, TWA_EINVAL, "twa_init: window_start must be finite and >= 0");
+    if (o.traj_offset < 0 || o.traj_offset > MAX_COUNTER)
+        return set_error(nullptr, TWA_EINVAL, "twa_init: traj_offset must be in [0, 2^32-1]");
+
+    twa_ctx* c = new (std::nothrow) twa_ctx();
+    if (!c) return set_error(nullptr, TWA_ENOMEM, "twa_init: host allocation failed");
+    c->N = N;
+    c->alpha = alpha;
+    c->w = w;
+    c->Gamma = Gamma;
+    c->dt = dt;
+    c->seed = seed;
+    c->opts = o;
+    c->stream = (cudaStream_t)o.stream;
+    c->n_window = (int64_t)floor(o.window_start / dt + 0.5);
+    int rc = TWA_OK;
+    auto fail = [&](int code) {
+        g_init_error = c->err;
+        twa_destroy(c);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        twa::cuda_check(c, e, "cudaGetDevice");
+        return fail(TWA_ECUDA);
+    }
+    if (cudaMalloc(&c->W64, sizeof(double) * N * N) != cudaSuccess ||
+        cudaMalloc(&c->L64, sizeof(double) * N * N) != cudaSuccess ||
+        cudaMalloc(&c->d_t, sizeof(int64_t)) != cudaSuccess || cudaMalloc(&c->d_count, sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_flags, sizeof(unsigned long long) * twa::FLAG_COUNT) != cudaSuccess) {
+        set_error(c, TWA_ENOMEM, "twa_init: device allocation failed");
+        return fail(TWA_ENOMEM);
+    }
+    if (cudaMemsetAsync(c->d_t, 0, sizeof(int64_t), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_count, 0, sizeof(int64_t), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned long long) * twa::FLAG_COUNT, c->stream) != cudaSuccess) {
+        set_error(c, TWA_ECUDA, "twa_init: cudaMemsetAsync failed");
+        return fail(TWA_ECUDA);
+    }
+    if ((rc = twa::setup_pump(c))) return fail(rc);
+    if (use_tc(c) && (rc = twa::tc_prepare(c))) return fail(rc);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        twa::cuda_check(c, e, "twa_init");
+        return fail(TWA_ECUDA);
+    }
+    *out = c;
+    return TWA_OK;
+}
+
+int twa_run(twa_ctx* c, int64_t M, int64_t steps) {
+    if (!c) return set_error(nullptr, TWA_EINVAL, "twa_run: ctx is NULL");
+    if (M < 1 || M > (int64_t)1 << 30) return set_error(c, TWA_EINVAL, "twa_run: M must be in [1, 2^30]");
+    if (steps < 0) return set_error(c, TWA_EINVAL, "twa_run: steps must be >= 0");
+    if (c->M != 0 && M != c->M)
+        return set_error(c, TWA_EINVAL, "twa_run: M differs from the trajectory count fixed by the first call");
+    if (c->steps + steps > MAX_COUNTER) return set_error(c, TWA_EINVAL, "twa_run: step counter would exceed 2^32-1");
+    if (c->opts.traj_offset + M - 1 > MAX_COUNTER)
+        return set_error(c, TWA_EINVAL, "twa_run: traj_offset + M exceeds the 32-bit trajectory counter");
+    int rc;
+    if (c->M == 0) {
+        if ((rc = fix_M(c, M))) return rc;
+        rc = use_tc(c) ? twa::tc_init_state(c) : twa::f64_init_state(c);
+        if (rc) return rc;
+    }
+    if (steps == 0) return TWA_OK;
+    rc = use_tc(c) ? twa::tc_run(c, steps) : twa::f64_run(c, steps);
+    if (rc) return rc;
+    c->steps += steps;
+    return TWA_OK;
+}
+
+int twa_sync(twa_ctx* c) {
+    if (!c) return set_error(nullptr, TWA_EINVAL, "twa_sync: ctx is NULL");
+    return check_device_flags(c);
+}
+
+int twa_observables(twa_ctx* c, twa_obs* out) {
+    if (!c || !out) return set_error(c, TWA_EINVAL, "twa_observables: NULL argument");
+    if (c->M == 0) return set_error(c, TWA_ESTATE, "twa_observables: no trajectories yet");
+    int rc = check_device_flags(c);
+    if (rc) return rc;
+    int64_t cnt = 0;
+    TWA_CUDA(c, cudaMemcpy(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
+    if (cnt == 0) return set_error(c, TWA_ESTATE, "twa_observables: no step inside the averaging window yet");
+    memset(out, 0, sizeof(*out));
+    if ((rc = twa::reduce_observables(c, out))) return rc;
+    out->M = c->M;
+    out->steps = c->steps;
+    out->w_max = c->w_max;
+    out->w_min = c->w_min;
+    out->w_tilde = (c->Gamma > 0) ? c->w_max / (c->Gamma * (double)c->N) : INFINITY;
+    out->stability = fmax(c->Gamma * (double)c->N, c->w_max) * c->dt;
+    out->min_pivot = c->min_pivot;
+    out->clipped = c->clipped;
+    unsigned long long fl[twa::FLAG_COUNT];
+    TWA_CUDA(c, cudaMemcpy(fl, c->d_flags, sizeof(fl), cudaMemcpyDeviceToHost));
+    out->nonfinite = (int64_t)fl[twa::FLAG_NONFINITE];
+    return TWA_OK;
+}
+
+int twa_get_state(twa_ctx* c, double* sx, double* sy, double* sz, int on_device) {
+    if (!c || !sx || !sy || !sz) return set_error(c, TWA_EINVAL, "twa_get_state: NULL argument");
+    if (c->M == 0) return set_error(c, TWA_ESTATE, "twa_get_state: no trajectories yet");
+    const int64_t M = c->M, N = c->N;
+    const size_t row = sizeof(double) * N;
+    if (use_tc(c)) {
+        double *dx = sx, *dy = sy, *dz = sz, *tmp = nullptr;
+        if (!on_device) {
+            TWA_CUDA(c, cudaMallocAsync(&tmp, 3 * row * M, c->stream));
+            dx = tmp;
+            dy = tmp + M * N;
+            dz = tmp + 2 * M * N;
+        }
+        int rc = twa::tc_get_state(c, dx, dy, dz);
+        if (rc) return rc;
+        if (!on_device) {
+            TWA_CUDA(c, cudaMemcpyAsync(sx, dx, row * M, cudaMemcpyDeviceToHost, c->stream));
+            TWA_CUDA(c, cudaMemcpyAsync(sy, dy, row * M, cudaMemcpyDeviceToHost, c->stream));
+            TWA_CUDA(c, cudaMemcpyAsync(sz, dz, row * M, cudaMemcpyDeviceToHost, c->stream));
+            TWA_CUDA(c, cudaFreeAsync(tmp, c->stream));
+        }
+    } else {
+        const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        TWA_CUDA(c, cudaMemcpy2DAsync(sx, row, c->xy, 2 * row, row, M, k, c->stream));
+        TWA_CUDA(c, cudaMemcpy2DAsync(sy, row, c->xy + N, 2 * row, row, M, k, c->stream));
+        TWA_CUDA(c, cudaMemcpyAsync(sz, c->z, row * M, k, c->stream));
+    }
+    return check_device_flags(c);
+}
+
+int twa_set_state(twa_ctx* c, int64_t M, const double* sx, const double* sy, const double* sz, int on_device) {
+    if (!c || !sx || !sy || !sz) return set_error(c, TWA_EINVAL, "twa_set_state: NULL argument");
+    if (M < 1 || M > (int64_t)1 << 30) return set_error(c, TWA_EINVAL, "twa_set_state: M must be in [1, 2^30]");
+    if (c->M != 0 && M != c->M) return set_error(c, TWA_EINVAL, "twa_set_state: M differs from the fixed M");
+    int rc;
+    if (c->M == 0 && (rc = fix_M(c, M))) return rc;
+    const int64_t N = c->N;
+    const size_t row = sizeof(double) * N;
+    if (use_tc(c)) {
+        const double *dx = sx, *dy = sy, *dz = sz;
+        double* tmp = nullptr;
+        if (!on_device) {
+            TWA_CUDA(c, cudaMallocAsync(&tmp, 3 * row * M, c->stream));
+            TWA_CUDA(c, cudaMemcpyAsync(tmp, sx, row * M, cudaMemcpyHostToDevice, c->stream));
+            TWA_CUDA(c, cudaMemcpyAsync(tmp + M * N, sy, row * M, cudaMemcpyHostToDevice, c->stream));
+            TWA_CUDA(c, cudaMemcpyAsync(tmp + 2 * M * N, sz, row * M, cudaMemcpyHostToDevice, c->stream));
+            dx = tmp;
+            dy = tmp + M * N;
+            dz = tmp + 2 * M * N;
+        }
+        rc = twa::tc_set_state(c, dx, dy, dz);
+        if (tmp) cudaFreeAsync(tmp, c->stream);
+        if (rc) return rc;
+    } else {
+        const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        TWA_CUDA(c, cudaMemcpy2DAsync(c->xy, 2 * row, sx, row, row, M, k, c->stream));
+        TWA_CUDA(c, cudaMemcpy2DAsync(c->xy + N, 2 * row, sy, row, row, M, k, c->stream));
+        TWA_CUDA(c, cudaMemcpyAsync(c->z, sz, row * M, k, c->stream));
+        if ((rc = twa::f64_state_changed(c))) return rc;
+    }
+    if (!on_device) TWA_CUDA(c, cudaStreamSynchronize(c->stream));
+    return TWA_OK;
+}
+
+int twa_get_moments(twa_ctx* c, double* out, int on_device) {
+    if (!c || !out) return set_error(c, TWA_EINVAL, "twa_get_moments: NULL argument");
+    if (c->M == 0) return set_error(c, TWA_ESTATE, "twa_get_moments: no trajectories yet");
+    int64_t cnt = 0;
+    TWA_CUDA(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    TWA_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (cnt == 0) return set_error(c, TWA_ESTATE, "twa_get_moments: no step inside the averaging window yet");
+    const int64_t n = 5 * c->M;
+    double* dst = out;
+    if (!on_device) TWA_CUDA(c, cudaMallocAsync(&dst, sizeof(double) * n, c->stream));
+    k_window_means<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->mom, c->d_count, dst, n);
+    TWA_CUDA(c, cudaGetLastError());
+    if (!on_device) {
+        TWA_CUDA(c, cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+        TWA_CUDA(c, cudaFreeAsync(dst, c->stream));
+    }
+    return check_device_flags(c);
+}
+
+int twa_field(twa_ctx* c, const double* s, double* P, int64_t K) {
+    if (!c || !s || !P) return set_error(c, TWA_EINVAL, "twa_field: NULL argument");
+    if (K < 1 || K > (int64_t)1 << 30) return set_error(c, TWA_EINVAL, "twa_field: K must be in [1, 2^30]");
+    return use_tc(c) ? twa::tc_field(c, s, P, K) : twa::f64_field(c, s, P, K);
+}
+
+int twa_reduce_moments(const double* means, int64_t M, int64_t N, twa_obs* out) {
+    if (!means || !out || M < 1 || N < 1) return set_error(nullptr, TWA_EINVAL, "twa_reduce_moments: bad argument");
+    twa_ctx tmp;
+    tmp.N = N;
+    tmp.M = M;
+    int rc = TWA_OK;
+    if (cudaMalloc(&tmp.mom, sizeof(double) * 5 * M) != cudaSuccess ||
+        cudaMalloc(&tmp.d_count, sizeof(int64_t)) != cudaSuccess) {
+        rc = set_error(nullptr, TWA_ENOMEM, "twa_reduce_moments: device allocation failed");
+    } else {
+        const int64_t one = 1;
+        memset(out, 0, sizeof(*out));
+        if (cudaMemcpy(tmp.mom, means, sizeof(double) * 5 * M, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(tmp.d_count, &one, sizeof(one), cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = set_error(nullptr, TWA_ECUDA, "twa_reduce_moments: upload failed");
+        } else if ((rc = twa::reduce_observables(&tmp, out))) {
+            g_init_error = tmp.err;
+        }
+        out->M = M;
+    }
+    if (tmp.mom) cudaFree(tmp.mom);
+    if (tmp.d_count) cudaFree(tmp.d_count);
+    tmp.mom = nullptr;
+    tmp.d_count = nullptr;
+    return rc;
+}
+
+int twa_profile(twa_ctx* c, int enable) {
+    if (!c) return set_error(nullptr, TWA_EINVAL, "twa_profile: ctx is NULL");
+    c->profiling = enable != 0;
+    return TWA_OK;
+}
+
+int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches) {
+    if (!c) return set_error(nullptr, TWA_EINVAL, "twa_profile_read: ctx is NULL");
+    TWA_CUDA(c, cudaStreamSynchronize(c->stream));
+    double t[TWA_PROF_KINDS] = {0};
+    int64_t n[TWA_PROF_KINDS] = {0};
+    int rc = TWA_OK;
+    for (auto& r : c->prof) {
+        float e = 0.f;
+        if (cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) rc = TWA_ECUDA;
+        if (r.kind >= 0 && r.kind < TWA_PROF_KINDS) {
+            t[r.kind] += e;
+            n[r.kind] += 1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->prof.clear();
+    for (int k = 0; k < TWA_PROF_KINDS; ++k) {
+        if (ms) ms[k] = t[k];
+        if (launches) launches[k] = n[k];
+    }
+    if (rc) return set_error(c, rc, "twa_profile_read: cudaEventElapsedTime failed");
+    return TWA_OK;
+}
+
+const char* twa_last_error(const twa_ctx* c) {
+    if (!c) return g_init_error.c_str();
+    return c->err.c_str();
+}
+
+void twa_destroy(twa_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& r : c->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    free_run_buffers(c);
+    if (c->tc) twa::tc_free(c);
+    void* p[] = {c->W64, c->L64, c->d_t, c->d_count, c->d_flags};
+    for (void* q : p)
+        if (q) cudaFree(q);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// Internal declarations of libtwa: the context, device helpers shared by the
+// kernels, and the host launchers each .cu file provides.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/twa.h"
+
+namespace twa {
+
+// ---------------------------------------------------------------------------
+// device flag words (ctx->d_flags)
+enum : int {
+    FLAG_NONFINITE = 0,   // spin components found NaN/Inf
+    FLAG_TIMEOUT = 1,     // bounded waits that gave up
+    FLAG_DONE = 2,        // last-block counter of the per-step closing kernel
+    FLAG_NOTPSD = 3,      // Cholesky pivots <= 0 (count)
+    FLAG_NOTPSD_IDX = 4,  // first failing pivot index + 1 (atomicMin-free: set once)
+    FLAG_COUNT = 8
+};
+
+// Row tiles of the tensor-core path: 128 sites per tile.
+constexpr int TC_BM = 128;
+// Column tiles: 256 B-operand rows = 128 trajectories x (x, y).
+constexpr int TC_BN = 256;
+constexpr int TC_BK = 64;
+
+struct TcState;  // tensor-core path buffers (twa_tc.cu)
+
+}  // namespace twa
+
+struct twa_ctx {
+    // parameters (Eq. 2 and Eq. S1)
+    int64_t N = 0;
+    double alpha = 0, w = 0, Gamma = 0, dt = 0;
+    uint64_t seed = 0;
+    twa_opts opts{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+
+    // set-up products (FP64, [N][N])
+    double* W64 = nullptr;
+    double* L64 = nullptr;
+    double w_max = 0, w_min = 0, min_pivot = 0;
+    int64_t clipped = 0;
+
+    // run state
+    int64_t M = 0;           // 0 until the first run / set_state
+    int64_t steps = 0;       // completed steps (host mirror of d_t)
+    int64_t n_window = 0;    // samples after step t are taken when t > n_window
+    int64_t* d_t = nullptr;  // device step counter
+    unsigned long long* d_flags = nullptr;
+    double* mom = nullptr;   // [M][5] window sums (FP64)
+    int64_t* d_count = nullptr;  // window samples taken (device)
+
+    // FP64 path buffers
+    double* xy = nullptr;    // [2M][N]: row 2m = x of trajectory m, 2m+1 = y
+    double* z = nullptr;     // [M][N]
+    double* xyp = nullptr;   // predictor
+    double* zp = nullptr;
+    double* hxy = nullptr;   // s + f(s)/2
+    double* hz = nullptr;
+    double* eta = nullptr;   // [2M][N] normals, then L.eta, then the noise part of B
+    double* pf = nullptr;    // [2M][N] pump field W.s
+    double* xi = nullptr;    // [M][2] collective normals
+    double* S = nullptr;     // [M][4] collective sums of the current state
+    double* Sp = nullptr;    // [M][4] collective sums of the predictor
+
+    // tensor-core (BF16 / BF16X3) path
+    twa::TcState* tc = nullptr;
+
+    // per-launch event timing (twa_profile)
+    struct ProfRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    bool profiling = false;
+    std::vector<ProfRec> prof;
+};
+
+namespace twa {
+// Brackets one launch with CUDA events on the context's stream when profiling.
+struct ProfScope {
+    twa_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(twa_ctx* ctx, int k) : c(ctx), kind(k) {
+        if (c->profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, c->stream);
+    }
+    ~ProfScope() {
+        if (c->profiling && a && b) {
+            cudaEventRecord(b, c->stream);
+            c->prof.push_back({kind, a, b});
+        }
+    }
+};
+}  // namespace twa
+
+namespace twa {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): a 10-round bijection of a
+// 128-bit counter under a 64-bit key. Round: (c0, c1, c2, c3) ->
+// (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the key is
+// bumped by the Weyl constants between rounds.
+__host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#else
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Pump/collective noise stream 0 and initial-sign stream 1 (see twa.h).
+constexpr uint32_t STREAM_NOISE = 0;
+constexpr uint32_t STREAM_INIT = 1;
+
+// Two FP64 standard normals from one Philox call: 53-bit uniforms
+// u = (k + 1/2) 2^-53 from words (0,1) and (2,3), then Box-Muller.
+__device__ __forceinline__ void normal2_f64(uint64_t seed, uint32_t m, uint32_t t, uint32_t i,
+                                            double& gx, double& gy) {
+    const uint4 r = philox10(make_uint4(m, t, i, STREAM_NOISE), (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t k1 = ((((uint64_t)r.x) << 32) | r.y) >> 11;
+    const uint64_t k2 = ((((uint64_t)r.z) << 32) | r.w) >> 11;
+    const double u1 = ((double)k1 + 0.5) * 0x1p-53;
+    const double u2 = ((double)k2 + 0.5) * 0x1p-53;
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    gx = rad * c;
+    gy = rad * s;
+}
+
+// FP32 variant from the same Philox words (words 0 and 2 as 32-bit uniforms in
+// (0, 1]); used by the mixed-precision path, whose noise is rounded to BF16.
+__device__ __forceinline__ void normal2_f32(uint64_t seed, uint32_t m, uint32_t t, uint32_t i,
+                                            float& gx, float& gy) {
+    const uint4 r = philox10(make_uint4(m, t, i, STREAM_NOISE), (uint32_t)seed, (uint32_t)(seed >> 32));
+    const float u1 = fmaf((float)r.x, 0x1p-32f, 0x1p-33f);
+    const float u2 = fmaf((float)r.z, 0x1p-32f, 0x1p-33f);
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    gx = rad * c;
+    gy = rad * s;
+}
+
+// Discrete-Wigner signs of site i of trajectory m: low bits of words 0 and 1.
+__device__ __forceinline__ void init_signs(uint64_t seed, uint32_t m, uint32_t i, double& sx, double& sy) {
+    const uint4 r = philox10(make_uint4(m, 0u, i, STREAM_INIT), (uint32_t)seed, (uint32_t)(seed >> 32));
+    sx = (r.x & 1u) ? 1.0 : -1.0;
+    sy = (r.y & 1u) ? 1.0 : -1.0;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// twa_setup.cu
+int setup_pump(twa_ctx* c);                      // W64, L64, pivots, spectrum
+// twa_fp64.cu
+int f64_alloc(twa_ctx* c);
+void f64_free(twa_ctx* c);
+int f64_init_state(twa_ctx* c);
+int f64_run(twa_ctx* c, int64_t steps);
+int f64_state_changed(twa_ctx* c);               // recompute sums after set_state
+int f64_field(twa_ctx* c, const double* s, double* P, int64_t K);
+void gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+              int64_t n_i, int64_t n_n, int64_t K, double alpha, double beta, bool tri_a, bool lower_only,
+              cudaStream_t st);
+// twa_tc.cu
+int tc_prepare(twa_ctx* c);                      // BF16 images of W and L
+int tc_alloc(twa_ctx* c);
+void tc_free_run(twa_ctx* c);                    // trajectory buffers only
+void tc_free(twa_ctx* c);                        // everything, including the images
+int tc_init_state(twa_ctx* c);
+int tc_run(twa_ctx* c, int64_t steps);
+int tc_state_changed(twa_ctx* c);
+int tc_get_state(twa_ctx* c, double* sx, double* sy, double* sz);   // device buffers
+int tc_set_state(twa_ctx* c, const double* sx, const double* sy, const double* sz);
+int tc_field(twa_ctx* c, const double* s, double* P, int64_t K);
+// twa_reduce.cu
+int reduce_observables(twa_ctx* c, twa_obs* out);  // device FP64 reduction, synchronises
+
+// error helpers (twa_api.cu)
+int set_error(twa_ctx* c, int code, const std::string& msg);
+int cuda_check(twa_ctx* c, cudaError_t e, const char* what);
+
+}  // namespace twa
+
+#define TWA_CUDA(c, call)                                              \
+    do {                                                               \
+        cudaError_t e__ = (call);                                      \
+        if (e__ != cudaSuccess) return ::twa::cuda_check((c), e__, #call); \
+    } while (0)

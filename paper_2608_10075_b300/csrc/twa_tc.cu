@@ -1,0 +1,873 @@
+// Mixed-precision tensor-core path (sm_103a): the two per-step contractions of
+// Eq. S1 -- the pump field sum_j w_ij s^a_j and the correlated noise (L eta)_i --
+// run as tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators in TMEM) on
+// tiles that TMA stages into shared memory; the stochastic-Heun update is the
+// epilogue of the same kernel.
+//
+// Operands (K = site index j, contiguous):
+//   A = W or L images, [N][ldk] BF16, rows = sites i (MMA M = 128 per tile)
+//   B = state images,  [2M][ldk] BF16, row 2m = s^x of trajectory m, row
+//       2m+1 = s^y (MMA N = 256 per tile = 128 trajectories x (x, y))
+// so accumulator column 2j / 2j+1 of a tile holds the x / y field of trajectory
+// m0 + j at site i0 + lane, and every epilogue thread owns one site.
+//
+// Precision modes: BF16 (one term, hi*hi) or BF16X3 (hi*hi + hi*lo + lo*hi,
+// hi = bf16(v), lo = bf16(v - hi)), FP32 accumulation. The noise eta is drawn
+// in FP32 and rounded to BF16 once, so L.eta is exact up to the L split.
+//
+// Step = noise kernel, predictor kernel (W.s and L.eta, two accumulators),
+// corrector kernel (W.s~), closing kernel (moments). Collective sums S^a are
+// passed between kernels as per-row-tile partial sums, reduced in a fixed order.
+#include <math.h>
+
+#include <cudaTypedefs.h>
+
+#include "twa_internal.cuh"
+
+namespace twa {
+
+struct TcState {
+    int64_t M = 0, N = 0, ldk = 0, n_rt = 0, n_ct = 0;
+    int terms = 3;                               // 1 (BF16) or 3 (BF16X3)
+    __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
+    float *X = nullptr, *Y = nullptr, *Z = nullptr;       // state [M][N]
+    float *Xp = nullptr, *Yp = nullptr, *Zp = nullptr;    // predictor
+    float *Hx = nullptr, *Hy = nullptr, *Hz = nullptr;    // s + f(s)/2
+    float *Bx = nullptr, *By = nullptr;                   // noise part of the field increment
+    __nv_bfloat16 *Shi = nullptr, *Slo = nullptr;         // images of s   [2M][ldk]
+    __nv_bfloat16 *Phi = nullptr, *Plo = nullptr;         // images of s~  [2M][ldk]
+    __nv_bfloat16* E = nullptr;                           // eta           [2M][ldk]
+    float* XI = nullptr;                                  // [M][2]
+    float* part = nullptr;                                // [n_rt][M][4] sums of s
+    float* partp = nullptr;                               // [n_rt][M][4] sums of s~
+    CUtensorMap tmWhi, tmWlo, tmLhi, tmLlo, tmShi, tmSlo, tmPhi, tmPlo, tmE;
+};
+
+namespace {
+
+constexpr int BM = TC_BM, BN = TC_BN, BK = TC_BK;
+constexpr int STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;                    // 16 KB
+constexpr int B_BYTES = BN * BK * 2;                    // 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB
+constexpr int NTHREADS = 192;                           // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int SMEM_TILES = STAGES * STAGE_BYTES;
+constexpr int SMEM_EXTRA = 8 * 16 + 16 + BM * 2 * 4 + BM * 2 * 4 + 4 * BM * 3 * 4;
+constexpr int SMEM_TOTAL = SMEM_TILES + SMEM_EXTRA + 1024;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits: 2 s
+
+enum Mode { MODE_FIELD = 0, MODE_PRED = 1, MODE_CORR = 2 };
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity; gives up after WAIT_NS (or at once
+// when another CTA has already given up and `follow_abort` is set), counting the
+// timeout in flags[FLAG_TIMEOUT].
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long* flags,
+                                       bool follow_abort) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    volatile unsigned long long* vf = flags;
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (follow_abort && vf[FLAG_TIMEOUT] != 0ull) return false;
+        if (gtimer() - t0 > WAIT_NS) {
+            atomicAdd(&flags[FLAG_TIMEOUT], 1ull);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with
+// 128-byte swizzle: 8-row x 128 B atoms, stride between atoms (SBO) 1024 B,
+// descriptor version 1, layout SWIZZLE_128B (= 2 at bits 61-63).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
+        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 16 consecutive FP32 columns: thread = lane, v[c] = column col + c.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t off, float v, bool with_lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[off] = h;
+    if (with_lo) lo[off] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+struct TcMaps {
+    CUtensorMap a0, a1, a2, a3, b0, b1, b2;
+};
+
+struct TcArgs {
+    int64_t N, M, ldk, n_rt, n_vec;   // n_vec: B rows (2M, or K for the field mode)
+    float G, dt, sgdt, sdt;
+    int renorm;
+    // state and outputs
+    const float *X, *Y, *Z;           // PRED: s; CORR: s~
+    const float *Hx, *Hy, *Hz;        // CORR
+    const float *Bnx, *Bny;           // CORR
+    float *oX, *oY, *oZ;              // PRED: s~; CORR: s'
+    float *oHx, *oHy, *oHz;           // PRED
+    float *oBnx, *oBny;               // PRED
+    __nv_bfloat16 *oHi, *oLo;         // images of the output state
+    const float* XI;
+    const float* part_in;             // sums of the input state, [n_rt][M][4]
+    float* part_out;                  // sums of the output state
+    float* field_out;                 // FIELD: [n_vec][N]
+    unsigned long long* flags;
+};
+
+template <int MODE, int NT0, int NT1>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMaps maps, const TcArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* tiles = smem;
+    uint64_t* full = (uint64_t*)(smem + SMEM_TILES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accb = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(accb + 2);
+    float* sS = (float*)(tmem_slot + 4);        // [BM][2] input sums of the tile's trajectories
+    float* sXI = sS + BM * 2;                   // [BM][2]
+    float* red = sXI + BM * 2;                  // [4][BM][3]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = (int64_t)blockIdx.y * BM;     // first site of the tile
+    const int64_t n0 = (int64_t)blockIdx.x * BN;     // first B row (= 2 m0)
+    const int64_t m0 = n0 >> 1;
+    const int nk = (int)((args.N + BK - 1) / BK);
+    int nk1 = (int)((i0 + BM + BK - 1) / BK);        // L is lower triangular
+    if (nk1 > nk) nk1 = nk;
+    constexpr int NPH = (MODE == MODE_PRED) ? 2 : 1;
+    constexpr uint32_t NCOLS = (MODE == MODE_PRED) ? 512 : 256;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            uint32_t stage = 0, ph = 0;
+            int last_ph[STAGES];
+            bool issued[STAGES];
+            for (int s = 0; s < STAGES; ++s) { issued[s] = false; last_ph[s] = 0; }
+            bool ok = true;
+            for (int p = 0; p < NPH && ok; ++p) {
+                const int nkp = (p == 0) ? nk : nk1;
+                const int na = (p == 0) ? (NT0 == 3 ? 2 : 1) : (NT1 == 2 ? 2 : 1);
+                const int nb = (p == 0) ? (NT0 == 3 ? 2 : 1) : 1;
+                const uint32_t bytes = na * A_BYTES + nb * B_BYTES;
+                for (int kt = 0; kt < nkp; ++kt) {
+                    if (!mbar_wait(&empty[stage], ph ^ 1u, args.flags, true)) { ok = false; break; }
+                    mbar_expect_tx(&full[stage], bytes);
+                    uint8_t* st = tiles + stage * STAGE_BYTES;
+                    const int kx = kt * BK;
+                    if (p == 0) {
+                        tma_load(st, &maps.a0, &full[stage], kx, (int)i0);
+                        if (NT0 == 3) tma_load(st + A_BYTES, &maps.a1, &full[stage], kx, (int)i0);
+                        tma_load(st + 2 * A_BYTES, &maps.b0, &full[stage], kx, (int)n0);
+                        if (NT0 == 3) tma_load(st + 2 * A_BYTES + B_BYTES, &maps.b1, &full[stage], kx, (int)n0);
+                    } else {
+                        tma_load(st, &maps.a2, &full[stage], kx, (int)i0);
+                        if (NT1 == 2) tma_load(st + A_BYTES, &maps.a3, &full[stage], kx, (int)i0);
+                        tma_load(st + 2 * A_BYTES, &maps.b2, &full[stage], kx, (int)n0);
+                    }
+                    issued[stage] = true;
+                    last_ph[stage] = (int)ph;
+                    if (++stage == STAGES) { stage = 0; ph ^= 1u; }
+                }
+            }
+            if (!ok) {
+                // let copies already in flight land before the CTA can exit
+                for (int s = 0; s < STAGES; ++s)
+                    if (issued[s]) mbar_wait(&full[s], (uint32_t)last_ph[s], args.flags, false);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t stage = 0, ph = 0;
+            bool ok = true;
+            for (int p = 0; p < NPH && ok; ++p) {
+                const int nkp = (p == 0) ? nk : nk1;
+                const uint32_t dcol = tmem + (uint32_t)(p * BN);
+                for (int kt = 0; kt < nkp; ++kt) {
+                    if (!mbar_wait(&full[stage], ph, args.flags, true)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(tiles + stage * STAGE_BYTES);
+                    const uint32_t a1 = a0 + A_BYTES, b0 = a0 + 2 * A_BYTES, b1 = b0 + B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t ko = kk * 32;   // 16 BF16 = 32 B along the swizzled row
+                        mma_bf16(dcol, sdesc(a0 + ko), sdesc(b0 + ko), (kt > 0 || kk > 0) ? 1u : 0u);
+                        if (p == 0 && NT0 == 3) {
+                            mma_bf16(dcol, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
+                            mma_bf16(dcol, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+                        }
+                        if (p == 1 && NT1 == 2) mma_bf16(dcol, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+                    }
+                    mma_commit(&empty[stage]);
+                    if (++stage == STAGES) { stage = 0; ph ^= 1u; }
+                }
+            }
+            mma_commit(accb);   // accumulators complete (or drained, after an abort)
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;                       // TMEM lane quadrant of this warp
+        const int et = threadIdx.x - 64;              // 0..127
+        const int64_t i = i0 + 32 * q + lane;         // site of this thread
+        const bool site_ok = i < args.N;
+        const int64_t M = args.M;
+        if (MODE != MODE_FIELD) {
+            // collective sums of the input state for this tile's 128 trajectories
+            const int64_t m = m0 + et;
+            float sx = 0.f, sy = 0.f;
+            if (m < M) {
+                for (int64_t r = 0; r < args.n_rt; ++r) {
+                    const float4 v = *(const float4*)(args.part_in + (r * M + m) * 4);
+                    sx += v.x;
+                    sy += v.y;
+                }
+            }
+            sS[2 * et] = sx;
+            sS[2 * et + 1] = sy;
+            if (MODE == MODE_PRED) {
+                sXI[2 * et] = (m < M) ? args.XI[2 * m] : 0.f;
+                sXI[2 * et + 1] = (m < M) ? args.XI[2 * m + 1] : 0.f;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+        const bool acc_ok = mbar_wait(accb, 0, args.flags, false);
+        tc_fence_after();
+        const bool live = acc_ok && (((volatile unsigned long long*)args.flags)[FLAG_TIMEOUT] == 0ull);
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+        if (live) {
+            if (MODE == MODE_FIELD) {
+                for (int c = 0; c < BN / 16; ++c) {
+                    float v[16];
+                    tmem_ld16(trow + 16 * c, v);
+                    tmem_ld_wait();
+                    if (site_ok) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int64_t n = n0 + 16 * c + j;
+                            if (n < args.n_vec) args.field_out[n * args.N + i] = v[j];
+                        }
+                    }
+                }
+            } else {
+                const float G = args.G, dt = args.dt;
+                unsigned nonfinite = 0;
+                for (int c = 0; c < BN / 16; ++c) {
+                    float pv[16], qv[16];
+                    tmem_ld16(trow + 16 * c, pv);
+                    if (MODE == MODE_PRED) tmem_ld16(trow + BN + 16 * c, qv);
+                    tmem_ld_wait();
+                    float rx[8], ry[8], rz[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int jl = 8 * c + jj;             // local trajectory 0..127
+                        const int64_t m = m0 + jl;
+                        rx[jj] = ry[jj] = rz[jj] = 0.f;
+                        if (!site_ok || m >= M) continue;
+                        const int64_t e = m * args.N + i;
+                        const float x = args.X[e], y = args.Y[e], z = args.Z[e];
+                        if (MODE == MODE_PRED) {
+                            // B^a = 1/2 (G S^a - P^a) dt + sqrt(G dt) xi^a - sqrt(dt) (L eta^a)
+                            const float bnx = args.sgdt * sXI[2 * jl] - args.sdt * qv[2 * jj];
+                            const float bny = args.sgdt * sXI[2 * jl + 1] - args.sdt * qv[2 * jj + 1];
+                            const float Bxv = 0.5f * (G * sS[2 * jl] - pv[2 * jj]) * dt + bnx;
+                            const float Byv = 0.5f * (G * sS[2 * jl + 1] - pv[2 * jj + 1]) * dt + bny;
+                            const float fx = z * Bxv, fy = z * Byv, fz = -(x * Bxv + y * Byv);
+                            const float xp = x + fx, yp = y + fy, zp = z + fz;
+                            args.oX[e] = xp;
+                            args.oY[e] = yp;
+                            args.oZ[e] = zp;
+                            args.oHx[e] = fmaf(0.5f, fx, x);
+                            args.oHy[e] = fmaf(0.5f, fy, y);
+                            args.oHz[e] = fmaf(0.5f, fz, z);
+                            args.oBnx[e] = bnx;
+                            args.oBny[e] = bny;
+                            const int64_t r0 = (2 * m) * args.ldk + i;
+                            split_store(args.oHi, args.oLo, r0, xp, NT0 == 3);
+                            split_store(args.oHi, args.oLo, r0 + args.ldk, yp, NT0 == 3);
+                            rx[jj] = xp;
+                            ry[jj] = yp;
+                            rz[jj] = zp;
+                        } else {
+                            // corrector: s' = h + f(s~)/2, then |s'| = sqrt(3)
+                            const float Bxv = 0.5f * (G * sS[2 * jl] - pv[2 * jj]) * dt + args.Bnx[e];
+                            const float Byv = 0.5f * (G * sS[2 * jl + 1] - pv[2 * jj + 1]) * dt + args.Bny[e];
+                            float nx = fmaf(0.5f, z * Bxv, args.Hx[e]);
+                            float ny = fmaf(0.5f, z * Byv, args.Hy[e]);
+                            float nz = fmaf(-0.5f, x * Bxv + y * Byv, args.Hz[e]);
+                            if (args.renorm) {
+                                const float s = sqrtf(3.0f / (nx * nx + ny * ny + nz * nz));
+                                nx *= s;
+                                ny *= s;
+                                nz *= s;
+                            }
+                            if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) ++nonfinite;
+                            args.oX[e] = nx;
+                            args.oY[e] = ny;
+                            args.oZ[e] = nz;
+                            const int64_t r0 = (2 * m) * args.ldk + i;
+                            split_store(args.oHi, args.oLo, r0, nx, NT0 == 3);
+                            split_store(args.oHi, args.oLo, r0 + args.ldk, ny, NT0 == 3);
+                            rx[jj] = nx;
+                            ry[jj] = ny;
+                            rz[jj] = nz;
+                        }
+                    }
+                    // partial sums over this warp's 32 sites
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+#pragma unroll
+                        for (int o = 16; o; o >>= 1) {
+                            rx[jj] += __shfl_xor_sync(0xffffffffu, rx[jj], o);
+                            ry[jj] += __shfl_xor_sync(0xffffffffu, ry[jj], o);
+                            rz[jj] += __shfl_xor_sync(0xffffffffu, rz[jj], o);
+                        }
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            float* rr = red + (q * BM + 8 * c + jj) * 3;
+                            rr[0] = rx[jj];
+                            rr[1] = ry[jj];
+                            rr[2] = rz[jj];
+                        }
+                    }
+                }
+                if (MODE == MODE_CORR) {
+                    const unsigned tot = __reduce_add_sync(0xffffffffu, nonfinite);
+                    if (lane == 0 && tot) atomicAdd(&args.flags[FLAG_NONFINITE], (unsigned long long)tot);
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                const int64_t m = m0 + et;
+                if (m < M) {
+                    float4 o;
+                    o.x = red[(0 * BM + et) * 3] + red[(1 * BM + et) * 3] + red[(2 * BM + et) * 3] + red[(3 * BM + et) * 3];
+                    o.y = red[(0 * BM + et) * 3 + 1] + red[(1 * BM + et) * 3 + 1] + red[(2 * BM + et) * 3 + 1] +
+                          red[(3 * BM + et) * 3 + 1];
+                    o.z = red[(0 * BM + et) * 3 + 2] + red[(1 * BM + et) * 3 + 2] + red[(2 * BM + et) * 3 + 2] +
+                          red[(3 * BM + et) * 3 + 2];
+                    o.w = 0.f;
+                    *(float4*)(args.part_out + ((int64_t)blockIdx.y * M + m) * 4) = o;
+                }
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise kernels of the mixed path
+
+__global__ void k_split_matrix(const double* src, int64_t N, int64_t ldk, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+    const int64_t n2 = N * ldk;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / ldk, k = e - r * ldk;
+        const float v = (k < N) ? (float)src[r * N + k] : 0.f;
+        // hi = bf16(v), lo = bf16(v - hi): the pair carries ~16 significant bits
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[e] = h;
+        lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+__global__ void k_init_tc(float* X, float* Y, float* Z, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t M, int64_t N,
+                          int64_t ldk, uint64_t seed, float init_sz, int64_t m0) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= M * N) return;
+    const int64_t m = e / N, i = e - m * N;
+    double sx, sy;
+    init_signs(seed, (uint32_t)(m0 + m), (uint32_t)i, sx, sy);
+    X[e] = (float)sx;
+    Y[e] = (float)sy;
+    Z[e] = init_sz;
+    hi[(2 * m) * ldk + i] = __float2bfloat16_rn((float)sx);
+    hi[(2 * m + 1) * ldk + i] = __float2bfloat16_rn((float)sy);
+    lo[(2 * m) * ldk + i] = __float2bfloat16_rn(0.f);
+    lo[(2 * m + 1) * ldk + i] = __float2bfloat16_rn(0.f);
+}
+
+// Images and per-row-tile sums of an arbitrary FP32 state (after set_state).
+__global__ void k_images_tc(const float* X, const float* Y, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t M,
+                            int64_t N, int64_t ldk) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= M * N) return;
+    const int64_t m = e / N, i = e - m * N;
+    split_store(hi, lo, (2 * m) * ldk + i, X[e], true);
+    split_store(hi, lo, (2 * m + 1) * ldk + i, Y[e], true);
+}
+
+// part[r][m] = sums over sites [128 r, 128 r + 128) of (x, y, z); one warp per (r, m).
+__global__ void k_part_tc(const float* X, const float* Y, const float* Z, float* part, int64_t M, int64_t N,
+                          int64_t n_rt) {
+    const int64_t w = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_rt * M) return;
+    const int64_t r = w / M, m = w - r * M;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int k = lane; k < BM; k += 32) {
+        const int64_t i = r * BM + k;
+        if (i < N) {
+            sx += X[m * N + i];
+            sy += Y[m * N + i];
+            sz += Z[m * N + i];
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (lane == 0) *(float4*)(part + (r * M + m) * 4) = make_float4(sx, sy, sz, 0.f);
+}
+
+// Noise of step t: eta (FP32 Box-Muller, rounded to BF16) into the B-operand
+// image rows 2m / 2m+1, and the collective pair xi (site index N) into XI.
+__global__ void k_noise_tc(__nv_bfloat16* E, float* XI, int64_t M, int64_t N, int64_t ldk, uint64_t seed,
+                           const int64_t* d_t, int64_t m0) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t NP = N + 1;
+    if (e >= M * NP) return;
+    const int64_t m = e / NP, i = e - m * NP;
+    const uint32_t t = (uint32_t)(*d_t);
+    float gx, gy;
+    normal2_f32(seed, (uint32_t)(m0 + m), t, (uint32_t)i, gx, gy);
+    if (i < N) {
+        E[(2 * m) * ldk + i] = __float2bfloat16_rn(gx);
+        E[(2 * m + 1) * ldk + i] = __float2bfloat16_rn(gy);
+    } else {
+        XI[2 * m] = gx;
+        XI[2 * m + 1] = gy;
+    }
+}
+
+// Closing kernel: S^a from the corrector's partial sums (FP32, fixed order), the
+// FP64 window moments, and the step counter (last block).
+__global__ void k_close_tc(const float* part, int64_t M, int64_t n_rt, double* mom, int64_t* d_t, int64_t n_window,
+                           int64_t* d_count, unsigned long long* flags) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t1 = *d_t + 1;
+    if (m < M && t1 > n_window) {
+        double sx = 0, sy = 0, sz = 0;
+        for (int64_t r = 0; r < n_rt; ++r) {
+            const float4 v = *(const float4*)(part + (r * M + m) * 4);
+            sx += v.x;
+            sy += v.y;
+            sz += v.z;
+        }
+        const double A = 0.25 * (sx * sx + sy * sy);
+        double* mm = mom + 5 * m;
+        mm[0] += sz;
+        mm[1] += A;
+        mm[2] += A * A;
+        mm[3] += A * sz;
+        mm[4] += sz * sz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long done = atomicAdd(&flags[FLAG_DONE], 1ull);
+        if (done == gridDim.x - 1) {
+            flags[FLAG_DONE] = 0ull;
+            if (t1 > n_window) *d_count += 1;
+            __threadfence();
+            *d_t = t1;
+        }
+    }
+}
+
+__global__ void k_f32_to_f64_rows(const float* X, const float* Y, const float* Z, double* x, double* y, double* z,
+                                  int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    x[e] = X[e];
+    y[e] = Y[e];
+    z[e] = Z[e];
+}
+
+__global__ void k_f64_to_f32_rows(const double* x, const double* y, const double* z, float* X, float* Y, float* Z,
+                                  int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    X[e] = (float)x[e];
+    Y[e] = (float)y[e];
+    Z[e] = (float)z[e];
+}
+
+__global__ void k_split_vectors(const double* s, int64_t K, int64_t N, int64_t ldk, __nv_bfloat16* hi,
+                                __nv_bfloat16* lo) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= K * N) return;
+    const int64_t r = e / N, k = e - r * N;
+    split_store(hi, lo, r * ldk + k, (float)s[e], true);
+}
+
+__global__ void k_widen(const float* a, double* b, int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) b[e] = a[e];
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map: inner dimension K (extent kext, row pitch ldk elements),
+// outer dimension rows; box 64 x box_rows with 128-byte swizzle. Reads outside
+// the extents return zeros.
+int make_map(twa_ctx* c, CUtensorMap* map, const void* base, int64_t rows, int64_t kext, int64_t ldk, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return set_error(c, TWA_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)kext, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ldk * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(c, TWA_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return TWA_OK;
+}
+
+template <int MODE, int NT0, int NT1>
+int launch_tc(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_rt, int64_t n_ct) {
+    auto kern = k_tc<MODE, NT0, NT1>;
+    static bool attr = false;
+    if (!attr) {
+        TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
+        attr = true;
+    }
+    dim3 grid((unsigned)n_ct, (unsigned)n_rt);
+    kern<<<grid, NTHREADS, SMEM_TOTAL, c->stream>>>(maps, a);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+TcArgs base_args(twa_ctx* c) {
+    TcState* t = c->tc;
+    TcArgs a{};
+    a.N = t->N;
+    a.M = t->M;
+    a.ldk = t->ldk;
+    a.n_rt = t->n_rt;
+    a.n_vec = 2 * t->M;
+    a.G = (float)c->Gamma;
+    a.dt = (float)c->dt;
+    a.sgdt = (float)sqrt(c->Gamma * c->dt);
+    a.sdt = (float)sqrt(c->dt);
+    a.renorm = c->opts.renormalize;
+    a.flags = c->d_flags;
+    return a;
+}
+
+}  // namespace
+
+int tc_prepare(twa_ctx* c) {
+    if (!c->tc) c->tc = new TcState();
+    TcState* t = c->tc;
+    t->N = c->N;
+    t->ldk = (c->N + 7) / 8 * 8;
+    t->n_rt = (c->N + BM - 1) / BM;
+    t->terms = (c->opts.precision == TWA_PREC_BF16) ? 1 : 3;
+    const size_t nb = sizeof(__nv_bfloat16) * (size_t)c->N * t->ldk;
+    __nv_bfloat16** m4[] = {&t->Whi, &t->Wlo, &t->Lhi, &t->Llo};
+    for (auto p : m4)
+        if (cudaMalloc(p, nb) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc BF16 images");
+    const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
+    k_split_matrix<<<g, 256, 0, c->stream>>>(c->W64, c->N, t->ldk, t->Whi, t->Wlo);
+    k_split_matrix<<<g, 256, 0, c->stream>>>(c->L64, c->N, t->ldk, t->Lhi, t->Llo);
+    TWA_CUDA(c, cudaGetLastError());
+    int rc;
+    if ((rc = make_map(c, &t->tmWhi, t->Whi, c->N, c->N, t->ldk, BM))) return rc;
+    if ((rc = make_map(c, &t->tmWlo, t->Wlo, c->N, c->N, t->ldk, BM))) return rc;
+    if ((rc = make_map(c, &t->tmLhi, t->Lhi, c->N, c->N, t->ldk, BM))) return rc;
+    if ((rc = make_map(c, &t->tmLlo, t->Llo, c->N, c->N, t->ldk, BM))) return rc;
+    return TWA_OK;
+}
+
+int tc_alloc(twa_ctx* c) {
+    TcState* t = c->tc;
+    t->M = c->M;
+    t->n_ct = (2 * c->M + BN - 1) / BN;
+    const size_t mn = (size_t)c->M * c->N;
+    float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Hx, &t->Hy, &t->Hz, &t->Bx, &t->By};
+    for (auto p : f)
+        if (cudaMalloc(p, sizeof(float) * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc state");
+    const size_t ni = sizeof(__nv_bfloat16) * 2 * (size_t)c->M * t->ldk;
+    __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E};
+    for (auto p : b) {
+        if (cudaMalloc(p, ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc images");
+        TWA_CUDA(c, cudaMemsetAsync(*p, 0, ni, c->stream));
+    }
+    if (cudaMalloc(&t->XI, sizeof(float) * 2 * c->M) != cudaSuccess ||
+        cudaMalloc(&t->part, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess ||
+        cudaMalloc(&t->partp, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess)
+        return set_error(c, TWA_ENOMEM, "cudaMalloc sums");
+    int rc;
+    const int64_t R = 2 * c->M;
+    if ((rc = make_map(c, &t->tmShi, t->Shi, R, c->N, t->ldk, BN))) return rc;
+    if ((rc = make_map(c, &t->tmSlo, t->Slo, R, c->N, t->ldk, BN))) return rc;
+    if ((rc = make_map(c, &t->tmPhi, t->Phi, R, c->N, t->ldk, BN))) return rc;
+    if ((rc = make_map(c, &t->tmPlo, t->Plo, R, c->N, t->ldk, BN))) return rc;
+    if ((rc = make_map(c, &t->tmE, t->E, R, c->N, t->ldk, BN))) return rc;
+    return TWA_OK;
+}
+
+void tc_free_run(twa_ctx* c) {
+    TcState* t = c->tc;
+    if (!t) return;
+    float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Hx, &t->Hy, &t->Hz, &t->Bx, &t->By, &t->XI,
+                   &t->part, &t->partp};
+    for (auto p : f) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E};
+    for (auto p : b) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+}
+
+void tc_free(twa_ctx* c) {
+    TcState* t = c->tc;
+    if (!t) return;
+    tc_free_run(c);
+    void* all[] = {t->Whi, t->Wlo, t->Lhi, t->Llo};
+    for (void* p : all)
+        if (p) cudaFree(p);
+    delete t;
+    c->tc = nullptr;
+}
+
+int tc_state_changed(twa_ctx* c) {
+    TcState* t = c->tc;
+    const int64_t MN = c->M * c->N;
+    k_images_tc<<<nblk(MN, 256), 256, 0, c->stream>>>(t->X, t->Y, t->Shi, t->Slo, c->M, c->N, t->ldk);
+    k_part_tc<<<nblk(t->n_rt * c->M, 8), 256, 0, c->stream>>>(t->X, t->Y, t->Z, t->part, c->M, c->N, t->n_rt);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+int tc_init_state(twa_ctx* c) {
+    TcState* t = c->tc;
+    k_init_tc<<<nblk(c->M * c->N, 256), 256, 0, c->stream>>>(t->X, t->Y, t->Z, t->Shi, t->Slo, c->M, c->N, t->ldk,
+                                                            c->seed, (float)c->opts.init_state,
+                                                            c->opts.traj_offset);
+    TWA_CUDA(c, cudaGetLastError());
+    k_part_tc<<<nblk(t->n_rt * c->M, 8), 256, 0, c->stream>>>(t->X, t->Y, t->Z, t->part, c->M, c->N, t->n_rt);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+int tc_run(twa_ctx* c, int64_t steps) {
+    TcState* t = c->tc;
+    const int64_t M = c->M, N = c->N;
+    TcMaps pm{};
+    pm.a0 = t->tmWhi; pm.a1 = t->tmWlo; pm.a2 = t->tmLhi; pm.a3 = t->tmLlo;
+    pm.b0 = t->tmShi; pm.b1 = t->tmSlo; pm.b2 = t->tmE;
+    TcMaps cm{};
+    cm.a0 = t->tmWhi; cm.a1 = t->tmWlo; cm.a2 = t->tmLhi; cm.a3 = t->tmLlo;
+    cm.b0 = t->tmPhi; cm.b1 = t->tmPlo; cm.b2 = t->tmE;
+
+    TcArgs pa = base_args(c);
+    pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z;
+    pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
+    pa.oHx = t->Hx; pa.oHy = t->Hy; pa.oHz = t->Hz;
+    pa.oBnx = t->Bx; pa.oBny = t->By;
+    pa.oHi = t->Phi; pa.oLo = t->Plo;
+    pa.XI = t->XI;
+    pa.part_in = t->part; pa.part_out = t->partp;
+
+    TcArgs ca = base_args(c);
+    ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp;
+    ca.Hx = t->Hx; ca.Hy = t->Hy; ca.Hz = t->Hz;
+    ca.Bnx = t->Bx; ca.Bny = t->By;
+    ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
+    ca.oHi = t->Shi; ca.oLo = t->Slo;
+    ca.part_in = t->partp; ca.part_out = t->part;
+
+    for (int64_t s = 0; s < steps; ++s) {
+        {
+            ProfScope p(c, TWA_PROF_NOISE);
+            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(t->E, t->XI, M, N, t->ldk, c->seed, c->d_t,
+                                                                     c->opts.traj_offset);
+        }
+        int rc;
+        {
+            ProfScope p(c, TWA_PROF_PREDICT);
+            rc = (t->terms == 3) ? launch_tc<MODE_PRED, 3, 2>(c, pm, pa, t->n_rt, t->n_ct)
+                                 : launch_tc<MODE_PRED, 1, 1>(c, pm, pa, t->n_rt, t->n_ct);
+        }
+        if (rc) return rc;
+        {
+            ProfScope p(c, TWA_PROF_CORRECT);
+            rc = (t->terms == 3) ? launch_tc<MODE_CORR, 3, 0>(c, cm, ca, t->n_rt, t->n_ct)
+                                 : launch_tc<MODE_CORR, 1, 0>(c, cm, ca, t->n_rt, t->n_ct);
+        }
+        if (rc) return rc;
+        {
+            ProfScope p(c, TWA_PROF_CLOSE);
+            k_close_tc<<<nblk(M, 256), 256, 0, c->stream>>>(t->part, M, t->n_rt, c->mom, c->d_t, c->n_window,
+                                                            c->d_count, c->d_flags);
+        }
+    }
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+int tc_get_state(twa_ctx* c, double* sx, double* sy, double* sz) {
+    TcState* t = c->tc;
+    const int64_t MN = c->M * c->N;
+    k_f32_to_f64_rows<<<nblk(MN, 256), 256, 0, c->stream>>>(t->X, t->Y, t->Z, sx, sy, sz, MN);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+int tc_set_state(twa_ctx* c, const double* sx, const double* sy, const double* sz) {
+    TcState* t = c->tc;
+    const int64_t MN = c->M * c->N;
+    k_f64_to_f32_rows<<<nblk(MN, 256), 256, 0, c->stream>>>(sx, sy, sz, t->X, t->Y, t->Z, MN);
+    TWA_CUDA(c, cudaGetLastError());
+    return tc_state_changed(c);
+}
+
+int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
+    TcState* t = c->tc;
+    const int64_t N = c->N, ldk = t->ldk;
+    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    float* out = nullptr;
+    const size_t ni = sizeof(__nv_bfloat16) * (size_t)K * ldk;
+    TWA_CUDA(c, cudaMallocAsync(&hi, ni, c->stream));
+    TWA_CUDA(c, cudaMallocAsync(&lo, ni, c->stream));
+    TWA_CUDA(c, cudaMallocAsync(&out, sizeof(float) * K * N, c->stream));
+    TWA_CUDA(c, cudaMemsetAsync(hi, 0, ni, c->stream));
+    TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
+    k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo);
+    TcMaps fm{};
+    fm.a0 = t->tmWhi; fm.a1 = t->tmWlo; fm.a2 = t->tmLhi; fm.a3 = t->tmLlo;
+    int rc;
+    if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, BN))) return rc;
+    if ((rc = make_map(c, &fm.b1, lo, K, N, ldk, BN))) return rc;
+    fm.b2 = fm.b0;
+    TcArgs fa = base_args(c);
+    fa.n_vec = K;
+    fa.field_out = out;
+    const int64_t n_ct = (K + BN - 1) / BN;
+    if (t->terms == 3) rc = launch_tc<MODE_FIELD, 3, 0>(c, fm, fa, t->n_rt, n_ct);
+    else rc = launch_tc<MODE_FIELD, 1, 0>(c, fm, fa, t->n_rt, n_ct);
+    if (rc) return rc;
+    k_widen<<<nblk(K * N, 256), 256, 0, c->stream>>>(out, P, K * N);
+    cudaFreeAsync(hi, c->stream);
+    cudaFreeAsync(lo, c->stream);
+    cudaFreeAsync(out, c->stream);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+}  // namespace twa

@@ -1,0 +1,244 @@
+"""ctypes binding of libtwa (include/twa.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module loads it, converts
+Python arguments to C types and turns status codes into exceptions. PyTorch is
+used only for device buffers and the current CUDA stream. If libtwa.so is
+missing the import of ``lib()`` fails loudly: there is no CPU fallback.
+"""
+import ctypes
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtwa.so")
+
+TWA_OK = 0
+ERRORS = {-1: "TWA_EINVAL", -2: "TWA_ENOTPSD", -3: "TWA_ENOMEM", -4: "TWA_ECUDA", -5: "TWA_ETIMEOUT",
+          -6: "TWA_ENONFINITE", -7: "TWA_ESTATE", -8: "TWA_EUNSUPPORTED"}
+PRECISION = {"fp64": 0, "bf16": 1, "bf16x3": 2}
+
+
+class TWAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("init_state", ctypes.c_int), ("window_start", ctypes.c_double),
+                ("renormalize", ctypes.c_int), ("clip_negative", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("traj_offset", ctypes.c_int64)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("Sz", "Sz_se", "sigma_z", "sigma_z_se", "SpSm", "SpSm_se",
+                                                  "G2num", "G2num_se", "g2", "g2_se")] + \
+               [(n, ctypes.c_int64) for n in ("M", "steps", "samples")] + \
+               [(n, ctypes.c_double) for n in ("w_max", "w_min", "w_tilde", "stability", "min_pivot")] + \
+               [(n, ctypes.c_int64) for n in ("clipped", "nonfinite")]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_SIGNATURES = {
+    "twa_version": (ctypes.c_char_p, []),
+    "twa_opts_default": (ctypes.c_int, [ctypes.POINTER(Opts)]),
+    "twa_init": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(Opts)]),
+    "twa_run": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64]),
+    "twa_sync": (ctypes.c_int, [_P]),
+    "twa_observables": (ctypes.c_int, [_P, ctypes.POINTER(Obs)]),
+    "twa_get_state": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "twa_set_state": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int]),
+    "twa_get_moments": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "twa_field": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
+    "twa_reduce_moments": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
+    "twa_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "twa_profile_read": (ctypes.c_int, [_P, _P, _P]),
+    "twa_last_error": (ctypes.c_char_p, [_P]),
+    "twa_destroy": (None, [_P]),
+}
+
+
+def lib():
+    """Load libtwa.so (built in-tree by paper_2608_10075_b300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libtwa.so not built: run `python -m paper_2608_10075_b300.build` (%s)" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error(ctx=None):
+    return lib().twa_last_error(ctx).decode()
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (contiguous float64)."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), bool(x.is_cuda)
+    import numpy as np
+    if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"] and x.dtype == np.float64):
+        raise ValueError("expected a C-contiguous float64 numpy array or a torch tensor")
+    return ctypes.c_void_p(x.ctypes.data), False
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class TWA:
+    """One context of the C library: parameters, pump matrix, factor, trajectories.
+
+    Mirrors twa_init / twa_run / twa_observables; see include/twa.h.
+    """
+
+    def __init__(self, N, alpha, w, Gamma, dt, seed=0, precision="fp64", init_state=-1, window_start=0.0,
+                 renormalize=True, clip_negative=False, stream=None, traj_offset=0):
+        L = lib()
+        o = Opts()
+        L.twa_opts_default(ctypes.byref(o))
+        o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        o.init_state = int(init_state)
+        o.window_start = float(window_start)
+        o.renormalize = 1 if renormalize else 0
+        o.clip_negative = 1 if clip_negative else 0
+        o.stream = _stream_handle(stream)
+        o.traj_offset = int(traj_offset)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        a = float(alpha)
+        rc = L.twa_init(ctypes.byref(h), int(N), a, float(w), float(Gamma), float(dt),
+                        int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o))
+        if rc != TWA_OK:
+            raise TWAError(rc, last_error(None))
+        self._h = h
+        self.N, self.alpha, self.w, self.Gamma, self.dt = int(N), a, float(w), float(Gamma), float(dt)
+        self.seed, self.precision = int(seed), precision
+        self.M = None
+
+    def _check(self, rc):
+        if rc != TWA_OK:
+            raise TWAError(rc, last_error(self._h))
+
+    def run(self, M, steps):
+        self._check(lib().twa_run(self._h, int(M), int(steps)))
+        self.M = int(M)
+        return self
+
+    def sync(self):
+        self._check(lib().twa_sync(self._h))
+
+    def observables(self):
+        o = Obs()
+        self._check(lib().twa_observables(self._h, ctypes.byref(o)))
+        return o.as_dict()
+
+    def get_state(self, out=None, device=None):
+        """Spins as three [M][N] float64 arrays: torch CUDA tensors when `device`
+        is given (or `out` holds CUDA tensors), numpy arrays otherwise."""
+        M, N = self.M, self.N
+        if out is None:
+            if device is not None:
+                import torch
+                out = tuple(torch.empty((M, N), dtype=torch.float64, device=device) for _ in range(3))
+            else:
+                import numpy as np
+                out = tuple(np.empty((M, N)) for _ in range(3))
+        (px, dx), (py, _), (pz, _) = (_ptr(a) for a in out)
+        self._check(lib().twa_get_state(self._h, px, py, pz, 1 if dx else 0))
+        return out
+
+    def set_state(self, sx, sy, sz):
+        (px, dx), (py, _), (pz, _) = (_ptr(a) for a in (sx, sy, sz))
+        M = int(sx.shape[0])
+        self._check(lib().twa_set_state(self._h, M, px, py, pz, 1 if dx else 0))
+        self.M = M
+
+    def moments(self):
+        """Per-trajectory window means [M][5]: S^z, A, A^2, A S^z, (S^z)^2."""
+        import numpy as np
+        out = np.empty((self.M, 5))
+        self._check(lib().twa_get_moments(self._h, ctypes.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def field(self, s, out=None):
+        """P[k] = W s[k] for a CUDA float64 tensor s of shape [K][N]."""
+        import torch
+        if out is None:
+            out = torch.empty_like(s)
+        (ps, ds), (po, do) = _ptr(s), _ptr(out)
+        if not (ds and do):
+            raise ValueError("field() takes CUDA tensors")
+        self._check(lib().twa_field(self._h, ps, po, int(s.shape[0])))
+        return out
+
+    def profile(self, enable=True):
+        self._check(lib().twa_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kind: (total ms, launches)} of the kernels timed since profile()."""
+        ms = (ctypes.c_double * len(PROF_KINDS))()
+        n = (ctypes.c_int64 * len(PROF_KINDS))()
+        self._check(lib().twa_profile_read(self._h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(PROF_KINDS)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().twa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+PROF_KINDS = ("noise", "predict", "correct", "close", "gemm64", "elem64")
+
+
+def reduce_moments(means, N):
+    """Observables of per-trajectory window means [M][5] (host float64), e.g. the
+    concatenated shards of one ensemble, reduced on the device."""
+    import numpy as np
+    a = np.ascontiguousarray(means, dtype=np.float64)
+    o = Obs()
+    rc = lib().twa_reduce_moments(ctypes.c_void_p(a.ctypes.data), int(a.shape[0]), int(N), ctypes.byref(o))
+    if rc != TWA_OK:
+        raise TWAError(rc, last_error(None))
+    return o.as_dict()
+
+
+def header_functions():
+    """Names of the functions include/twa.h declares (for the export check)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "twa.h")
+    with open(hdr) as f:
+        return re.findall(r"^TWA_API [^(]*?\b(twa_\w+)\(", f.read(), flags=re.M)
+
+
+INF = math.inf

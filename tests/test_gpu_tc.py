@@ -1,0 +1,141 @@
+"""Parity of the mixed-precision tensor-core path (tcgen05, BF16 operands, FP32
+accumulation and state) with the FP64 CPU oracle, through the C ABI.
+
+Contraction bound. Write v = hi + lo + r with hi = bf16(v), lo = bf16(v - hi):
+|hi - v| <= 2^-9 |v| and |r| <= 2^-9 |v - hi| <= 2^-18 |v|. The three-term
+product hi_w hi_s + hi_w lo_s + lo_w hi_s misses lo_w lo_s and the residuals,
+so each product w s is off by at most ~3 * 2^-18 |w s| (plus 2^-24 from the
+FP32 rounding of W), and the FP32 sum over N terms adds N 2^-24 sum |w s| in
+the worst case. Single-term BF16 is off by ~2 * 2^-9 |w s| per product. The
+tests use these bounds with a factor of two of margin.
+
+Trajectories. The mixed path rounds its normals to BF16 (relative 2^-9), so a
+trajectory only stays close to the oracle's for a few steps; beyond that the
+comparison is statistical: ensemble observables within 3 standard errors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.twa_oracle import TWAOracle, pump_matrix
+
+pytestmark = pytest.mark.gpu
+
+
+def _twa():
+    from paper_2608_10075_b300 import twa
+    return twa
+
+
+def _field_check(prec, N, K, alpha, w, seed=2):
+    import torch
+    twa = _twa()
+    rng = np.random.default_rng(seed)
+    s = rng.choice([-1.0, 1.0], size=(K, N)) * rng.uniform(0.2, 1.7, size=(K, N))
+    W = pump_matrix(N, alpha, w)
+    with twa.TWA(N, alpha, w, 1.0, 1e-4, precision=prec) as g:
+        P = g.field(torch.tensor(s, device="cuda")).cpu().numpy()
+    ref = s @ W.T
+    absref = np.abs(s) @ np.abs(W).T
+    if prec == "bf16x3":
+        bound = 2.0 * (3 * 2.0 ** -18 + 2.0 ** -24 + N * 2.0 ** -24) * absref
+    else:
+        bound = 2.0 * (2 * 2.0 ** -9 + N * 2.0 ** -24) * absref
+    err = np.abs(P - ref)
+    assert np.all(err <= bound + 1e-30), float(np.max(err / absref))
+    return float(np.max(err / absref))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("N,K", [(16, 8), (300, 600), (129, 257), (1024, 512)])
+def test_field_contraction_bound(prec, N, K):
+    # several 128-site row tiles and 256-row column tiles, with ragged tails
+    _field_check(prec, N, K, 1.0, N / 2.0)
+
+
+def test_field_bf16x3_is_much_better_than_bf16():
+    e3 = _field_check("bf16x3", 300, 256, 0.5, 150.0)
+    e1 = _field_check("bf16", 300, 256, 0.5, 150.0)
+    assert e3 < e1 / 50
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_initial_state_is_exact(prec):
+    twa = _twa()
+    N, M = 300, 200
+    o = TWAOracle(N, 1.0, 10.0, 1.0, 1e-3, 7, M, init_sz=1.0)
+    with twa.TWA(N, 1.0, 10.0, 1.0, 1e-3, seed=7, precision=prec, init_state=1) as g:
+        g.run(M, 0)
+        gx, gy, gz = g.get_state()
+    assert np.array_equal(gx, o.sx) and np.array_equal(gy, o.sy) and np.array_equal(gz, o.sz)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("N,M", [(300, 200), (128, 128), (45, 3)])
+def test_trajectories_track_oracle_for_a_few_steps(prec, tol, N, M):
+    twa = _twa()
+    alpha, w, G, dt = 1.0, 8.0, 1.0, 2e-3
+    o = TWAOracle(N, alpha, w, G, dt, 11, M)
+    with twa.TWA(N, alpha, w, G, dt, seed=11, precision=prec) as g:
+        for _ in range(3):
+            o.run(1)
+            g.run(M, 1)
+            gx, gy, gz = g.get_state()
+            err = max(np.max(np.abs(gx - o.sx)), np.max(np.abs(gy - o.sy)), np.max(np.abs(gz - o.sz)))
+            assert err < tol, err
+            # spins keep length sqrt(3) up to FP32 rounding
+            assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 5e-6
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_ensemble_observables_within_3se(prec):
+    # N = 256, alpha = 1, w = 32, M = 512, dt = 1e-3, T = 1, window (0.5, 1]
+    N, alpha, w, G, dt, M, T, t0 = 256, 1.0, 32.0, 1.0, 1e-3, 512, 1.0, 0.5
+    steps = int(round(T / dt))
+    twa = _twa()
+    o = TWAOracle(N, alpha, w, G, dt, 5, M, window_start=t0)
+    o.run(steps)
+    ob = o.observables()
+    with twa.TWA(N, alpha, w, G, dt, seed=5, precision=prec, window_start=t0) as g:
+        g.run(M, steps)
+        gb = g.observables()
+    for k in ("Sz", "SpSm", "G2num", "g2"):
+        assert abs(gb[k] - ob[k]) <= 3.0 * math.hypot(gb[k + "_se"], ob[k + "_se"]), (k, gb[k], ob[k])
+    assert gb["nonfinite"] == 0
+
+
+def test_full_size_sampled_trajectories():
+    # N = 10^4, alpha = 1, w = N/2, dt = 2e-5, M = 1024 in the launch shape the
+    # benchmark times; three trajectories recomputed one by one by the oracle.
+    twa = _twa()
+    N, alpha, w, G, dt, M = 10000, 1.0, 5000.0, 1.0, 2e-5, 1024
+    with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3") as g:
+        g.run(M, 2)
+        gx, gy, gz = g.get_state()
+    assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 5e-6
+    W = pump_matrix(N, alpha, w)
+    L = np.linalg.cholesky(W)
+    for m in (0, 517, 1023):
+        o = TWAOracle(N, alpha, w, G, dt, 0, 1, m0=m, W=W, L=L)
+        o.run(2)
+        err = max(np.max(np.abs(gx[m] - o.sx[0])), np.max(np.abs(gy[m] - o.sy[0])), np.max(np.abs(gz[m] - o.sz[0])))
+        assert err < 1e-2, (m, err)
+
+
+def test_full_size_sampled_field():
+    # the contraction kernel at N = 10^4 on 2 x 1024 vectors, rows sampled one by one
+    import torch
+    twa = _twa()
+    N, K = 10000, 2048
+    rng = np.random.default_rng(3)
+    s = rng.choice([-1.0, 1.0], size=(K, N))
+    with twa.TWA(N, 1.0, 5000.0, 1.0, 2e-5, precision="bf16x3") as g:
+        P = g.field(torch.tensor(s, device="cuda")).cpu().numpy()
+    d = np.arange(N)
+    for i in (0, 1, 127, 128, 4999, 9871, 9999):
+        wrow = 5000.0 / (np.abs(i - d) + 1.0)
+        for k in (0, 255, 256, 1500, 2047):
+            ref = float(wrow @ s[k])
+            bound = 2.0 * (3 * 2.0 ** -18 + (N + 1) * 2.0 ** -24) * float(np.abs(wrow) @ np.abs(s[k]))
+            assert abs(P[k, i] - ref) <= bound, (i, k, P[k, i], ref)
