@@ -131,19 +131,25 @@ def contraction_flops(N, M, terms_w=3, terms_l=2):
     return wflops + lflops, wflops
 
 
+def host_threads():
+    """Threads the oracle's BLAS uses (its matmuls are the only parallel part)."""
+    try:
+        from threadpoolctl import threadpool_info
+        return max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except ImportError:
+        # OpenBLAS defaults to one thread per available core
+        return len(os.sched_getaffinity(0))
+
+
 def cpu_oracle_rate(N, M_sample, steps, cfg):
     """Time the FP64 CPU oracle (as it stands) on a trajectory sample."""
-    import numpy as np  # noqa: F401
-    from threadpoolctl import threadpool_info
-
     from oracle.twa_oracle import TWAOracle
     o = TWAOracle(N, cfg["alpha"], cfg["w"], cfg["Gamma"], cfg["dt"], 0, M_sample)
     o.run(1)   # warm-up step (first-touch of buffers)
     t0 = time.perf_counter()
     o.run(steps)
     el = time.perf_counter() - t0
-    threads = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
-    return N * M_sample * steps / el, el, threads
+    return N * M_sample * steps / el, el, host_threads()
 
 
 def run_reference(args, rank, world):
@@ -152,7 +158,6 @@ def run_reference(args, rank, world):
     N = CFG["N"]
     K, Wm = args.steps, args.warmup
     from oracle.twa_oracle import TWAOracle
-    from threadpoolctl import threadpool_info
     t_setup = time.perf_counter()
     o = TWAOracle(N, CFG["alpha"], CFG["w"], CFG["Gamma"], CFG["dt"], 0, REF_SAMPLE_M)
     t_setup = time.perf_counter() - t_setup
@@ -160,7 +165,7 @@ def run_reference(args, rank, world):
     t0 = time.perf_counter()
     o.run(K)
     el = time.perf_counter() - t0
-    threads = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    threads = host_threads()
     v = N * REF_SAMPLE_M * K / el
     sample = "%d of the %d trajectories, all %d sites, %d timed steps (+%d warm-up); W, L set-up %.1f s untimed" % (
         REF_SAMPLE_M, CFG["M"], N, K, Wm, t_setup)

@@ -284,7 +284,9 @@ int setup_pump(twa_ctx* c) {
     }
 
     // spectrum: Lanczos on W
-    const int kmax = (int)(N < 256 ? N : 256);
+    // the low end of the spectrum is dense for long-range pumps, so the Krylov
+    // space is taken large (the full space for N <= 1024)
+    const int kmax = (int)(N < 1024 ? N : 1024);
     double* lz = nullptr;
     TWA_CUDA(c, cudaMallocAsync(&lz, sizeof(double) * (4 * N + 2 * kmax + 8), st));
     double *v0 = lz, *v1 = lz + N, *v2 = lz + 2 * N, *y = lz + 3 * N;
