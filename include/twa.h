@@ -180,6 +180,33 @@ TWA_API int twa_field(twa_ctx* ctx, const double* s, double* P, int64_t K);
  * Errors: TWA_EINVAL (NULL, M < 1), TWA_ENOMEM, TWA_ECUDA. */
 TWA_API int twa_reduce_moments(const double* means, int64_t M, int64_t N, twa_obs* out);
 
+/* Largest M that twa_reduce_moments_noalloc accepts. */
+#define TWA_NOALLOC_MAX_M 65536
+
+/* Allocation-free variant of twa_reduce_moments, for callers that cannot call
+ * cudaMalloc or any allocating routine: code that runs inside a host
+ * application whose memory manager owns the whole device (a framework's pool
+ * that has reserved it, or a strict memory budget), and latency-critical loops
+ * whose policy forbids allocation after start-up. The paper has no counterpart;
+ * this is an engineering variant of the same ensemble reduction.
+ *
+ * Arguments, layout and result are those of twa_reduce_moments (host `means`
+ * [M][5], host *out). Instead of device buffers from cudaMalloc it stages the
+ * means, the sample count and the results in one file-scope __device__ array of
+ * 16 + 5 * TWA_NOALLOC_MAX_M doubles (about 2.6 MB), which every GPU that loads
+ * libtwa holds until the process exits.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress) with the device current; make that first call before
+ *    any stream capture. Later calls on the device reuse the address.
+ *  - Work runs on the legacy default stream and the call returns once the
+ *    results are on the host. It calls no cudaMalloc, cudaFree or other
+ *    allocating routine.
+ *  - Every call on a device shares the one array and rewrites the count, the
+ *    means and the results it uses; calls that overlap on the GPU (from several
+ *    host threads) race and must be serialised by the caller.
+ * Errors: TWA_EINVAL (NULL, M < 1, N < 1, M > TWA_NOALLOC_MAX_M), TWA_ECUDA. */
+TWA_API int twa_reduce_moments_noalloc(const double* means, int64_t M, int64_t N, twa_obs* out);
+
 /* Start (enable = 1) or stop (0) timing every kernel the context launches with
  * a pair of CUDA events recorded on its stream around the launch. Recording
  * adds no synchronisation. Errors: TWA_EINVAL. */

@@ -6,8 +6,17 @@
 // observables, delete-one block jackknife over min(32, M) contiguous blocks
 // (block b = trajectories [b M / B, (b+1) M / B)) for g2. All FP64.
 #include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
 
 #include "twa_internal.cuh"
+
+// Scratch of twa_reduce_moments_noalloc: [0] sample count (int64 bits),
+// [8, 16) results, [16, 16 + 5 M) the per-trajectory window means. Held by every
+// device that loads the library; shared by all calls on that device.
+static __device__ __align__(256) double twa_noalloc_scratch[16 + 5 * (int64_t)TWA_NOALLOC_MAX_M];
 
 namespace twa {
 namespace {
@@ -142,3 +151,65 @@ int reduce_observables(twa_ctx* c, twa_obs* o) {
 }
 
 }  // namespace twa
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_base[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (the host-side symbol is only a stand-in, not a device address).
+int noalloc_base(double** base) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return twa::cuda_check(nullptr, e, "twa_reduce_moments_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return twa::set_error(nullptr, TWA_EUNSUPPORTED, "twa_reduce_moments_noalloc: device index >= 64");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        double* p = nullptr;
+        e = cudaGetSymbolAddress((void**)&p, twa_noalloc_scratch);
+        if (e != cudaSuccess) return twa::cuda_check(nullptr, e, "twa_reduce_moments_noalloc: cudaGetSymbolAddress");
+        g_noalloc_base[dev] = p;
+    }
+    *base = g_noalloc_base[dev];
+    return TWA_OK;
+}
+}  // namespace
+
+extern "C" int twa_reduce_moments_noalloc(const double* means, int64_t M, int64_t N, twa_obs* out) {
+    if (!means || !out || M < 1 || N < 1)
+        return twa::set_error(nullptr, TWA_EINVAL, "twa_reduce_moments_noalloc: NULL pointer, M < 1 or N < 1");
+    if (M > TWA_NOALLOC_MAX_M)
+        return twa::set_error(nullptr, TWA_EINVAL,
+                              "twa_reduce_moments_noalloc: M = " + std::to_string((long long)M) +
+                                  " exceeds the static scratch limit TWA_NOALLOC_MAX_M = " +
+                                  std::to_string((long long)TWA_NOALLOC_MAX_M));
+    double* base = nullptr;
+    int rc = noalloc_base(&base);
+    if (rc) return rc;
+    const int64_t one = 1;
+    cudaError_t e = cudaMemcpy(base, &one, sizeof(one), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + 16, means, sizeof(double) * 5 * M, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return twa::cuda_check(nullptr, e, "twa_reduce_moments_noalloc: upload");
+    twa::k_observables<<<1, twa::RT>>>(base + 16, reinterpret_cast<const int64_t*>(base), M, base + 8);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return twa::cuda_check(nullptr, e, "twa_reduce_moments_noalloc: launch");
+    double h[8];
+    e = cudaMemcpy(h, base + 8, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return twa::cuda_check(nullptr, e, "twa_reduce_moments_noalloc: download");
+    memset(out, 0, sizeof(*out));
+    out->Sz = h[0];
+    out->Sz_se = h[1];
+    out->sigma_z = h[0] / N;
+    out->sigma_z_se = h[1] / N;
+    out->SpSm = h[2];
+    out->SpSm_se = h[3];
+    out->G2num = h[4];
+    out->G2num_se = h[5];
+    out->g2 = h[6];
+    out->g2_se = h[7];
+    out->M = M;
+    out->samples = 1;
+    return TWA_OK;
+}

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "twa_get_moments": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "twa_field": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
     "twa_reduce_moments": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
+    "twa_reduce_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
     "twa_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "twa_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "twa_last_error": (ctypes.c_char_p, [_P]),
@@ -228,6 +229,23 @@ def reduce_moments(means, N):
     a = np.ascontiguousarray(means, dtype=np.float64)
     o = Obs()
     rc = lib().twa_reduce_moments(ctypes.c_void_p(a.ctypes.data), int(a.shape[0]), int(N), ctypes.byref(o))
+    if rc != TWA_OK:
+        raise TWAError(rc, last_error(None))
+    return o.as_dict()
+
+
+NOALLOC_MAX_M = 65536
+
+
+def reduce_moments_noalloc(means, N):
+    """Same as reduce_moments, for callers that cannot allocate device memory:
+    the library stages the data in a fixed device array of NOALLOC_MAX_M
+    trajectories (see twa_reduce_moments_noalloc in include/twa.h). Calls on one
+    device share that array, so concurrent callers must serialise."""
+    import numpy as np
+    a = np.ascontiguousarray(means, dtype=np.float64)
+    o = Obs()
+    rc = lib().twa_reduce_moments_noalloc(ctypes.c_void_p(a.ctypes.data), int(a.shape[0]), int(N), ctypes.byref(o))
     if rc != TWA_OK:
         raise TWAError(rc, last_error(None))
     return o.as_dict()
