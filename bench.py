@@ -119,16 +119,16 @@ class ClockSampler:
 
 
 def contraction_flops(N, M, terms_w=3, terms_l=2):
-    """Tensor-core FLOPs of one predictor and one corrector launch.
+    """Tensor-core FLOPs per launch of each contraction kernel.
 
-    Predictor: W.s over all N^2 entries for 2M columns with `terms_w` products
-    (BF16X3: 3), plus L.eta over the N(N+1)/2 lower-triangular entries with
-    `terms_l` products (hi and lo of L against the BF16 noise). Corrector: W.s~.
+    predict / correct: W.s over all N^2 entries for 2M columns with `terms_w`
+    products (BF16X3: 3); noise_factor: L.eta over the N(N+1)/2 lower-triangular
+    entries with `terms_l` products (hi and lo of L against the BF16 noise).
     """
     cols = 2 * M
     wflops = 2.0 * N * N * cols * terms_w
     lflops = 2.0 * (N * (N + 1) / 2.0) * cols * terms_l
-    return wflops + lflops, wflops
+    return {"predict": wflops, "correct": wflops, "noise_factor": lflops}
 
 
 def host_threads():
@@ -141,15 +141,19 @@ def host_threads():
         return len(os.sched_getaffinity(0))
 
 
-def cpu_oracle_rate(N, M_sample, steps, cfg):
-    """Time the FP64 CPU oracle (as it stands) on a trajectory sample."""
+def cpu_oracle_rate(N, M_sample, steps, cfg, min_seconds=10.0):
+    """Time the FP64 CPU oracle (as it stands) on a trajectory sample: at least
+    `steps` steps and at least `min_seconds` of host work."""
     from oracle.twa_oracle import TWAOracle
     o = TWAOracle(N, cfg["alpha"], cfg["w"], cfg["Gamma"], cfg["dt"], 0, M_sample)
     o.run(1)   # warm-up step (first-touch of buffers)
     t0 = time.perf_counter()
-    o.run(steps)
+    done = 0
+    while done < steps or time.perf_counter() - t0 < min_seconds:
+        o.run(1)
+        done += 1
     el = time.perf_counter() - t0
-    return N * M_sample * steps / el, el, host_threads()
+    return N * M_sample * done / el, el, host_threads(), done
 
 
 def run_reference(args, rank, world):
@@ -229,19 +233,18 @@ def run_ours(args, rank, world, dist):
     ctx.run(M, kp)
     prof = ctx.profile_read()
     ctx.profile(False)
-    pred_ms = prof["predict"][0] / max(prof["predict"][1], 1)
-    corr_ms = prof["correct"][0] / max(prof["correct"][1], 1)
     step_kernel_ms = sum(v[0] for v in prof.values()) / max(kp, 1)
     terms_w = 3 if CFG["precision"] == "bf16x3" else 1
     terms_l = 2 if CFG["precision"] == "bf16x3" else 1
-    pflops, cflops = contraction_flops(N, M, terms_w, terms_l)
+    flops = contraction_flops(N, M, terms_w, terms_l)
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    dominant = "predict" if prof["predict"][0] >= prof["correct"][0] else "correct"
-    d_ms = pred_ms if dominant == "predict" else corr_ms
-    d_flops = pflops if dominant == "predict" else cflops
+    dominant = max(flops, key=lambda k: prof[k][0])
+    d_ms = prof[dominant][0] / max(prof[dominant][1], 1)
+    d_flops = flops[dominant]
     achieved = d_flops / (d_ms * 1e-3) / 1e12
-    traffic = recorded_traffic("twa_tc.cu", "tc_predict_n10000.md") if dominant == "predict" else None
+    contraction_tflops = sum(flops[k] * prof[k][1] for k in flops) / (sum(prof[k][0] for k in flops) * 1e-3) / 1e12
+    traffic = recorded_traffic("twa_tc.cu", "tc_%s_n10000.md" % dominant)
 
     # ---- end to end through the C ABI with host buffers ----
     xs = [torch.empty((M, N), dtype=torch.float64, pin_memory=True) for _ in range(3)]
@@ -266,8 +269,7 @@ def run_ours(args, rank, world, dist):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        steps_cpu = 3
-        v, el, threads = cpu_oracle_rate(N, REF_SAMPLE_M, steps_cpu, CFG)
+        v, el, threads, steps_cpu = cpu_oracle_rate(N, REF_SAMPLE_M, 3, CFG)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d trajectories x %d sites x %d steps of the same workload (%.1f s); W, L set-up untimed"
                          % (REF_SAMPLE_M, N, steps_cpu, el)}
@@ -285,12 +287,14 @@ def run_ours(args, rank, world, dist):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s bf16_tflops_sustained" % peak_src,
                          "kernel_ms": d_ms, "flops_per_launch": d_flops,
+                         "all_contractions_tflops": contraction_tflops,
+                         "all_contractions_frac": contraction_tflops / peak,
                          "kernel_ms_per_step": {k: v[0] / max(kp, 1) for k, v in prof.items() if v[1]},
                          "step_kernel_ms": step_kernel_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                     "note": "set_state from pinned host FP64 buffers, K steps, moments and observables to host"},
-            "gpu_launches": 4 * K,
+            "gpu_launches": 5 * K,
             "clocks": clk,
             "observables": {k: obs[k] for k in ("sigma_z", "SpSm", "g2", "w_tilde", "stability", "nonfinite")},
         }
@@ -302,8 +306,8 @@ def run_ours(args, rank, world, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -89,12 +89,13 @@ typedef struct twa_opts {
 
 /* kernel classes timed by twa_profile_read */
 #define TWA_PROF_NOISE     0   /* Philox normals of a step                      */
-#define TWA_PROF_PREDICT   1   /* W.s and L.eta contraction + Heun predictor    */
+#define TWA_PROF_PREDICT   1   /* W.s contraction + Heun predictor              */
 #define TWA_PROF_CORRECT   2   /* W.s~ contraction + Heun corrector             */
 #define TWA_PROF_CLOSE     3   /* collective sums + window moments              */
 #define TWA_PROF_GEMM64    4   /* FP64 path: one SIMT contraction               */
 #define TWA_PROF_ELEM64    5   /* FP64 path: elementwise / reduction kernels    */
-#define TWA_PROF_KINDS     6
+#define TWA_PROF_NOISE_FACTOR 6 /* mixed path: L.eta contraction -> noise part  */
+#define TWA_PROF_KINDS     7
 
 typedef struct twa_obs {
     /* ensemble means over trajectories of the per-trajectory window means, and

@@ -1,5 +1,6 @@
 // C-ABI entry points of libtwa (declared and documented in include/twa.h).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -60,6 +61,49 @@ int fix_M(twa_ctx* c, int64_t M) {
         c->M = 0;
     }
     return rc;
+}
+
+int run_eager(twa_ctx* c, int64_t steps) { return use_tc(c) ? twa::tc_run(c, steps) : twa::f64_run(c, steps); }
+
+// Capture one step on a private stream into a CUDA graph. The step's kernels read
+// the step counter from device memory, so the same graph serves every step.
+int capture_step(twa_ctx* c) {
+    if (!c->capture_stream) TWA_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = c->stream;
+    c->stream = c->capture_stream;
+    cudaGraph_t g = nullptr;
+    int rc = TWA_OK;
+    if (cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = TWA_ECUDA;
+    } else {
+        rc = run_eager(c, 1);
+        if (cudaStreamEndCapture(c->capture_stream, &g) != cudaSuccess) rc = TWA_ECUDA;
+    }
+    c->stream = saved;
+    if (rc == TWA_OK && g && cudaGraphInstantiate(&c->step_graph, g, 0) != cudaSuccess) {
+        c->step_graph = nullptr;
+        rc = TWA_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // a failed capture leaves nothing pending: steps then run eagerly
+    return rc;
+}
+
+// Steps either replay the captured step graph or launch the kernels directly
+// (profiling, very short runs, or TWA_NO_GRAPH set).
+int run_steps(twa_ctx* c, int64_t steps) {
+    if (c->profiling || steps < 3 || c->graph_failed || getenv("TWA_NO_GRAPH")) return run_eager(c, steps);
+    int rc;
+    if (!c->step_graph) {
+        if ((rc = run_eager(c, 1))) return rc;   // first launches set kernel attributes outside any capture
+        --steps;
+        if (capture_step(c) != TWA_OK) {
+            c->graph_failed = true;
+            return run_eager(c, steps);
+        }
+    }
+    for (int64_t s = 0; s < steps; ++s) TWA_CUDA(c, cudaGraphLaunch(c->step_graph, c->stream));
+    return TWA_OK;
 }
 
 int check_device_flags(twa_ctx* c) {
@@ -176,8 +220,7 @@ int twa_run(twa_ctx* c, int64_t M, int64_t steps) {
         if (rc) return rc;
     }
     if (steps == 0) return TWA_OK;
-    rc = use_tc(c) ? twa::tc_run(c, steps) : twa::f64_run(c, steps);
-    if (rc) return rc;
+    if ((rc = run_steps(c, steps))) return rc;
     c->steps += steps;
     return TWA_OK;
 }
@@ -366,6 +409,8 @@ const char* twa_last_error(const twa_ctx* c) {
 void twa_destroy(twa_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (auto& r : c->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

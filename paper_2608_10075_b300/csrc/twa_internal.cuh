@@ -76,6 +76,11 @@ struct twa_ctx {
     // tensor-core (BF16 / BF16X3) path
     twa::TcState* tc = nullptr;
 
+    // one captured step, replayed by twa_run (no host launch overhead per kernel)
+    cudaGraphExec_t step_graph = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    bool graph_failed = false;
+
     // per-launch event timing (twa_profile)
     struct ProfRec {
         int kind;

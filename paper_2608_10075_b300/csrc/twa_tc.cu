@@ -1,24 +1,33 @@
-// Mixed-precision tensor-core path (sm_103a): the two per-step contractions of
-// Eq. S1 -- the pump field sum_j w_ij s^a_j and the correlated noise (L eta)_i --
-// run as tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators in TMEM) on
-// tiles that TMA stages into shared memory; the stochastic-Heun update is the
-// epilogue of the same kernel.
+// Mixed-precision tensor-core path (sm_103a): the per-step contractions of Eq. S1
+// -- the pump field sum_j w_ij s^a_j and the correlated noise (L eta)_i -- run as
+// tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators in TMEM) on tiles that
+// TMA stages into shared memory; the stochastic-Heun update is the epilogue of
+// the contraction that needs it.
 //
 // Operands (K = site index j, contiguous):
 //   A = W or L images, [N][ldk] BF16, rows = sites i (MMA M = 128 per tile)
-//   B = state images,  [2M][ldk] BF16, row 2m = s^x of trajectory m, row
-//       2m+1 = s^y (MMA N = 256 per tile = 128 trajectories x (x, y))
-// so accumulator column 2j / 2j+1 of a tile holds the x / y field of trajectory
-// m0 + j at site i0 + lane, and every epilogue thread owns one site.
+//   B = state / noise images, [2M][ldk] BF16, row 2m = x of trajectory m, row
+//       2m+1 = y (MMA N = BN per tile = BN/2 trajectories x (x, y))
+// so accumulator column 2j / 2j+1 of a tile holds the x / y contraction of
+// trajectory m0 + j at site i0 + lane, and every epilogue thread owns one site.
 //
 // Precision modes: BF16 (one term, hi*hi) or BF16X3 (hi*hi + hi*lo + lo*hi,
 // hi = bf16(v), lo = bf16(v - hi)), FP32 accumulation. The noise eta is drawn
-// in FP32 and rounded to BF16 once, so L.eta is exact up to the L split.
+// in FP32 and rounded to BF16 once, so L.eta needs the two terms of L only.
 //
-// Step = noise kernel, predictor kernel (W.s and L.eta, two accumulators),
-// corrector kernel (W.s~), closing kernel (moments). Collective sums S^a are
-// passed between kernels as per-row-tile partial sums, reduced in a fixed order.
+// Kernel structure: persistent CTAs (at most one per SM) walk a static list of
+// (row tile, trajectory tile) pairs. Warp 0 streams K tiles through a ring of
+// shared-memory stages with TMA, running ahead across tile boundaries; warp 1
+// issues the MMAs into one of two TMEM accumulators; warps 2-5 run the epilogue
+// of the previous tile from the other accumulator, so epilogue and main loop
+// overlap. Every wait on an mbarrier is bounded in time and reports a timeout.
+//
+// A step is: noise, L.eta (-> noise part of the field increment), W.s with the
+// Heun predictor, W.s~ with the corrector, closing kernel (moments). Collective
+// sums S^a are passed between kernels as per-row-tile partial sums, reduced in
+// a fixed order.
 #include <math.h>
+#include <stdlib.h>
 
 #include <cudaTypedefs.h>
 
@@ -27,8 +36,10 @@
 namespace twa {
 
 struct TcState {
-    int64_t M = 0, N = 0, ldk = 0, n_rt = 0, n_ct = 0;
+    int64_t M = 0, N = 0, ldk = 0, n_rt = 0;
     int terms = 3;                               // 1 (BF16) or 3 (BF16X3)
+    int bn = 256, kc = 0;                        // tile width and K-stage configuration
+    int num_sms = 148;
     __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
     float *X = nullptr, *Y = nullptr, *Z = nullptr;       // state [M][N]
     float *Xp = nullptr, *Yp = nullptr, *Zp = nullptr;    // predictor
@@ -45,27 +56,46 @@ struct TcState {
 
 namespace {
 
-constexpr int BM = TC_BM, BN = TC_BN, BK = TC_BK;
-constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 2;                    // 16 KB
-constexpr int B_BYTES = BN * BK * 2;                    // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB
+constexpr int BM = TC_BM;
 constexpr int NTHREADS = 192;                           // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-constexpr int SMEM_TILES = STAGES * STAGE_BYTES;
-constexpr int SMEM_EXTRA = 8 * 16 + 16 + BM * 2 * 4 + BM * 2 * 4 + 4 * BM * 3 * 4;
-constexpr int SMEM_TOTAL = SMEM_TILES + SMEM_EXTRA + 1024;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 
-enum Mode { MODE_FIELD = 0, MODE_PRED = 1, MODE_CORR = 2 };
+enum Mode { MODE_FIELD = 0, MODE_LETA = 1, MODE_PRED = 2, MODE_CORR = 3 };
 
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// K-stage configurations: K tile width, swizzle and ring depth.
+template <int KC>
+struct KCfg;
+template <>
+struct KCfg<0> {   // 64 BF16 = 128 B rows, SWIZZLE_128B, two stages
+    static constexpr int BK = 64, STAGES = 2;
+    static constexpr uint64_t LAYOUT = 2;   // descriptor layout code of SWIZZLE_128B
+    static constexpr uint32_t SBO = 1024;   // 8 rows x 128 B
+};
+template <>
+struct KCfg<1> {   // 32 BF16 = 64 B rows, SWIZZLE_64B, four stages
+    static constexpr int BK = 32, STAGES = 4;
+    static constexpr uint64_t LAYOUT = 4;   // SWIZZLE_64B
+    static constexpr uint32_t SBO = 512;    // 8 rows x 64 B
+};
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+template <int BN, int KC>
+struct Geo {
+    static constexpr int BK = KCfg<KC>::BK, STAGES = KCfg<KC>::STAGES;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int TILES = STAGES * STAGE_BYTES;
+    static constexpr int NTRAJ = BN / 2;
+    static constexpr int EXTRA = (2 * STAGES + 4) * 8 + 16 + NTRAJ * 2 * 4 * 2 + 4 * NTRAJ * 3 * 4;
+    static constexpr int SMEM = TILES + EXTRA + 1024;
+    static constexpr uint32_t NCOLS = (2 * BN <= 256) ? 256 : 512;
+    // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits
+    // 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint64_t gtimer() {
     uint64_t t;
@@ -80,6 +110,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
@@ -120,20 +154,21 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
         : "memory");
 }
 
-// Shared-memory matrix descriptor for a K-major tile written by TMA with
-// 128-byte swizzle: 8-row x 128 B atoms, stride between atoms (SBO) 1024 B,
-// descriptor version 1, layout SWIZZLE_128B (= 2 at bits 61-63).
+// Shared-memory matrix descriptor of a K-major tile that TMA wrote with the
+// configuration's swizzle: 8-row atoms SBO bytes apart, descriptor version 1,
+// swizzle layout code at bits 61-63.
+template <int KC>
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(KCfg<KC>::SBO >> 4) << 32) |
+           ((uint64_t)1 << 46) | (KCfg<KC>::LAYOUT << 61);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
-        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -158,6 +193,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t off, float v, bool with_lo) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[off] = h;
@@ -165,62 +202,65 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
 }
 
 struct TcMaps {
-    CUtensorMap a0, a1, a2, a3, b0, b1, b2;
+    CUtensorMap a0, a1, b0, b1;   // a0/a1: hi/lo of W or L; b0/b1: hi/lo of the B operand
 };
 
 struct TcArgs {
-    int64_t N, M, ldk, n_rt, n_vec;   // n_vec: B rows (2M, or K for the field mode)
+    int64_t N, M, ldk, n_rt, n_vec;   // n_vec: B rows (2M, or K vectors in the field mode)
     float G, dt, sgdt, sdt;
     int renorm;
-    // state and outputs
     const float *X, *Y, *Z;           // PRED: s; CORR: s~
-    const float *Hx, *Hy, *Hz;        // CORR
-    const float *Bnx, *Bny;           // CORR
+    const float *Hx, *Hy, *Hz;        // CORR: s + f(s)/2
+    const float *Bnx, *Bny;           // PRED, CORR: noise part of the field increment
     float *oX, *oY, *oZ;              // PRED: s~; CORR: s'
     float *oHx, *oHy, *oHz;           // PRED
-    float *oBnx, *oBny;               // PRED
+    float *oBnx, *oBny;               // LETA
     __nv_bfloat16 *oHi, *oLo;         // images of the output state
-    const float* XI;
+    const float* XI;                  // LETA: collective normals [M][2]
     const float* part_in;             // sums of the input state, [n_rt][M][4]
     float* part_out;                  // sums of the output state
     float* field_out;                 // FIELD: [n_vec][N]
     unsigned long long* flags;
 };
 
-template <int MODE, int NT0, int NT1>
+template <int MODE, int NT, int BN, int KC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMaps maps, const TcArgs args) {
+    using G_ = Geo<BN, KC>;
+    constexpr int BK = G_::BK, STAGES = G_::STAGES, NTRAJ = G_::NTRAJ;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* tiles = smem;
-    uint64_t* full = (uint64_t*)(smem + SMEM_TILES);
+    uint64_t* full = (uint64_t*)(smem + G_::TILES);
     uint64_t* empty = full + STAGES;
-    uint64_t* accb = empty + STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(accb + 2);
-    float* sS = (float*)(tmem_slot + 4);        // [BM][2] input sums of the tile's trajectories
-    float* sXI = sS + BM * 2;                   // [BM][2]
-    float* red = sXI + BM * 2;                  // [4][BM][3]
+    uint64_t* tfull = empty + STAGES;            // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;                // [2] accumulator drained by the epilogue
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    float* sS = (float*)(tmem_slot + 4);         // [NTRAJ][2] input sums (or xi) of the tile's trajectories
+    float* red = sS + 2 * NTRAJ * 2;             // [4][NTRAJ][3]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i0 = (int64_t)blockIdx.y * BM;     // first site of the tile
-    const int64_t n0 = (int64_t)blockIdx.x * BN;     // first B row (= 2 m0)
-    const int64_t m0 = n0 >> 1;
     const int nk = (int)((args.N + BK - 1) / BK);
-    int nk1 = (int)((i0 + BM + BK - 1) / BK);        // L is lower triangular
-    if (nk1 > nk) nk1 = nk;
-    constexpr int NPH = (MODE == MODE_PRED) ? 2 : 1;
-    constexpr uint32_t NCOLS = (MODE == MODE_PRED) ? 512 : 256;
+    const int64_t n_ct = (args.n_vec + BN - 1) / BN;
+    const int64_t ntiles = args.n_rt * n_ct;
+    // operands: W/L hi (+ lo), B hi (+ lo)
+    constexpr int NA = (NT >= 2) ? 2 : 1;
+    constexpr int NB = (NT == 3) ? 2 : 1;
+    constexpr uint32_t TX = NA * G_::A_BYTES + NB * G_::B_BYTES;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(NCOLS));
+                     "r"(G_::NCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -228,37 +268,45 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    auto k_tiles = [&](int64_t rt) -> int {
+        if (MODE != MODE_LETA) return nk;
+        const int k1 = (int)((rt * BM + BM + BK - 1) / BK);   // L is lower triangular
+        return k1 < nk ? k1 : nk;
+    };
+
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
             uint32_t stage = 0, ph = 0;
             int last_ph[STAGES];
             bool issued[STAGES];
-            for (int s = 0; s < STAGES; ++s) { issued[s] = false; last_ph[s] = 0; }
+            for (int s = 0; s < STAGES; ++s) {
+                issued[s] = false;
+                last_ph[s] = 0;
+            }
             bool ok = true;
-            for (int p = 0; p < NPH && ok; ++p) {
-                const int nkp = (p == 0) ? nk : nk1;
-                const int na = (p == 0) ? (NT0 == 3 ? 2 : 1) : (NT1 == 2 ? 2 : 1);
-                const int nb = (p == 0) ? (NT0 == 3 ? 2 : 1) : 1;
-                const uint32_t bytes = na * A_BYTES + nb * B_BYTES;
-                for (int kt = 0; kt < nkp; ++kt) {
-                    if (!mbar_wait(&empty[stage], ph ^ 1u, args.flags, true)) { ok = false; break; }
-                    mbar_expect_tx(&full[stage], bytes);
-                    uint8_t* st = tiles + stage * STAGE_BYTES;
-                    const int kx = kt * BK;
-                    if (p == 0) {
-                        tma_load(st, &maps.a0, &full[stage], kx, (int)i0);
-                        if (NT0 == 3) tma_load(st + A_BYTES, &maps.a1, &full[stage], kx, (int)i0);
-                        tma_load(st + 2 * A_BYTES, &maps.b0, &full[stage], kx, (int)n0);
-                        if (NT0 == 3) tma_load(st + 2 * A_BYTES + B_BYTES, &maps.b1, &full[stage], kx, (int)n0);
-                    } else {
-                        tma_load(st, &maps.a2, &full[stage], kx, (int)i0);
-                        if (NT1 == 2) tma_load(st + A_BYTES, &maps.a3, &full[stage], kx, (int)i0);
-                        tma_load(st + 2 * A_BYTES, &maps.b2, &full[stage], kx, (int)n0);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int64_t rt = t / n_ct, ct = t - rt * n_ct;
+                const int y_a = (int)(rt * BM), y_b = (int)(ct * BN);
+                const int nkt = k_tiles(rt);
+                for (int kt = 0; kt < nkt; ++kt) {
+                    if (!mbar_wait(&empty[stage], ph ^ 1u, args.flags, true)) {
+                        ok = false;
+                        break;
                     }
+                    mbar_expect_tx(&full[stage], TX);
+                    uint8_t* st = tiles + stage * G_::STAGE_BYTES;
+                    const int kx = kt * BK;
+                    tma_load(st, &maps.a0, &full[stage], kx, y_a);
+                    if (NA == 2) tma_load(st + G_::A_BYTES, &maps.a1, &full[stage], kx, y_a);
+                    tma_load(st + 2 * G_::A_BYTES, &maps.b0, &full[stage], kx, y_b);
+                    if (NB == 2) tma_load(st + 2 * G_::A_BYTES + G_::B_BYTES, &maps.b1, &full[stage], kx, y_b);
                     issued[stage] = true;
                     last_ph[stage] = (int)ph;
-                    if (++stage == STAGES) { stage = 0; ph ^= 1u; }
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             if (!ok) {
@@ -272,97 +320,138 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
         if (lane == 0) {
             uint32_t stage = 0, ph = 0;
             bool ok = true;
-            for (int p = 0; p < NPH && ok; ++p) {
-                const int nkp = (p == 0) ? nk : nk1;
-                const uint32_t dcol = tmem + (uint32_t)(p * BN);
-                for (int kt = 0; kt < nkp; ++kt) {
-                    if (!mbar_wait(&full[stage], ph, args.flags, true)) { ok = false; break; }
+            int it = 0, last_b = -1;
+            uint32_t last_par = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+                const int b = it & 1;
+                const uint32_t use = (uint32_t)(it >> 1);
+                if (!mbar_wait(&tempty[b], (use & 1u) ^ 1u, args.flags, true)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dcol = tmem + (uint32_t)(b * BN);
+                const int nkt = k_tiles(t / n_ct);
+                for (int kt = 0; kt < nkt; ++kt) {
+                    if (!mbar_wait(&full[stage], ph, args.flags, true)) {
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(tiles + stage * STAGE_BYTES);
-                    const uint32_t a1 = a0 + A_BYTES, b0 = a0 + 2 * A_BYTES, b1 = b0 + B_BYTES;
+                    const uint32_t a0 = smem_u32(tiles + stage * G_::STAGE_BYTES);
+                    const uint32_t a1 = a0 + G_::A_BYTES, b0 = a0 + 2 * G_::A_BYTES, b1 = b0 + G_::B_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t ko = kk * 32;   // 16 BF16 = 32 B along the swizzled row
-                        mma_bf16(dcol, sdesc(a0 + ko), sdesc(b0 + ko), (kt > 0 || kk > 0) ? 1u : 0u);
-                        if (p == 0 && NT0 == 3) {
-                            mma_bf16(dcol, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
-                            mma_bf16(dcol, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+                        mma_bf16(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b0 + ko), G_::IDESC,
+                                 (kt > 0 || kk > 0) ? 1u : 0u);
+                        if (NT == 3) {
+                            mma_bf16(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b1 + ko), G_::IDESC, 1u);
+                            mma_bf16(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
                         }
-                        if (p == 1 && NT1 == 2) mma_bf16(dcol, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+                        if (NT == 2) mma_bf16(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
                     }
                     mma_commit(&empty[stage]);
-                    if (++stage == STAGES) { stage = 0; ph ^= 1u; }
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        ph ^= 1u;
+                    }
                 }
+                mma_commit(&tfull[b]);   // this tile's accumulator is complete (or drained, after an abort)
+                last_b = b;
+                last_par = use & 1u;
             }
-            mma_commit(accb);   // accumulators complete (or drained, after an abort)
+            // MMAs still in flight must finish before the accumulators are freed
+            if (last_b >= 0) mbar_wait(&tfull[last_b], last_par, args.flags, false);
         }
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
-        const int q = warp & 3;                       // TMEM lane quadrant of this warp
-        const int et = threadIdx.x - 64;              // 0..127
-        const int64_t i = i0 + 32 * q + lane;         // site of this thread
-        const bool site_ok = i < args.N;
+        const int q = warp & 3;              // TMEM lane quadrant of this warp
+        const int et = threadIdx.x - 64;     // 0..127
         const int64_t M = args.M;
-        if (MODE != MODE_FIELD) {
-            // collective sums of the input state for this tile's 128 trajectories
-            const int64_t m = m0 + et;
-            float sx = 0.f, sy = 0.f;
-            if (m < M) {
-                for (int64_t r = 0; r < args.n_rt; ++r) {
-                    const float4 v = *(const float4*)(args.part_in + (r * M + m) * 4);
-                    sx += v.x;
-                    sy += v.y;
-                }
-            }
-            sS[2 * et] = sx;
-            sS[2 * et + 1] = sy;
-            if (MODE == MODE_PRED) {
-                sXI[2 * et] = (m < M) ? args.XI[2 * m] : 0.f;
-                sXI[2 * et + 1] = (m < M) ? args.XI[2 * m + 1] : 0.f;
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-        }
-        const bool acc_ok = mbar_wait(accb, 0, args.flags, false);
-        tc_fence_after();
-        const bool live = acc_ok && (((volatile unsigned long long*)args.flags)[FLAG_TIMEOUT] == 0ull);
-        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-        if (live) {
-            if (MODE == MODE_FIELD) {
-                for (int c = 0; c < BN / 16; ++c) {
-                    float v[16];
-                    tmem_ld16(trow + 16 * c, v);
-                    tmem_ld_wait();
-                    if (site_ok) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int64_t n = n0 + 16 * c + j;
-                            if (n < args.n_vec) args.field_out[n * args.N + i] = v[j];
+        const float Gm = args.G, dt = args.dt;
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int b = it & 1;
+            const uint32_t use = (uint32_t)(it >> 1);
+            const int64_t rt = t / n_ct, ct = t - rt * n_ct;
+            const int64_t i0 = rt * BM, n0 = ct * BN, m0 = n0 >> 1;
+            const int64_t i = i0 + 32 * q + lane;        // site of this thread
+            const bool site_ok = i < args.N;
+            epi_sync();                                   // smem of the previous tile is free
+            if (MODE == MODE_PRED || MODE == MODE_CORR) {
+                for (int j = et; j < NTRAJ; j += 128) {
+                    const int64_t m = m0 + j;
+                    float sx = 0.f, sy = 0.f;
+                    if (m < M) {
+                        for (int64_t r = 0; r < args.n_rt; ++r) {
+                            const float4 v = *(const float4*)(args.part_in + (r * M + m) * 4);
+                            sx += v.x;
+                            sy += v.y;
                         }
                     }
+                    sS[2 * j] = sx;
+                    sS[2 * j + 1] = sy;
                 }
-            } else {
-                const float G = args.G, dt = args.dt;
-                unsigned nonfinite = 0;
+            } else if (MODE == MODE_LETA) {
+                for (int j = et; j < NTRAJ; j += 128) {
+                    const int64_t m = m0 + j;
+                    sS[2 * j] = (m < M) ? args.XI[2 * m] : 0.f;
+                    sS[2 * j + 1] = (m < M) ? args.XI[2 * m + 1] : 0.f;
+                }
+            }
+            epi_sync();
+            const bool acc_ok = mbar_wait(&tfull[b], use & 1u, args.flags, true);
+            tc_fence_after();
+            // warp-uniform, so that the .sync.aligned TMEM loads and the shuffles
+            // below are reached by every lane or by none
+            const bool live =
+                __all_sync(0xffffffffu, acc_ok && (((volatile unsigned long long*)args.flags)[FLAG_TIMEOUT] == 0ull));
+            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN);
+            unsigned nonfinite = 0;
+            if (live) {
                 for (int c = 0; c < BN / 16; ++c) {
-                    float pv[16], qv[16];
+                    float pv[16];
                     tmem_ld16(trow + 16 * c, pv);
-                    if (MODE == MODE_PRED) tmem_ld16(trow + BN + 16 * c, qv);
                     tmem_ld_wait();
+                    if (MODE == MODE_FIELD) {
+                        if (site_ok) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int64_t n = n0 + 16 * c + j;
+                                if (n < args.n_vec) args.field_out[n * args.N + i] = pv[j];
+                            }
+                        }
+                        continue;
+                    }
+                    if (MODE == MODE_LETA) {
+                        // noise part of the field increment: sqrt(G dt) xi^a - sqrt(dt) (L eta^a)_i
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const int jl = 8 * c + jj;
+                            const int64_t m = m0 + jl;
+                            if (!site_ok || m >= M) continue;
+                            const int64_t e = m * args.N + i;
+                            args.oBnx[e] = args.sgdt * sS[2 * jl] - args.sdt * pv[2 * jj];
+                            args.oBny[e] = args.sgdt * sS[2 * jl + 1] - args.sdt * pv[2 * jj + 1];
+                        }
+                        continue;
+                    }
                     float rx[8], ry[8], rz[8];
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
-                        const int jl = 8 * c + jj;             // local trajectory 0..127
+                        const int jl = 8 * c + jj;            // local trajectory
                         const int64_t m = m0 + jl;
                         rx[jj] = ry[jj] = rz[jj] = 0.f;
                         if (!site_ok || m >= M) continue;
                         const int64_t e = m * args.N + i;
                         const float x = args.X[e], y = args.Y[e], z = args.Z[e];
+                        // B^a = 1/2 (G S^a - P^a) dt + noise part
+                        const float Bxv = 0.5f * (Gm * sS[2 * jl] - pv[2 * jj]) * dt + args.Bnx[e];
+                        const float Byv = 0.5f * (Gm * sS[2 * jl + 1] - pv[2 * jj + 1]) * dt + args.Bny[e];
+                        const int64_t r0 = (2 * m) * args.ldk + i;
                         if (MODE == MODE_PRED) {
-                            // B^a = 1/2 (G S^a - P^a) dt + sqrt(G dt) xi^a - sqrt(dt) (L eta^a)
-                            const float bnx = args.sgdt * sXI[2 * jl] - args.sdt * qv[2 * jj];
-                            const float bny = args.sgdt * sXI[2 * jl + 1] - args.sdt * qv[2 * jj + 1];
-                            const float Bxv = 0.5f * (G * sS[2 * jl] - pv[2 * jj]) * dt + bnx;
-                            const float Byv = 0.5f * (G * sS[2 * jl + 1] - pv[2 * jj + 1]) * dt + bny;
+                            // f = s x (B^y, -B^x, 0); s~ = s + f; h = s + f/2
                             const float fx = z * Bxv, fy = z * Byv, fz = -(x * Bxv + y * Byv);
                             const float xp = x + fx, yp = y + fy, zp = z + fz;
                             args.oX[e] = xp;
@@ -371,18 +460,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                             args.oHx[e] = fmaf(0.5f, fx, x);
                             args.oHy[e] = fmaf(0.5f, fy, y);
                             args.oHz[e] = fmaf(0.5f, fz, z);
-                            args.oBnx[e] = bnx;
-                            args.oBny[e] = bny;
-                            const int64_t r0 = (2 * m) * args.ldk + i;
-                            split_store(args.oHi, args.oLo, r0, xp, NT0 == 3);
-                            split_store(args.oHi, args.oLo, r0 + args.ldk, yp, NT0 == 3);
+                            split_store(args.oHi, args.oLo, r0, xp, NT == 3);
+                            split_store(args.oHi, args.oLo, r0 + args.ldk, yp, NT == 3);
                             rx[jj] = xp;
                             ry[jj] = yp;
                             rz[jj] = zp;
                         } else {
                             // corrector: s' = h + f(s~)/2, then |s'| = sqrt(3)
-                            const float Bxv = 0.5f * (G * sS[2 * jl] - pv[2 * jj]) * dt + args.Bnx[e];
-                            const float Byv = 0.5f * (G * sS[2 * jl + 1] - pv[2 * jj + 1]) * dt + args.Bny[e];
                             float nx = fmaf(0.5f, z * Bxv, args.Hx[e]);
                             float ny = fmaf(0.5f, z * Byv, args.Hy[e]);
                             float nz = fmaf(-0.5f, x * Bxv + y * Byv, args.Hz[e]);
@@ -396,9 +480,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                             args.oX[e] = nx;
                             args.oY[e] = ny;
                             args.oZ[e] = nz;
-                            const int64_t r0 = (2 * m) * args.ldk + i;
-                            split_store(args.oHi, args.oLo, r0, nx, NT0 == 3);
-                            split_store(args.oHi, args.oLo, r0 + args.ldk, ny, NT0 == 3);
+                            split_store(args.oHi, args.oLo, r0, nx, NT == 3);
+                            split_store(args.oHi, args.oLo, r0 + args.ldk, ny, NT == 3);
                             rx[jj] = nx;
                             ry[jj] = ny;
                             rz[jj] = nz;
@@ -417,37 +500,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                     if (lane == 0) {
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj) {
-                            float* rr = red + (q * BM + 8 * c + jj) * 3;
+                            float* rr = red + (q * NTRAJ + 8 * c + jj) * 3;
                             rr[0] = rx[jj];
                             rr[1] = ry[jj];
                             rr[2] = rz[jj];
                         }
                     }
                 }
-                if (MODE == MODE_CORR) {
-                    const unsigned tot = __reduce_add_sync(0xffffffffu, nonfinite);
-                    if (lane == 0 && tot) atomicAdd(&args.flags[FLAG_NONFINITE], (unsigned long long)tot);
-                }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                const int64_t m = m0 + et;
-                if (m < M) {
+            }
+            // accumulator b may be overwritten by the next tile's MMAs
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (MODE == MODE_CORR) {
+                const unsigned tot = __reduce_add_sync(0xffffffffu, nonfinite);
+                if (lane == 0 && tot) atomicAdd(&args.flags[FLAG_NONFINITE], (unsigned long long)tot);
+            }
+            if (MODE == MODE_PRED || MODE == MODE_CORR) {
+                epi_sync();   // every epilogue thread, live or not
+                for (int j = et; j < NTRAJ; j += 128) {
+                    const int64_t m = m0 + j;
+                    if (!live || m >= M) continue;
                     float4 o;
-                    o.x = red[(0 * BM + et) * 3] + red[(1 * BM + et) * 3] + red[(2 * BM + et) * 3] + red[(3 * BM + et) * 3];
-                    o.y = red[(0 * BM + et) * 3 + 1] + red[(1 * BM + et) * 3 + 1] + red[(2 * BM + et) * 3 + 1] +
-                          red[(3 * BM + et) * 3 + 1];
-                    o.z = red[(0 * BM + et) * 3 + 2] + red[(1 * BM + et) * 3 + 2] + red[(2 * BM + et) * 3 + 2] +
-                          red[(3 * BM + et) * 3 + 2];
+                    o.x = red[(0 * NTRAJ + j) * 3] + red[(1 * NTRAJ + j) * 3] + red[(2 * NTRAJ + j) * 3] +
+                          red[(3 * NTRAJ + j) * 3];
+                    o.y = red[(0 * NTRAJ + j) * 3 + 1] + red[(1 * NTRAJ + j) * 3 + 1] + red[(2 * NTRAJ + j) * 3 + 1] +
+                          red[(3 * NTRAJ + j) * 3 + 1];
+                    o.z = red[(0 * NTRAJ + j) * 3 + 2] + red[(1 * NTRAJ + j) * 3 + 2] + red[(2 * NTRAJ + j) * 3 + 2] +
+                          red[(3 * NTRAJ + j) * 3 + 2];
                     o.w = 0.f;
-                    *(float4*)(args.part_out + ((int64_t)blockIdx.y * M + m) * 4) = o;
+                    *(float4*)(args.part_out + (rt * M + m) * 4) = o;
                 }
             }
         }
-        tc_fence_before();
     }
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G_::NCOLS));
     }
 }
 
@@ -482,7 +572,7 @@ __global__ void k_init_tc(float* X, float* Y, float* Z, __nv_bfloat16* hi, __nv_
     lo[(2 * m + 1) * ldk + i] = __float2bfloat16_rn(0.f);
 }
 
-// Images and per-row-tile sums of an arbitrary FP32 state (after set_state).
+// Images of an arbitrary FP32 state (after set_state).
 __global__ void k_images_tc(const float* X, const float* Y, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t M,
                             int64_t N, int64_t ldk) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -618,34 +708,51 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2-D BF16 tensor map: inner dimension K (extent kext, row pitch ldk elements),
-// outer dimension rows; box 64 x box_rows with 128-byte swizzle. Reads outside
-// the extents return zeros.
-int make_map(twa_ctx* c, CUtensorMap* map, const void* base, int64_t rows, int64_t kext, int64_t ldk, int box_rows) {
+// outer dimension rows; box (K tile) x box_rows with the K configuration's
+// swizzle. Reads outside the extents return zeros.
+int make_map(twa_ctx* c, CUtensorMap* map, const void* base, int64_t rows, int64_t kext, int64_t ldk, int box_rows,
+             int kc) {
     auto fn = encode_fn();
     if (!fn) return set_error(c, TWA_ECUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {(cuuint64_t)kext, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ldk * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(kc == 0 ? KCfg<0>::BK : KCfg<1>::BK), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, kc == 0 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(c, TWA_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return TWA_OK;
 }
 
-template <int MODE, int NT0, int NT1>
-int launch_tc(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_rt, int64_t n_ct) {
-    auto kern = k_tc<MODE, NT0, NT1>;
+template <int MODE, int NT, int BN, int KC>
+int launch_one(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_tiles) {
+    auto kern = k_tc<MODE, NT, BN, KC>;
     static bool attr = false;
     if (!attr) {
-        TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
+        TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<BN, KC>::SMEM));
         attr = true;
     }
-    dim3 grid((unsigned)n_ct, (unsigned)n_rt);
-    kern<<<grid, NTHREADS, SMEM_TOTAL, c->stream>>>(maps, a);
+    const int64_t g = n_tiles < c->tc->num_sms ? n_tiles : c->tc->num_sms;
+    kern<<<(unsigned)g, NTHREADS, Geo<BN, KC>::SMEM, c->stream>>>(maps, a);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
+}
+
+template <int MODE, int NT>
+int launch_cfg(twa_ctx* c, const TcMaps& maps, const TcArgs& a) {
+    const int bn = c->tc->bn, kc = c->tc->kc;
+    const int64_t n_tiles = a.n_rt * ((a.n_vec + bn - 1) / bn);
+#define TWA_TC_CASE(BN_, KC_) \
+    if (bn == BN_ && kc == KC_) return launch_one<MODE, NT, BN_, KC_>(c, maps, a, n_tiles);
+    TWA_TC_CASE(256, 0)
+    TWA_TC_CASE(256, 1)
+    TWA_TC_CASE(192, 0)
+    TWA_TC_CASE(192, 1)
+    TWA_TC_CASE(128, 0)
+    TWA_TC_CASE(128, 1)
+#undef TWA_TC_CASE
+    return set_error(c, TWA_EUNSUPPORTED, "tensor-core tile configuration not compiled");
 }
 
 TcArgs base_args(twa_ctx* c) {
@@ -665,6 +772,33 @@ TcArgs base_args(twa_ctx* c) {
     return a;
 }
 
+int env_int(const char* name, int dflt) {
+    const char* v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+
+int make_state_maps(twa_ctx* c) {
+    TcState* t = c->tc;
+    int rc;
+    const int64_t R = 2 * c->M;
+    if ((rc = make_map(c, &t->tmShi, t->Shi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmSlo, t->Slo, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmPhi, t->Phi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmPlo, t->Plo, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmE, t->E, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    return TWA_OK;
+}
+
+int make_matrix_maps(twa_ctx* c) {
+    TcState* t = c->tc;
+    int rc;
+    if ((rc = make_map(c, &t->tmWhi, t->Whi, c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmWlo, t->Wlo, c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmLhi, t->Lhi, c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmLlo, t->Llo, c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    return TWA_OK;
+}
+
 }  // namespace
 
 int tc_prepare(twa_ctx* c) {
@@ -674,6 +808,16 @@ int tc_prepare(twa_ctx* c) {
     t->ldk = (c->N + 7) / 8 * 8;
     t->n_rt = (c->N + BM - 1) / BM;
     t->terms = (c->opts.precision == TWA_PREC_BF16) ? 1 : 3;
+    // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1}.
+    // Default measured fastest at N = 10^4, M = 1024: 256-wide tiles, four 32-wide
+    // K stages (SWIZZLE_64B).
+    t->bn = env_int("TWA_TC_BN", 256);
+    t->kc = env_int("TWA_TC_KC", 1);
+    if (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1))
+        return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0 or 1");
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
+        t->num_sms = sms;
     const size_t nb = sizeof(__nv_bfloat16) * (size_t)c->N * t->ldk;
     __nv_bfloat16** m4[] = {&t->Whi, &t->Wlo, &t->Lhi, &t->Llo};
     for (auto p : m4)
@@ -682,18 +826,12 @@ int tc_prepare(twa_ctx* c) {
     k_split_matrix<<<g, 256, 0, c->stream>>>(c->W64, c->N, t->ldk, t->Whi, t->Wlo);
     k_split_matrix<<<g, 256, 0, c->stream>>>(c->L64, c->N, t->ldk, t->Lhi, t->Llo);
     TWA_CUDA(c, cudaGetLastError());
-    int rc;
-    if ((rc = make_map(c, &t->tmWhi, t->Whi, c->N, c->N, t->ldk, BM))) return rc;
-    if ((rc = make_map(c, &t->tmWlo, t->Wlo, c->N, c->N, t->ldk, BM))) return rc;
-    if ((rc = make_map(c, &t->tmLhi, t->Lhi, c->N, c->N, t->ldk, BM))) return rc;
-    if ((rc = make_map(c, &t->tmLlo, t->Llo, c->N, c->N, t->ldk, BM))) return rc;
-    return TWA_OK;
+    return make_matrix_maps(c);
 }
 
 int tc_alloc(twa_ctx* c) {
     TcState* t = c->tc;
     t->M = c->M;
-    t->n_ct = (2 * c->M + BN - 1) / BN;
     const size_t mn = (size_t)c->M * c->N;
     float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Hx, &t->Hy, &t->Hz, &t->Bx, &t->By};
     for (auto p : f)
@@ -708,14 +846,7 @@ int tc_alloc(twa_ctx* c) {
         cudaMalloc(&t->part, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess ||
         cudaMalloc(&t->partp, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess)
         return set_error(c, TWA_ENOMEM, "cudaMalloc sums");
-    int rc;
-    const int64_t R = 2 * c->M;
-    if ((rc = make_map(c, &t->tmShi, t->Shi, R, c->N, t->ldk, BN))) return rc;
-    if ((rc = make_map(c, &t->tmSlo, t->Slo, R, c->N, t->ldk, BN))) return rc;
-    if ((rc = make_map(c, &t->tmPhi, t->Phi, R, c->N, t->ldk, BN))) return rc;
-    if ((rc = make_map(c, &t->tmPlo, t->Plo, R, c->N, t->ldk, BN))) return rc;
-    if ((rc = make_map(c, &t->tmE, t->E, R, c->N, t->ldk, BN))) return rc;
-    return TWA_OK;
+    return make_state_maps(c);
 }
 
 void tc_free_run(twa_ctx* c) {
@@ -768,20 +899,21 @@ int tc_init_state(twa_ctx* c) {
 int tc_run(twa_ctx* c, int64_t steps) {
     TcState* t = c->tc;
     const int64_t M = c->M, N = c->N;
-    TcMaps pm{};
-    pm.a0 = t->tmWhi; pm.a1 = t->tmWlo; pm.a2 = t->tmLhi; pm.a3 = t->tmLlo;
-    pm.b0 = t->tmShi; pm.b1 = t->tmSlo; pm.b2 = t->tmE;
-    TcMaps cm{};
-    cm.a0 = t->tmWhi; cm.a1 = t->tmWlo; cm.a2 = t->tmLhi; cm.a3 = t->tmLlo;
-    cm.b0 = t->tmPhi; cm.b1 = t->tmPlo; cm.b2 = t->tmE;
+    TcMaps lm{t->tmLhi, t->tmLlo, t->tmE, t->tmE};
+    TcMaps pm{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo};
+    TcMaps cm{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo};
+
+    TcArgs la = base_args(c);
+    la.XI = t->XI;
+    la.oBnx = t->Bx;
+    la.oBny = t->By;
 
     TcArgs pa = base_args(c);
     pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z;
+    pa.Bnx = t->Bx; pa.Bny = t->By;
     pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
     pa.oHx = t->Hx; pa.oHy = t->Hy; pa.oHz = t->Hz;
-    pa.oBnx = t->Bx; pa.oBny = t->By;
     pa.oHi = t->Phi; pa.oLo = t->Plo;
-    pa.XI = t->XI;
     pa.part_in = t->part; pa.part_out = t->partp;
 
     TcArgs ca = base_args(c);
@@ -792,23 +924,27 @@ int tc_run(twa_ctx* c, int64_t steps) {
     ca.oHi = t->Shi; ca.oLo = t->Slo;
     ca.part_in = t->partp; ca.part_out = t->part;
 
+    const bool x3 = t->terms == 3;
     for (int64_t s = 0; s < steps; ++s) {
+        int rc;
         {
             ProfScope p(c, TWA_PROF_NOISE);
             k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(t->E, t->XI, M, N, t->ldk, c->seed, c->d_t,
                                                                      c->opts.traj_offset);
         }
-        int rc;
+        {
+            ProfScope p(c, TWA_PROF_NOISE_FACTOR);
+            rc = x3 ? launch_cfg<MODE_LETA, 2>(c, lm, la) : launch_cfg<MODE_LETA, 1>(c, lm, la);
+        }
+        if (rc) return rc;
         {
             ProfScope p(c, TWA_PROF_PREDICT);
-            rc = (t->terms == 3) ? launch_tc<MODE_PRED, 3, 2>(c, pm, pa, t->n_rt, t->n_ct)
-                                 : launch_tc<MODE_PRED, 1, 1>(c, pm, pa, t->n_rt, t->n_ct);
+            rc = x3 ? launch_cfg<MODE_PRED, 3>(c, pm, pa) : launch_cfg<MODE_PRED, 1>(c, pm, pa);
         }
         if (rc) return rc;
         {
             ProfScope p(c, TWA_PROF_CORRECT);
-            rc = (t->terms == 3) ? launch_tc<MODE_CORR, 3, 0>(c, cm, ca, t->n_rt, t->n_ct)
-                                 : launch_tc<MODE_CORR, 1, 0>(c, cm, ca, t->n_rt, t->n_ct);
+            rc = x3 ? launch_cfg<MODE_CORR, 3>(c, cm, ca) : launch_cfg<MODE_CORR, 1>(c, cm, ca);
         }
         if (rc) return rc;
         {
@@ -850,17 +986,15 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
     k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo);
     TcMaps fm{};
-    fm.a0 = t->tmWhi; fm.a1 = t->tmWlo; fm.a2 = t->tmLhi; fm.a3 = t->tmLlo;
+    fm.a0 = t->tmWhi;
+    fm.a1 = t->tmWlo;
     int rc;
-    if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, BN))) return rc;
-    if ((rc = make_map(c, &fm.b1, lo, K, N, ldk, BN))) return rc;
-    fm.b2 = fm.b0;
+    if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &fm.b1, lo, K, N, ldk, t->bn, t->kc))) return rc;
     TcArgs fa = base_args(c);
     fa.n_vec = K;
     fa.field_out = out;
-    const int64_t n_ct = (K + BN - 1) / BN;
-    if (t->terms == 3) rc = launch_tc<MODE_FIELD, 3, 0>(c, fm, fa, t->n_rt, n_ct);
-    else rc = launch_tc<MODE_FIELD, 1, 0>(c, fm, fa, t->n_rt, n_ct);
+    rc = (t->terms == 3) ? launch_cfg<MODE_FIELD, 3>(c, fm, fa) : launch_cfg<MODE_FIELD, 1>(c, fm, fa);
     if (rc) return rc;
     k_widen<<<nblk(K * N, 256), 256, 0, c->stream>>>(out, P, K * N);
     cudaFreeAsync(hi, c->stream);

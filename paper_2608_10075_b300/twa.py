@@ -219,7 +219,7 @@ class TWA:
         self.close()
 
 
-PROF_KINDS = ("noise", "predict", "correct", "close", "gemm64", "elem64")
+PROF_KINDS = ("noise", "predict", "correct", "close", "gemm64", "elem64", "noise_factor")
 
 
 def reduce_moments(means, N):
