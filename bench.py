@@ -267,6 +267,36 @@ def run_ours(args, rank, world, dist):
     h2d = 3 * 8 * M * N
     d2h = mom_bytes + 160
 
+    ctx.close()
+
+    # ---- beside the dense route: the FFT route and the plain FP64 GPU path ----
+    def side_run(precision, route, steps, warm):
+        g = twa.TWA(N, CFG["alpha"], CFG["w"], CFG["Gamma"], CFG["dt"], seed=0, precision=precision,
+                    stream=stream, traj_offset=rank * M, ws_route=route)
+        g.run(M, warm)
+        g.sync()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        g.run(M, steps)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t_ms = a0.elapsed_time(a1) / steps
+        g.profile(True)
+        g.run(M, min(steps, 20))
+        p = g.profile_read()
+        g.close()
+        return {"value": N * M * world / (t_ms * 1e-3), "ms_per_step": t_ms, "steps": steps,
+                "kernel_ms_per_step": {k: v[0] / v[1] for k, v in p.items() if v[1]}}
+
+    side = {}
+    if not args.no_side:
+        side["fft_route"] = side_run(CFG["precision"], "fft", min(K, 300), 3)
+        side["fft_route"]["speedup_vs_dense"] = side["fft_route"]["value"] / value
+        side["fp64_gpu"] = side_run("fp64", "dense", 2, 1)
+        side["fp64_gpu"]["mixed_speedup"] = value / side["fp64_gpu"]["value"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, el, threads, steps_cpu = cpu_oracle_rate(N, REF_SAMPLE_M, 3, CFG)
@@ -298,8 +328,8 @@ def run_ours(args, rank, world, dist):
             "clocks": clk,
             "observables": {k: obs[k] for k in ("sigma_z", "SpSm", "g2", "w_tilde", "stability", "nonfinite")},
         }
+        line.update(side)
         print(json.dumps(line), flush=True)
-    ctx.close()
     return 0
 
 
@@ -310,6 +340,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="skip the FFT-route and FP64-GPU legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -85,7 +85,13 @@ typedef struct twa_opts {
     int64_t traj_offset;    /* global index of trajectory 0 in the Philox counter
                                (default 0): shards of one ensemble use disjoint
                                offsets and reproduce the unsharded run exactly     */
+    int    ws_route;        /* pump field sum_j w_ij s_j: TWA_ROUTE_DENSE (default,
+                               any W) or TWA_ROUTE_FFT (uses that Eq. 2 is Toeplitz;
+                               BF16 modes only, 2N - 1 <= 28672)                   */
 } twa_opts;
+
+#define TWA_ROUTE_DENSE 0   /* tensor-core contraction with the dense W          */
+#define TWA_ROUTE_FFT   1   /* circulant-embedding FFT convolution, FP32         */
 
 /* kernel classes timed by twa_profile_read */
 #define TWA_PROF_NOISE     0   /* Philox normals of a step                      */

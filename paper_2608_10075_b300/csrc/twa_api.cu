@@ -157,6 +157,10 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         return set_error(nullptr, TWA_EINVAL, "twa_init: window_start must be finite and >= 0");
     if (o.traj_offset < 0 || o.traj_offset > MAX_COUNTER)
         return set_error(nullptr, TWA_EINVAL, "twa_init: traj_offset must be in [0, 2^32-1]");
+    if (o.ws_route != TWA_ROUTE_DENSE && o.ws_route != TWA_ROUTE_FFT)
+        return set_error(nullptr, TWA_EINVAL, "twa_init: ws_route must be TWA_ROUTE_DENSE or TWA_ROUTE_FFT");
+    if (o.ws_route == TWA_ROUTE_FFT && o.precision == TWA_PREC_FP64)
+        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the FFT route runs with the BF16 precisions only");
 
     twa_ctx* c = new (std::nothrow) twa_ctx();
     if (!c) return set_error(nullptr, TWA_ENOMEM, "twa_init: host allocation failed");
@@ -195,6 +199,7 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
     }
     if ((rc = twa::setup_pump(c))) return fail(rc);
     if (use_tc(c) && (rc = twa::tc_prepare(c))) return fail(rc);
+    if (o.ws_route == TWA_ROUTE_FFT && (rc = twa::fft_prepare(c))) return fail(rc);
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         twa::cuda_check(c, e, "twa_init");
@@ -417,6 +422,7 @@ void twa_destroy(twa_ctx* c) {
     }
     free_run_buffers(c);
     if (c->tc) twa::tc_free(c);
+    twa::fft_free(c);
     void* p[] = {c->W64, c->L64, c->d_t, c->d_count, c->d_flags};
     for (void* q : p)
         if (q) cudaFree(q);

@@ -1,0 +1,440 @@
+// Toeplitz route for the pump field of Eq. S1. The pump matrix of Eq. 2 depends
+// only on |i - j|, so sum_j w_ij s_j is a linear convolution of s with
+// c_d = w / (1 + d)^alpha. Embedding W in a circulant matrix of size P >= 2N - 1
+// (first column c_0, c_1, .., c_{N-1}, 0 .., 0, c_{N-1}, .., c_1) turns it into
+// a cyclic convolution: W s = first N entries of IFFT(lambda . FFT(s, zero padded)),
+// lambda = FFT of that column (real, because the column is symmetric).
+//
+// Since W is real, one complex transform of z = s^x + i s^y gives both
+// components: W z = W s^x + i W s^y. One CTA holds one trajectory's transform in
+// shared memory (P complex FP32 values, P = 2^a 3^b 5^c <= 28672), runs an
+// in-place mixed-radix decimation-in-frequency FFT whose output is in digit-
+// reversed order, multiplies by lambda stored in that same order, and runs the
+// inverse as decimation in time, which takes digit-reversed input and returns
+// natural order: no permutation pass. The Heun predictor / corrector of the
+// trajectory then run in the same kernel, with the collective sums S^a reduced
+// in the block.
+#include <math.h>
+
+#include "twa_internal.cuh"
+
+namespace twa {
+namespace {
+
+constexpr int FT = 1024;                 // threads per CTA
+constexpr int64_t FFT_MAX_P = 28672;     // P complex FP32 values in shared memory (224 KB)
+
+struct FftArgs {
+    int64_t N, M, P;
+    int nst;
+    int radix[40];
+    const float* lam;
+    const float2* tw;
+    float G, dt;
+    int renorm;
+    const float *X, *Y, *Z;              // PRED: s; CORR: s~
+    const float *Hx, *Hy, *Hz;           // CORR
+    const float *Bnx, *Bny;              // noise part of the field increment
+    float *oX, *oY, *oZ;                 // PRED: s~; CORR: s'
+    float *oHx, *oHy, *oHz;              // PRED
+    double* mom;                         // CORR: window sums [M][5]
+    int64_t* d_t;
+    int64_t* d_count;
+    int64_t n_window;
+    unsigned long long* flags;
+    const double* field_in;              // FIELD: [K][N]
+    double* field_out;
+    int64_t K;
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// Radix-R DFT in registers: y_k = sum_q a_q exp(-+ 2 pi i q k / R) (INV: +).
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* a) {
+    if (R == 2) {
+        const float2 t = a[1];
+        a[1] = csub(a[0], t);
+        a[0] = cadd(a[0], t);
+    } else if (R == 4) {
+        const float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+        const float2 t2 = cadd(a[1], a[3]), t3 = csub(a[1], a[3]);
+        // forward: y1 = t1 - i t3, y3 = t1 + i t3; inverse: the signs swap
+        const float2 mi = INV ? make_float2(-t3.y, t3.x) : make_float2(t3.y, -t3.x);
+        a[0] = cadd(t0, t2);
+        a[2] = csub(t0, t2);
+        a[1] = cadd(t1, mi);
+        a[3] = csub(t1, mi);
+    } else if (R == 3) {
+        const float h = 0.86602540378443865f;   // sin(2 pi / 3)
+        const float2 s = cadd(a[1], a[2]), d = csub(a[1], a[2]);
+        const float2 m = make_float2(a[0].x - 0.5f * s.x, a[0].y - 0.5f * s.y);
+        // forward: y1 = m - i h d, y2 = m + i h d
+        const float2 ihd = INV ? make_float2(-h * d.y, h * d.x) : make_float2(h * d.y, -h * d.x);
+        a[0] = cadd(a[0], s);
+        a[1] = cadd(m, ihd);
+        a[2] = csub(m, ihd);
+    } else {   // R == 5
+        const float c1 = 0.30901699437494742f, s1 = 0.95105651629515357f;   // cos, sin of 2 pi / 5
+        const float c2 = -0.80901699437494742f, s2 = 0.58778525229247313f;  // cos, sin of 4 pi / 5
+        const float2 p1 = cadd(a[1], a[4]), m1 = csub(a[1], a[4]);
+        const float2 p2 = cadd(a[2], a[3]), m2 = csub(a[2], a[3]);
+        const float2 r1 = make_float2(a[0].x + c1 * p1.x + c2 * p2.x, a[0].y + c1 * p1.y + c2 * p2.y);
+        const float2 r2 = make_float2(a[0].x + c2 * p1.x + c1 * p2.x, a[0].y + c2 * p1.y + c1 * p2.y);
+        // imaginary parts: sum of sin terms times (a_q - a_{5-q})
+        const float2 q1 = make_float2(s1 * m1.x + s2 * m2.x, s1 * m1.y + s2 * m2.y);
+        const float2 q2 = make_float2(s2 * m1.x - s1 * m2.x, s2 * m1.y - s1 * m2.y);
+        // forward: y1 = r1 - i q1, y4 = r1 + i q1, y2 = r2 - i q2, y3 = r2 + i q2
+        const float2 iq1 = INV ? make_float2(-q1.y, q1.x) : make_float2(q1.y, -q1.x);
+        const float2 iq2 = INV ? make_float2(-q2.y, q2.x) : make_float2(q2.y, -q2.x);
+        a[0] = cadd(a[0], cadd(p1, p2));
+        a[1] = cadd(r1, iq1);
+        a[4] = csub(r1, iq1);
+        a[2] = cadd(r2, iq2);
+        a[3] = csub(r2, iq2);
+    }
+}
+
+// One stage over butterflies of radix R and stride m (span L = m R): DIF applies
+// the small DFT then the twiddles w_L^{jk}; DIT (inverse) undoes the twiddles,
+// then the inverse DFT. w_L^{jk} = tw[j k P / L] with j k < L, so no reduction.
+template <int R, bool INV>
+__device__ __forceinline__ void stage_r(float2* buf, int64_t P, int64_t m, const float2* __restrict__ tw) {
+    const int64_t L = m * R, step = P / L, nb = P / R;
+    for (int64_t u = threadIdx.x; u < nb; u += FT) {
+        const int64_t b = u / m, j = u - b * m, base = b * L + j;
+        float2 a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = buf[base + q * m];
+        if (!INV) {
+            dft<R, false>(a);
+#pragma unroll
+            for (int k = 1; k < R; ++k) a[k] = cmul(a[k], __ldg(&tw[j * k * step]));
+        } else {
+#pragma unroll
+            for (int k = 1; k < R; ++k) a[k] = cmulc(a[k], __ldg(&tw[j * k * step]));
+            dft<R, true>(a);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) buf[base + q * m] = a[q];
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void stage(float2* buf, int64_t P, int r, int64_t m, const float2* tw) {
+    switch (r) {
+        case 4: stage_r<4, INV>(buf, P, m, tw); break;
+        case 2: stage_r<2, INV>(buf, P, m, tw); break;
+        case 3: stage_r<3, INV>(buf, P, m, tw); break;
+        default: stage_r<5, INV>(buf, P, m, tw); break;
+    }
+}
+
+// buf <- P * (C buf) for the circulant C with spectrum lam (digit-reversed order).
+__device__ void circulant_conv(float2* buf, const FftArgs& a) {
+    int64_t m = a.P;
+    for (int s = 0; s < a.nst; ++s) {
+        m /= a.radix[s];
+        stage<false>(buf, a.P, a.radix[s], m, a.tw);
+        __syncthreads();
+    }
+    for (int64_t p = threadIdx.x; p < a.P; p += FT) {
+        const float l = __ldg(&a.lam[p]);
+        buf[p] = make_float2(buf[p].x * l, buf[p].y * l);
+    }
+    __syncthreads();
+    for (int s = a.nst - 1; s >= 0; --s) {
+        stage<true>(buf, a.P, a.radix[s], m, a.tw);
+        m *= a.radix[s];
+        __syncthreads();
+    }
+}
+
+// Sum of v over the block (all threads receive it). `scratch` holds 32 floats.
+__device__ float block_sum(float v, float* scratch) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) scratch[w] = v;
+    __syncthreads();
+    float t = (l < FT / 32) ? scratch[l] : 0.f;
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
+// Load s^x + i s^y of trajectory m into buf (zero padded to P); returns S^x, S^y.
+__device__ float2 load_state(float2* buf, const float* X, const float* Y, const FftArgs& a, float* scratch) {
+    float sx = 0.f, sy = 0.f;
+    for (int64_t i = threadIdx.x; i < a.P; i += FT) {
+        float2 v = make_float2(0.f, 0.f);
+        if (i < a.N) v = make_float2(X[i], Y[i]);
+        buf[i] = v;
+        sx += v.x;
+        sy += v.y;
+    }
+    const float Sx = block_sum(sx, scratch);
+    const float Sy = block_sum(sy, scratch);
+    return make_float2(Sx, Sy);
+}
+
+__global__ void __launch_bounds__(FT, 1) k_fft_pred(const FftArgs a) {
+    extern __shared__ float2 buf[];
+    __shared__ float scratch[32];
+    const int64_t m = blockIdx.x, off = m * a.N;
+    const float2 S = load_state(buf, a.X + off, a.Y + off, a, scratch);
+    __syncthreads();
+    circulant_conv(buf, a);
+    const float inv = 1.0f / (float)a.P, G = a.G, dt = a.dt;
+    for (int64_t i = threadIdx.x; i < a.N; i += FT) {
+        const int64_t e = off + i;
+        const float2 pf = buf[i];
+        const float x = a.X[e], y = a.Y[e], z = a.Z[e];
+        // B^a = 1/2 (G S^a - (W s^a)_i) dt + noise part; f = s x (B^y, -B^x, 0)
+        const float Bx = 0.5f * (G * S.x - pf.x * inv) * dt + a.Bnx[e];
+        const float By = 0.5f * (G * S.y - pf.y * inv) * dt + a.Bny[e];
+        const float fx = z * Bx, fy = z * By, fz = -(x * Bx + y * By);
+        a.oX[e] = x + fx;
+        a.oY[e] = y + fy;
+        a.oZ[e] = z + fz;
+        a.oHx[e] = fmaf(0.5f, fx, x);
+        a.oHy[e] = fmaf(0.5f, fy, y);
+        a.oHz[e] = fmaf(0.5f, fz, z);
+    }
+}
+
+__global__ void __launch_bounds__(FT, 1) k_fft_corr(const FftArgs a) {
+    extern __shared__ float2 buf[];
+    __shared__ float scratch[32];
+    const int64_t m = blockIdx.x, off = m * a.N;
+    const int64_t t1 = *a.d_t + 1;
+    const float2 S = load_state(buf, a.X + off, a.Y + off, a, scratch);
+    __syncthreads();
+    circulant_conv(buf, a);
+    const float inv = 1.0f / (float)a.P, G = a.G, dt = a.dt;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    unsigned bad = 0;
+    for (int64_t i = threadIdx.x; i < a.N; i += FT) {
+        const int64_t e = off + i;
+        const float2 pf = buf[i];
+        const float x = a.X[e], y = a.Y[e], z = a.Z[e];
+        const float Bx = 0.5f * (G * S.x - pf.x * inv) * dt + a.Bnx[e];
+        const float By = 0.5f * (G * S.y - pf.y * inv) * dt + a.Bny[e];
+        // s' = h + f(s~)/2, then |s'| = sqrt(3)
+        float nx = fmaf(0.5f, z * Bx, a.Hx[e]);
+        float ny = fmaf(0.5f, z * By, a.Hy[e]);
+        float nz = fmaf(-0.5f, x * Bx + y * By, a.Hz[e]);
+        if (a.renorm) {
+            const float s = sqrtf(3.0f / (nx * nx + ny * ny + nz * nz));
+            nx *= s;
+            ny *= s;
+            nz *= s;
+        }
+        if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) ++bad;
+        a.oX[e] = nx;
+        a.oY[e] = ny;
+        a.oZ[e] = nz;
+        sx += nx;
+        sy += ny;
+        sz += nz;
+    }
+    const float Sx = block_sum(sx, scratch), Sy = block_sum(sy, scratch), Sz = block_sum(sz, scratch);
+    const unsigned nb = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && nb) atomicAdd(&a.flags[FLAG_NONFINITE], (unsigned long long)nb);
+    if (threadIdx.x == 0) {
+        if (t1 > a.n_window) {
+            // window moments S^z, A, A^2, A S^z, (S^z)^2 with A = ((S^x)^2 + (S^y)^2) / 4
+            const double dx = Sx, dy = Sy, dz = Sz;
+            const double A = 0.25 * (dx * dx + dy * dy);
+            double* mm = a.mom + 5 * m;
+            mm[0] += dz;
+            mm[1] += A;
+            mm[2] += A * A;
+            mm[3] += A * dz;
+            mm[4] += dz * dz;
+        }
+        __threadfence();
+        const unsigned long long done = atomicAdd(&a.flags[FLAG_DONE], 1ull);
+        if (done == gridDim.x - 1) {   // last trajectory of the step: advance the counter
+            a.flags[FLAG_DONE] = 0ull;
+            if (t1 > a.n_window) *a.d_count += 1;
+            __threadfence();
+            *a.d_t = t1;
+        }
+    }
+}
+
+// W s for caller vectors: vectors 2b and 2b+1 share one complex transform.
+__global__ void __launch_bounds__(FT, 1) k_fft_field(const FftArgs a) {
+    extern __shared__ float2 buf[];
+    const int64_t k0 = 2 * (int64_t)blockIdx.x, k1 = k0 + 1;
+    for (int64_t i = threadIdx.x; i < a.P; i += FT) {
+        float2 v = make_float2(0.f, 0.f);
+        if (i < a.N) {
+            v.x = (float)a.field_in[k0 * a.N + i];
+            if (k1 < a.K) v.y = (float)a.field_in[k1 * a.N + i];
+        }
+        buf[i] = v;
+    }
+    __syncthreads();
+    circulant_conv(buf, a);
+    const double inv = 1.0 / (double)a.P;
+    for (int64_t i = threadIdx.x; i < a.N; i += FT) {
+        a.field_out[k0 * a.N + i] = (double)buf[i].x * inv;
+        if (k1 < a.K) a.field_out[k1 * a.N + i] = (double)buf[i].y * inv;
+    }
+}
+
+// exp(-2 pi i n / P), accurate to FP32 rounding (FP64 sincospi).
+__global__ void k_fft_twiddles(float2* tw, int64_t P) {
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n >= P) return;
+    double s, c;
+    sincospi(2.0 * (double)n / (double)P, &s, &c);
+    tw[n] = make_float2((float)c, (float)-s);
+}
+
+struct RadixPlan {
+    int nst;
+    int radix[40];
+};
+
+// Spectrum of the circulant embedding, lam_k = c_0 + 2 sum_{d=1}^{N-1} c_d cos(2 pi k d / P)
+// with c_d = W[0][d], written at the DIF output position p of frequency k (mixed-
+// radix digit reversal). FP64 sum of FP32 cosines of exactly reduced arguments.
+__global__ void k_fft_lambda(float* lam, const double* W, int64_t N, int64_t P, const RadixPlan plan) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    int64_t rem = p, span = P, k = 0, weight = 1;
+    for (int s = 0; s < plan.nst; ++s) {
+        span /= plan.radix[s];
+        const int64_t ks = rem / span;
+        rem -= ks * span;
+        k += ks * weight;
+        weight *= plan.radix[s];
+    }
+    double acc = W[0];
+    int64_t r = 0;   // k d mod P, advanced by k each term (k < P)
+    for (int64_t d = 1; d < N; ++d) {
+        r += k;
+        if (r >= P) r -= P;
+        acc += 2.0 * W[d] * (double)cospif(2.0f * (float)r / (float)P);
+    }
+    lam[p] = (float)acc;
+}
+
+bool smooth(int64_t v) {
+    for (int f : {2, 3, 5})
+        while (v % f == 0) v /= f;
+    return v == 1;
+}
+
+FftArgs base_args(twa_ctx* c) {
+    FftArgs a{};
+    const FftPlan* f = c->fft;
+    a.N = c->N;
+    a.M = c->M;
+    a.P = f->P;
+    a.nst = f->nst;
+    for (int s = 0; s < f->nst; ++s) a.radix[s] = f->radix[s];
+    a.lam = f->lam;
+    a.tw = f->tw;
+    a.G = (float)c->Gamma;
+    a.dt = (float)c->dt;
+    a.renorm = c->opts.renormalize;
+    a.flags = c->d_flags;
+    return a;
+}
+
+int set_smem(twa_ctx* c, const void* kern) {
+    TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(c->fft->P * sizeof(float2))));
+    return TWA_OK;
+}
+
+}  // namespace
+
+int fft_prepare(twa_ctx* c) {
+    int64_t P = 2 * c->N - 1;
+    while (!smooth(P)) ++P;
+    if (P > FFT_MAX_P)
+        return set_error(c, TWA_EUNSUPPORTED, "FFT route: transform length " + std::to_string((long long)P) +
+                                                  " does not fit in shared memory (2N - 1 <= 28672 needed)");
+    FftPlan* f = new FftPlan();
+    c->fft = f;
+    f->P = P;
+    int64_t v = P;
+    f->nst = 0;
+    while (v % 4 == 0) { f->radix[f->nst++] = 4; v /= 4; }
+    while (v % 2 == 0) { f->radix[f->nst++] = 2; v /= 2; }
+    while (v % 3 == 0) { f->radix[f->nst++] = 3; v /= 3; }
+    while (v % 5 == 0) { f->radix[f->nst++] = 5; v /= 5; }
+    if (cudaMalloc(&f->lam, sizeof(float) * P) != cudaSuccess || cudaMalloc(&f->tw, sizeof(float2) * P) != cudaSuccess)
+        return set_error(c, TWA_ENOMEM, "cudaMalloc FFT plan");
+    RadixPlan rp{};
+    rp.nst = f->nst;
+    for (int s = 0; s < f->nst; ++s) rp.radix[s] = f->radix[s];
+    const unsigned g = (unsigned)((P + 255) / 256);
+    k_fft_twiddles<<<g, 256, 0, c->stream>>>(f->tw, P);
+    k_fft_lambda<<<g, 256, 0, c->stream>>>(f->lam, c->W64, c->N, P, rp);
+    TWA_CUDA(c, cudaGetLastError());
+    int rc;
+    if ((rc = set_smem(c, (const void*)k_fft_pred)) || (rc = set_smem(c, (const void*)k_fft_corr)) ||
+        (rc = set_smem(c, (const void*)k_fft_field)))
+        return rc;
+    return TWA_OK;
+}
+
+void fft_free(twa_ctx* c) {
+    if (!c->fft) return;
+    if (c->fft->lam) cudaFree(c->fft->lam);
+    if (c->fft->tw) cudaFree(c->fft->tw);
+    delete c->fft;
+    c->fft = nullptr;
+}
+
+int fft_predict(twa_ctx* c) {
+    TcState* t = c->tc;
+    FftArgs a = base_args(c);
+    a.X = t->X; a.Y = t->Y; a.Z = t->Z;
+    a.Bnx = t->Bx; a.Bny = t->By;
+    a.oX = t->Xp; a.oY = t->Yp; a.oZ = t->Zp;
+    a.oHx = t->Hx; a.oHy = t->Hy; a.oHz = t->Hz;
+    k_fft_pred<<<(unsigned)c->M, FT, c->fft->P * sizeof(float2), c->stream>>>(a);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+int fft_correct(twa_ctx* c) {
+    TcState* t = c->tc;
+    FftArgs a = base_args(c);
+    a.X = t->Xp; a.Y = t->Yp; a.Z = t->Zp;
+    a.Hx = t->Hx; a.Hy = t->Hy; a.Hz = t->Hz;
+    a.Bnx = t->Bx; a.Bny = t->By;
+    a.oX = t->X; a.oY = t->Y; a.oZ = t->Z;
+    a.mom = c->mom;
+    a.d_t = c->d_t;
+    a.d_count = c->d_count;
+    a.n_window = c->n_window;
+    k_fft_corr<<<(unsigned)c->M, FT, c->fft->P * sizeof(float2), c->stream>>>(a);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+int fft_field(twa_ctx* c, const double* s, double* P, int64_t K) {
+    FftArgs a = base_args(c);
+    a.field_in = s;
+    a.field_out = P;
+    a.K = K;
+    k_fft_field<<<(unsigned)((K + 1) / 2), FT, c->fft->P * sizeof(float2), c->stream>>>(a);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+}  // namespace twa

@@ -31,7 +31,34 @@ constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
 constexpr int TC_BK = 64;
 
-struct TcState;  // tensor-core path buffers (twa_tc.cu)
+// Buffers of the mixed-precision path (twa_tc.cu, twa_fft.cu).
+struct TcState {
+    int64_t M = 0, N = 0, ldk = 0, n_rt = 0;
+    int terms = 3;                               // 1 (BF16) or 3 (BF16X3)
+    int bn = 256, kc = 0;                        // tile width and K-stage configuration
+    int num_sms = 148;
+    __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
+    float *X = nullptr, *Y = nullptr, *Z = nullptr;       // state [M][N]
+    float *Xp = nullptr, *Yp = nullptr, *Zp = nullptr;    // predictor
+    float *Hx = nullptr, *Hy = nullptr, *Hz = nullptr;    // s + f(s)/2
+    float *Bx = nullptr, *By = nullptr;                   // noise part of the field increment
+    __nv_bfloat16 *Shi = nullptr, *Slo = nullptr;         // images of s   [2M][ldk]
+    __nv_bfloat16 *Phi = nullptr, *Plo = nullptr;         // images of s~  [2M][ldk]
+    __nv_bfloat16* E = nullptr;                           // eta           [2M][ldk]
+    float* XI = nullptr;                                  // [M][2]
+    float* part = nullptr;                                // [n_rt][M][4] sums of s
+    float* partp = nullptr;                               // [n_rt][M][4] sums of s~
+    CUtensorMap tmWhi, tmWlo, tmLhi, tmLlo, tmShi, tmSlo, tmPhi, tmPlo, tmE;
+};
+
+// Circulant-embedding FFT plan of the Toeplitz pump matrix (twa_fft.cu).
+struct FftPlan {
+    int64_t P = 0;               // transform length, P >= 2N - 1, P = 2^a 3^b 5^c
+    int nst = 0;                 // number of stages
+    int radix[40] = {0};         // radix of each stage (DIF order)
+    float* lam = nullptr;        // spectrum of the embedding, in the DIF output order
+    float2* tw = nullptr;        // exp(-2 pi i n / P), n < P
+};
 
 }  // namespace twa
 
@@ -73,8 +100,9 @@ struct twa_ctx {
     double* S = nullptr;     // [M][4] collective sums of the current state
     double* Sp = nullptr;    // [M][4] collective sums of the predictor
 
-    // tensor-core (BF16 / BF16X3) path
+    // tensor-core (BF16 / BF16X3) path, and the FFT plan of the Toeplitz route
     twa::TcState* tc = nullptr;
+    twa::FftPlan* fft = nullptr;
 
     // one captured step, replayed by twa_run (no host launch overhead per kernel)
     cudaGraphExec_t step_graph = nullptr;
@@ -202,6 +230,12 @@ int tc_state_changed(twa_ctx* c);
 int tc_get_state(twa_ctx* c, double* sx, double* sy, double* sz);   // device buffers
 int tc_set_state(twa_ctx* c, const double* sx, const double* sy, const double* sz);
 int tc_field(twa_ctx* c, const double* s, double* P, int64_t K);
+// twa_fft.cu
+int fft_prepare(twa_ctx* c);                     // plan, twiddles, spectrum of the embedding
+void fft_free(twa_ctx* c);
+int fft_predict(twa_ctx* c);                     // W.s by FFT + Heun predictor (one step)
+int fft_correct(twa_ctx* c);                     // W.s~ by FFT + corrector + moments (one step)
+int fft_field(twa_ctx* c, const double* s, double* P, int64_t K);
 // twa_reduce.cu
 int reduce_observables(twa_ctx* c, twa_obs* out);  // device FP64 reduction, synchronises
 

@@ -35,25 +35,6 @@
 
 namespace twa {
 
-struct TcState {
-    int64_t M = 0, N = 0, ldk = 0, n_rt = 0;
-    int terms = 3;                               // 1 (BF16) or 3 (BF16X3)
-    int bn = 256, kc = 0;                        // tile width and K-stage configuration
-    int num_sms = 148;
-    __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
-    float *X = nullptr, *Y = nullptr, *Z = nullptr;       // state [M][N]
-    float *Xp = nullptr, *Yp = nullptr, *Zp = nullptr;    // predictor
-    float *Hx = nullptr, *Hy = nullptr, *Hz = nullptr;    // s + f(s)/2
-    float *Bx = nullptr, *By = nullptr;                   // noise part of the field increment
-    __nv_bfloat16 *Shi = nullptr, *Slo = nullptr;         // images of s   [2M][ldk]
-    __nv_bfloat16 *Phi = nullptr, *Plo = nullptr;         // images of s~  [2M][ldk]
-    __nv_bfloat16* E = nullptr;                           // eta           [2M][ldk]
-    float* XI = nullptr;                                  // [M][2]
-    float* part = nullptr;                                // [n_rt][M][4] sums of s
-    float* partp = nullptr;                               // [n_rt][M][4] sums of s~
-    CUtensorMap tmWhi, tmWlo, tmLhi, tmLlo, tmShi, tmSlo, tmPhi, tmPlo, tmE;
-};
-
 namespace {
 
 constexpr int BM = TC_BM;
@@ -937,6 +918,20 @@ int tc_run(twa_ctx* c, int64_t steps) {
             rc = x3 ? launch_cfg<MODE_LETA, 2>(c, lm, la) : launch_cfg<MODE_LETA, 1>(c, lm, la);
         }
         if (rc) return rc;
+        if (c->fft) {
+            // Toeplitz route: W.s by FFT with the Heun update in the same kernel
+            {
+                ProfScope p(c, TWA_PROF_PREDICT);
+                rc = fft_predict(c);
+            }
+            if (rc) return rc;
+            {
+                ProfScope p(c, TWA_PROF_CORRECT);
+                rc = fft_correct(c);
+            }
+            if (rc) return rc;
+            continue;
+        }
         {
             ProfScope p(c, TWA_PROF_PREDICT);
             rc = x3 ? launch_cfg<MODE_PRED, 3>(c, pm, pa) : launch_cfg<MODE_PRED, 1>(c, pm, pa);
@@ -974,6 +969,7 @@ int tc_set_state(twa_ctx* c, const double* sx, const double* sy, const double* s
 }
 
 int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
+    if (c->fft) return fft_field(c, s, P, K);
     TcState* t = c->tc;
     const int64_t N = c->N, ldk = t->ldk;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;

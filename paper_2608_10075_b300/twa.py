@@ -28,7 +28,10 @@ class TWAError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("init_state", ctypes.c_int), ("window_start", ctypes.c_double),
                 ("renormalize", ctypes.c_int), ("clip_negative", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("traj_offset", ctypes.c_int64)]
+                ("traj_offset", ctypes.c_int64), ("ws_route", ctypes.c_int)]
+
+
+ROUTE = {"dense": 0, "fft": 1}
 
 
 class Obs(ctypes.Structure):
@@ -112,7 +115,7 @@ class TWA:
     """
 
     def __init__(self, N, alpha, w, Gamma, dt, seed=0, precision="fp64", init_state=-1, window_start=0.0,
-                 renormalize=True, clip_negative=False, stream=None, traj_offset=0):
+                 renormalize=True, clip_negative=False, stream=None, traj_offset=0, ws_route="dense"):
         L = lib()
         o = Opts()
         L.twa_opts_default(ctypes.byref(o))
@@ -123,6 +126,7 @@ class TWA:
         o.clip_negative = 1 if clip_negative else 0
         o.stream = _stream_handle(stream)
         o.traj_offset = int(traj_offset)
+        o.ws_route = ROUTE[ws_route] if isinstance(ws_route, str) else int(ws_route)
         self._stream = stream
         h = ctypes.c_void_p()
         a = float(alpha)
