@@ -179,6 +179,49 @@ TWA_API int twa_get_moments(twa_ctx* ctx, double* out, int on_device);
  * stream. Errors: TWA_EINVAL (NULL, K < 1). */
 TWA_API int twa_field(twa_ctx* ctx, const double* s, double* P, int64_t K);
 
+/* objectives of twa_grad */
+#define TWA_OBJ_SPSM 0      /* <S+S->, window and ensemble mean, normal ordered */
+#define TWA_OBJ_G2   1      /* g2 = <S+S+S-S-> / <S+S->^2                      */
+
+typedef struct twa_grad_req {
+    int     objective;      /* TWA_OBJ_SPSM or TWA_OBJ_G2                          */
+    int     want_alpha;     /* 1: also dJ/dalpha (needs 0 < alpha < inf)           */
+    int64_t M;              /* trajectories (Philox indices traj_offset + 0..M-1)  */
+    int64_t steps;          /* steps from the discrete-Wigner start                */
+    int64_t checkpoint;     /* steps between stored states; <= 0 selects 64       */
+} twa_grad_req;
+
+typedef struct twa_grad_out {
+    double J;                       /* objective of the forward run                */
+    double dJ_dw, dJ_dw_se;         /* pathwise derivative and standard error      */
+    double dJ_dalpha, dJ_dalpha_se; /* (0 when want_alpha = 0)                     */
+    int64_t M, steps, samples;      /* samples: steps inside the averaging window  */
+} twa_grad_out;
+
+/* Pathwise gradient of a steady-state objective with respect to the pump
+ * prefactor w and exponent alpha of Eq. 2 at fixed noise (spec pattern 3:
+ * not in the paper, which computes no derivatives).
+ *
+ * Runs its own forward pass of `steps` stochastic-Heun steps from the initial
+ * state (the same trajectories twa_run would produce: same seed, counters and
+ * precision; it neither reads nor changes the state of twa_run), storing the
+ * state every `checkpoint` steps, then the reverse sweep: each block is
+ * recomputed from its checkpoint and the cotangent is pulled back through the
+ * renormalisation, the Heun corrector and the predictor, with W.beta
+ * contractions on the precision path of the context (FP64 SIMT or BF16X3
+ * tensor cores with an FP32 tape). Parameter derivatives use dW/dw = W/w,
+ * dL/dw = L/(2w), dW/dalpha = -ln(1+|i-j|) W and the Cholesky derivative
+ * dL = L Phi(L^-1 dW L^-T). The objective is linearised at the forward run's
+ * ensemble means (g2 through the quotient rule).
+ *
+ * per_traj: NULL or a host array [M][2] receiving M times each trajectory's
+ * contribution to (dJ/dw, dJ/dalpha); their mean is the returned derivative and
+ * their standard deviation / sqrt(M) the returned SE. Synchronises.
+ * Errors: TWA_EINVAL (NULL, M < 1, steps < 1), TWA_ESTATE (no step inside the
+ * window), TWA_EUNSUPPORTED (want_alpha with alpha = 0 or inf, w = 0),
+ * TWA_ENOMEM, TWA_ECUDA, TWA_ENONFINITE. */
+TWA_API int twa_grad(twa_ctx* ctx, const twa_grad_req* req, twa_grad_out* out, double* per_traj);
+
 /* Ensemble reduction alone: observables and standard errors (the same FP64
  * device reduction twa_observables uses) of M caller-supplied per-trajectory
  * window means, `means` a host array [M][5] in the twa_get_moments order. Used

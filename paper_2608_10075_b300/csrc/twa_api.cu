@@ -348,6 +348,23 @@ int twa_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     return use_tc(c) ? twa::tc_field(c, s, P, K) : twa::f64_field(c, s, P, K);
 }
 
+int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_traj) {
+    if (!c || !r || !out) return set_error(c, TWA_EINVAL, "twa_grad: NULL argument");
+    if (r->objective != TWA_OBJ_SPSM && r->objective != TWA_OBJ_G2)
+        return set_error(c, TWA_EINVAL, "twa_grad: unknown objective");
+    if (r->M < 1 || r->M > (int64_t)1 << 30) return set_error(c, TWA_EINVAL, "twa_grad: M must be in [1, 2^30]");
+    if (r->steps < 1 || r->steps > MAX_COUNTER) return set_error(c, TWA_EINVAL, "twa_grad: steps must be in [1, 2^32-1]");
+    if (c->opts.traj_offset + r->M - 1 > MAX_COUNTER)
+        return set_error(c, TWA_EINVAL, "twa_grad: traj_offset + M exceeds the 32-bit trajectory counter");
+    if (!(c->w > 0.0)) return set_error(c, TWA_EUNSUPPORTED, "twa_grad: needs w > 0");
+    if (r->want_alpha && (c->alpha == 0.0 || isinf(c->alpha)))
+        return set_error(c, TWA_EUNSUPPORTED, "twa_grad: d/dalpha needs 0 < alpha < inf");
+    memset(out, 0, sizeof(*out));
+    int rc = twa::grad(c, r, out, per_traj);
+    if (rc) return rc;
+    return check_device_flags(c);
+}
+
 int twa_reduce_moments(const double* means, int64_t M, int64_t N, twa_obs* out) {
     if (!means || !out || M < 1 || N < 1) return set_error(nullptr, TWA_EINVAL, "twa_reduce_moments: bad argument");
     twa_ctx tmp;

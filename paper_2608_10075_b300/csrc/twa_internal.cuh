@@ -49,6 +49,13 @@ struct TcState {
     float* part = nullptr;                                // [n_rt][M][4] sums of s
     float* partp = nullptr;                               // [n_rt][M][4] sums of s~
     CUtensorMap tmWhi, tmWlo, tmLhi, tmLlo, tmShi, tmSlo, tmPhi, tmPlo, tmE;
+    // extra N x N operands (the adjoint's dW/dalpha and dL/dalpha), hi/lo images
+    __nv_bfloat16 *Xhi[2] = {nullptr, nullptr}, *Xlo[2] = {nullptr, nullptr};
+    CUtensorMap tmXhi[2], tmXlo[2];
+    // vector images for tc_contract_f32 (rows fixed at first use)
+    int64_t vec_rows = 0;
+    __nv_bfloat16 *Vhi = nullptr, *Vlo = nullptr;
+    CUtensorMap tmVhi, tmVlo;
 };
 
 // Circulant-embedding FFT plan of the Toeplitz pump matrix (twa_fft.cu).
@@ -230,12 +237,18 @@ int tc_state_changed(twa_ctx* c);
 int tc_get_state(twa_ctx* c, double* sx, double* sy, double* sz);   // device buffers
 int tc_set_state(twa_ctx* c, const double* sx, const double* sy, const double* sz);
 int tc_field(twa_ctx* c, const double* s, double* P, int64_t K);
+// out[k] = A in[k] for FP32 device vectors [K][N] with BF16X3 (or BF16) tensor-core
+// contractions; which: 0 = W, 1 = L (lower), 2, 3 = the extra matrices below.
+int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t K);
+int tc_set_extra_matrix(twa_ctx* c, int slot, const double* A64);   // slot 0 or 1, [N][N] FP64
 // twa_fft.cu
 int fft_prepare(twa_ctx* c);                     // plan, twiddles, spectrum of the embedding
 void fft_free(twa_ctx* c);
 int fft_predict(twa_ctx* c);                     // W.s by FFT + Heun predictor (one step)
 int fft_correct(twa_ctx* c);                     // W.s~ by FFT + corrector + moments (one step)
 int fft_field(twa_ctx* c, const double* s, double* P, int64_t K);
+// twa_adjoint.cu
+int grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_traj);
 // twa_reduce.cu
 int reduce_observables(twa_ctx* c, twa_obs* out);  // device FP64 reduction, synchronises
 

@@ -668,6 +668,14 @@ __global__ void k_split_vectors(const double* s, int64_t K, int64_t N, int64_t l
     split_store(hi, lo, r * ldk + k, (float)s[e], true);
 }
 
+__global__ void k_split_vectors_f32(const float* s, int64_t K, int64_t N, int64_t ldk, __nv_bfloat16* hi,
+                                    __nv_bfloat16* lo) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= K * N) return;
+    const int64_t r = e / N, k = e - r * N;
+    split_store(hi, lo, r * ldk + k, s[e], true);
+}
+
 __global__ void k_widen(const float* a, double* b, int64_t n) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e < n) b[e] = a[e];
@@ -846,10 +854,59 @@ void tc_free_run(twa_ctx* c) {
     }
 }
 
+int tc_set_extra_matrix(twa_ctx* c, int slot, const double* A64) {
+    TcState* t = c->tc;
+    if (slot < 0 || slot > 1) return set_error(c, TWA_EINVAL, "tc_set_extra_matrix: slot");
+    const size_t nb = sizeof(__nv_bfloat16) * (size_t)c->N * t->ldk;
+    if (!t->Xhi[slot]) {
+        if (cudaMalloc(&t->Xhi[slot], nb) != cudaSuccess || cudaMalloc(&t->Xlo[slot], nb) != cudaSuccess)
+            return set_error(c, TWA_ENOMEM, "cudaMalloc extra matrix images");
+    }
+    const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
+    k_split_matrix<<<g, 256, 0, c->stream>>>(A64, c->N, t->ldk, t->Xhi[slot], t->Xlo[slot]);
+    TWA_CUDA(c, cudaGetLastError());
+    int rc;
+    if ((rc = make_map(c, &t->tmXhi[slot], t->Xhi[slot], c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    return make_map(c, &t->tmXlo[slot], t->Xlo[slot], c->N, c->N, t->ldk, BM, t->kc);
+}
+
+int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t K) {
+    TcState* t = c->tc;
+    int rc;
+    if (t->vec_rows != K) {
+        if (t->Vhi) cudaFree(t->Vhi);
+        if (t->Vlo) cudaFree(t->Vlo);
+        const size_t ni = sizeof(__nv_bfloat16) * (size_t)K * t->ldk;
+        t->Vhi = t->Vlo = nullptr;
+        if (cudaMalloc(&t->Vhi, ni) != cudaSuccess || cudaMalloc(&t->Vlo, ni) != cudaSuccess)
+            return set_error(c, TWA_ENOMEM, "cudaMalloc vector images");
+        TWA_CUDA(c, cudaMemsetAsync(t->Vhi, 0, ni, c->stream));
+        TWA_CUDA(c, cudaMemsetAsync(t->Vlo, 0, ni, c->stream));
+        if ((rc = make_map(c, &t->tmVhi, t->Vhi, K, c->N, t->ldk, t->bn, t->kc))) return rc;
+        if ((rc = make_map(c, &t->tmVlo, t->Vlo, K, c->N, t->ldk, t->bn, t->kc))) return rc;
+        t->vec_rows = K;
+    }
+    k_split_vectors_f32<<<nblk(K * c->N, 256), 256, 0, c->stream>>>(in, K, c->N, t->ldk, t->Vhi, t->Vlo);
+    TcMaps m{};
+    if (which == 0) { m.a0 = t->tmWhi; m.a1 = t->tmWlo; }
+    else if (which == 1) { m.a0 = t->tmLhi; m.a1 = t->tmLlo; }
+    else if ((which == 2 || which == 3) && t->Xhi[which - 2]) { m.a0 = t->tmXhi[which - 2]; m.a1 = t->tmXlo[which - 2]; }
+    else return set_error(c, TWA_EINVAL, "tc_contract_f32: unknown operand");
+    m.b0 = t->tmVhi;
+    m.b1 = t->tmVlo;
+    TcArgs a = base_args(c);
+    a.n_vec = K;
+    a.field_out = out;
+    return (t->terms == 3) ? launch_cfg<MODE_FIELD, 3>(c, m, a) : launch_cfg<MODE_FIELD, 1>(c, m, a);
+}
+
 void tc_free(twa_ctx* c) {
     TcState* t = c->tc;
     if (!t) return;
     tc_free_run(c);
+    void* extra[] = {t->Xhi[0], t->Xhi[1], t->Xlo[0], t->Xlo[1], t->Vhi, t->Vlo};
+    for (void* p : extra)
+        if (p) cudaFree(p);
     void* all[] = {t->Whi, t->Wlo, t->Lhi, t->Llo};
     for (void* p : all)
         if (p) cudaFree(p);

@@ -45,6 +45,21 @@ class Obs(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class GradReq(ctypes.Structure):
+    _fields_ = [("objective", ctypes.c_int), ("want_alpha", ctypes.c_int), ("M", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("checkpoint", ctypes.c_int64)]
+
+
+class GradOut(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("J", "dJ_dw", "dJ_dw_se", "dJ_dalpha", "dJ_dalpha_se")] + \
+               [(n, ctypes.c_int64) for n in ("M", "steps", "samples")]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+OBJECTIVE = {"SpSm": 0, "g2": 1}
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -62,6 +77,7 @@ _SIGNATURES = {
     "twa_field": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
     "twa_reduce_moments": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
     "twa_reduce_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
+    "twa_grad": (ctypes.c_int, [_P, ctypes.POINTER(GradReq), ctypes.POINTER(GradOut), _P]),
     "twa_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "twa_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "twa_last_error": (ctypes.c_char_p, [_P]),
@@ -194,6 +210,20 @@ class TWA:
             raise ValueError("field() takes CUDA tensors")
         self._check(lib().twa_field(self._h, ps, po, int(s.shape[0])))
         return out
+
+    def grad(self, objective, M, steps, checkpoint=64, want_alpha=True, per_traj=False):
+        """Pathwise dJ/dw and dJ/dalpha at fixed noise (twa_grad). With per_traj,
+        also the [M][2] per-trajectory samples whose mean is the derivative."""
+        import numpy as np
+        r = GradReq(OBJECTIVE[objective], 1 if want_alpha else 0, int(M), int(steps), int(checkpoint))
+        o = GradOut()
+        buf = np.empty((int(M), 2)) if per_traj else None
+        p = ctypes.c_void_p(buf.ctypes.data) if per_traj else None
+        self._check(lib().twa_grad(self._h, ctypes.byref(r), ctypes.byref(o), p))
+        d = o.as_dict()
+        if per_traj:
+            d["per_traj"] = buf
+        return d
 
     def profile(self, enable=True):
         self._check(lib().twa_profile(self._h, 1 if enable else 0))
