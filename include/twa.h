@@ -196,6 +196,8 @@ typedef struct twa_grad_out {
     double dJ_dw, dJ_dw_se;         /* pathwise derivative and standard error      */
     double dJ_dalpha, dJ_dalpha_se; /* (0 when want_alpha = 0)                     */
     int64_t M, steps, samples;      /* samples: steps inside the averaging window  */
+    double mu[5];                   /* forward ensemble means of the window moments
+                                       S^z, A, A^2, A S^z, (S^z)^2                 */
 } twa_grad_out;
 
 /* Pathwise gradient of a steady-state objective with respect to the pump

@@ -194,6 +194,7 @@ __global__ void k_a_objective(const double* mom, int64_t M, int64_t nsamp, int o
     for (int k = 0; k < 5; ++k) out[k] = c[k];
     out[5] = J;
     out[6] = 1.0 / ((double)M * (double)nsamp);
+    for (int k = 0; k < 5; ++k) out[7 + k] = mu[k];
 }
 
 template <typename T>
@@ -499,7 +500,7 @@ struct Adjoint {
             (rc = alloc(&tQ, 2 * MN * C)) || (rc = alloc(&txi, 2 * M * C)))
             return rc;
         if ((rc = alloc(&tS, 4 * M * C)) || (rc = alloc(&tSt, 4 * M * C)) || (rc = alloc(&tSn, 4 * M * C)) ||
-            (rc = alloc(&mom, 5 * M)) || (rc = alloc(&obj, 8)) || (rc = alloc(&gpart, 2 * M)) ||
+            (rc = alloc(&mom, 5 * M)) || (rc = alloc(&obj, 16)) || (rc = alloc(&gpart, 2 * M)) ||
             (rc = alloc(&sumbt, 2 * M)) || (rc = alloc(&sumb, 2 * M)) || (rc = alloc(&res, 8)))
             return rc;
         T** vec2[] = {&lxy, &luxy, &btxy, &gtxy, &Wbt, &bxy, &lpxy, &Wb, &Ds, &Dst, &LdE};
@@ -634,7 +635,7 @@ int run_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
     if ((rc = a.backward())) return rc;
     k_a_reduce<<<1, 256, 0, c->stream>>>(a.gpart, a.M, a.res);
     TWA_CUDA(c, cudaGetLastError());
-    double res[4], obj[8];
+    double res[4], obj[16];
     TWA_CUDA(c, cudaMemcpyAsync(res, a.res, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
     TWA_CUDA(c, cudaMemcpyAsync(obj, a.obj, sizeof(obj), cudaMemcpyDeviceToHost, c->stream));
     if (per_traj) {
@@ -652,6 +653,7 @@ int run_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
     out->M = a.M;
     out->steps = a.steps;
     out->samples = a.nsamp;
+    for (int k = 0; k < 5; ++k) out->mu[k] = obj[7 + k];
     return TWA_OK;
 }
 

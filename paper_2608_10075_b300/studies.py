@@ -1,0 +1,157 @@
+"""Precision and gradient studies on the GPU, through the C ABI.
+
+    python -m paper_2608_10075_b300.studies precision [--M-ref 512] [--steps S]
+    python -m paper_2608_10075_b300.studies gradients [--M 2048] [--steps S]
+
+precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
+window (1, 2]. The same trajectories (same seed and counters) run on the FP64
+path and on the mixed paths (BF16, BF16X3, BF16X3 with the FFT pump field);
+each observable is reported with its standard error and, per mixed path, the
+paired difference to FP64 (mean over trajectories of the per-trajectory
+difference, and its standard error), which isolates the arithmetic error from
+the sampling noise.
+
+gradients: N = 1024, alpha = 1, w = N Gamma / 4, dt = 1e-4, T = 2, window
+(1, 2], checkpoints every 64 steps. twa_grad (BF16X3) gives d<S+S->/dw,
+d<S+S->/dalpha and dg2/dalpha; central differences with common random numbers
+(the same seed, delta = 1e-4) of the mixed forward run check them.
+
+Each study prints one JSON line per case.
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import twa
+from .configs import ADJOINT_N1024, MIXED_N1024
+
+KEYS = ("Sz", "SpSm", "G2num", "g2")
+
+
+def _linear_samples(means):
+    """Per-trajectory samples of S^z, <S+S->, <S+S+S-S-> from window means."""
+    Sz, A, A2, ASz, Sz2 = means.T
+    return {"Sz": Sz, "SpSm": A + 0.5 * Sz, "G2num": A2 + 2 * ASz - Sz / 3 + 0.5 * Sz2 - 4.0 / 3.0 * A}
+
+
+def _run(N, alpha, w, G, dt, steps, M, t0, precision, route="dense"):
+    t = time.perf_counter()
+    with twa.TWA(N, alpha, w, G, dt, seed=0, precision=precision, window_start=t0, ws_route=route) as g:
+        g.run(M, steps)
+        obs = g.observables()
+        means = g.moments()
+    return obs, means, time.perf_counter() - t
+
+
+def precision_study(args):
+    c = MIXED_N1024
+    N, w, G, dt = c["N"], c["w"], c["Gamma"], c["dt"]
+    steps = args.steps or int(round(c["T"] / dt))
+    t0 = steps * dt - c["window"]
+    for alpha in c["alphas"]:
+        ref_obs, ref_means, ref_t = _run(N, alpha, w, G, dt, steps, args.M_ref, t0, "fp64")
+        ref_s = _linear_samples(ref_means)
+        line = {"study": "precision", "N": N, "alpha": alpha, "w": w, "dt": dt, "steps": steps,
+                "M_ref": args.M_ref, "stability": ref_obs["stability"], "w_tilde": ref_obs["w_tilde"],
+                "fp64": {k: [ref_obs[k], ref_obs[k + "_se"]] for k in KEYS}, "fp64_seconds": ref_t}
+        for name, prec, route in (("bf16", "bf16", "dense"), ("bf16x3", "bf16x3", "dense"),
+                                  ("bf16x3_fft", "bf16x3", "fft")):
+            obs, means, secs = _run(N, alpha, w, G, dt, steps, args.M_ref, t0, prec, route)
+            s = _linear_samples(means)
+            paired = {}
+            for k in ("Sz", "SpSm", "G2num"):
+                d = s[k] - ref_s[k]
+                paired[k] = [float(d.mean()), float(d.std(ddof=1) / math.sqrt(len(d)))]
+            line[name] = {"obs": {k: [obs[k], obs[k + "_se"]] for k in KEYS},
+                          "diff_over_se": {k: abs(obs[k] - ref_obs[k]) / math.hypot(obs[k + "_se"], ref_obs[k + "_se"])
+                                           for k in KEYS},
+                          "paired_diff": paired, "seconds": secs}
+        if args.M_full > args.M_ref:
+            obs, _, secs = _run(N, alpha, w, G, dt, steps, args.M_full, t0, "bf16x3")
+            line["bf16x3_full_M"] = {"M": args.M_full, "obs": {k: [obs[k], obs[k + "_se"]] for k in KEYS},
+                                     "seconds": secs}
+        print(json.dumps(line), flush=True)
+
+
+def _observables(N, alpha, w, G, dt, steps, M, t0):
+    with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3", window_start=t0) as g:
+        g.run(M, steps)
+        return g.observables()
+
+
+def gradient_study(args):
+    c = ADJOINT_N1024
+    N, alpha, w, G, dt = c["N"], c["alpha"], c["w"], c["Gamma"], c["dt"]
+    steps = args.steps or int(round(c["T"] / dt))
+    t0 = 0.5 * steps * dt            # window: the second half of the run
+    M, d = args.M, c["delta"]
+    out = {"study": "gradients", "N": N, "alpha": alpha, "w": w, "dt": dt, "steps": steps, "M": M,
+           "checkpoint": c["checkpoint"], "delta": d}
+    for obj in ("SpSm", "g2"):
+        t = time.perf_counter()
+        with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3", window_start=t0) as g:
+            r = g.grad(obj, M, steps, checkpoint=c["checkpoint"], want_alpha=True)
+        out["adjoint_" + obj] = {**r, "seconds": time.perf_counter() - t}
+    fd = {}
+    t = time.perf_counter()
+    for key, (a2, w2, h) in {"w": (alpha, None, w * d), "alpha": (None, w, d)}.items():
+        vals = []
+        for s in (+1, -1):
+            aa = alpha + s * d if key == "alpha" else alpha
+            ww = w * (1 + s * d) if key == "w" else w
+            vals.append(_observables(N, aa, ww, G, dt, steps, M, t0))
+        for obj in ("SpSm", "g2"):
+            fd["d%s_d%s" % (obj, key)] = (vals[0][obj] - vals[1][obj]) / (2 * h)
+    out["crn_fd"] = fd
+    out["crn_fd_seconds"] = time.perf_counter() - t
+    # the same differences through twa_grad's own forward run (the run the adjoint
+    # differentiates), from the forward means it returns
+    fdt = {}
+    for key, h in (("w", w * d), ("alpha", d)):
+        vals = []
+        for s in (+1, -1):
+            aa = alpha + s * d if key == "alpha" else alpha
+            ww = w * (1 + s * d) if key == "w" else w
+            with twa.TWA(N, aa, ww, G, dt, seed=0, precision="bf16x3", window_start=t0) as g:
+                mu = g.grad("SpSm", M, steps, checkpoint=c["checkpoint"], want_alpha=False)["mu"]
+            Sz, A, A2, ASz, Sz2 = mu
+            spsm = A + 0.5 * Sz
+            vals.append({"SpSm": spsm, "g2": (A2 + 2 * ASz - Sz / 3 + 0.5 * Sz2 - 4.0 / 3.0 * A) / spsm ** 2})
+        for obj in ("SpSm", "g2"):
+            fdt["d%s_d%s" % (obj, key)] = (vals[0][obj] - vals[1][obj]) / (2 * h)
+    out["crn_fd_same_forward"] = fdt
+    out["rel_diff_same_forward"] = {
+        "dSpSm_dw": abs(out["adjoint_SpSm"]["dJ_dw"] - fdt["dSpSm_dw"]) / abs(fdt["dSpSm_dw"]),
+        "dSpSm_dalpha": abs(out["adjoint_SpSm"]["dJ_dalpha"] - fdt["dSpSm_dalpha"]) / abs(fdt["dSpSm_dalpha"]),
+        "dg2_dalpha": abs(out["adjoint_g2"]["dJ_dalpha"] - fdt["dg2_dalpha"]) / abs(fdt["dg2_dalpha"]),
+    }
+    out["rel_diff"] = {
+        "dSpSm_dw": abs(out["adjoint_SpSm"]["dJ_dw"] - fd["dSpSm_dw"]) / abs(fd["dSpSm_dw"]),
+        "dSpSm_dalpha": abs(out["adjoint_SpSm"]["dJ_dalpha"] - fd["dSpSm_dalpha"]) / abs(fd["dSpSm_dalpha"]),
+        "dg2_dalpha": abs(out["adjoint_g2"]["dJ_dalpha"] - fd["dg2_dalpha"]) / abs(fd["dg2_dalpha"]),
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    p = sub.add_parser("precision")
+    p.add_argument("--M-ref", type=int, default=512)
+    p.add_argument("--M-full", type=int, default=MIXED_N1024["M"])
+    p.add_argument("--steps", type=int, default=0)
+    q = sub.add_parser("gradients")
+    q.add_argument("--M", type=int, default=ADJOINT_N1024["M"])
+    q.add_argument("--steps", type=int, default=0)
+    a = ap.parse_args()
+    if a.cmd == "precision":
+        precision_study(a)
+    else:
+        gradient_study(a)
+
+
+if __name__ == "__main__":
+    main()

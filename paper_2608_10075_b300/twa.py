@@ -52,10 +52,12 @@ class GradReq(ctypes.Structure):
 
 class GradOut(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("J", "dJ_dw", "dJ_dw_se", "dJ_dalpha", "dJ_dalpha_se")] + \
-               [(n, ctypes.c_int64) for n in ("M", "steps", "samples")]
+               [(n, ctypes.c_int64) for n in ("M", "steps", "samples")] + [("mu", ctypes.c_double * 5)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "mu"}
+        d["mu"] = list(self.mu)
+        return d
 
 
 OBJECTIVE = {"SpSm": 0, "g2": 1}

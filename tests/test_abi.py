@@ -28,26 +28,23 @@ def test_binding_signatures_cover_header():
     assert set(twa.header_functions()) == set(twa._SIGNATURES)
 
 
-def test_struct_layouts_match_header(tmp_path):
+@pytest.mark.parametrize("pyclass,ctype", [(twa.Opts, "twa_opts"), (twa.Obs, "twa_obs"),
+                                           (twa.GradReq, "twa_grad_req"), (twa.GradOut, "twa_grad_out")])
+def test_struct_layouts_match_header(tmp_path, pyclass, ctype):
     # compile the header with the host C compiler and compare sizes and offsets
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     src = tmp_path / "layout.c"
-    fields_o = [f for f, _ in twa.Opts._fields_]
-    fields_b = [f for f, _ in twa.Obs._fields_]
+    fields = [f for f, _ in pyclass._fields_]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "twa.h"', "int main(void) {",
-             '  printf("%zu %zu\\n", sizeof(twa_opts), sizeof(twa_obs));']
-    lines += ['  printf("%%zu\\n", offsetof(twa_opts, %s));' % f for f in fields_o]
-    lines += ['  printf("%%zu\\n", offsetof(twa_obs, %s));' % f for f in fields_b]
+             '  printf("%%zu\\n", sizeof(%s));' % ctype]
+    lines += ['  printf("%%zu\\n", offsetof(%s, %s));' % (ctype, f) for f in fields]
     lines += ["  return 0; }"]
     src.write_text("\n".join(lines))
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I" + inc, str(src), "-o", str(exe)], check=True)
-    vals = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    assert int(vals[0]) == ctypes.sizeof(twa.Opts)
-    assert int(vals[1]) == ctypes.sizeof(twa.Obs)
-    offs = [int(v) for v in vals[2:]]
-    assert offs[:len(fields_o)] == [getattr(twa.Opts, f).offset for f in fields_o]
-    assert offs[len(fields_o):] == [getattr(twa.Obs, f).offset for f in fields_b]
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(pyclass)
+    assert vals[1:] == [getattr(pyclass, f).offset for f in fields]
 
 
 def test_defaults():
