@@ -224,6 +224,36 @@ typedef struct twa_grad_out {
  * TWA_ENOMEM, TWA_ECUDA, TWA_ENONFINITE. */
 TWA_API int twa_grad(twa_ctx* ctx, const twa_grad_req* req, twa_grad_out* out, double* per_traj);
 
+/* one point of a batched scan */
+typedef struct twa_point {
+    int64_t N;              /* sites                                               */
+    double  alpha, w;       /* pump matrix of Eq. 2                                */
+    double  Gamma, dt;      /* collective decay, time step                         */
+    int64_t steps;          /* steps to run from the discrete-Wigner start          */
+    double  window_start;   /* averaging window start time (as twa_opts)           */
+} twa_point;
+
+/* Run many parameter points of uneven N together (spec pattern 2, e.g. a
+ * phase-diagram scan) and return each point's observables in out[0..n-1].
+ *
+ * Every point gets its own pump matrix, Cholesky factor and M trajectories (seed
+ * and opts as for twa_init; opts->precision must be TWA_PREC_BF16 or
+ * TWA_PREC_BF16X3, opts->window_start is replaced by each point's). Each step of
+ * all points still running is one grouped persistent launch per kernel class:
+ * the tensor-core tiles of all points form one list, largest problems first,
+ * walked by one CTA per SM; the step is captured once per set of running points
+ * as a CUDA graph and replayed. Points with fewer steps drop out as they finish.
+ * The results equal those of running every point alone with twa_run.
+ *
+ * Tile shapes: unless TWA_TC_BN / TWA_TC_KC are set in the environment, a
+ * built-in autotuner times the compiled configurations on a few steps of the
+ * batch (the state is saved and restored around the trials) and keeps the
+ * fastest. tiles: NULL or int[2] receiving the chosen (BN, K-stage config).
+ * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (FP64 precision), plus those of twa_init
+ * and twa_sync. Synchronises. */
+TWA_API int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,
+                          twa_obs* out, int* tiles);
+
 /* Ensemble reduction alone: observables and standard errors (the same FP64
  * device reduction twa_observables uses) of M caller-supplied per-trajectory
  * window means, `means` a host array [M][5] in the twa_get_moments order. Used

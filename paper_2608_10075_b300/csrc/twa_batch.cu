@@ -1,0 +1,231 @@
+// Batched scans (twa_batch_run): many (N, alpha, w) points advanced together by
+// grouped persistent launches, replayed as CUDA graphs, with tile shapes from a
+// built-in autotuner.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "twa_internal.cuh"
+
+namespace {
+
+// Device copy of a context's trajectories and window sums (autotuning trials
+// advance the state; it is put back afterwards).
+struct Snapshot {
+    float *X = nullptr, *Y = nullptr, *Z = nullptr;
+    double* mom = nullptr;
+    int64_t t = 0, count = 0;
+};
+
+int snapshot(twa_ctx* c, Snapshot& s) {
+    const size_t mn = sizeof(float) * c->M * c->N;
+    if (cudaMalloc(&s.X, mn) != cudaSuccess || cudaMalloc(&s.Y, mn) != cudaSuccess ||
+        cudaMalloc(&s.Z, mn) != cudaSuccess || cudaMalloc(&s.mom, sizeof(double) * 5 * c->M) != cudaSuccess)
+        return twa::set_error(c, TWA_ENOMEM, "batch autotuner: cudaMalloc snapshot");
+    twa::TcState* t = c->tc;
+    TWA_CUDA(c, cudaMemcpyAsync(s.X, t->X, mn, cudaMemcpyDeviceToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(s.Y, t->Y, mn, cudaMemcpyDeviceToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(s.Z, t->Z, mn, cudaMemcpyDeviceToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(s.mom, c->mom, sizeof(double) * 5 * c->M, cudaMemcpyDeviceToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(&s.t, c->d_t, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(&s.count, c->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    TWA_CUDA(c, cudaStreamSynchronize(c->stream));
+    return TWA_OK;
+}
+
+int restore(twa_ctx* c, Snapshot& s) {
+    const size_t mn = sizeof(float) * c->M * c->N;
+    twa::TcState* t = c->tc;
+    TWA_CUDA(c, cudaMemcpyAsync(t->X, s.X, mn, cudaMemcpyDeviceToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(t->Y, s.Y, mn, cudaMemcpyDeviceToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(t->Z, s.Z, mn, cudaMemcpyDeviceToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(c->mom, s.mom, sizeof(double) * 5 * c->M, cudaMemcpyDeviceToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(c->d_t, &s.t, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(c->d_count, &s.count, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    int rc = twa::tc_state_changed(c);   // images and partial sums of the restored state
+    if (rc) return rc;
+    TWA_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(s.X);
+    cudaFree(s.Y);
+    cudaFree(s.Z);
+    cudaFree(s.mom);
+    s = Snapshot();
+    return TWA_OK;
+}
+
+int set_tiles_all(std::vector<twa_ctx*>& ctx, int bn, int kc) {
+    for (twa_ctx* c : ctx) {
+        int rc = twa::tc_set_tiles(c, bn, kc);
+        if (rc) return rc;
+    }
+    return TWA_OK;
+}
+
+// Time `steps` grouped steps of all contexts (ms per step, CUDA events).
+int time_batch(std::vector<twa_ctx*>& ctx, int steps, float* ms) {
+    twa_ctx* lead = ctx[0];
+    twa::TcBatch* b = nullptr;
+    int rc = twa::tc_batch_build(ctx.data(), (int)ctx.size(), lead, &b);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    rc = twa::tc_batch_step(lead, b);   // untimed: first launch of this configuration
+    cudaEventRecord(e0, lead->stream);
+    for (int s = 0; s < steps && !rc; ++s) rc = twa::tc_batch_step(lead, b);
+    cudaEventRecord(e1, lead->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    *ms /= steps;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    twa::tc_batch_free(b);
+    return rc;
+}
+
+// Pick the fastest compiled tile configuration for this batch.
+int autotune(std::vector<twa_ctx*>& ctx, int* bn, int* kc) {
+    const int cand[][2] = {{256, 1}, {192, 1}, {256, 0}, {128, 1}};
+    std::vector<Snapshot> snap(ctx.size());
+    for (size_t p = 0; p < ctx.size(); ++p) {
+        int rc = snapshot(ctx[p], snap[p]);
+        if (rc) return rc;
+    }
+    float best = INFINITY;
+    for (auto& cd : cand) {
+        int rc = set_tiles_all(ctx, cd[0], cd[1]);
+        if (rc) return rc;
+        float ms = 0.f;
+        if ((rc = time_batch(ctx, 3, &ms))) return rc;
+        if (ms < best) {
+            best = ms;
+            *bn = cd[0];
+            *kc = cd[1];
+        }
+    }
+    for (size_t p = 0; p < ctx.size(); ++p) {
+        int rc = restore(ctx[p], snap[p]);
+        if (rc) return rc;
+    }
+    return set_tiles_all(ctx, *bn, *kc);
+}
+
+// Run `reps` steps of the running points as replays of one captured step.
+int run_stage(std::vector<twa_ctx*>& active, int64_t reps, cudaStream_t cap) {
+    twa_ctx* lead = active[0];
+    twa::TcBatch* b = nullptr;
+    int rc = twa::tc_batch_build(active.data(), (int)active.size(), lead, &b);
+    if (rc) return rc;
+    cudaStream_t saved = lead->stream;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    lead->stream = cap;
+    bool graph = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (graph) {
+        rc = twa::tc_batch_step(lead, b);
+        graph = cudaStreamEndCapture(cap, &g) == cudaSuccess && rc == TWA_OK &&
+                cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    }
+    lead->stream = saved;
+    cudaGetLastError();
+    rc = TWA_OK;
+    for (int64_t s = 0; s < reps && rc == TWA_OK; ++s) {
+        if (graph) {
+            if (cudaGraphLaunch(ge, lead->stream) != cudaSuccess) rc = twa::set_error(lead, TWA_ECUDA, "cudaGraphLaunch");
+        } else {
+            rc = twa::tc_batch_step(lead, b);   // capture unavailable: launch directly
+        }
+    }
+    if (cudaStreamSynchronize(lead->stream) != cudaSuccess && rc == TWA_OK)
+        rc = twa::set_error(lead, TWA_ECUDA, "batch stage failed");
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    twa::tc_batch_free(b);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,
+                             twa_obs* out, int* tiles) {
+    using twa::set_error;
+    if (!pts || !out || n < 1 || n > 65536) return set_error(nullptr, TWA_EINVAL, "twa_batch_run: bad points or n");
+    if (M < 1 || M > (int64_t)1 << 30) return set_error(nullptr, TWA_EINVAL, "twa_batch_run: M must be in [1, 2^30]");
+    twa_opts o;
+    twa_opts_default(&o);
+    o.precision = TWA_PREC_BF16X3;
+    if (opts) o = *opts;
+    if (o.precision != TWA_PREC_BF16 && o.precision != TWA_PREC_BF16X3)
+        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: batches run on the BF16 precision paths");
+    o.ws_route = TWA_ROUTE_DENSE;
+    for (int p = 0; p < n; ++p)
+        if (pts[p].steps < 1 || pts[p].steps > 0xFFFFFFFFll)
+            return set_error(nullptr, TWA_EINVAL, "twa_batch_run: every point needs 1 <= steps < 2^32");
+    std::vector<twa_ctx*> ctx(n, nullptr);
+    auto cleanup = [&](int rc) {
+        for (twa_ctx* c : ctx) twa_destroy(c);
+        return rc;
+    };
+    int rc;
+    for (int p = 0; p < n; ++p) {
+        twa_opts op = o;
+        op.window_start = pts[p].window_start;
+        rc = twa_init(&ctx[p], pts[p].N, pts[p].alpha, pts[p].w, pts[p].Gamma, pts[p].dt, seed, &op);
+        if (rc) return cleanup(rc);   // message stays in twa_last_error(NULL)
+        if ((rc = twa_run(ctx[p], M, 0))) {
+            set_error(nullptr, rc, ctx[p]->err);
+            return cleanup(rc);
+        }
+    }
+    twa_ctx* lead = ctx[0];
+    int bn = lead->tc->bn, kc = lead->tc->kc;
+    if (!getenv("TWA_TC_BN") && !getenv("TWA_TC_KC")) {
+        if ((rc = autotune(ctx, &bn, &kc))) {
+            set_error(nullptr, rc, lead->err);
+            return cleanup(rc);
+        }
+    }
+    if (tiles) {
+        tiles[0] = bn;
+        tiles[1] = kc;
+    }
+    // stages: the running set shrinks as points reach their step counts
+    std::vector<int64_t> ends;
+    for (int p = 0; p < n; ++p) ends.push_back(pts[p].steps);
+    std::sort(ends.begin(), ends.end());
+    ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error(nullptr, TWA_ECUDA, "twa_batch_run: cudaStreamCreate");
+        return cleanup(TWA_ECUDA);
+    }
+    int64_t done = 0;
+    for (int64_t end : ends) {
+        std::vector<int> idx;
+        for (int p = 0; p < n; ++p)
+            if (pts[p].steps > done) idx.push_back(p);
+        // largest problems first in the tile list
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return pts[a].N > pts[b].N; });
+        std::vector<twa_ctx*> active;
+        for (int p : idx) active.push_back(ctx[p]);
+        if ((rc = run_stage(active, end - done, cap))) {
+            set_error(nullptr, rc, active[0]->err);
+            cudaStreamDestroy(cap);
+            return cleanup(rc);
+        }
+        done = end;
+    }
+    cudaStreamDestroy(cap);
+    for (int p = 0; p < n; ++p) {
+        ctx[p]->steps = pts[p].steps;
+        if ((rc = twa_observables(ctx[p], &out[p]))) {
+            set_error(nullptr, rc, ctx[p]->err);
+            return cleanup(rc);
+        }
+    }
+    return cleanup(TWA_OK);
+}

@@ -241,6 +241,12 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K);
 // contractions; which: 0 = W, 1 = L (lower), 2, 3 = the extra matrices below.
 int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t K);
 int tc_set_extra_matrix(twa_ctx* c, int slot, const double* A64);   // slot 0 or 1, [N][N] FP64
+// batches of contexts advanced by grouped launches (twa_tc.cu)
+struct TcBatch;
+int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out);
+int tc_batch_step(twa_ctx* lead, TcBatch* b);   // one step of every context: 6 launches
+void tc_batch_free(TcBatch* b);
+int tc_set_tiles(twa_ctx* c, int bn, int kc);
 // twa_fft.cu
 int fft_prepare(twa_ctx* c);                     // plan, twiddles, spectrum of the embedding
 void fft_free(twa_ctx* c);

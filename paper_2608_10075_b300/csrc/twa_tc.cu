@@ -204,8 +204,21 @@ struct TcArgs {
     unsigned long long* flags;
 };
 
+// A batch of problems in one launch: descriptor table (tensor maps in global
+// memory, 64-byte aligned) and the prefix sums of their tile counts.
+struct alignas(64) GroupDesc {
+    TcMaps maps;
+    TcArgs args;
+};
+struct Group {
+    const GroupDesc* desc;
+    const int64_t* start;   // [count + 1]: first flat tile of each problem
+    int count;              // 0: a single problem, given by the launch arguments
+};
+
 template <int MODE, int NT, int BN, int KC>
-__global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMaps maps, const TcArgs args) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMaps maps, const TcArgs args,
+                                                   const Group grp) {
     using G_ = Geo<BN, KC>;
     constexpr int BK = G_::BK, STAGES = G_::STAGES, NTRAJ = G_::NTRAJ;
     extern __shared__ uint8_t smem_raw[];
@@ -220,9 +233,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
     float* red = sS + 2 * NTRAJ * 2;             // [4][NTRAJ][3]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (int)((args.N + BK - 1) / BK);
-    const int64_t n_ct = (args.n_vec + BN - 1) / BN;
-    const int64_t ntiles = args.n_rt * n_ct;
+    // flat tile list: one problem, or the problems of the group one after another
+    const int64_t ntiles = grp.count ? grp.start[grp.count] : args.n_rt * ((args.n_vec + BN - 1) / BN);
+    // problem of flat tile t and the tile's (row tile, trajectory tile) within it
+    auto resolve = [&](int64_t t, const TcMaps*& mp, const TcArgs*& ap, int64_t& rt, int64_t& ct) {
+        int64_t tl = t;
+        if (grp.count == 0) {
+            mp = &maps;
+            ap = &args;
+        } else {
+            int lo = 0, hi = grp.count - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (grp.start[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            mp = &grp.desc[lo].maps;
+            ap = &grp.desc[lo].args;
+            tl = t - grp.start[lo];
+        }
+        const int64_t nct = (ap->n_vec + BN - 1) / BN;
+        rt = tl / nct;
+        ct = tl - rt * nct;
+    };
     // operands: W/L hi (+ lo), B hi (+ lo)
     constexpr int NA = (NT >= 2) ? 2 : 1;
     constexpr int NB = (NT == 3) ? 2 : 1;
@@ -249,7 +282,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    auto k_tiles = [&](int64_t rt) -> int {
+    auto k_tiles = [&](const TcArgs* ap, int64_t rt) -> int {
+        const int nk = (int)((ap->N + BK - 1) / BK);
         if (MODE != MODE_LETA) return nk;
         const int k1 = (int)((rt * BM + BM + BK - 1) / BK);   // L is lower triangular
         return k1 < nk ? k1 : nk;
@@ -266,10 +300,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 last_ph[s] = 0;
             }
             bool ok = true;
+            const TcMaps* prev = nullptr;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int64_t rt = t / n_ct, ct = t - rt * n_ct;
+                const TcMaps* mp;
+                const TcArgs* ap;
+                int64_t rt, ct;
+                resolve(t, mp, ap, rt, ct);
+                if (grp.count && mp != prev) {
+                    // descriptors written to global memory before the launch: make them
+                    // visible to the tensor-map proxy before the first copy through them
+                    const CUtensorMap* ms[4] = {&mp->a0, &mp->a1, &mp->b0, &mp->b1};
+                    for (int k = 0; k < 4; ++k)
+                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ms[k]) : "memory");
+                    prev = mp;
+                }
                 const int y_a = (int)(rt * BM), y_b = (int)(ct * BN);
-                const int nkt = k_tiles(rt);
+                const int nkt = k_tiles(ap, rt);
                 for (int kt = 0; kt < nkt; ++kt) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u, args.flags, true)) {
                         ok = false;
@@ -278,10 +324,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                     mbar_expect_tx(&full[stage], TX);
                     uint8_t* st = tiles + stage * G_::STAGE_BYTES;
                     const int kx = kt * BK;
-                    tma_load(st, &maps.a0, &full[stage], kx, y_a);
-                    if (NA == 2) tma_load(st + G_::A_BYTES, &maps.a1, &full[stage], kx, y_a);
-                    tma_load(st + 2 * G_::A_BYTES, &maps.b0, &full[stage], kx, y_b);
-                    if (NB == 2) tma_load(st + 2 * G_::A_BYTES + G_::B_BYTES, &maps.b1, &full[stage], kx, y_b);
+                    tma_load(st, &mp->a0, &full[stage], kx, y_a);
+                    if (NA == 2) tma_load(st + G_::A_BYTES, &mp->a1, &full[stage], kx, y_a);
+                    tma_load(st + 2 * G_::A_BYTES, &mp->b0, &full[stage], kx, y_b);
+                    if (NB == 2) tma_load(st + 2 * G_::A_BYTES + G_::B_BYTES, &mp->b1, &full[stage], kx, y_b);
                     issued[stage] = true;
                     last_ph[stage] = (int)ph;
                     if (++stage == STAGES) {
@@ -312,7 +358,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 }
                 tc_fence_after();
                 const uint32_t dcol = tmem + (uint32_t)(b * BN);
-                const int nkt = k_tiles(t / n_ct);
+                const TcMaps* mp;
+                const TcArgs* ap;
+                int64_t rt, ct;
+                resolve(t, mp, ap, rt, ct);
+                const int nkt = k_tiles(ap, rt);
                 for (int kt = 0; kt < nkt; ++kt) {
                     if (!mbar_wait(&full[stage], ph, args.flags, true)) {
                         ok = false;
@@ -349,13 +399,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
         // ---------------- epilogue (warps 2..5) ----------------
         const int q = warp & 3;              // TMEM lane quadrant of this warp
         const int et = threadIdx.x - 64;     // 0..127
-        const int64_t M = args.M;
-        const float Gm = args.G, dt = args.dt;
         int it = 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
             const int b = it & 1;
             const uint32_t use = (uint32_t)(it >> 1);
-            const int64_t rt = t / n_ct, ct = t - rt * n_ct;
+            const TcMaps* mp_;
+            const TcArgs* ap_;
+            int64_t rt, ct;
+            resolve(t, mp_, ap_, rt, ct);
+            const TcArgs& args = *ap_;        // this tile's problem (shadows the launch argument)
+            const int64_t M = args.M;
+            const float Gm = args.G, dt = args.dt;
             const int64_t i0 = rt * BM, n0 = ct * BN, m0 = n0 >> 1;
             const int64_t i = i0 + 32 * q + lane;        // site of this thread
             const bool site_ok = i < args.N;
@@ -642,6 +696,81 @@ __global__ void k_close_tc(const float* part, int64_t M, int64_t n_rt, double* m
     }
 }
 
+// ---------------------------------------------------------------------------
+// grouped per-step kernels of a batch of problems
+
+struct StepDesc {
+    __nv_bfloat16* E;
+    float* XI;
+    const float* part;
+    double* mom;
+    int64_t* d_t;
+    int64_t* d_count;
+    int64_t M, N, ldk, n_rt, n_window, m0;
+    uint64_t seed;
+};
+
+__device__ __forceinline__ int find_problem(const int64_t* start, int n, int64_t e) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Noise of every problem's current step (start = prefix of M (N + 1)).
+__global__ void k_noise_group(const StepDesc* sd, const int64_t* start, int n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= start[n]) return;
+    const int p = find_problem(start, n, e);
+    const StepDesc& d = sd[p];
+    const int64_t el = e - start[p], NP = d.N + 1;
+    const int64_t m = el / NP, i = el - m * NP;
+    float gx, gy;
+    normal2_f32(d.seed, (uint32_t)(d.m0 + m), (uint32_t)(*d.d_t), (uint32_t)i, gx, gy);
+    if (i < d.N) {
+        d.E[(2 * m) * d.ldk + i] = __float2bfloat16_rn(gx);
+        d.E[(2 * m + 1) * d.ldk + i] = __float2bfloat16_rn(gy);
+    } else {
+        d.XI[2 * m] = gx;
+        d.XI[2 * m + 1] = gy;
+    }
+}
+
+// Window moments of every problem (start = prefix of M); counters advance later.
+__global__ void k_close_group(const StepDesc* sd, const int64_t* start, int n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= start[n]) return;
+    const int p = find_problem(start, n, e);
+    const StepDesc& d = sd[p];
+    const int64_t m = e - start[p];
+    if (*d.d_t + 1 <= d.n_window) return;
+    double sx = 0, sy = 0, sz = 0;
+    for (int64_t r = 0; r < d.n_rt; ++r) {
+        const float4 v = *(const float4*)(d.part + (r * d.M + m) * 4);
+        sx += v.x;
+        sy += v.y;
+        sz += v.z;
+    }
+    const double A = 0.25 * (sx * sx + sy * sy);
+    double* mm = d.mom + 5 * m;
+    mm[0] += sz;
+    mm[1] += A;
+    mm[2] += A * A;
+    mm[3] += A * sz;
+    mm[4] += sz * sz;
+}
+
+__global__ void k_advance_group(const StepDesc* sd, int n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t t1 = *sd[p].d_t + 1;
+    if (t1 > sd[p].n_window) *sd[p].d_count += 1;
+    *sd[p].d_t = t1;
+}
+
 __global__ void k_f32_to_f64_rows(const float* X, const float* Y, const float* Z, double* x, double* y, double* z,
                                   int64_t n) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -715,7 +844,7 @@ int make_map(twa_ctx* c, CUtensorMap* map, const void* base, int64_t rows, int64
 }
 
 template <int MODE, int NT, int BN, int KC>
-int launch_one(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_tiles) {
+int launch_one(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_tiles, const Group& grp) {
     auto kern = k_tc<MODE, NT, BN, KC>;
     static bool attr = false;
     if (!attr) {
@@ -723,17 +852,19 @@ int launch_one(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_tiles)
         attr = true;
     }
     const int64_t g = n_tiles < c->tc->num_sms ? n_tiles : c->tc->num_sms;
-    kern<<<(unsigned)g, NTHREADS, Geo<BN, KC>::SMEM, c->stream>>>(maps, a);
+    kern<<<(unsigned)g, NTHREADS, Geo<BN, KC>::SMEM, c->stream>>>(maps, a, grp);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }
 
+// One problem (grp.count = 0) or a group of problems in one persistent launch.
 template <int MODE, int NT>
-int launch_cfg(twa_ctx* c, const TcMaps& maps, const TcArgs& a) {
+int launch_cfg(twa_ctx* c, const TcMaps& maps, const TcArgs& a, const Group& grp = Group{nullptr, nullptr, 0},
+               int64_t group_tiles = 0) {
     const int bn = c->tc->bn, kc = c->tc->kc;
-    const int64_t n_tiles = a.n_rt * ((a.n_vec + bn - 1) / bn);
+    const int64_t n_tiles = grp.count ? group_tiles : a.n_rt * ((a.n_vec + bn - 1) / bn);
 #define TWA_TC_CASE(BN_, KC_) \
-    if (bn == BN_ && kc == KC_) return launch_one<MODE, NT, BN_, KC_>(c, maps, a, n_tiles);
+    if (bn == BN_ && kc == KC_) return launch_one<MODE, NT, BN_, KC_>(c, maps, a, n_tiles, grp);
     TWA_TC_CASE(256, 0)
     TWA_TC_CASE(256, 1)
     TWA_TC_CASE(192, 0)
@@ -1055,6 +1186,118 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     cudaFreeAsync(out, c->stream);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches: several contexts advanced together, one launch per kernel class
+
+struct TcBatch {
+    int n = 0;
+    bool x3 = true;
+    int64_t tiles = 0, noise_elems = 0, traj = 0;
+    GroupDesc *lg = nullptr, *pg = nullptr, *cg = nullptr;   // device descriptor tables
+    StepDesc* sd = nullptr;
+    int64_t *tstart = nullptr, *nstart = nullptr, *mstart = nullptr;
+    TcArgs flag_args{};
+};
+
+void tc_batch_free(TcBatch* b) {
+    if (!b) return;
+    void* p[] = {b->lg, b->pg, b->cg, b->sd, b->tstart, b->nstart, b->mstart};
+    for (void* q : p)
+        if (q) cudaFree(q);
+    delete b;
+}
+
+int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
+    *out = nullptr;
+    TcBatch* b = new TcBatch();
+    b->n = n;
+    b->x3 = lead->tc->terms == 3;
+    std::vector<GroupDesc> lg(n), pg(n), cg(n);
+    std::vector<StepDesc> sd(n);
+    std::vector<int64_t> ts(n + 1, 0), ns(n + 1, 0), ms(n + 1, 0);
+    for (int p = 0; p < n; ++p) {
+        twa_ctx* c = ctxs[p];
+        TcState* t = c->tc;
+        if (!t || t->terms != lead->tc->terms || t->bn != lead->tc->bn || t->kc != lead->tc->kc || c->M == 0) {
+            tc_batch_free(b);
+            return set_error(lead, TWA_EINVAL, "batch: contexts differ in precision or tiles, or have no trajectories");
+        }
+        TcArgs la = base_args(c), pa = base_args(c), ca = base_args(c);
+        la.flags = pa.flags = ca.flags = lead->d_flags;
+        la.XI = t->XI; la.oBnx = t->Bx; la.oBny = t->By;
+        pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z; pa.Bnx = t->Bx; pa.Bny = t->By;
+        pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp; pa.oHx = t->Hx; pa.oHy = t->Hy; pa.oHz = t->Hz;
+        pa.oHi = t->Phi; pa.oLo = t->Plo; pa.part_in = t->part; pa.part_out = t->partp;
+        ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp; ca.Hx = t->Hx; ca.Hy = t->Hy; ca.Hz = t->Hz;
+        ca.Bnx = t->Bx; ca.Bny = t->By; ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
+        ca.oHi = t->Shi; ca.oLo = t->Slo; ca.part_in = t->partp; ca.part_out = t->part;
+        lg[p].maps = TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmE};
+        pg[p].maps = TcMaps{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo};
+        cg[p].maps = TcMaps{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo};
+        lg[p].args = la;
+        pg[p].args = pa;
+        cg[p].args = ca;
+        sd[p] = StepDesc{t->E, t->XI, t->part, c->mom, c->d_t, c->d_count, c->M, c->N, t->ldk, t->n_rt,
+                         c->n_window, c->opts.traj_offset, c->seed};
+        ts[p + 1] = ts[p] + t->n_rt * ((2 * c->M + t->bn - 1) / t->bn);
+        ns[p + 1] = ns[p] + c->M * (c->N + 1);
+        ms[p + 1] = ms[p] + c->M;
+    }
+    b->tiles = ts[n];
+    b->noise_elems = ns[n];
+    b->traj = ms[n];
+    b->flag_args = base_args(lead);
+    bool ok = cudaMalloc(&b->lg, sizeof(GroupDesc) * n) == cudaSuccess &&
+              cudaMalloc(&b->pg, sizeof(GroupDesc) * n) == cudaSuccess &&
+              cudaMalloc(&b->cg, sizeof(GroupDesc) * n) == cudaSuccess &&
+              cudaMalloc(&b->sd, sizeof(StepDesc) * n) == cudaSuccess &&
+              cudaMalloc(&b->tstart, sizeof(int64_t) * (n + 1)) == cudaSuccess &&
+              cudaMalloc(&b->nstart, sizeof(int64_t) * (n + 1)) == cudaSuccess &&
+              cudaMalloc(&b->mstart, sizeof(int64_t) * (n + 1)) == cudaSuccess;
+    ok = ok && cudaMemcpy(b->lg, lg.data(), sizeof(GroupDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->pg, pg.data(), sizeof(GroupDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->cg, cg.data(), sizeof(GroupDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->sd, sd.data(), sizeof(StepDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->tstart, ts.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->nstart, ns.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->mstart, ms.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        tc_batch_free(b);
+        return set_error(lead, TWA_ENOMEM, "batch: descriptor upload failed");
+    }
+    *out = b;
+    return TWA_OK;
+}
+
+int tc_batch_step(twa_ctx* lead, TcBatch* b) {
+    const TcMaps none{};
+    int rc;
+    k_noise_group<<<nblk(b->noise_elems, 256), 256, 0, lead->stream>>>(b->sd, b->nstart, b->n);
+    rc = b->x3 ? launch_cfg<MODE_LETA, 2>(lead, none, b->flag_args, Group{b->lg, b->tstart, b->n}, b->tiles)
+               : launch_cfg<MODE_LETA, 1>(lead, none, b->flag_args, Group{b->lg, b->tstart, b->n}, b->tiles);
+    if (rc) return rc;
+    rc = b->x3 ? launch_cfg<MODE_PRED, 3>(lead, none, b->flag_args, Group{b->pg, b->tstart, b->n}, b->tiles)
+               : launch_cfg<MODE_PRED, 1>(lead, none, b->flag_args, Group{b->pg, b->tstart, b->n}, b->tiles);
+    if (rc) return rc;
+    rc = b->x3 ? launch_cfg<MODE_CORR, 3>(lead, none, b->flag_args, Group{b->cg, b->tstart, b->n}, b->tiles)
+               : launch_cfg<MODE_CORR, 1>(lead, none, b->flag_args, Group{b->cg, b->tstart, b->n}, b->tiles);
+    if (rc) return rc;
+    k_close_group<<<nblk(b->traj, 256), 256, 0, lead->stream>>>(b->sd, b->mstart, b->n);
+    k_advance_group<<<nblk(b->n, 128), 128, 0, lead->stream>>>(b->sd, b->n);
+    TWA_CUDA(lead, cudaGetLastError());
+    return TWA_OK;
+}
+
+// Change the tile configuration of a context (re-encodes its tensor maps).
+int tc_set_tiles(twa_ctx* c, int bn, int kc) {
+    TcState* t = c->tc;
+    t->bn = bn;
+    t->kc = kc;
+    int rc = make_matrix_maps(c);
+    if (rc) return rc;
+    return c->M ? make_state_maps(c) : TWA_OK;
 }
 
 }  // namespace twa

@@ -107,27 +107,32 @@ def gradient_study(args):
             fd["d%s_d%s" % (obj, key)] = (vals[0][obj] - vals[1][obj]) / (2 * h)
     out["crn_fd"] = fd
     out["crn_fd_seconds"] = time.perf_counter() - t
-    # the same differences through twa_grad's own forward run (the run the adjoint
-    # differentiates), from the forward means it returns
-    fdt = {}
-    for key, h in (("w", w * d), ("alpha", d)):
-        vals = []
-        for s in (+1, -1):
-            aa = alpha + s * d if key == "alpha" else alpha
-            ww = w * (1 + s * d) if key == "w" else w
-            with twa.TWA(N, aa, ww, G, dt, seed=0, precision="bf16x3", window_start=t0) as g:
-                mu = g.grad("SpSm", M, steps, checkpoint=c["checkpoint"], want_alpha=False)["mu"]
-            Sz, A, A2, ASz, Sz2 = mu
-            spsm = A + 0.5 * Sz
-            vals.append({"SpSm": spsm, "g2": (A2 + 2 * ASz - Sz / 3 + 0.5 * Sz2 - 4.0 / 3.0 * A) / spsm ** 2})
-        for obj in ("SpSm", "g2"):
-            fdt["d%s_d%s" % (obj, key)] = (vals[0][obj] - vals[1][obj]) / (2 * h)
-    out["crn_fd_same_forward"] = fdt
-    out["rel_diff_same_forward"] = {
-        "dSpSm_dw": abs(out["adjoint_SpSm"]["dJ_dw"] - fdt["dSpSm_dw"]) / abs(fdt["dSpSm_dw"]),
-        "dSpSm_dalpha": abs(out["adjoint_SpSm"]["dJ_dalpha"] - fdt["dSpSm_dalpha"]) / abs(fdt["dSpSm_dalpha"]),
-        "dg2_dalpha": abs(out["adjoint_g2"]["dJ_dalpha"] - fdt["dg2_dalpha"]) / abs(fdt["dg2_dalpha"]),
-    }
+    # The same differences through twa_grad's own forward run (the run the adjoint
+    # differentiates), from the forward means it returns. The BF16 hi/lo images of
+    # W and L represent w_ij to ~2^-17 relative, so a parameter step delta moves the
+    # represented matrix by delta plus rounding of that size: differences need
+    # delta >> 2^-17 (1e-3 leaves ~2^-17 / 2e-3 = 0.4 % of rounding in the quotient).
+    for dd in (d, 10 * d):
+        fdt = {}
+        for key, h in (("w", w * dd), ("alpha", dd)):
+            vals = []
+            for s in (+1, -1):
+                aa = alpha + s * dd if key == "alpha" else alpha
+                ww = w * (1 + s * dd) if key == "w" else w
+                with twa.TWA(N, aa, ww, G, dt, seed=0, precision="bf16x3", window_start=t0) as g:
+                    mu = g.grad("SpSm", M, steps, checkpoint=c["checkpoint"], want_alpha=False)["mu"]
+                Sz, A, A2, ASz, Sz2 = mu
+                spsm = A + 0.5 * Sz
+                vals.append({"SpSm": spsm, "g2": (A2 + 2 * ASz - Sz / 3 + 0.5 * Sz2 - 4.0 / 3.0 * A) / spsm ** 2})
+            for obj in ("SpSm", "g2"):
+                fdt["d%s_d%s" % (obj, key)] = (vals[0][obj] - vals[1][obj]) / (2 * h)
+        tag = "delta_%g" % dd
+        out["crn_fd_same_forward_" + tag] = fdt
+        out["rel_diff_same_forward_" + tag] = {
+            "dSpSm_dw": abs(out["adjoint_SpSm"]["dJ_dw"] - fdt["dSpSm_dw"]) / abs(fdt["dSpSm_dw"]),
+            "dSpSm_dalpha": abs(out["adjoint_SpSm"]["dJ_dalpha"] - fdt["dSpSm_dalpha"]) / abs(fdt["dSpSm_dalpha"]),
+            "dg2_dalpha": abs(out["adjoint_g2"]["dJ_dalpha"] - fdt["dg2_dalpha"]) / abs(fdt["dg2_dalpha"]),
+        }
     out["rel_diff"] = {
         "dSpSm_dw": abs(out["adjoint_SpSm"]["dJ_dw"] - fd["dSpSm_dw"]) / abs(fd["dSpSm_dw"]),
         "dSpSm_dalpha": abs(out["adjoint_SpSm"]["dJ_dalpha"] - fd["dSpSm_dalpha"]) / abs(fd["dSpSm_dalpha"]),
@@ -136,9 +141,44 @@ def gradient_study(args):
     print(json.dumps(out), flush=True)
 
 
+def scan_study(args):
+    """The 96-point scan (N in {100, 300, 1000, 3000}, six alpha, four w, M = 512,
+    dt = 0.02 / (N Gamma)) over a shortened horizon T: one batched run against the
+    same points run one after another. Throughput counts N M steps per point."""
+    from .configs import SCAN_POINTS, scan_points
+    pts = scan_points()
+    for p in pts:
+        p["steps"] = max(1, int(round(args.T / p["dt"])))
+        p["window_start"] = 0.5 * p["steps"] * p["dt"]
+    M = SCAN_POINTS["M"]
+    units = sum(p["N"] * M * p["steps"] for p in pts)
+    t = time.perf_counter()
+    res, tiles = twa.batch_run(pts, M, seed=0, precision=args.precision)
+    t_batch = time.perf_counter() - t
+    line = {"study": "scan", "points": len(pts), "M": M, "T": args.T, "precision": args.precision,
+            "spin_traj_steps": units, "batched_seconds": t_batch, "batched_rate": units / t_batch,
+            "tiles": list(tiles), "nonfinite": sum(r["nonfinite"] for r in res)}
+    if args.sequential:
+        t = time.perf_counter()
+        for p in pts:
+            with twa.TWA(p["N"], p["alpha"], p["w"], p["Gamma"], p["dt"], seed=0, precision=args.precision,
+                         window_start=p["window_start"]) as g:
+                g.run(M, p["steps"])
+                g.sync()
+        t_seq = time.perf_counter() - t
+        line.update(sequential_seconds=t_seq, sequential_rate=units / t_seq, batch_speedup=t_seq / t_batch)
+    line["sample"] = [{k: res[i][k] for k in ("sigma_z", "SpSm", "g2", "w_tilde")} | {"N": pts[i]["N"],
+                      "alpha": pts[i]["alpha"], "w": pts[i]["w"]} for i in range(0, len(pts), 23)]
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
+    s = sub.add_parser("scan")
+    s.add_argument("--T", type=float, default=0.02, help="horizon in 1/Gamma (the full scan is T = 1)")
+    s.add_argument("--precision", default="bf16x3")
+    s.add_argument("--sequential", action="store_true", help="also run the points one by one")
     p = sub.add_parser("precision")
     p.add_argument("--M-ref", type=int, default=512)
     p.add_argument("--M-full", type=int, default=MIXED_N1024["M"])
@@ -149,6 +189,8 @@ def main():
     a = ap.parse_args()
     if a.cmd == "precision":
         precision_study(a)
+    elif a.cmd == "scan":
+        scan_study(a)
     else:
         gradient_study(a)
 

@@ -62,6 +62,12 @@ class GradOut(ctypes.Structure):
 
 OBJECTIVE = {"SpSm": 0, "g2": 1}
 
+
+class Point(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("alpha", ctypes.c_double), ("w", ctypes.c_double),
+                ("Gamma", ctypes.c_double), ("dt", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("window_start", ctypes.c_double)]
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -80,6 +86,8 @@ _SIGNATURES = {
     "twa_reduce_moments": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
     "twa_reduce_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
     "twa_grad": (ctypes.c_int, [_P, ctypes.POINTER(GradReq), ctypes.POINTER(GradOut), _P]),
+    "twa_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(Opts),
+                                     _P, _P]),
     "twa_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "twa_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "twa_last_error": (ctypes.c_char_p, [_P]),
@@ -268,6 +276,26 @@ def reduce_moments(means, N):
     if rc != TWA_OK:
         raise TWAError(rc, last_error(None))
     return o.as_dict()
+
+
+def batch_run(points, M, seed=0, precision="bf16x3", stream=None):
+    """twa_batch_run: points = list of dicts with N, alpha, w, Gamma, dt, steps,
+    window_start. Returns (list of observables dicts, (BN, K-stage config))."""
+    arr = (Point * len(points))()
+    for k, p in enumerate(points):
+        arr[k] = Point(int(p["N"]), float(p["alpha"]), float(p["w"]), float(p["Gamma"]), float(p["dt"]),
+                       int(p["steps"]), float(p.get("window_start", 0.0)))
+    o = Opts()
+    lib().twa_opts_default(ctypes.byref(o))
+    o.precision = PRECISION[precision]
+    o.stream = _stream_handle(stream)
+    out = (Obs * len(points))()
+    tiles = (ctypes.c_int * 2)()
+    rc = lib().twa_batch_run(ctypes.cast(arr, ctypes.c_void_p), len(points), int(M), int(seed) & (2 ** 64 - 1),
+                             ctypes.byref(o), ctypes.cast(out, ctypes.c_void_p), ctypes.cast(tiles, ctypes.c_void_p))
+    if rc != TWA_OK:
+        raise TWAError(rc, last_error(None))
+    return [x.as_dict() for x in out], (tiles[0], tiles[1])
 
 
 NOALLOC_MAX_M = 65536

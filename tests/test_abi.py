@@ -29,7 +29,8 @@ def test_binding_signatures_cover_header():
 
 
 @pytest.mark.parametrize("pyclass,ctype", [(twa.Opts, "twa_opts"), (twa.Obs, "twa_obs"),
-                                           (twa.GradReq, "twa_grad_req"), (twa.GradOut, "twa_grad_out")])
+                                           (twa.GradReq, "twa_grad_req"), (twa.GradOut, "twa_grad_out"),
+                                           (twa.Point, "twa_point")])
 def test_struct_layouts_match_header(tmp_path, pyclass, ctype):
     # compile the header with the host C compiler and compare sizes and offsets
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
