@@ -176,9 +176,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": 1e3 * el / max(K, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("M=1024 trajectories/GPU", "M=%d-trajectory sample" % REF_SAMPLE_M)
-                       + " (FP64 CPU oracle)", "N": N, "M": REF_SAMPLE_M, "alpha": CFG["alpha"], "w": CFG["w"],
-                       "dt": CFG["dt"]},
+            "config": {"workload": "TWA stochastic Heun, N=10000 alpha=1 w=5000 Gamma=1 dt=2e-5, "
+                                   "%d-trajectory sample of the M=1024 ensemble, FP64 CPU oracle" % REF_SAMPLE_M,
+                       "N": N, "M": REF_SAMPLE_M, "alpha": CFG["alpha"], "w": CFG["w"], "dt": CFG["dt"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
