@@ -87,13 +87,16 @@ typedef struct twa_opts {
                                offsets and reproduce the unsharded run exactly     */
     int    ws_route;        /* pump field sum_j w_ij s_j: TWA_ROUTE_DENSE (default,
                                any W) or TWA_ROUTE_FFT (uses that Eq. 2 is Toeplitz;
-                               BF16 modes only, 2N - 1 <= 28672)                   */
+                               BF16 modes only, 2N - 1 <= 28000)                   */
 } twa_opts;
 
 #define TWA_ROUTE_DENSE 0   /* tensor-core contraction with the dense W          */
 #define TWA_ROUTE_FFT   1   /* circulant-embedding FFT convolution, FP32         */
 
-/* kernel classes timed by twa_profile_read */
+/* kernel classes timed by twa_profile_read. On the dense mixed-precision
+   route the predictor and corrector launches of step t also carry the L.eta
+   tiles of step t + 1; TWA_PROF_NOISE_FACTOR then counts only the standalone
+   L.eta launch that opens a run (and every step of the FFT route).           */
 #define TWA_PROF_NOISE     0   /* Philox normals of a step                      */
 #define TWA_PROF_PREDICT   1   /* W.s contraction + Heun predictor              */
 #define TWA_PROF_CORRECT   2   /* W.s~ contraction + Heun corrector             */
@@ -295,9 +298,13 @@ TWA_API int twa_reduce_moments_noalloc(const double* means, int64_t M, int64_t N
 TWA_API int twa_profile(twa_ctx* ctx, int enable);
 
 /* Synchronise, then return per kernel class (TWA_PROF_*) the summed event time
- * in ms and the number of launches since profiling started, and clear the
- * record. Both arrays hold TWA_PROF_KINDS entries (either may be NULL). */
-TWA_API int twa_profile_read(twa_ctx* ctx, double* ms, int64_t* launches);
+ * in ms, the number of launches and the summed algorithmic tensor-core FLOPs
+ * of the dense mixed-precision contractions (2 x multiply-adds of the defined
+ * product over its nonzero entries -- all of W, the lower triangle of L --
+ * times the BF16 products per entry; 0 for other classes) since profiling
+ * started, and clear the record. Each array holds TWA_PROF_KINDS entries and
+ * may be NULL. */
+TWA_API int twa_profile_read(twa_ctx* ctx, double* ms, int64_t* launches, double* flops);
 
 /* One-line description of the last error on ctx (or of the last failed
  * twa_init when ctx is NULL). Never NULL. */

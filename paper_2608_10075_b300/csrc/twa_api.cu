@@ -63,11 +63,14 @@ int fix_M(twa_ctx* c, int64_t M) {
     return rc;
 }
 
-int run_eager(twa_ctx* c, int64_t steps) { return use_tc(c) ? twa::tc_run(c, steps) : twa::f64_run(c, steps); }
+int run_eager(twa_ctx* c, int64_t t0, int64_t steps) {
+    return use_tc(c) ? twa::tc_run(c, t0, steps) : twa::f64_run(c, steps);
+}
 
-// Capture one step on a private stream into a CUDA graph. The step's kernels read
-// the step counter from device memory, so the same graph serves every step.
-int capture_step(twa_ctx* c) {
+// Capture step t on a private stream into the graph of its parity. The step's
+// kernels read the step counter from device memory, so one graph serves every
+// step of that parity (the dense mixed-precision step alternates two buffers).
+int capture_step(twa_ctx* c, int64_t t) {
     if (!c->capture_stream) TWA_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
     cudaStream_t saved = c->stream;
     c->stream = c->capture_stream;
@@ -76,12 +79,13 @@ int capture_step(twa_ctx* c) {
     if (cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         rc = TWA_ECUDA;
     } else {
-        rc = run_eager(c, 1);
+        rc = use_tc(c) ? twa::tc_launch_step(c, t) : twa::f64_run(c, 1);
         if (cudaStreamEndCapture(c->capture_stream, &g) != cudaSuccess) rc = TWA_ECUDA;
     }
     c->stream = saved;
-    if (rc == TWA_OK && g && cudaGraphInstantiate(&c->step_graph, g, 0) != cudaSuccess) {
-        c->step_graph = nullptr;
+    cudaGraphExec_t& slot = c->step_graph[t & 1];
+    if (rc == TWA_OK && g && cudaGraphInstantiate(&slot, g, 0) != cudaSuccess) {
+        slot = nullptr;
         rc = TWA_ECUDA;
     }
     if (g) cudaGraphDestroy(g);
@@ -89,20 +93,32 @@ int capture_step(twa_ctx* c) {
     return rc;
 }
 
-// Steps either replay the captured step graph or launch the kernels directly
+void drop_graphs(twa_ctx* c) {
+    for (auto& g : c->step_graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// Steps either replay the captured step graphs or launch the kernels directly
 // (profiling, very short runs, or TWA_NO_GRAPH set).
 int run_steps(twa_ctx* c, int64_t steps) {
-    if (c->profiling || steps < 3 || c->graph_failed || getenv("TWA_NO_GRAPH")) return run_eager(c, steps);
+    int64_t t = c->steps;
+    if (c->profiling || steps < 4 || c->graph_failed || getenv("TWA_NO_GRAPH")) return run_eager(c, t, steps);
     int rc;
-    if (!c->step_graph) {
-        if ((rc = run_eager(c, 1))) return rc;   // first launches set kernel attributes outside any capture
+    if (!c->step_graph[0]) {
+        if ((rc = run_eager(c, t, 1))) return rc;   // first launches set kernel attributes outside any capture
+        ++t;
         --steps;
-        if (capture_step(c) != TWA_OK) {
+        if (capture_step(c, t) != TWA_OK || capture_step(c, t + 1) != TWA_OK) {
+            drop_graphs(c);
             c->graph_failed = true;
-            return run_eager(c, steps);
+            return run_eager(c, t, steps);
         }
     }
-    for (int64_t s = 0; s < steps; ++s) TWA_CUDA(c, cudaGraphLaunch(c->step_graph, c->stream));
+    if (use_tc(c) && (rc = twa::tc_prime(c, t))) return rc;
+    for (int64_t s = 0; s < steps; ++s) TWA_CUDA(c, cudaGraphLaunch(c->step_graph[(t + s) & 1], c->stream));
+    if (use_tc(c)) twa::tc_steps_done(c, t + steps);
     return TWA_OK;
 }
 
@@ -398,10 +414,10 @@ int twa_profile(twa_ctx* c, int enable) {
     return TWA_OK;
 }
 
-int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches) {
+int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches, double* flops) {
     if (!c) return set_error(nullptr, TWA_EINVAL, "twa_profile_read: ctx is NULL");
     TWA_CUDA(c, cudaStreamSynchronize(c->stream));
-    double t[TWA_PROF_KINDS] = {0};
+    double t[TWA_PROF_KINDS] = {0}, f[TWA_PROF_KINDS] = {0};
     int64_t n[TWA_PROF_KINDS] = {0};
     int rc = TWA_OK;
     for (auto& r : c->prof) {
@@ -410,6 +426,7 @@ int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches) {
         if (r.kind >= 0 && r.kind < TWA_PROF_KINDS) {
             t[r.kind] += e;
             n[r.kind] += 1;
+            f[r.kind] += r.flops;
         }
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -418,6 +435,7 @@ int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches) {
     for (int k = 0; k < TWA_PROF_KINDS; ++k) {
         if (ms) ms[k] = t[k];
         if (launches) launches[k] = n[k];
+        if (flops) flops[k] = f[k];
     }
     if (rc) return set_error(c, rc, "twa_profile_read: cudaEventElapsedTime failed");
     return TWA_OK;
@@ -431,7 +449,7 @@ const char* twa_last_error(const twa_ctx* c) {
 void twa_destroy(twa_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    drop_graphs(c);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (auto& r : c->prof) {
         cudaEventDestroy(r.a);

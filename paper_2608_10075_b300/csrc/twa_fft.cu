@@ -7,7 +7,7 @@
 //
 // Since W is real, one complex transform of z = s^x + i s^y gives both
 // components: W z = W s^x + i W s^y. One CTA holds one trajectory's transform in
-// shared memory (P complex FP32 values, P = 2^a 3^b 5^c <= 28672), runs an
+// shared memory (P complex FP32 values, P = 2^a 3^b 5^c <= 28000), runs an
 // in-place mixed-radix decimation-in-frequency FFT whose output is in digit-
 // reversed order, multiplies by lambda stored in that same order, and runs the
 // inverse as decimation in time, which takes digit-reversed input and returns
@@ -22,7 +22,9 @@ namespace twa {
 namespace {
 
 constexpr int FT = 1024;                 // threads per CTA
-constexpr int64_t FFT_MAX_P = 28672;     // P complex FP32 values in shared memory (224 KB)
+constexpr int64_t FFT_MAX_P = 28000;     // P complex FP32 values in shared memory (219 KB)
+constexpr int TW_LO = 128;               // two-level twiddles: w^n = hi[n / 128] lo[n % 128]
+constexpr int64_t TW_HI_MAX = (FFT_MAX_P + TW_LO - 1) / TW_LO;
 
 struct FftArgs {
     int64_t N, M, P;
@@ -102,24 +104,33 @@ __device__ __forceinline__ void dft(float2* a) {
     }
 }
 
+// Twiddles w^n = exp(-2 pi i n / P) from two small shared-memory tables:
+// w^n = hi[n / 128] * lo[n % 128] (one complex product, FP32 accurate).
+struct Tw {
+    const float2* hi;
+    const float2* lo;
+    __device__ __forceinline__ float2 operator[](int64_t n) const { return cmul(hi[n >> 7], lo[n & (TW_LO - 1)]); }
+};
+
 // One stage over butterflies of radix R and stride m (span L = m R): DIF applies
 // the small DFT then the twiddles w_L^{jk}; DIT (inverse) undoes the twiddles,
-// then the inverse DFT. w_L^{jk} = tw[j k P / L] with j k < L, so no reduction.
+// then the inverse DFT. w_L^{jk} = w^{j k P / L} with j k < L, so no reduction.
 template <int R, bool INV>
-__device__ __forceinline__ void stage_r(float2* buf, int64_t P, int64_t m, const float2* __restrict__ tw) {
-    const int64_t L = m * R, step = P / L, nb = P / R;
-    for (int64_t u = threadIdx.x; u < nb; u += FT) {
-        const int64_t b = u / m, j = u - b * m, base = b * L + j;
+__device__ __forceinline__ void stage_r(float2* buf, int64_t P64, int64_t m64, const Tw tw) {
+    // P <= FFT_MAX_P: 32-bit index arithmetic
+    const int P = (int)P64, m = (int)m64, L = m * R, step = P / L, nb = P / R;
+    for (int u = threadIdx.x; u < nb; u += FT) {
+        const int b = u / m, j = u - b * m, base = b * L + j;
         float2 a[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) a[q] = buf[base + q * m];
         if (!INV) {
             dft<R, false>(a);
 #pragma unroll
-            for (int k = 1; k < R; ++k) a[k] = cmul(a[k], __ldg(&tw[j * k * step]));
+            for (int k = 1; k < R; ++k) a[k] = cmul(a[k], tw[j * k * step]);
         } else {
 #pragma unroll
-            for (int k = 1; k < R; ++k) a[k] = cmulc(a[k], __ldg(&tw[j * k * step]));
+            for (int k = 1; k < R; ++k) a[k] = cmulc(a[k], tw[j * k * step]);
             dft<R, true>(a);
         }
 #pragma unroll
@@ -128,7 +139,7 @@ __device__ __forceinline__ void stage_r(float2* buf, int64_t P, int64_t m, const
 }
 
 template <bool INV>
-__device__ __forceinline__ void stage(float2* buf, int64_t P, int r, int64_t m, const float2* tw) {
+__device__ __forceinline__ void stage(float2* buf, int64_t P, int r, int64_t m, const Tw tw) {
     switch (r) {
         case 4: stage_r<4, INV>(buf, P, m, tw); break;
         case 2: stage_r<2, INV>(buf, P, m, tw); break;
@@ -138,11 +149,18 @@ __device__ __forceinline__ void stage(float2* buf, int64_t P, int r, int64_t m, 
 }
 
 // buf <- P * (C buf) for the circulant C with spectrum lam (digit-reversed order).
+// The twiddle tables live in shared memory right after the P values of buf.
 __device__ void circulant_conv(float2* buf, const FftArgs& a) {
+    float2* thi = buf + a.P;
+    float2* tlo = thi + TW_HI_MAX;
+    for (int64_t k = threadIdx.x; k * TW_LO < a.P; k += FT) thi[k] = a.tw[k * TW_LO];
+    for (int j = threadIdx.x; j < TW_LO; j += FT) tlo[j] = (j < a.P) ? a.tw[j] : make_float2(1.f, 0.f);
+    __syncthreads();
+    const Tw tw{thi, tlo};
     int64_t m = a.P;
     for (int s = 0; s < a.nst; ++s) {
         m /= a.radix[s];
-        stage<false>(buf, a.P, a.radix[s], m, a.tw);
+        stage<false>(buf, a.P, a.radix[s], m, tw);
         __syncthreads();
     }
     for (int64_t p = threadIdx.x; p < a.P; p += FT) {
@@ -151,7 +169,7 @@ __device__ void circulant_conv(float2* buf, const FftArgs& a) {
     }
     __syncthreads();
     for (int s = a.nst - 1; s >= 0; --s) {
-        stage<true>(buf, a.P, a.radix[s], m, a.tw);
+        stage<true>(buf, a.P, a.radix[s], m, tw);
         m *= a.radix[s];
         __syncthreads();
     }
@@ -352,9 +370,12 @@ FftArgs base_args(twa_ctx* c) {
     return a;
 }
 
+// shared memory of one FFT CTA: the transform and the two twiddle tables
+size_t smem_bytes(int64_t P) { return sizeof(float2) * (size_t)(P + TW_HI_MAX + TW_LO); }
+
 int set_smem(twa_ctx* c, const void* kern) {
     TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(c->fft->P * sizeof(float2))));
+                                     (int)smem_bytes(c->fft->P)));
     return TWA_OK;
 }
 
@@ -365,7 +386,7 @@ int fft_prepare(twa_ctx* c) {
     while (!smooth(P)) ++P;
     if (P > FFT_MAX_P)
         return set_error(c, TWA_EUNSUPPORTED, "FFT route: transform length " + std::to_string((long long)P) +
-                                                  " does not fit in shared memory (2N - 1 <= 28672 needed)");
+                                                  " does not fit in shared memory (2N - 1 <= 28000 needed)");
     FftPlan* f = new FftPlan();
     c->fft = f;
     f->P = P;
@@ -406,7 +427,7 @@ int fft_predict(twa_ctx* c) {
     a.Bnx = t->Bx; a.Bny = t->By;
     a.oX = t->Xp; a.oY = t->Yp; a.oZ = t->Zp;
     a.oHx = t->Hx; a.oHy = t->Hy; a.oHz = t->Hz;
-    k_fft_pred<<<(unsigned)c->M, FT, c->fft->P * sizeof(float2), c->stream>>>(a);
+    k_fft_pred<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(a);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }
@@ -422,7 +443,7 @@ int fft_correct(twa_ctx* c) {
     a.d_t = c->d_t;
     a.d_count = c->d_count;
     a.n_window = c->n_window;
-    k_fft_corr<<<(unsigned)c->M, FT, c->fft->P * sizeof(float2), c->stream>>>(a);
+    k_fft_corr<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(a);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }
@@ -432,7 +453,7 @@ int fft_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     a.field_in = s;
     a.field_out = P;
     a.K = K;
-    k_fft_field<<<(unsigned)((K + 1) / 2), FT, c->fft->P * sizeof(float2), c->stream>>>(a);
+    k_fft_field<<<(unsigned)((K + 1) / 2), FT, smem_bytes(c->fft->P), c->stream>>>(a);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }

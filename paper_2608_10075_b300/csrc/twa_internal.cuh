@@ -56,6 +56,13 @@ struct TcState {
     int64_t vec_rows = 0;
     __nv_bfloat16 *Vhi = nullptr, *Vlo = nullptr;
     CUtensorMap tmVhi, tmVlo;
+    // dense step: the L.eta tiles of step t + 1 share the predictor's and the
+    // corrector's launches of step t, so the noise part alternates between two
+    // buffers, (Bx, By) for even steps and (Bx1, By1) for odd ones
+    float *Bx1 = nullptr, *By1 = nullptr;
+    int64_t bn_ready = -1;          // step whose noise part is in its buffer (-1: none)
+    bool separate_leta = false;     // run L.eta as a launch of its own each step instead
+    struct MixPlan* mix = nullptr;  // descriptor tables and tile schedules of the two launches
 };
 
 // Circulant-embedding FFT plan of the Toeplitz pump matrix (twa_fft.cu).
@@ -112,7 +119,7 @@ struct twa_ctx {
     twa::FftPlan* fft = nullptr;
 
     // one captured step, replayed by twa_run (no host launch overhead per kernel)
-    cudaGraphExec_t step_graph = nullptr;
+    cudaGraphExec_t step_graph[2] = {nullptr, nullptr};   // captured step, by parity of the step index
     cudaStream_t capture_stream = nullptr;
     bool graph_failed = false;
 
@@ -120,6 +127,7 @@ struct twa_ctx {
     struct ProfRec {
         int kind;
         cudaEvent_t a, b;
+        double flops;   // algorithmic tensor-core FLOPs of the launch (0: none)
     };
     bool profiling = false;
     std::vector<ProfRec> prof;
@@ -130,15 +138,16 @@ namespace twa {
 struct ProfScope {
     twa_ctx* c;
     int kind;
+    double flops;
     cudaEvent_t a = nullptr, b = nullptr;
-    ProfScope(twa_ctx* ctx, int k) : c(ctx), kind(k) {
+    ProfScope(twa_ctx* ctx, int k, double fl = 0.0) : c(ctx), kind(k), flops(fl) {
         if (c->profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
             cudaEventRecord(a, c->stream);
     }
     ~ProfScope() {
         if (c->profiling && a && b) {
             cudaEventRecord(b, c->stream);
-            c->prof.push_back({kind, a, b});
+            c->prof.push_back({kind, a, b, flops});
         }
     }
 };
@@ -232,7 +241,13 @@ int tc_alloc(twa_ctx* c);
 void tc_free_run(twa_ctx* c);                    // trajectory buffers only
 void tc_free(twa_ctx* c);                        // everything, including the images
 int tc_init_state(twa_ctx* c);
-int tc_run(twa_ctx* c, int64_t steps);
+int tc_run(twa_ctx* c, int64_t t0, int64_t steps);   // steps t0 .. t0 + steps - 1, launched directly
+// Graph support: tc_launch_step(c, t) launches step t with no host bookkeeping;
+// on the dense route it needs tc_prime(c, t) first, and tc_steps_done(c, t + n)
+// records after n steps that the noise part of step t + n is in its buffer.
+int tc_prime(twa_ctx* c, int64_t t);
+int tc_launch_step(twa_ctx* c, int64_t t);
+void tc_steps_done(twa_ctx* c, int64_t t_next);
 int tc_state_changed(twa_ctx* c);
 int tc_get_state(twa_ctx* c, double* sx, double* sy, double* sz);   // device buffers
 int tc_set_state(twa_ctx* c, const double* sx, const double* sy, const double* sz);

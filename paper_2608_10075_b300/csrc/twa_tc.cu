@@ -16,18 +16,25 @@
 // in FP32 and rounded to BF16 once, so L.eta needs the two terms of L only.
 //
 // Kernel structure: persistent CTAs (at most one per SM) walk a static list of
-// (row tile, trajectory tile) pairs. Warp 0 streams K tiles through a ring of
+// (row tile, trajectory tile) pairs, strided or from a host-built schedule. Warp 0 streams K tiles through a ring of
 // shared-memory stages with TMA, running ahead across tile boundaries; warp 1
 // issues the MMAs into one of two TMEM accumulators; warps 2-5 run the epilogue
 // of the previous tile from the other accumulator, so epilogue and main loop
 // overlap. Every wait on an mbarrier is bounded in time and reports a timeout.
 //
-// A step is: noise, L.eta (-> noise part of the field increment), W.s with the
-// Heun predictor, W.s~ with the corrector, closing kernel (moments). Collective
-// sums S^a are passed between kernels as per-row-tile partial sums, reduced in
-// a fixed order.
+// A step t is: noise of step t + 1; one launch with the tiles of W.s and the
+// Heun predictor plus part of the L.eta tiles of step t + 1 (-> noise part of
+// its field increment); one launch with W.s~ and the corrector plus the other
+// L.eta tiles; closing kernel (moments). The first step of a run computes its
+// own noise part first. Collective sums S^a are passed between kernels as
+// per-row-tile partial sums, reduced in a fixed order.
 #include <math.h>
 #include <stdlib.h>
+
+#include <algorithm>
+#include <functional>
+#include <queue>
+#include <vector>
 
 #include <cudaTypedefs.h>
 
@@ -41,7 +48,9 @@ constexpr int BM = TC_BM;
 constexpr int NTHREADS = 192;                           // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 
-enum Mode { MODE_FIELD = 0, MODE_LETA = 1, MODE_PRED = 2, MODE_CORR = 3 };
+// MODE_MIX: tiles of several modes in one launch, each problem's mode and term
+// count read from its group descriptor.
+enum Mode { MODE_FIELD = 0, MODE_LETA = 1, MODE_PRED = 2, MODE_CORR = 3, MODE_MIX = 4 };
 
 // K-stage configurations: K tile width, swizzle and ring depth.
 template <int KC>
@@ -206,14 +215,20 @@ struct TcArgs {
 
 // A batch of problems in one launch: descriptor table (tensor maps in global
 // memory, 64-byte aligned) and the prefix sums of their tile counts.
-struct alignas(64) GroupDesc {
+struct GroupDesc {   // 64-byte aligned through its tensor maps
     TcMaps maps;
     TcArgs args;
+    int mode, nt;           // kernel mode and term count of this problem's tiles (MODE_MIX launches)
 };
 struct Group {
     const GroupDesc* desc;
     const int64_t* start;   // [count + 1]: first flat tile of each problem
     int count;              // 0: a single problem, given by the launch arguments
+    // optional explicit schedule: CTA b runs flat tiles sched[sched_start[b] ..
+    // sched_start[b + 1]) in that order (else tiles b, b + grid, b + 2 grid, ...)
+    const int32_t* sched = nullptr;
+    const int32_t* sched_start = nullptr;
+    int ctas = 0;   // grid of a scheduled launch
 };
 
 template <int MODE, int NT, int BN, int KC>
@@ -235,9 +250,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // flat tile list: one problem, or the problems of the group one after another
     const int64_t ntiles = grp.count ? grp.start[grp.count] : args.n_rt * ((args.n_vec + BN - 1) / BN);
-    // problem of flat tile t and the tile's (row tile, trajectory tile) within it
-    auto resolve = [&](int64_t t, const TcMaps*& mp, const TcArgs*& ap, int64_t& rt, int64_t& ct) {
+    // this CTA's tiles: the k-th is tile_of(k), k < n_mine
+    const int64_t n_mine = grp.sched ? (int64_t)(grp.sched_start[blockIdx.x + 1] - grp.sched_start[blockIdx.x])
+                                     : ((int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+    auto tile_of = [&](int64_t k) -> int64_t {
+        return grp.sched ? (int64_t)grp.sched[grp.sched_start[blockIdx.x] + k] : (int64_t)blockIdx.x + k * gridDim.x;
+    };
+    // problem of flat tile t, the tile's (row tile, trajectory tile) within it, and
+    // its mode and term count (the template's, except in MODE_MIX launches)
+    auto resolve = [&](int64_t t, const TcMaps*& mp, const TcArgs*& ap, int64_t& rt, int64_t& ct, int& md,
+                       int& nt) {
         int64_t tl = t;
+        md = MODE;
+        nt = NT;
         if (grp.count == 0) {
             mp = &maps;
             ap = &args;
@@ -251,15 +276,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             mp = &grp.desc[lo].maps;
             ap = &grp.desc[lo].args;
             tl = t - grp.start[lo];
+            if (MODE == MODE_MIX) {
+                md = grp.desc[lo].mode;
+                nt = grp.desc[lo].nt;
+            }
         }
         const int64_t nct = (ap->n_vec + BN - 1) / BN;
         rt = tl / nct;
         ct = tl - rt * nct;
+        // L.eta: row tile r needs 2r + 2 K stages (triangular L); hand out the
+        // longest tiles first so the persistent CTAs finish together
+        if (md == MODE_LETA) rt = ap->n_rt - 1 - rt;
     };
-    // operands: W/L hi (+ lo), B hi (+ lo)
-    constexpr int NA = (NT >= 2) ? 2 : 1;
-    constexpr int NB = (NT == 3) ? 2 : 1;
-    constexpr uint32_t TX = NA * G_::A_BYTES + NB * G_::B_BYTES;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -282,9 +310,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    auto k_tiles = [&](const TcArgs* ap, int64_t rt) -> int {
+    auto k_tiles = [&](const TcArgs* ap, int64_t rt, int md) -> int {
         const int nk = (int)((ap->N + BK - 1) / BK);
-        if (MODE != MODE_LETA) return nk;
+        if (md != MODE_LETA) return nk;
         const int k1 = (int)((rt * BM + BM + BK - 1) / BK);   // L is lower triangular
         return k1 < nk ? k1 : nk;
     };
@@ -301,11 +329,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             }
             bool ok = true;
             const TcMaps* prev = nullptr;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int64_t k = 0; k < n_mine && ok; ++k) {
+                const int64_t t = tile_of(k);
                 const TcMaps* mp;
                 const TcArgs* ap;
                 int64_t rt, ct;
-                resolve(t, mp, ap, rt, ct);
+                int md, nt;
+                resolve(t, mp, ap, rt, ct, md, nt);
+                // operands of this tile: W/L hi (+ lo), B hi (+ lo)
+                const int na = (nt >= 2) ? 2 : 1, nb = (nt == 3) ? 2 : 1;
+                const uint32_t tx = na * G_::A_BYTES + nb * G_::B_BYTES;
                 if (grp.count && mp != prev) {
                     // descriptors written to global memory before the launch: make them
                     // visible to the tensor-map proxy before the first copy through them
@@ -315,19 +348,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                     prev = mp;
                 }
                 const int y_a = (int)(rt * BM), y_b = (int)(ct * BN);
-                const int nkt = k_tiles(ap, rt);
+                const int nkt = k_tiles(ap, rt, md);
                 for (int kt = 0; kt < nkt; ++kt) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u, args.flags, true)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&full[stage], TX);
+                    mbar_expect_tx(&full[stage], tx);
                     uint8_t* st = tiles + stage * G_::STAGE_BYTES;
                     const int kx = kt * BK;
                     tma_load(st, &mp->a0, &full[stage], kx, y_a);
-                    if (NA == 2) tma_load(st + G_::A_BYTES, &mp->a1, &full[stage], kx, y_a);
+                    if (na == 2) tma_load(st + G_::A_BYTES, &mp->a1, &full[stage], kx, y_a);
                     tma_load(st + 2 * G_::A_BYTES, &mp->b0, &full[stage], kx, y_b);
-                    if (NB == 2) tma_load(st + 2 * G_::A_BYTES + G_::B_BYTES, &mp->b1, &full[stage], kx, y_b);
+                    if (nb == 2) tma_load(st + 2 * G_::A_BYTES + G_::B_BYTES, &mp->b1, &full[stage], kx, y_b);
                     issued[stage] = true;
                     last_ph[stage] = (int)ph;
                     if (++stage == STAGES) {
@@ -349,7 +382,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             bool ok = true;
             int it = 0, last_b = -1;
             uint32_t last_par = 0;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+            for (int64_t k = 0; k < n_mine && ok; ++k, ++it) {
+                const int64_t t = tile_of(k);
                 const int b = it & 1;
                 const uint32_t use = (uint32_t)(it >> 1);
                 if (!mbar_wait(&tempty[b], (use & 1u) ^ 1u, args.flags, true)) {
@@ -361,8 +395,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 const TcMaps* mp;
                 const TcArgs* ap;
                 int64_t rt, ct;
-                resolve(t, mp, ap, rt, ct);
-                const int nkt = k_tiles(ap, rt);
+                int md, nt;
+                resolve(t, mp, ap, rt, ct, md, nt);
+                const int nkt = k_tiles(ap, rt, md);
                 for (int kt = 0; kt < nkt; ++kt) {
                     if (!mbar_wait(&full[stage], ph, args.flags, true)) {
                         ok = false;
@@ -376,11 +411,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                         const uint32_t ko = kk * 32;   // 16 BF16 = 32 B along the swizzled row
                         mma_bf16(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b0 + ko), G_::IDESC,
                                  (kt > 0 || kk > 0) ? 1u : 0u);
-                        if (NT == 3) {
+                        if (nt == 3) {
                             mma_bf16(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b1 + ko), G_::IDESC, 1u);
                             mma_bf16(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
                         }
-                        if (NT == 2) mma_bf16(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
+                        if (nt == 2) mma_bf16(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
                     }
                     mma_commit(&empty[stage]);
                     if (++stage == STAGES) {
@@ -400,21 +435,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
         const int q = warp & 3;              // TMEM lane quadrant of this warp
         const int et = threadIdx.x - 64;     // 0..127
         int it = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        for (int64_t k = 0; k < n_mine; ++k, ++it) {
+            const int64_t t = tile_of(k);
             const int b = it & 1;
             const uint32_t use = (uint32_t)(it >> 1);
             const TcMaps* mp_;
             const TcArgs* ap_;
             int64_t rt, ct;
-            resolve(t, mp_, ap_, rt, ct);
+            int md, nt;
+            resolve(t, mp_, ap_, rt, ct, md, nt);
             const TcArgs& args = *ap_;        // this tile's problem (shadows the launch argument)
             const int64_t M = args.M;
-            const float Gm = args.G, dt = args.dt;
+            // every rounding of the epilogue is spelled out (fmaf, __fmul_rn,
+            // __fadd_rn), so that all kernel variants give the same bits
+            const float Gm = args.G, hdt = 0.5f * args.dt;
             const int64_t i0 = rt * BM, n0 = ct * BN, m0 = n0 >> 1;
             const int64_t i = i0 + 32 * q + lane;        // site of this thread
             const bool site_ok = i < args.N;
             epi_sync();                                   // smem of the previous tile is free
-            if (MODE == MODE_PRED || MODE == MODE_CORR) {
+            if (md == MODE_PRED || md == MODE_CORR) {
                 for (int j = et; j < NTRAJ; j += 128) {
                     const int64_t m = m0 + j;
                     float sx = 0.f, sy = 0.f;
@@ -428,7 +467,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                     sS[2 * j] = sx;
                     sS[2 * j + 1] = sy;
                 }
-            } else if (MODE == MODE_LETA) {
+            } else if (md == MODE_LETA) {
                 for (int j = et; j < NTRAJ; j += 128) {
                     const int64_t m = m0 + j;
                     sS[2 * j] = (m < M) ? args.XI[2 * m] : 0.f;
@@ -449,7 +488,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                     float pv[16];
                     tmem_ld16(trow + 16 * c, pv);
                     tmem_ld_wait();
-                    if (MODE == MODE_FIELD) {
+                    if (md == MODE_FIELD) {
                         if (site_ok) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
@@ -459,7 +498,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                         }
                         continue;
                     }
-                    if (MODE == MODE_LETA) {
+                    if (md == MODE_LETA) {
                         // noise part of the field increment: sqrt(G dt) xi^a - sqrt(dt) (L eta^a)_i
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj) {
@@ -467,8 +506,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                             const int64_t m = m0 + jl;
                             if (!site_ok || m >= M) continue;
                             const int64_t e = m * args.N + i;
-                            args.oBnx[e] = args.sgdt * sS[2 * jl] - args.sdt * pv[2 * jj];
-                            args.oBny[e] = args.sgdt * sS[2 * jl + 1] - args.sdt * pv[2 * jj + 1];
+                            args.oBnx[e] = fmaf(-args.sdt, pv[2 * jj], __fmul_rn(args.sgdt, sS[2 * jl]));
+                            args.oBny[e] = fmaf(-args.sdt, pv[2 * jj + 1], __fmul_rn(args.sgdt, sS[2 * jl + 1]));
                         }
                         continue;
                     }
@@ -482,41 +521,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                         const int64_t e = m * args.N + i;
                         const float x = args.X[e], y = args.Y[e], z = args.Z[e];
                         // B^a = 1/2 (G S^a - P^a) dt + noise part
-                        const float Bxv = 0.5f * (Gm * sS[2 * jl] - pv[2 * jj]) * dt + args.Bnx[e];
-                        const float Byv = 0.5f * (Gm * sS[2 * jl + 1] - pv[2 * jj + 1]) * dt + args.Bny[e];
+                        const float Bxv = fmaf(fmaf(Gm, sS[2 * jl], -pv[2 * jj]), hdt, args.Bnx[e]);
+                        const float Byv = fmaf(fmaf(Gm, sS[2 * jl + 1], -pv[2 * jj + 1]), hdt, args.Bny[e]);
                         const int64_t r0 = (2 * m) * args.ldk + i;
-                        if (MODE == MODE_PRED) {
+                        if (md == MODE_PRED) {
                             // f = s x (B^y, -B^x, 0); s~ = s + f; h = s + f/2
-                            const float fx = z * Bxv, fy = z * Byv, fz = -(x * Bxv + y * Byv);
-                            const float xp = x + fx, yp = y + fy, zp = z + fz;
+                            const float fx = __fmul_rn(z, Bxv), fy = __fmul_rn(z, Byv);
+                            const float fz = -fmaf(x, Bxv, __fmul_rn(y, Byv));
+                            const float xp = __fadd_rn(x, fx), yp = __fadd_rn(y, fy), zp = __fadd_rn(z, fz);
                             args.oX[e] = xp;
                             args.oY[e] = yp;
                             args.oZ[e] = zp;
                             args.oHx[e] = fmaf(0.5f, fx, x);
                             args.oHy[e] = fmaf(0.5f, fy, y);
                             args.oHz[e] = fmaf(0.5f, fz, z);
-                            split_store(args.oHi, args.oLo, r0, xp, NT == 3);
-                            split_store(args.oHi, args.oLo, r0 + args.ldk, yp, NT == 3);
+                            split_store(args.oHi, args.oLo, r0, xp, nt == 3);
+                            split_store(args.oHi, args.oLo, r0 + args.ldk, yp, nt == 3);
                             rx[jj] = xp;
                             ry[jj] = yp;
                             rz[jj] = zp;
                         } else {
                             // corrector: s' = h + f(s~)/2, then |s'| = sqrt(3)
-                            float nx = fmaf(0.5f, z * Bxv, args.Hx[e]);
-                            float ny = fmaf(0.5f, z * Byv, args.Hy[e]);
-                            float nz = fmaf(-0.5f, x * Bxv + y * Byv, args.Hz[e]);
+                            float nx = fmaf(0.5f, __fmul_rn(z, Bxv), args.Hx[e]);
+                            float ny = fmaf(0.5f, __fmul_rn(z, Byv), args.Hy[e]);
+                            float nz = fmaf(-0.5f, fmaf(x, Bxv, __fmul_rn(y, Byv)), args.Hz[e]);
                             if (args.renorm) {
-                                const float s = sqrtf(3.0f / (nx * nx + ny * ny + nz * nz));
-                                nx *= s;
-                                ny *= s;
-                                nz *= s;
+                                const float s = sqrtf(3.0f / fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz))));
+                                nx = __fmul_rn(nx, s);
+                                ny = __fmul_rn(ny, s);
+                                nz = __fmul_rn(nz, s);
                             }
                             if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) ++nonfinite;
                             args.oX[e] = nx;
                             args.oY[e] = ny;
                             args.oZ[e] = nz;
-                            split_store(args.oHi, args.oLo, r0, nx, NT == 3);
-                            split_store(args.oHi, args.oLo, r0 + args.ldk, ny, NT == 3);
+                            split_store(args.oHi, args.oLo, r0, nx, nt == 3);
+                            split_store(args.oHi, args.oLo, r0 + args.ldk, ny, nt == 3);
                             rx[jj] = nx;
                             ry[jj] = ny;
                             rz[jj] = nz;
@@ -547,11 +587,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
-            if (MODE == MODE_CORR) {
+            if (md == MODE_CORR) {
                 const unsigned tot = __reduce_add_sync(0xffffffffu, nonfinite);
                 if (lane == 0 && tot) atomicAdd(&args.flags[FLAG_NONFINITE], (unsigned long long)tot);
             }
-            if (MODE == MODE_PRED || MODE == MODE_CORR) {
+            // (md is the same for the four epilogue warps: they walk the same tiles)
+            if (md == MODE_PRED || md == MODE_CORR) {
                 epi_sync();   // every epilogue thread, live or not
                 for (int j = et; j < NTRAJ; j += 128) {
                     const int64_t m = m0 + j;
@@ -641,15 +682,15 @@ __global__ void k_part_tc(const float* X, const float* Y, const float* Z, float*
     if (lane == 0) *(float4*)(part + (r * M + m) * 4) = make_float4(sx, sy, sz, 0.f);
 }
 
-// Noise of step t: eta (FP32 Box-Muller, rounded to BF16) into the B-operand
-// image rows 2m / 2m+1, and the collective pair xi (site index N) into XI.
+// Noise of step t = *d_t + toff: eta (FP32 Box-Muller, rounded to BF16) into the
+// B-operand image rows 2m / 2m+1, and the collective pair xi (site index N) into XI.
 __global__ void k_noise_tc(__nv_bfloat16* E, float* XI, int64_t M, int64_t N, int64_t ldk, uint64_t seed,
-                           const int64_t* d_t, int64_t m0) {
+                           const int64_t* d_t, int64_t toff, int64_t m0) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t NP = N + 1;
     if (e >= M * NP) return;
     const int64_t m = e / NP, i = e - m * NP;
-    const uint32_t t = (uint32_t)(*d_t);
+    const uint32_t t = (uint32_t)(*d_t + toff);
     float gx, gy;
     normal2_f32(seed, (uint32_t)(m0 + m), t, (uint32_t)i, gx, gy);
     if (i < N) {
@@ -851,7 +892,7 @@ int launch_one(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_tiles,
         TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<BN, KC>::SMEM));
         attr = true;
     }
-    const int64_t g = n_tiles < c->tc->num_sms ? n_tiles : c->tc->num_sms;
+    const int64_t g = grp.sched ? grp.ctas : (n_tiles < c->tc->num_sms ? n_tiles : c->tc->num_sms);
     kern<<<(unsigned)g, NTHREADS, Geo<BN, KC>::SMEM, c->stream>>>(maps, a, grp);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
@@ -933,6 +974,9 @@ int tc_prepare(twa_ctx* c) {
     // K stages (SWIZZLE_64B).
     t->bn = env_int("TWA_TC_BN", 256);
     t->kc = env_int("TWA_TC_KC", 1);
+    // TWA_SEPARATE_LETA=1: dense step as separate noise, L.eta, predictor and
+    // corrector launches instead of the two mixed launches (same results)
+    t->separate_leta = env_int("TWA_SEPARATE_LETA", 0) != 0;
     if (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1))
         return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0 or 1");
     int sms = 0;
@@ -969,11 +1013,16 @@ int tc_alloc(twa_ctx* c) {
     return make_state_maps(c);
 }
 
+namespace {
+void mix_free(TcState* t);
+}
+
 void tc_free_run(twa_ctx* c) {
     TcState* t = c->tc;
     if (!t) return;
-    float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Hx, &t->Hy, &t->Hz, &t->Bx, &t->By, &t->XI,
-                   &t->part, &t->partp};
+    mix_free(t);
+    float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Hx, &t->Hy, &t->Hz, &t->Bx, &t->By, &t->Bx1,
+                   &t->By1, &t->XI, &t->part, &t->partp};
     for (auto p : f) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -1047,6 +1096,7 @@ void tc_free(twa_ctx* c) {
 
 int tc_state_changed(twa_ctx* c) {
     TcState* t = c->tc;
+    t->bn_ready = -1;
     const int64_t MN = c->M * c->N;
     k_images_tc<<<nblk(MN, 256), 256, 0, c->stream>>>(t->X, t->Y, t->Shi, t->Slo, c->M, c->N, t->ldk);
     k_part_tc<<<nblk(t->n_rt * c->M, 8), 256, 0, c->stream>>>(t->X, t->Y, t->Z, t->part, c->M, c->N, t->n_rt);
@@ -1056,6 +1106,7 @@ int tc_state_changed(twa_ctx* c) {
 
 int tc_init_state(twa_ctx* c) {
     TcState* t = c->tc;
+    t->bn_ready = -1;
     k_init_tc<<<nblk(c->M * c->N, 256), 256, 0, c->stream>>>(t->X, t->Y, t->Z, t->Shi, t->Slo, c->M, c->N, t->ldk,
                                                             c->seed, (float)c->opts.init_state,
                                                             c->opts.traj_offset);
@@ -1065,78 +1116,325 @@ int tc_init_state(twa_ctx* c) {
     return TWA_OK;
 }
 
-int tc_run(twa_ctx* c, int64_t steps) {
+// ---------------------------------------------------------------------------
+// the dense step as two mixed persistent launches
+
+// Descriptor tables and tile schedules of the dense step. Launch 0 holds the
+// predictor of step t, launch 1 its corrector; each also takes a share of the
+// L.eta tiles of step t + 1 (the noise part depends only on that step's noise),
+// so the triangular L.eta needs no launch of its own and fills the tails of the
+// two W.s launches.
+struct MixPlan {
+    GroupDesc* desc = nullptr;                // [parity of t][launch][W problem, L.eta problem]
+    int64_t* start = nullptr;                 // {0, W tiles, W tiles + L.eta tiles}
+    int32_t* list[2] = {nullptr, nullptr};    // per launch: flat tiles, CTA after CTA
+    int32_t* first[2] = {nullptr, nullptr};   // per launch: [ctas + 1] offsets into list
+    int ctas[2] = {0, 0};
+    int64_t tiles[2] = {0, 0};
+    double flops[2] = {0.0, 0.0};             // algorithmic tensor-core FLOPs per launch
+    double leta_flops = 0.0, w_flops = 0.0;   // of a standalone L.eta or W.s launch
+    std::vector<GroupDesc> host;              // host copy of desc
+};
+
+namespace {
+
+void mix_free(TcState* t) {
+    MixPlan* p = t->mix;
+    if (!p) return;
+    void* q[] = {p->desc, p->start, p->list[0], p->list[1], p->first[0], p->first[1]};
+    for (void* x : q)
+        if (x) cudaFree(x);
+    delete p;
+    t->mix = nullptr;
+    t->bn_ready = -1;
+}
+
+// Longest-processing-time list scheduling: the tiles, longest first, each to
+// the CTA with the least work so far (ties to the lower CTA index); a CTA runs
+// its tiles in the order received. Returns the largest CTA load.
+int64_t lpt_schedule(std::vector<std::pair<int64_t, int32_t>> jobs, int ctas, std::vector<int32_t>* list,
+                     std::vector<int32_t>* first) {
+    std::stable_sort(jobs.begin(), jobs.end(),
+                     [](const std::pair<int64_t, int32_t>& a, const std::pair<int64_t, int32_t>& b) {
+                         return a.first > b.first;
+                     });
+    using Load = std::pair<int64_t, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < ctas; ++b) heap.push({0, b});
+    std::vector<std::vector<int32_t>> per(list ? ctas : 0);
+    for (const auto& j : jobs) {
+        Load l = heap.top();
+        heap.pop();
+        if (list) per[l.second].push_back(j.second);
+        heap.push({l.first + j.first, l.second});
+    }
+    int64_t span = 0;
+    while (!heap.empty()) {
+        span = std::max(span, heap.top().first);
+        heap.pop();
+    }
+    if (list) {
+        list->clear();
+        first->assign(1, 0);
+        for (int b = 0; b < ctas; ++b) {
+            list->insert(list->end(), per[b].begin(), per[b].end());
+            first->push_back((int32_t)list->size());
+        }
+    }
+    return span;
+}
+
+int mix_build(twa_ctx* c) {
     TcState* t = c->tc;
-    const int64_t M = c->M, N = c->N;
-    TcMaps lm{t->tmLhi, t->tmLlo, t->tmE, t->tmE};
-    TcMaps pm{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo};
-    TcMaps cm{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo};
+    const int64_t M = c->M, N = c->N, MN = M * N;
+    const int bn = t->bn, bk = t->kc == 0 ? KCfg<0>::BK : KCfg<1>::BK;
+    const int ntw = t->terms, ntl = t->terms == 3 ? 2 : 1;
+    const int64_t nct = (2 * M + bn - 1) / bn, nk = (N + bk - 1) / bk;
+    const int64_t Tw = t->n_rt * nct, Tl = Tw;
+    if (Tw + Tl > INT32_MAX) return set_error(c, TWA_EUNSUPPORTED, "dense step: too many tiles");
+    if (!t->Bx1 && (cudaMalloc(&t->Bx1, sizeof(float) * MN) != cudaSuccess ||
+                    cudaMalloc(&t->By1, sizeof(float) * MN) != cudaSuccess))
+        return set_error(c, TWA_ENOMEM, "cudaMalloc noise part");
 
+    // tile costs in K stages x products; algorithmic FLOPs per tile
+    auto rows_of = [&](int64_t rt) { return std::min<int64_t>(BM, N - rt * BM); };
+    auto cols_of = [&](int64_t ct) { return (double)std::min<int64_t>(bn, 2 * M - ct * bn); };
+    std::vector<std::pair<int64_t, int32_t>> wjobs, ljobs;
+    std::vector<double> fl(Tw + Tl);
+    for (int64_t x = 0; x < Tw; ++x) {
+        const int64_t rt = x / nct, ct = x - rt * nct;
+        wjobs.push_back({nk * ntw, (int32_t)x});
+        fl[x] = 2.0 * rows_of(rt) * (double)N * cols_of(ct) * ntw;
+    }
+    for (int64_t x = 0; x < Tl; ++x) {
+        const int64_t rt = t->n_rt - 1 - x / nct, ct = x % nct;   // the kernel's L.eta tile order
+        const int64_t k1 = std::min<int64_t>((rt * BM + BM + bk - 1) / bk, nk);
+        ljobs.push_back({k1 * ntl, (int32_t)(Tw + x)});
+        const double r0 = (double)(rt * BM), r1 = r0 + rows_of(rt);
+        fl[Tw + x] = 2.0 * ((r1 * (r1 + 1) - r0 * (r0 + 1)) / 2.0) * cols_of(ct) * ntl;   // lower triangle
+    }
+    std::stable_sort(ljobs.begin(), ljobs.end(),
+                     [](const std::pair<int64_t, int32_t>& a, const std::pair<int64_t, int32_t>& b) {
+                         return a.first > b.first;
+                     });
+    // the predictor's launch takes the kl longest L.eta tiles, the corrector's the rest
+    auto ctas_for = [&](int64_t n) { return (int)std::min<int64_t>(n, t->num_sms); };
+    auto span_of = [&](int64_t kl) {
+        std::vector<std::pair<int64_t, int32_t>> a(wjobs), b(wjobs);
+        a.insert(a.end(), ljobs.begin(), ljobs.begin() + kl);
+        b.insert(b.end(), ljobs.begin() + kl, ljobs.end());
+        return lpt_schedule(a, ctas_for((int64_t)a.size()), nullptr, nullptr) +
+               lpt_schedule(b, ctas_for((int64_t)b.size()), nullptr, nullptr);
+    };
+    const int64_t stride = std::max<int64_t>(1, Tl / 256);
+    int64_t best_k = 0, best = span_of(0);
+    for (int64_t kl = stride; kl <= Tl; kl += stride) {
+        const int64_t s = span_of(kl);
+        if (s < best) best = s, best_k = kl;
+    }
+
+    MixPlan* p = new MixPlan();
+    t->mix = p;
+    std::vector<int32_t> lists[2], firsts[2];
+    std::vector<int> seen(Tw + Tl, 0);
+    for (int L = 0; L < 2; ++L) {
+        std::vector<std::pair<int64_t, int32_t>> jobs(wjobs);
+        if (L == 0) jobs.insert(jobs.end(), ljobs.begin(), ljobs.begin() + best_k);
+        else jobs.insert(jobs.end(), ljobs.begin() + best_k, ljobs.end());
+        p->ctas[L] = ctas_for((int64_t)jobs.size());
+        p->tiles[L] = (int64_t)jobs.size();
+        lpt_schedule(jobs, p->ctas[L], &lists[L], &firsts[L]);
+        for (int32_t x : lists[L]) {
+            p->flops[L] += fl[x];
+            seen[x] += (x < Tw) ? 1 : 2;
+        }
+    }
+    for (int64_t x = Tl; x-- > 0;) p->leta_flops += fl[Tw + x];
+    for (int64_t x = Tw; x-- > 0;) p->w_flops += fl[x];
+    // every W tile in both launches, every L.eta tile in exactly one
+    for (int64_t x = 0; x < Tw + Tl; ++x)
+        if (seen[x] != 2) return set_error(c, TWA_EUNSUPPORTED, "dense step: internal error in the tile schedule");
+
+    // descriptors: [parity][launch][problem]
+    const TcMaps lm{t->tmLhi, t->tmLlo, t->tmE, t->tmE};
+    const TcMaps pm{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo};
+    const TcMaps cm{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo};
+    std::vector<GroupDesc> d(8);
+    for (int par = 0; par < 2; ++par) {
+        float* bx = par ? t->Bx1 : t->Bx;   // noise part of step t (this parity)
+        float* by = par ? t->By1 : t->By;
+        float* nx = par ? t->Bx : t->Bx1;   // ... and of step t + 1
+        float* ny = par ? t->By : t->By1;
+        TcArgs la = base_args(c);
+        la.XI = t->XI;
+        la.oBnx = nx;
+        la.oBny = ny;
+        TcArgs pa = base_args(c);
+        pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z;
+        pa.Bnx = bx; pa.Bny = by;
+        pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
+        pa.oHx = t->Hx; pa.oHy = t->Hy; pa.oHz = t->Hz;
+        pa.oHi = t->Phi; pa.oLo = t->Plo;
+        pa.part_in = t->part; pa.part_out = t->partp;
+        TcArgs ca = base_args(c);
+        ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp;
+        ca.Hx = t->Hx; ca.Hy = t->Hy; ca.Hz = t->Hz;
+        ca.Bnx = bx; ca.Bny = by;
+        ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
+        ca.oHi = t->Shi; ca.oLo = t->Slo;
+        ca.part_in = t->partp; ca.part_out = t->part;
+        GroupDesc* g = &d[4 * par];
+        g[0] = GroupDesc{pm, pa, MODE_PRED, ntw};
+        g[1] = GroupDesc{lm, la, MODE_LETA, ntl};
+        g[2] = GroupDesc{cm, ca, MODE_CORR, ntw};
+        g[3] = GroupDesc{lm, la, MODE_LETA, ntl};
+    }
+    p->host = d;
+    const int64_t st[3] = {0, Tw, Tw + Tl};
+    bool ok = cudaMalloc(&p->desc, sizeof(GroupDesc) * 8) == cudaSuccess &&
+              cudaMalloc(&p->start, sizeof(st)) == cudaSuccess;
+    for (int L = 0; L < 2 && ok; ++L)
+        ok = cudaMalloc(&p->list[L], sizeof(int32_t) * lists[L].size()) == cudaSuccess &&
+             cudaMalloc(&p->first[L], sizeof(int32_t) * firsts[L].size()) == cudaSuccess;
+    if (!ok) return set_error(c, TWA_ENOMEM, "cudaMalloc dense step plan");
+    ok = cudaMemcpy(p->desc, d.data(), sizeof(GroupDesc) * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->start, st, sizeof(st), cudaMemcpyHostToDevice) == cudaSuccess;
+    for (int L = 0; L < 2 && ok; ++L)
+        ok = cudaMemcpy(p->list[L], lists[L].data(), sizeof(int32_t) * lists[L].size(), cudaMemcpyHostToDevice) ==
+                 cudaSuccess &&
+             cudaMemcpy(p->first[L], firsts[L].data(), sizeof(int32_t) * firsts[L].size(),
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) return set_error(c, TWA_ECUDA, "dense step plan upload failed");
+    return TWA_OK;
+}
+
+}  // namespace
+
+static bool tc_mixed_step(const twa_ctx* c) { return c->tc && !c->fft; }
+
+namespace {
+// Noise of step t (= *d_t) and its noise part, by a standalone L.eta launch,
+// into the buffer of the step's parity.
+int noise_part_alone(twa_ctx* c, int64_t t) {
+    TcState* ts = c->tc;
+    {
+        ProfScope p(c, TWA_PROF_NOISE);
+        k_noise_tc<<<nblk(c->M * (c->N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, c->M, c->N, ts->ldk, c->seed,
+                                                                        c->d_t, 0, c->opts.traj_offset);
+    }
     TcArgs la = base_args(c);
-    la.XI = t->XI;
-    la.oBnx = t->Bx;
-    la.oBny = t->By;
+    la.XI = ts->XI;
+    la.oBnx = (t & 1) ? ts->Bx1 : ts->Bx;
+    la.oBny = (t & 1) ? ts->By1 : ts->By;
+    const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmE};
+    ProfScope p(c, TWA_PROF_NOISE_FACTOR, ts->mix->leta_flops);
+    return ts->terms == 3 ? launch_cfg<MODE_LETA, 2>(c, lm, la) : launch_cfg<MODE_LETA, 1>(c, lm, la);
+}
+}  // namespace
 
-    TcArgs pa = base_args(c);
-    pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z;
-    pa.Bnx = t->Bx; pa.Bny = t->By;
-    pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
-    pa.oHx = t->Hx; pa.oHy = t->Hy; pa.oHz = t->Hz;
-    pa.oHi = t->Phi; pa.oLo = t->Plo;
-    pa.part_in = t->part; pa.part_out = t->partp;
+// Noise part of step t into its buffer, unless already there.
+int tc_prime(twa_ctx* c, int64_t t) {
+    TcState* ts = c->tc;
+    if (!tc_mixed_step(c) || ts->separate_leta || ts->bn_ready == t) return TWA_OK;
+    int rc;
+    if (!ts->mix && (rc = mix_build(c))) return rc;
+    if ((rc = noise_part_alone(c, t))) return rc;
+    ts->bn_ready = t;
+    return TWA_OK;
+}
 
-    TcArgs ca = base_args(c);
-    ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp;
-    ca.Hx = t->Hx; ca.Hy = t->Hy; ca.Hz = t->Hz;
-    ca.Bnx = t->Bx; ca.Bny = t->By;
-    ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
-    ca.oHi = t->Shi; ca.oLo = t->Slo;
-    ca.part_in = t->partp; ca.part_out = t->part;
+void tc_steps_done(twa_ctx* c, int64_t t_next) {
+    if (tc_mixed_step(c)) c->tc->bn_ready = t_next;
+}
 
-    const bool x3 = t->terms == 3;
-    for (int64_t s = 0; s < steps; ++s) {
-        int rc;
+// Launches of step t alone, with no host-side bookkeeping (so that they can be
+// captured into a graph). The dense route needs the noise part of step t in its
+// buffer (tc_prime) and leaves that of step t + 1 in the other.
+int tc_launch_step(twa_ctx* c, int64_t t) {
+    TcState* ts = c->tc;
+    const int64_t M = c->M, N = c->N;
+    const bool x3 = ts->terms == 3;
+    int rc;
+    if (c->fft) {
+        // Toeplitz route: W.s by FFT with the Heun update in the same kernel
         {
             ProfScope p(c, TWA_PROF_NOISE);
-            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(t->E, t->XI, M, N, t->ldk, c->seed, c->d_t,
-                                                                     c->opts.traj_offset);
+            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, M, N, ts->ldk, c->seed, c->d_t,
+                                                                     0, c->opts.traj_offset);
         }
+        TcArgs la = base_args(c);
+        la.XI = ts->XI;
+        la.oBnx = ts->Bx;
+        la.oBny = ts->By;
+        const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmE};
         {
             ProfScope p(c, TWA_PROF_NOISE_FACTOR);
             rc = x3 ? launch_cfg<MODE_LETA, 2>(c, lm, la) : launch_cfg<MODE_LETA, 1>(c, lm, la);
         }
         if (rc) return rc;
-        if (c->fft) {
-            // Toeplitz route: W.s by FFT with the Heun update in the same kernel
-            {
-                ProfScope p(c, TWA_PROF_PREDICT);
-                rc = fft_predict(c);
-            }
-            if (rc) return rc;
-            {
-                ProfScope p(c, TWA_PROF_CORRECT);
-                rc = fft_correct(c);
-            }
-            if (rc) return rc;
-            continue;
-        }
         {
             ProfScope p(c, TWA_PROF_PREDICT);
-            rc = x3 ? launch_cfg<MODE_PRED, 3>(c, pm, pa) : launch_cfg<MODE_PRED, 1>(c, pm, pa);
+            rc = fft_predict(c);
         }
         if (rc) return rc;
         {
             ProfScope p(c, TWA_PROF_CORRECT);
-            rc = x3 ? launch_cfg<MODE_CORR, 3>(c, cm, ca) : launch_cfg<MODE_CORR, 1>(c, cm, ca);
+            rc = fft_correct(c);
+        }
+        return rc;
+    }
+    if (!ts->mix && (rc = mix_build(c))) return rc;
+    MixPlan* mp = ts->mix;
+    if (ts->separate_leta) {
+        // the same tiles as four separate launches: noise, L.eta, W.s + predictor,
+        // W.s~ + corrector (bit-identical results)
+        if ((rc = noise_part_alone(c, t))) return rc;
+        const GroupDesc* h = mp->host.data() + 4 * (t & 1);
+        {
+            ProfScope p(c, TWA_PROF_PREDICT, mp->w_flops);
+            rc = x3 ? launch_cfg<MODE_PRED, 3>(c, h[0].maps, h[0].args)
+                    : launch_cfg<MODE_PRED, 1>(c, h[0].maps, h[0].args);
         }
         if (rc) return rc;
         {
-            ProfScope p(c, TWA_PROF_CLOSE);
-            k_close_tc<<<nblk(M, 256), 256, 0, c->stream>>>(t->part, M, t->n_rt, c->mom, c->d_t, c->n_window,
-                                                            c->d_count, c->d_flags);
+            ProfScope p(c, TWA_PROF_CORRECT, mp->w_flops);
+            rc = x3 ? launch_cfg<MODE_CORR, 3>(c, h[2].maps, h[2].args)
+                    : launch_cfg<MODE_CORR, 1>(c, h[2].maps, h[2].args);
+        }
+        if (rc) return rc;
+    } else {
+        {
+            ProfScope p(c, TWA_PROF_NOISE);   // noise of step t + 1 (L.eta tiles below)
+            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, M, N, ts->ldk, c->seed, c->d_t,
+                                                                     1, c->opts.traj_offset);
+        }
+        const TcMaps none{};
+        const TcArgs fa = base_args(c);   // flags of the launch
+        const GroupDesc* dp = mp->desc + 4 * (t & 1);
+        for (int L = 0; L < 2; ++L) {
+            const Group g{dp + 2 * L, mp->start, 2, mp->list[L], mp->first[L], mp->ctas[L]};
+            ProfScope p(c, L == 0 ? TWA_PROF_PREDICT : TWA_PROF_CORRECT, mp->flops[L]);
+            rc = launch_cfg<MODE_MIX, 3>(c, none, fa, g, mp->tiles[L]);
+            if (rc) return rc;
         }
     }
+    {
+        ProfScope p(c, TWA_PROF_CLOSE);
+        k_close_tc<<<nblk(M, 256), 256, 0, c->stream>>>(ts->part, M, ts->n_rt, c->mom, c->d_t, c->n_window,
+                                                        c->d_count, c->d_flags);
+    }
     TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+// Steps t0 .. t0 + steps - 1, launched directly.
+int tc_run(twa_ctx* c, int64_t t0, int64_t steps) {
+    for (int64_t s = 0; s < steps; ++s) {
+        int rc;
+        if ((rc = tc_prime(c, t0 + s))) return rc;
+        if ((rc = tc_launch_step(c, t0 + s))) return rc;
+        tc_steps_done(c, t0 + s + 1);
+    }
     return TWA_OK;
 }
 
@@ -1224,6 +1522,7 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
             tc_batch_free(b);
             return set_error(lead, TWA_EINVAL, "batch: contexts differ in precision or tiles, or have no trajectories");
         }
+        t->bn_ready = -1;   // the batch steps use the noise-part buffer of even steps
         TcArgs la = base_args(c), pa = base_args(c), ca = base_args(c);
         la.flags = pa.flags = ca.flags = lead->d_flags;
         la.XI = t->XI; la.oBnx = t->Bx; la.oBny = t->By;
@@ -1293,6 +1592,11 @@ int tc_batch_step(twa_ctx* lead, TcBatch* b) {
 // Change the tile configuration of a context (re-encodes its tensor maps).
 int tc_set_tiles(twa_ctx* c, int bn, int kc) {
     TcState* t = c->tc;
+    mix_free(t);   // its descriptors and the captured steps hold the old tensor maps
+    for (auto& g : c->step_graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
     t->bn = bn;
     t->kc = kc;
     int rc = make_matrix_maps(c);

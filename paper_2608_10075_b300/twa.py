@@ -89,7 +89,7 @@ _SIGNATURES = {
     "twa_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(Opts),
                                      _P, _P]),
     "twa_profile": (ctypes.c_int, [_P, ctypes.c_int]),
-    "twa_profile_read": (ctypes.c_int, [_P, _P, _P]),
+    "twa_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "twa_last_error": (ctypes.c_char_p, [_P]),
     "twa_destroy": (None, [_P]),
 }
@@ -239,11 +239,13 @@ class TWA:
         self._check(lib().twa_profile(self._h, 1 if enable else 0))
 
     def profile_read(self):
-        """{kind: (total ms, launches)} of the kernels timed since profile()."""
+        """{kind: (total ms, launches, algorithmic tensor FLOPs)} of the kernels
+        timed since profile()."""
         ms = (ctypes.c_double * len(PROF_KINDS))()
         n = (ctypes.c_int64 * len(PROF_KINDS))()
-        self._check(lib().twa_profile_read(self._h, ms, n))
-        return {k: (ms[i], n[i]) for i, k in enumerate(PROF_KINDS)}
+        fl = (ctypes.c_double * len(PROF_KINDS))()
+        self._check(lib().twa_profile_read(self._h, ms, n, fl))
+        return {k: (ms[i], n[i], fl[i]) for i, k in enumerate(PROF_KINDS)}
 
     def close(self):
         if getattr(self, "_h", None):
