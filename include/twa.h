@@ -87,11 +87,27 @@ typedef struct twa_opts {
                                offsets and reproduce the unsharded run exactly     */
     int    ws_route;        /* pump field sum_j w_ij s_j: TWA_ROUTE_DENSE (default,
                                any W) or TWA_ROUTE_FFT (uses that Eq. 2 is Toeplitz;
-                               BF16 modes only, 2N - 1 <= 28000)                   */
+                               BF16 modes only, 2N - 2 <= 28000)                   */
+    int    noise_route;     /* draw of the pump noise chi (covariance w_ij dt, Sec. S1):
+                               TWA_NOISE_CHOLESKY (default: chi = L eta) or
+                               TWA_NOISE_CIRCULANT (FFT of the circulant embedding;
+                               needs ws_route = TWA_ROUTE_FFT). The two draws have the
+                               same law and different per-trajectory values.       */
 } twa_opts;
 
 #define TWA_ROUTE_DENSE 0   /* tensor-core contraction with the dense W          */
 #define TWA_ROUTE_FFT   1   /* circulant-embedding FFT convolution, FP32         */
+
+/* Pump-noise draws. Circulant: on a circle of even length P >= 2N - 2 (the
+   smallest 2^a 3^b 5^c), c_d = w / (1 + min(d, P - d))^alpha is the first row
+   of a circulant whose leading N x N block is W and whose eigenvalues lam_k
+   are >= 0 (the sequence is convex and decreasing on 0..P/2: Dietrich-Newsam).
+   With (a_k, b_k) the Box-Muller pair of Philox counter (m, t, k, stream 2),
+   Y_j = sum_k sqrt(lam_k / P) (a_k + i b_k) exp(+2 pi i j k / P), and
+   chi^x_j = Re Y_j, chi^y_j = Im Y_j for j < N: one FP32 transform per
+   trajectory and step instead of the L.eta contraction.                    */
+#define TWA_NOISE_CHOLESKY  0
+#define TWA_NOISE_CIRCULANT 1
 
 /* kernel classes timed by twa_profile_read. On the dense mixed-precision
    route the predictor and corrector launches of step t also carry the L.eta
@@ -223,8 +239,9 @@ typedef struct twa_grad_out {
  * contribution to (dJ/dw, dJ/dalpha); their mean is the returned derivative and
  * their standard deviation / sqrt(M) the returned SE. Synchronises.
  * Errors: TWA_EINVAL (NULL, M < 1, steps < 1), TWA_ESTATE (no step inside the
- * window), TWA_EUNSUPPORTED (want_alpha with alpha = 0 or inf, w = 0),
- * TWA_ENOMEM, TWA_ECUDA, TWA_ENONFINITE. */
+ * window), TWA_EUNSUPPORTED (want_alpha with alpha = 0 or inf, w = 0, a
+ * context with noise_route = TWA_NOISE_CIRCULANT), TWA_ENOMEM, TWA_ECUDA,
+ * TWA_ENONFINITE. */
 TWA_API int twa_grad(twa_ctx* ctx, const twa_grad_req* req, twa_grad_out* out, double* per_traj);
 
 /* one point of a batched scan */
@@ -241,7 +258,8 @@ typedef struct twa_point {
  *
  * Every point gets its own pump matrix, Cholesky factor and M trajectories (seed
  * and opts as for twa_init; opts->precision must be TWA_PREC_BF16 or
- * TWA_PREC_BF16X3, opts->window_start is replaced by each point's). Each step of
+ * TWA_PREC_BF16X3, opts->window_start is replaced by each point's, and every
+ * point runs the dense route with the Cholesky noise draw). Each step of
  * all points still running is one grouped persistent launch per kernel class:
  * the tensor-core tiles of all points form one list, largest problems first,
  * walked by one CTA per SM; the step is captured once per set of running points

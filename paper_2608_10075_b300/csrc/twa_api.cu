@@ -177,6 +177,10 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         return set_error(nullptr, TWA_EINVAL, "twa_init: ws_route must be TWA_ROUTE_DENSE or TWA_ROUTE_FFT");
     if (o.ws_route == TWA_ROUTE_FFT && o.precision == TWA_PREC_FP64)
         return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the FFT route runs with the BF16 precisions only");
+    if (o.noise_route != TWA_NOISE_CHOLESKY && o.noise_route != TWA_NOISE_CIRCULANT)
+        return set_error(nullptr, TWA_EINVAL, "twa_init: noise_route must be TWA_NOISE_CHOLESKY or TWA_NOISE_CIRCULANT");
+    if (o.noise_route == TWA_NOISE_CIRCULANT && o.ws_route != TWA_ROUTE_FFT)
+        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the circulant noise draw needs ws_route = TWA_ROUTE_FFT");
 
     twa_ctx* c = new (std::nothrow) twa_ctx();
     if (!c) return set_error(nullptr, TWA_ENOMEM, "twa_init: host allocation failed");
@@ -373,6 +377,8 @@ int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
     if (c->opts.traj_offset + r->M - 1 > MAX_COUNTER)
         return set_error(c, TWA_EINVAL, "twa_grad: traj_offset + M exceeds the 32-bit trajectory counter");
     if (!(c->w > 0.0)) return set_error(c, TWA_EUNSUPPORTED, "twa_grad: needs w > 0");
+    if (c->opts.noise_route != TWA_NOISE_CHOLESKY)
+        return set_error(c, TWA_EUNSUPPORTED, "twa_grad: differentiates the Cholesky noise draw only");
     if (r->want_alpha && (c->alpha == 0.0 || isinf(c->alpha)))
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: d/dalpha needs 0 < alpha < inf");
     memset(out, 0, sizeof(*out));

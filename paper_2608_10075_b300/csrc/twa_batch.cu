@@ -162,6 +162,7 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
     if (o.precision != TWA_PREC_BF16 && o.precision != TWA_PREC_BF16X3)
         return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: batches run on the BF16 precision paths");
     o.ws_route = TWA_ROUTE_DENSE;
+    o.noise_route = TWA_NOISE_CHOLESKY;
     for (int p = 0; p < n; ++p)
         if (pts[p].steps < 1 || pts[p].steps > 0xFFFFFFFFll)
             return set_error(nullptr, TWA_EINVAL, "twa_batch_run: every point needs 1 <= steps < 2^32");

@@ -1,9 +1,14 @@
 // Toeplitz route for the pump field of Eq. S1. The pump matrix of Eq. 2 depends
 // only on |i - j|, so sum_j w_ij s_j is a linear convolution of s with
-// c_d = w / (1 + d)^alpha. Embedding W in a circulant matrix of size P >= 2N - 1
-// (first column c_0, c_1, .., c_{N-1}, 0 .., 0, c_{N-1}, .., c_1) turns it into
-// a cyclic convolution: W s = first N entries of IFFT(lambda . FFT(s, zero padded)),
-// lambda = FFT of that column (real, because the column is symmetric).
+// c_d = w / (1 + d)^alpha. On a circle of even length P >= 2N - 2 the sequence
+// c_{min(d, P-d)}, d < P, is the first column of a symmetric circulant C whose
+// leading N x N block is W (every |i - j| < N is at most P / 2), so
+// W s = first N entries of IFFT(lambda . FFT(s, zero padded)), lambda = FFT of
+// that column (real, because the column is symmetric). The sequence is convex
+// and decreasing on 0..P/2, so lambda >= 0 (Dietrich-Newsam) and the same C
+// also draws the pump noise: with Z_k complex standard normal (Philox stream 2),
+// Y = IFFT-direction sum of sqrt(lambda_k / P) Z_k has Re Y and Im Y independent
+// with covariance C, i.e. chi^x and chi^y with covariance W on the first N sites.
 //
 // Since W is real, one complex transform of z = s^x + i s^y gives both
 // components: W z = W s^x + i W s^y. One CTA holds one trajectory's transform in
@@ -148,15 +153,30 @@ __device__ __forceinline__ void stage(float2* buf, int64_t P, int r, int64_t m, 
     }
 }
 
-// buf <- P * (C buf) for the circulant C with spectrum lam (digit-reversed order).
-// The twiddle tables live in shared memory right after the P values of buf.
-__device__ void circulant_conv(float2* buf, const FftArgs& a) {
+// Twiddle tables into shared memory right after the P values of buf.
+__device__ Tw load_twiddles(float2* buf, const FftArgs& a) {
     float2* thi = buf + a.P;
     float2* tlo = thi + TW_HI_MAX;
     for (int64_t k = threadIdx.x; k * TW_LO < a.P; k += FT) thi[k] = a.tw[k * TW_LO];
     for (int j = threadIdx.x; j < TW_LO; j += FT) tlo[j] = (j < a.P) ? a.tw[j] : make_float2(1.f, 0.f);
+    return Tw{thi, tlo};
+}
+
+// Unnormalised inverse transform, digit-reversed input -> natural order:
+// buf_j <- sum_k in_k exp(+2 pi i j k / P), in_k held at the position of k.
+__device__ void inverse_dit(float2* buf, const FftArgs& a, const Tw tw) {
+    int64_t m = 1;
+    for (int s = a.nst - 1; s >= 0; --s) {
+        stage<true>(buf, a.P, a.radix[s], m, tw);
+        m *= a.radix[s];
+        __syncthreads();
+    }
+}
+
+// buf <- P * (C buf) for the circulant C with spectrum lam (digit-reversed order).
+__device__ void circulant_conv(float2* buf, const FftArgs& a) {
+    const Tw tw = load_twiddles(buf, a);
     __syncthreads();
-    const Tw tw{thi, tlo};
     int64_t m = a.P;
     for (int s = 0; s < a.nst; ++s) {
         m /= a.radix[s];
@@ -168,11 +188,7 @@ __device__ void circulant_conv(float2* buf, const FftArgs& a) {
         buf[p] = make_float2(buf[p].x * l, buf[p].y * l);
     }
     __syncthreads();
-    for (int s = a.nst - 1; s >= 0; --s) {
-        stage<true>(buf, a.P, a.radix[s], m, tw);
-        m *= a.radix[s];
-        __syncthreads();
-    }
+    inverse_dit(buf, a, tw);
 }
 
 // Sum of v over the block (all threads receive it). `scratch` holds 32 floats.
@@ -288,6 +304,37 @@ __global__ void __launch_bounds__(FT, 1) k_fft_corr(const FftArgs a) {
     }
 }
 
+// Circulant draw of the pump noise of step t = *d_t for trajectory m: position p
+// of the inverse transform's input holds sqrt(lam_k / P) (a_k + i b_k), k its
+// frequency, (a_k, b_k) the FP32 Box-Muller pair of Philox counter (m, t, k, 2);
+// the transform returns Y_j in natural order, chi^x_j = Re Y_j, chi^y_j = Im Y_j.
+// Writes the noise part of the field increment, sqrt(G dt) xi^a - sqrt(dt) chi^a_j,
+// xi^a the collective normals of counter (m, t, N, 0).
+__global__ void __launch_bounds__(FT, 1) k_fft_noise(const FftArgs a, const float* nscale, const int32_t* nfreq,
+                                                     uint64_t seed, int64_t m0, float sgdt, float sdt, float* Bnx,
+                                                     float* Bny) {
+    extern __shared__ float2 buf[];
+    const int64_t m = blockIdx.x, off = m * a.N;
+    const uint32_t t = (uint32_t)(*a.d_t), mg = (uint32_t)(m0 + m);
+    const Tw tw = load_twiddles(buf, a);
+    for (int64_t p = threadIdx.x; p < a.P; p += FT) {
+        float ga, gb;
+        normal2_f32(seed, mg, t, (uint32_t)__ldg(&nfreq[p]), ga, gb, STREAM_CIRCULANT);
+        const float sc = __ldg(&nscale[p]);
+        buf[p] = make_float2(__fmul_rn(sc, ga), __fmul_rn(sc, gb));
+    }
+    float xi_x, xi_y;
+    normal2_f32(seed, mg, t, (uint32_t)a.N, xi_x, xi_y);
+    const float nx0 = __fmul_rn(sgdt, xi_x), ny0 = __fmul_rn(sgdt, xi_y);
+    __syncthreads();
+    inverse_dit(buf, a, tw);
+    for (int64_t j = threadIdx.x; j < a.N; j += FT) {
+        const float2 y = buf[j];
+        Bnx[off + j] = fmaf(-sdt, y.x, nx0);
+        Bny[off + j] = fmaf(-sdt, y.y, ny0);
+    }
+}
+
 // W s for caller vectors: vectors 2b and 2b+1 share one complex transform.
 __global__ void __launch_bounds__(FT, 1) k_fft_field(const FftArgs a) {
     extern __shared__ float2 buf[];
@@ -323,10 +370,23 @@ struct RadixPlan {
     int radix[40];
 };
 
-// Spectrum of the circulant embedding, lam_k = c_0 + 2 sum_{d=1}^{N-1} c_d cos(2 pi k d / P)
-// with c_d = W[0][d], written at the DIF output position p of frequency k (mixed-
-// radix digit reversal). FP64 sum of FP32 cosines of exactly reduced arguments.
-__global__ void k_fft_lambda(float* lam, const double* W, int64_t N, int64_t P, const RadixPlan plan) {
+// First column of the embedding on the circle of length P, for d <= P / 2:
+// c_d = w / (1 + d)^alpha (the expression of the pump-matrix kernel).
+__global__ void k_fft_sequence(double* cseq, int64_t P, double alpha, double w) {
+    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d > P / 2) return;
+    double v;
+    if (isinf(alpha)) v = (d == 0) ? w : 0.0;
+    else if (alpha == 0.0) v = w;
+    else v = w / pow((double)(d + 1), alpha);
+    cseq[d] = v;
+}
+
+// Spectrum lam_k = c_0 + 2 sum_{0<d<P/2} c_d cos(2 pi k d / P) + c_{P/2} (-1)^k
+// in FP64, written at the DIF output position p of frequency k (mixed-radix
+// digit reversal), with the noise-draw scale sqrt(max(lam_k, 0) / P) and k.
+__global__ void k_fft_lambda(float* lam, float* nscale, int32_t* nfreq, const double* cseq, int64_t P,
+                             const RadixPlan plan) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= P) return;
     int64_t rem = p, span = P, k = 0, weight = 1;
@@ -337,14 +397,17 @@ __global__ void k_fft_lambda(float* lam, const double* W, int64_t N, int64_t P, 
         k += ks * weight;
         weight *= plan.radix[s];
     }
-    double acc = W[0];
+    const int64_t h = P / 2;
+    double acc = cseq[0] + ((k & 1) ? -cseq[h] : cseq[h]);
     int64_t r = 0;   // k d mod P, advanced by k each term (k < P)
-    for (int64_t d = 1; d < N; ++d) {
+    for (int64_t d = 1; d < h; ++d) {
         r += k;
         if (r >= P) r -= P;
-        acc += 2.0 * W[d] * (double)cospif(2.0f * (float)r / (float)P);
+        acc += 2.0 * cseq[d] * cospi(2.0 * (double)r / (double)P);
     }
     lam[p] = (float)acc;
+    nscale[p] = (float)sqrt(fmax(acc, 0.0) / (double)P);
+    nfreq[p] = (int32_t)k;
 }
 
 bool smooth(int64_t v) {
@@ -382,11 +445,11 @@ int set_smem(twa_ctx* c, const void* kern) {
 }  // namespace
 
 int fft_prepare(twa_ctx* c) {
-    int64_t P = 2 * c->N - 1;
-    while (!smooth(P)) ++P;
+    int64_t P = 2 * c->N - 2 > 2 ? 2 * c->N - 2 : 2;
+    while (P % 2 || !smooth(P)) ++P;
     if (P > FFT_MAX_P)
         return set_error(c, TWA_EUNSUPPORTED, "FFT route: transform length " + std::to_string((long long)P) +
-                                                  " does not fit in shared memory (2N - 1 <= 28000 needed)");
+                                                  " does not fit in shared memory (2N - 2 <= 28000 needed)");
     FftPlan* f = new FftPlan();
     c->fft = f;
     f->P = P;
@@ -396,26 +459,33 @@ int fft_prepare(twa_ctx* c) {
     while (v % 2 == 0) { f->radix[f->nst++] = 2; v /= 2; }
     while (v % 3 == 0) { f->radix[f->nst++] = 3; v /= 3; }
     while (v % 5 == 0) { f->radix[f->nst++] = 5; v /= 5; }
-    if (cudaMalloc(&f->lam, sizeof(float) * P) != cudaSuccess || cudaMalloc(&f->tw, sizeof(float2) * P) != cudaSuccess)
+    double* cseq = nullptr;
+    if (cudaMalloc(&f->lam, sizeof(float) * P) != cudaSuccess || cudaMalloc(&f->tw, sizeof(float2) * P) != cudaSuccess ||
+        cudaMalloc(&f->nscale, sizeof(float) * P) != cudaSuccess ||
+        cudaMalloc(&f->nfreq, sizeof(int32_t) * P) != cudaSuccess ||
+        cudaMallocAsync(&cseq, sizeof(double) * (P / 2 + 1), c->stream) != cudaSuccess)
         return set_error(c, TWA_ENOMEM, "cudaMalloc FFT plan");
     RadixPlan rp{};
     rp.nst = f->nst;
     for (int s = 0; s < f->nst; ++s) rp.radix[s] = f->radix[s];
     const unsigned g = (unsigned)((P + 255) / 256);
     k_fft_twiddles<<<g, 256, 0, c->stream>>>(f->tw, P);
-    k_fft_lambda<<<g, 256, 0, c->stream>>>(f->lam, c->W64, c->N, P, rp);
+    k_fft_sequence<<<(unsigned)((P / 2 + 256) / 256), 256, 0, c->stream>>>(cseq, P, c->alpha, c->w);
+    k_fft_lambda<<<g, 256, 0, c->stream>>>(f->lam, f->nscale, f->nfreq, cseq, P, rp);
     TWA_CUDA(c, cudaGetLastError());
+    TWA_CUDA(c, cudaFreeAsync(cseq, c->stream));
     int rc;
     if ((rc = set_smem(c, (const void*)k_fft_pred)) || (rc = set_smem(c, (const void*)k_fft_corr)) ||
-        (rc = set_smem(c, (const void*)k_fft_field)))
+        (rc = set_smem(c, (const void*)k_fft_field)) || (rc = set_smem(c, (const void*)k_fft_noise)))
         return rc;
     return TWA_OK;
 }
 
 void fft_free(twa_ctx* c) {
     if (!c->fft) return;
-    if (c->fft->lam) cudaFree(c->fft->lam);
-    if (c->fft->tw) cudaFree(c->fft->tw);
+    void* p[] = {c->fft->lam, c->fft->tw, c->fft->nscale, c->fft->nfreq};
+    for (void* q : p)
+        if (q) cudaFree(q);
     delete c->fft;
     c->fft = nullptr;
 }
@@ -444,6 +514,17 @@ int fft_correct(twa_ctx* c) {
     a.d_count = c->d_count;
     a.n_window = c->n_window;
     k_fft_corr<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(a);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
+int fft_noise(twa_ctx* c) {
+    TcState* t = c->tc;
+    FftArgs a = base_args(c);
+    a.d_t = c->d_t;
+    k_fft_noise<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(
+        a, c->fft->nscale, c->fft->nfreq, c->seed, c->opts.traj_offset, (float)sqrt(c->Gamma * c->dt),
+        (float)sqrt(c->dt), t->Bx, t->By);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }

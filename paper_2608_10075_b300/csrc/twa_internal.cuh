@@ -67,11 +67,14 @@ struct TcState {
 
 // Circulant-embedding FFT plan of the Toeplitz pump matrix (twa_fft.cu).
 struct FftPlan {
-    int64_t P = 0;               // transform length, P >= 2N - 1, P = 2^a 3^b 5^c
+    int64_t P = 0;               // transform length: smallest even 2^a 3^b 5^c >= max(2, 2N - 2)
     int nst = 0;                 // number of stages
     int radix[40] = {0};         // radix of each stage (DIF order)
     float* lam = nullptr;        // spectrum of the embedding, in the DIF output order
     float2* tw = nullptr;        // exp(-2 pi i n / P), n < P
+    // circulant noise draw, in the same (digit-reversed) order as lam
+    float* nscale = nullptr;     // sqrt(max(lam_k, 0) / P)
+    int32_t* nfreq = nullptr;    // frequency k held at each position
 };
 
 }  // namespace twa
@@ -183,6 +186,7 @@ __host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_
 // Pump/collective noise stream 0 and initial-sign stream 1 (see twa.h).
 constexpr uint32_t STREAM_NOISE = 0;
 constexpr uint32_t STREAM_INIT = 1;
+constexpr uint32_t STREAM_CIRCULANT = 2;   // circulant noise draw: counter (m, t, frequency k, 2)
 
 // Two FP64 standard normals from one Philox call: 53-bit uniforms
 // u = (k + 1/2) 2^-53 from words (0,1) and (2,3), then Box-Muller.
@@ -203,8 +207,8 @@ __device__ __forceinline__ void normal2_f64(uint64_t seed, uint32_t m, uint32_t 
 // FP32 variant from the same Philox words (words 0 and 2 as 32-bit uniforms in
 // (0, 1]); used by the mixed-precision path, whose noise is rounded to BF16.
 __device__ __forceinline__ void normal2_f32(uint64_t seed, uint32_t m, uint32_t t, uint32_t i,
-                                            float& gx, float& gy) {
-    const uint4 r = philox10(make_uint4(m, t, i, STREAM_NOISE), (uint32_t)seed, (uint32_t)(seed >> 32));
+                                            float& gx, float& gy, uint32_t stream = STREAM_NOISE) {
+    const uint4 r = philox10(make_uint4(m, t, i, stream), (uint32_t)seed, (uint32_t)(seed >> 32));
     const float u1 = fmaf((float)r.x, 0x1p-32f, 0x1p-33f);
     const float u2 = fmaf((float)r.z, 0x1p-32f, 0x1p-33f);
     const float rad = sqrtf(-2.0f * logf(u1));
@@ -267,6 +271,7 @@ int fft_prepare(twa_ctx* c);                     // plan, twiddles, spectrum of 
 void fft_free(twa_ctx* c);
 int fft_predict(twa_ctx* c);                     // W.s by FFT + Heun predictor (one step)
 int fft_correct(twa_ctx* c);                     // W.s~ by FFT + corrector + moments (one step)
+int fft_noise(twa_ctx* c);                       // circulant noise draw -> noise part (one step)
 int fft_field(twa_ctx* c, const double* s, double* P, int64_t K);
 // twa_adjoint.cu
 int grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_traj);

@@ -1356,18 +1356,22 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
     const bool x3 = ts->terms == 3;
     int rc;
     if (c->fft) {
-        // Toeplitz route: W.s by FFT with the Heun update in the same kernel
-        {
+        // Toeplitz route: W.s by FFT with the Heun update in the same kernel; the
+        // noise part from L.eta, or from one transform of the circulant embedding
+        if (c->opts.noise_route == TWA_NOISE_CIRCULANT) {
             ProfScope p(c, TWA_PROF_NOISE);
-            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, M, N, ts->ldk, c->seed, c->d_t,
-                                                                     0, c->opts.traj_offset);
-        }
-        TcArgs la = base_args(c);
-        la.XI = ts->XI;
-        la.oBnx = ts->Bx;
-        la.oBny = ts->By;
-        const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmE};
-        {
+            rc = fft_noise(c);
+        } else {
+            {
+                ProfScope p(c, TWA_PROF_NOISE);
+                k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, M, N, ts->ldk, c->seed,
+                                                                         c->d_t, 0, c->opts.traj_offset);
+            }
+            TcArgs la = base_args(c);
+            la.XI = ts->XI;
+            la.oBnx = ts->Bx;
+            la.oBny = ts->By;
+            const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmE};
             ProfScope p(c, TWA_PROF_NOISE_FACTOR);
             rc = x3 ? launch_cfg<MODE_LETA, 2>(c, lm, la) : launch_cfg<MODE_LETA, 1>(c, lm, la);
         }

@@ -83,6 +83,13 @@ def test_init_rejects_bad_options():
     with pytest.raises(twa.TWAError) as e:
         twa.TWA(4, 1.0, 1.0, 1.0, 0.1, window_start=-1.0)
     assert e.value.code == -1
+    with pytest.raises(twa.TWAError) as e:
+        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision="bf16x3", ws_route="fft", noise_route=3)
+    assert e.value.code == -1 and "noise_route" in str(e.value)
+    # the circulant draw exists only beside the FFT pump field
+    with pytest.raises(twa.TWAError) as e:
+        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision="bf16x3", noise_route="circulant")
+    assert e.value.name == "TWA_EUNSUPPORTED"
 
 
 def test_null_context_calls_are_rejected():

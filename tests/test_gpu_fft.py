@@ -104,3 +104,85 @@ def test_fft_route_rejects_what_it_cannot_do():
     with pytest.raises(twa.TWAError) as e:
         twa.TWA(20000, 1.0, 1.0, 1.0, 1e-4, precision="bf16x3", ws_route="fft")
     assert e.value.name == "TWA_EUNSUPPORTED"
+
+
+# ---------------------------------------------------------------------------
+# circulant-embedding noise draw (fully FFT step)
+#
+# The step is then FP32 throughout: the FFT convolution (relative error a few
+# 1e-7) and the FP32 Box-Muller normals of the same Philox words the oracle turns
+# into FP64 normals (32-bit against 53-bit uniforms: relative 1e-7). Over a few
+# steps each spin component moves by O(sqrt(w dt)) per step, so a per-trajectory
+# difference of 5e-5 is two orders above the expected 1e-7 .. 1e-6 and far
+# below what any wrong frequency, scale or sign of the draw would give (O(1)).
+
+@pytest.mark.parametrize("N,M,alpha,w,steps", [(300, 48, 1.0, 20.0, 4), (37, 20, 0.5, 4.0, 6), (38, 9, 2.0, 10.0, 3),
+                                               (1, 6, 1.0, 2.0, 5), (200, 16, math.inf, 8.0, 3),
+                                               (128, 16, 0.0, 3.0, 3)])
+def test_circulant_route_tracks_its_oracle(N, M, alpha, w, steps):
+    from oracle.circulant import TWAOracleCirculant
+    twa = _twa()
+    dt = 1e-3
+    o = TWAOracleCirculant(N, alpha, w, 1.0, dt, 7, M)
+    o.run(steps)
+    with twa.TWA(N, alpha, w, 1.0, dt, seed=7, precision="bf16x3", ws_route="fft", noise_route="circulant") as g:
+        g.run(M, steps)
+        x, y, z = g.get_state()
+    # (alpha = 0: all but one eigenvalue of the embedding vanish, and their FP64
+    # rounding, different on the two sides, enters through sqrt: ~1e-7 here)
+    tol = 5e-5
+    for a, b in zip((x, y, z), (o.sx, o.sy, o.sz)):
+        assert np.max(np.abs(a - b)) < tol, np.max(np.abs(a - b))
+
+
+def test_circulant_route_ensemble_matches_the_cholesky_law():
+    # same law as chi = L eta: observables agree with the Cholesky oracle within 3 SE
+    N, alpha, w, G, dt, M, T, t0 = 256, 1.0, 32.0, 1.0, 1e-3, 512, 1.0, 0.5
+    steps = int(round(T / dt))
+    twa = _twa()
+    o = TWAOracle(N, alpha, w, G, dt, 5, M, window_start=t0)
+    o.run(steps)
+    ob = o.observables()
+    with twa.TWA(N, alpha, w, G, dt, seed=5, precision="bf16x3", window_start=t0, ws_route="fft",
+                 noise_route="circulant") as g:
+        g.run(M, steps)
+        gb = g.observables()
+    for k in ("Sz", "SpSm", "G2num", "g2"):
+        assert abs(gb[k] - ob[k]) <= 3.0 * math.hypot(gb[k + "_se"], ob[k + "_se"]), (k, gb[k], ob[k])
+
+
+def test_circulant_route_full_size_sampled():
+    # N = 10^4, M = 1024 (the benchmark's shape): trajectories 0 and 1023 against
+    # the oracle run on those two trajectories alone
+    from oracle.circulant import TWAOracleCirculant
+    twa = _twa()
+    N, alpha, w, G, dt, M, steps = 10000, 1.0, 5000.0, 1.0, 2e-5, 1024, 2
+    with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3", ws_route="fft", noise_route="circulant") as g:
+        g.run(M, steps)
+        x, y, z = g.get_state()
+    assert np.max(np.abs(x * x + y * y + z * z - 3.0)) < 5e-6
+    for m in (0, 1023):
+        o = TWAOracleCirculant(N, alpha, w, G, dt, 0, 1, m0=m)
+        o.run(steps)
+        err = max(np.max(np.abs(a[m] - b[0])) for a, b in zip((x, y, z), (o.sx, o.sy, o.sz)))
+        assert err < 5e-5, (m, err)
+
+
+def test_circulant_route_launches_no_contraction():
+    twa = _twa()
+    with twa.TWA(300, 1.0, 20.0, 1.0, 1e-3, precision="bf16x3", ws_route="fft", noise_route="circulant") as g:
+        g.run(64, 1)
+        g.profile(True)
+        g.run(64, 3)
+        p = g.profile_read()
+        g.profile(False)
+    assert p["noise"][1] == 3 and p["predict"][1] == 3 and p["correct"][1] == 3
+    assert p["noise_factor"][1] == 0
+
+
+def test_circulant_route_rejects_the_adjoint():
+    twa = _twa()
+    with twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="bf16x3", ws_route="fft", noise_route="circulant") as g:
+        with pytest.raises(twa.TWAError) as e:
+            g.grad("SpSm", M=8, steps=4)
+    assert e.value.name == "TWA_EUNSUPPORTED"
