@@ -50,14 +50,29 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
+# The tensor-core kernel and its device helpers occupy twa_tc.cu up to this line;
+# the host code after it does not change the kernel.
+KERNEL_SECTION_END = "// elementwise kernels of the mixed path"
+
+
+def kernel_source_sha(kernel_file):
+    """sha256 prefix of the kernel section of a source file (the whole file if
+    it has no section marker)."""
+    src = os.path.join(ROOT, "paper_2608_10075_b300", "csrc", kernel_file)
+    text = open(src, "rb").read()
+    cut = text.find(KERNEL_SECTION_END.encode())
+    return hashlib.sha256(text[:cut] if cut >= 0 else text).hexdigest()[:16]
+
+
 def recorded_traffic(kernel_file, summary):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (matching sha256 prefix); else None."""
+    the current kernel source (matching sha256 prefix of the kernel section);
+    else None."""
     path = os.path.join(ROOT, "profiles", summary)
     src = os.path.join(ROOT, "paper_2608_10075_b300", "csrc", kernel_file)
     if not (os.path.exists(path) and os.path.exists(src)):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha(kernel_file)
     txt = open(path).read()
     m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
