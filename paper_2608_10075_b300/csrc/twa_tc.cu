@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <functional>
 #include <queue>
+#include <type_traits>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -218,7 +219,7 @@ struct TcArgs {
 struct GroupDesc {   // 64-byte aligned through its tensor maps
     TcMaps maps;
     TcArgs args;
-    int mode, nt;           // kernel mode and term count of this problem's tiles (MODE_MIX launches)
+    int mode;               // kernel mode of this problem's tiles (MODE_MIX launches)
 };
 struct Group {
     const GroupDesc* desc;
@@ -277,8 +278,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             ap = &grp.desc[lo].args;
             tl = t - grp.start[lo];
             if (MODE == MODE_MIX) {
+                // W.s tiles take the template's term count, L.eta tiles one term
+                // fewer (their noise operand is a single BF16 value)
                 md = grp.desc[lo].mode;
-                nt = grp.desc[lo].nt;
+                nt = (md == MODE_LETA) ? (NT == 3 ? 2 : 1) : NT;
             }
         }
         const int64_t nct = (ap->n_vec + BN - 1) / BN;
@@ -483,12 +486,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 __all_sync(0xffffffffu, acc_ok && (((volatile unsigned long long*)args.flags)[FLAG_TIMEOUT] == 0ull));
             const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN);
             unsigned nonfinite = 0;
-            if (live) {
+            // the accumulator pass, compiled once per epilogue mode EM, so that each
+            // mode's loop is scheduled as in a kernel of that mode alone
+            auto run_tile = [&](auto em_tag) {
+                constexpr int EM = decltype(em_tag)::value;
+                constexpr bool WITH_LO = (NT == 3);   // images of the W.s operand: hi + lo
                 for (int c = 0; c < BN / 16; ++c) {
                     float pv[16];
                     tmem_ld16(trow + 16 * c, pv);
                     tmem_ld_wait();
-                    if (md == MODE_FIELD) {
+                    if constexpr (EM == MODE_FIELD) {
                         if (site_ok) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
@@ -496,9 +503,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                                 if (n < args.n_vec) args.field_out[n * args.N + i] = pv[j];
                             }
                         }
-                        continue;
-                    }
-                    if (md == MODE_LETA) {
+                    } else if constexpr (EM == MODE_LETA) {
                         // noise part of the field increment: sqrt(G dt) xi^a - sqrt(dt) (L eta^a)_i
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj) {
@@ -509,78 +514,87 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                             args.oBnx[e] = fmaf(-args.sdt, pv[2 * jj], __fmul_rn(args.sgdt, sS[2 * jl]));
                             args.oBny[e] = fmaf(-args.sdt, pv[2 * jj + 1], __fmul_rn(args.sgdt, sS[2 * jl + 1]));
                         }
-                        continue;
-                    }
-                    float rx[8], ry[8], rz[8];
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        const int jl = 8 * c + jj;            // local trajectory
-                        const int64_t m = m0 + jl;
-                        rx[jj] = ry[jj] = rz[jj] = 0.f;
-                        if (!site_ok || m >= M) continue;
-                        const int64_t e = m * args.N + i;
-                        const float x = args.X[e], y = args.Y[e], z = args.Z[e];
-                        // B^a = 1/2 (G S^a - P^a) dt + noise part
-                        const float Bxv = fmaf(fmaf(Gm, sS[2 * jl], -pv[2 * jj]), hdt, args.Bnx[e]);
-                        const float Byv = fmaf(fmaf(Gm, sS[2 * jl + 1], -pv[2 * jj + 1]), hdt, args.Bny[e]);
-                        const int64_t r0 = (2 * m) * args.ldk + i;
-                        if (md == MODE_PRED) {
-                            // f = s x (B^y, -B^x, 0); s~ = s + f; h = s + f/2
-                            const float fx = __fmul_rn(z, Bxv), fy = __fmul_rn(z, Byv);
-                            const float fz = -fmaf(x, Bxv, __fmul_rn(y, Byv));
-                            const float xp = __fadd_rn(x, fx), yp = __fadd_rn(y, fy), zp = __fadd_rn(z, fz);
-                            args.oX[e] = xp;
-                            args.oY[e] = yp;
-                            args.oZ[e] = zp;
-                            args.oHx[e] = fmaf(0.5f, fx, x);
-                            args.oHy[e] = fmaf(0.5f, fy, y);
-                            args.oHz[e] = fmaf(0.5f, fz, z);
-                            split_store(args.oHi, args.oLo, r0, xp, nt == 3);
-                            split_store(args.oHi, args.oLo, r0 + args.ldk, yp, nt == 3);
-                            rx[jj] = xp;
-                            ry[jj] = yp;
-                            rz[jj] = zp;
-                        } else {
-                            // corrector: s' = h + f(s~)/2, then |s'| = sqrt(3)
-                            float nx = fmaf(0.5f, __fmul_rn(z, Bxv), args.Hx[e]);
-                            float ny = fmaf(0.5f, __fmul_rn(z, Byv), args.Hy[e]);
-                            float nz = fmaf(-0.5f, fmaf(x, Bxv, __fmul_rn(y, Byv)), args.Hz[e]);
-                            if (args.renorm) {
-                                const float s = sqrtf(3.0f / fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz))));
-                                nx = __fmul_rn(nx, s);
-                                ny = __fmul_rn(ny, s);
-                                nz = __fmul_rn(nz, s);
-                            }
-                            if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) ++nonfinite;
-                            args.oX[e] = nx;
-                            args.oY[e] = ny;
-                            args.oZ[e] = nz;
-                            split_store(args.oHi, args.oLo, r0, nx, nt == 3);
-                            split_store(args.oHi, args.oLo, r0 + args.ldk, ny, nt == 3);
-                            rx[jj] = nx;
-                            ry[jj] = ny;
-                            rz[jj] = nz;
-                        }
-                    }
-                    // partial sums over this warp's 32 sites
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-#pragma unroll
-                        for (int o = 16; o; o >>= 1) {
-                            rx[jj] += __shfl_xor_sync(0xffffffffu, rx[jj], o);
-                            ry[jj] += __shfl_xor_sync(0xffffffffu, ry[jj], o);
-                            rz[jj] += __shfl_xor_sync(0xffffffffu, rz[jj], o);
-                        }
-                    }
-                    if (lane == 0) {
+                    } else {
+                        float rx[8], ry[8], rz[8];
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj) {
-                            float* rr = red + (q * NTRAJ + 8 * c + jj) * 3;
-                            rr[0] = rx[jj];
-                            rr[1] = ry[jj];
-                            rr[2] = rz[jj];
+                            const int jl = 8 * c + jj;            // local trajectory
+                            const int64_t m = m0 + jl;
+                            rx[jj] = ry[jj] = rz[jj] = 0.f;
+                            if (!site_ok || m >= M) continue;
+                            const int64_t e = m * args.N + i;
+                            const float x = args.X[e], y = args.Y[e], z = args.Z[e];
+                            // B^a = 1/2 (G S^a - P^a) dt + noise part
+                            const float Bxv = fmaf(fmaf(Gm, sS[2 * jl], -pv[2 * jj]), hdt, args.Bnx[e]);
+                            const float Byv = fmaf(fmaf(Gm, sS[2 * jl + 1], -pv[2 * jj + 1]), hdt, args.Bny[e]);
+                            const int64_t r0 = (2 * m) * args.ldk + i;
+                            if constexpr (EM == MODE_PRED) {
+                                // f = s x (B^y, -B^x, 0); s~ = s + f; h = s + f/2
+                                const float fx = __fmul_rn(z, Bxv), fy = __fmul_rn(z, Byv);
+                                const float fz = -fmaf(x, Bxv, __fmul_rn(y, Byv));
+                                const float xp = __fadd_rn(x, fx), yp = __fadd_rn(y, fy), zp = __fadd_rn(z, fz);
+                                args.oX[e] = xp;
+                                args.oY[e] = yp;
+                                args.oZ[e] = zp;
+                                args.oHx[e] = fmaf(0.5f, fx, x);
+                                args.oHy[e] = fmaf(0.5f, fy, y);
+                                args.oHz[e] = fmaf(0.5f, fz, z);
+                                split_store(args.oHi, args.oLo, r0, xp, WITH_LO);
+                                split_store(args.oHi, args.oLo, r0 + args.ldk, yp, WITH_LO);
+                                rx[jj] = xp;
+                                ry[jj] = yp;
+                                rz[jj] = zp;
+                            } else {
+                                // corrector: s' = h + f(s~)/2, then |s'| = sqrt(3)
+                                float nx = fmaf(0.5f, __fmul_rn(z, Bxv), args.Hx[e]);
+                                float ny = fmaf(0.5f, __fmul_rn(z, Byv), args.Hy[e]);
+                                float nz = fmaf(-0.5f, fmaf(x, Bxv, __fmul_rn(y, Byv)), args.Hz[e]);
+                                if (args.renorm) {
+                                    const float s = sqrtf(3.0f / fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz))));
+                                    nx = __fmul_rn(nx, s);
+                                    ny = __fmul_rn(ny, s);
+                                    nz = __fmul_rn(nz, s);
+                                }
+                                if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) ++nonfinite;
+                                args.oX[e] = nx;
+                                args.oY[e] = ny;
+                                args.oZ[e] = nz;
+                                split_store(args.oHi, args.oLo, r0, nx, WITH_LO);
+                                split_store(args.oHi, args.oLo, r0 + args.ldk, ny, WITH_LO);
+                                rx[jj] = nx;
+                                ry[jj] = ny;
+                                rz[jj] = nz;
+                            }
+                        }
+                        // partial sums over this warp's 32 sites
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+#pragma unroll
+                            for (int o = 16; o; o >>= 1) {
+                                rx[jj] += __shfl_xor_sync(0xffffffffu, rx[jj], o);
+                                ry[jj] += __shfl_xor_sync(0xffffffffu, ry[jj], o);
+                                rz[jj] += __shfl_xor_sync(0xffffffffu, rz[jj], o);
+                            }
+                        }
+                        if (lane == 0) {
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) {
+                                float* rr = red + (q * NTRAJ + 8 * c + jj) * 3;
+                                rr[0] = rx[jj];
+                                rr[1] = ry[jj];
+                                rr[2] = rz[jj];
+                            }
                         }
                     }
+                }
+            };
+            if (live) {
+                if constexpr (MODE != MODE_MIX) {
+                    run_tile(std::integral_constant<int, MODE>{});
+                } else {
+                    if (md == MODE_CORR) run_tile(std::integral_constant<int, MODE_CORR>{});
+                    else if (md == MODE_PRED) run_tile(std::integral_constant<int, MODE_PRED>{});
+                    else run_tile(std::integral_constant<int, MODE_LETA>{});
                 }
             }
             // accumulator b may be overwritten by the next tile's MMAs
@@ -1284,10 +1298,10 @@ int mix_build(twa_ctx* c) {
         ca.oHi = t->Shi; ca.oLo = t->Slo;
         ca.part_in = t->partp; ca.part_out = t->part;
         GroupDesc* g = &d[4 * par];
-        g[0] = GroupDesc{pm, pa, MODE_PRED, ntw};
-        g[1] = GroupDesc{lm, la, MODE_LETA, ntl};
-        g[2] = GroupDesc{cm, ca, MODE_CORR, ntw};
-        g[3] = GroupDesc{lm, la, MODE_LETA, ntl};
+        g[0] = GroupDesc{pm, pa, MODE_PRED};
+        g[1] = GroupDesc{lm, la, MODE_LETA};
+        g[2] = GroupDesc{cm, ca, MODE_CORR};
+        g[3] = GroupDesc{lm, la, MODE_LETA};
     }
     p->host = d;
     const int64_t st[3] = {0, Tw, Tw + Tl};
@@ -1418,7 +1432,8 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         for (int L = 0; L < 2; ++L) {
             const Group g{dp + 2 * L, mp->start, 2, mp->list[L], mp->first[L], mp->ctas[L]};
             ProfScope p(c, L == 0 ? TWA_PROF_PREDICT : TWA_PROF_CORRECT, mp->flops[L]);
-            rc = launch_cfg<MODE_MIX, 3>(c, none, fa, g, mp->tiles[L]);
+            rc = x3 ? launch_cfg<MODE_MIX, 3>(c, none, fa, g, mp->tiles[L])
+                    : launch_cfg<MODE_MIX, 1>(c, none, fa, g, mp->tiles[L]);
             if (rc) return rc;
         }
     }
