@@ -119,39 +119,87 @@ struct Tw {
 
 // One stage over butterflies of radix R and stride m (span L = m R): DIF applies
 // the small DFT then the twiddles w_L^{jk}; DIT (inverse) undoes the twiddles,
-// then the inverse DFT. w_L^{jk} = w^{j k P / L} with j k < L, so no reduction.
-template <int R, bool INV>
-__device__ __forceinline__ void stage_r(float2* buf, int64_t P64, int64_t m64, const Tw tw) {
-    // P <= FFT_MAX_P: 32-bit index arithmetic
-    const int P = (int)P64, m = (int)m64, L = m * R, step = P / L, nb = P / R;
+// then the inverse DFT. w_L^{jk} = w^{j k P / L} = (w^{j P / L})^k: one table
+// lookup per butterfly, the higher powers by complex products (k < R <= 5).
+// The butterfly's R inputs come from `ld(position)` and its outputs go to
+// `st(position, value)`: shared memory inside the transform, global memory in
+// the first and last stages, which thereby replace separate load/store passes.
+template <int R, bool INV, typename LD, typename ST>
+__device__ __forceinline__ void stage_io(int P, int m, const Tw tw, LD& ld, ST& st) {
+    const int L = m * R, step = P / L, nb = P / R;   // P <= FFT_MAX_P: 32-bit indices
     for (int u = threadIdx.x; u < nb; u += FT) {
         const int b = u / m, j = u - b * m, base = b * L + j;
         float2 a[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) a[q] = buf[base + q * m];
+        for (int q = 0; q < R; ++q) a[q] = ld(base + q * m);
+        float2 w[R];
+        w[1] = tw[j * step];
+#pragma unroll
+        for (int k = 2; k < R; ++k) w[k] = cmul(w[k - 1], w[1]);
         if (!INV) {
             dft<R, false>(a);
 #pragma unroll
-            for (int k = 1; k < R; ++k) a[k] = cmul(a[k], tw[j * k * step]);
+            for (int k = 1; k < R; ++k) a[k] = cmul(a[k], w[k]);
         } else {
 #pragma unroll
-            for (int k = 1; k < R; ++k) a[k] = cmulc(a[k], tw[j * k * step]);
+            for (int k = 1; k < R; ++k) a[k] = cmulc(a[k], w[k]);
             dft<R, true>(a);
         }
 #pragma unroll
-        for (int q = 0; q < R; ++q) buf[base + q * m] = a[q];
+        for (int q = 0; q < R; ++q) st(base + q * m, a[q]);
     }
 }
 
-template <bool INV>
-__device__ __forceinline__ void stage(float2* buf, int64_t P, int r, int64_t m, const Tw tw) {
+template <bool INV, typename LD, typename ST>
+__device__ __forceinline__ void stage_any(int r, int P, int m, const Tw tw, LD& ld, ST& st) {
     switch (r) {
-        case 4: stage_r<4, INV>(buf, P, m, tw); break;
-        case 2: stage_r<2, INV>(buf, P, m, tw); break;
-        case 3: stage_r<3, INV>(buf, P, m, tw); break;
-        default: stage_r<5, INV>(buf, P, m, tw); break;
+        case 4: stage_io<4, INV>(P, m, tw, ld, st); break;
+        case 2: stage_io<2, INV>(P, m, tw, ld, st); break;
+        case 3: stage_io<3, INV>(P, m, tw, ld, st); break;
+        default: stage_io<5, INV>(P, m, tw, ld, st); break;
     }
 }
+
+// Last forward stage, product with the spectrum and first inverse stage in one
+// pass: all three work on the same groups of R neighbouring positions (stride
+// m = 1, twiddles 1), so each group stays in registers.
+template <int R, typename LD, typename ST>
+__device__ __forceinline__ void middle_io(int P, const float* __restrict__ lam, LD& ld, ST& st) {
+    for (int u = threadIdx.x; u < P / R; u += FT) {
+        const int base = u * R;
+        float2 a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = ld(base + q);
+        dft<R, false>(a);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float l = __ldg(&lam[base + q]);
+            a[q] = make_float2(a[q].x * l, a[q].y * l);
+        }
+        dft<R, true>(a);
+#pragma unroll
+        for (int q = 0; q < R; ++q) st(base + q, a[q]);
+    }
+}
+
+template <typename LD, typename ST>
+__device__ __forceinline__ void middle_any(int r, int P, const float* lam, LD& ld, ST& st) {
+    switch (r) {
+        case 4: middle_io<4>(P, lam, ld, st); break;
+        case 2: middle_io<2>(P, lam, ld, st); break;
+        case 3: middle_io<3>(P, lam, ld, st); break;
+        default: middle_io<5>(P, lam, ld, st); break;
+    }
+}
+
+struct SmemLd {
+    const float2* buf;
+    __device__ __forceinline__ float2 operator()(int p) const { return buf[p]; }
+};
+struct SmemSt {
+    float2* buf;
+    __device__ __forceinline__ void operator()(int p, float2 v) const { buf[p] = v; }
+};
 
 // Twiddle tables into shared memory right after the P values of buf.
 __device__ Tw load_twiddles(float2* buf, const FftArgs& a) {
@@ -160,35 +208,6 @@ __device__ Tw load_twiddles(float2* buf, const FftArgs& a) {
     for (int64_t k = threadIdx.x; k * TW_LO < a.P; k += FT) thi[k] = a.tw[k * TW_LO];
     for (int j = threadIdx.x; j < TW_LO; j += FT) tlo[j] = (j < a.P) ? a.tw[j] : make_float2(1.f, 0.f);
     return Tw{thi, tlo};
-}
-
-// Unnormalised inverse transform, digit-reversed input -> natural order:
-// buf_j <- sum_k in_k exp(+2 pi i j k / P), in_k held at the position of k.
-__device__ void inverse_dit(float2* buf, const FftArgs& a, const Tw tw) {
-    int64_t m = 1;
-    for (int s = a.nst - 1; s >= 0; --s) {
-        stage<true>(buf, a.P, a.radix[s], m, tw);
-        m *= a.radix[s];
-        __syncthreads();
-    }
-}
-
-// buf <- P * (C buf) for the circulant C with spectrum lam (digit-reversed order).
-__device__ void circulant_conv(float2* buf, const FftArgs& a) {
-    const Tw tw = load_twiddles(buf, a);
-    __syncthreads();
-    int64_t m = a.P;
-    for (int s = 0; s < a.nst; ++s) {
-        m /= a.radix[s];
-        stage<false>(buf, a.P, a.radix[s], m, tw);
-        __syncthreads();
-    }
-    for (int64_t p = threadIdx.x; p < a.P; p += FT) {
-        const float l = __ldg(&a.lam[p]);
-        buf[p] = make_float2(buf[p].x * l, buf[p].y * l);
-    }
-    __syncthreads();
-    inverse_dit(buf, a, tw);
 }
 
 // Sum of v over the block (all threads receive it). `scratch` holds 32 floats.
@@ -203,83 +222,156 @@ __device__ float block_sum(float v, float* scratch) {
     return t;
 }
 
-// Load s^x + i s^y of trajectory m into buf (zero padded to P); returns S^x, S^y.
-__device__ float2 load_state(float2* buf, const float* X, const float* Y, const FftArgs& a, float* scratch) {
+// P * (C v) for the circulant C with spectrum lam (digit-reversed order), v read
+// by `in(position)` (zero beyond the vector) and the result handed to
+// `out(position, value)`; `after_first` runs after the first stage (all threads,
+// may synchronise), `before_last` before the last one. buf holds the transform
+// and, after it, the twiddle tables.
+template <typename IN, typename OUT, typename F1, typename F2>
+__device__ __forceinline__ void circulant_io(float2* buf, const FftArgs& a, IN& in, OUT& out, F1 after_first,
+                                             F2 before_last) {
+    const Tw tw = load_twiddles(buf, a);
+    SmemLd sld{buf};
+    SmemSt sst{buf};
+    const int P = (int)a.P, nst = a.nst;
+    __syncthreads();
+    if (nst == 1) {
+        after_first();
+        before_last();
+        middle_any(a.radix[0], P, a.lam, in, out);
+        return;
+    }
+    int m = P;
+    for (int s = 0; s + 1 < nst; ++s) {
+        m /= a.radix[s];
+        if (s == 0) stage_any<false>(a.radix[s], P, m, tw, in, sst);
+        else stage_any<false>(a.radix[s], P, m, tw, sld, sst);
+        __syncthreads();
+        if (s == 0) after_first();
+    }
+    middle_any(a.radix[nst - 1], P, a.lam, sld, sst);
+    __syncthreads();
+    m = a.radix[nst - 1];
+    for (int s = nst - 2; s >= 0; --s) {
+        if (s == 0) {
+            before_last();
+            stage_any<true>(a.radix[s], P, m, tw, sld, out);
+        } else {
+            stage_any<true>(a.radix[s], P, m, tw, sld, sst);
+        }
+        m *= a.radix[s];
+        __syncthreads();
+    }
+}
+
+// First-stage input: s^x + i s^y of one trajectory (zero beyond N), summing
+// S^x, S^y on the way.
+struct StateIn {
+    const float *X, *Y;
+    int N;
     float sx = 0.f, sy = 0.f;
-    for (int64_t i = threadIdx.x; i < a.P; i += FT) {
-        float2 v = make_float2(0.f, 0.f);
-        if (i < a.N) v = make_float2(X[i], Y[i]);
-        buf[i] = v;
+    __device__ __forceinline__ float2 operator()(int p) {
+        if (p >= N) return make_float2(0.f, 0.f);
+        const float2 v = make_float2(__ldg(&X[p]), __ldg(&Y[p]));
         sx += v.x;
         sy += v.y;
+        return v;
     }
-    const float Sx = block_sum(sx, scratch);
-    const float Sy = block_sum(sy, scratch);
-    return make_float2(Sx, Sy);
-}
+};
 
-__global__ void __launch_bounds__(FT, 1) k_fft_pred(const FftArgs a) {
-    extern __shared__ float2 buf[];
-    __shared__ float scratch[32];
-    const int64_t m = blockIdx.x, off = m * a.N;
-    const float2 S = load_state(buf, a.X + off, a.Y + off, a, scratch);
-    __syncthreads();
-    circulant_conv(buf, a);
-    const float inv = 1.0f / (float)a.P, G = a.G, dt = a.dt;
-    for (int64_t i = threadIdx.x; i < a.N; i += FT) {
+// Heun predictor at site i from P (W s)_i (Eq. S1; every rounding spelled out).
+struct PredOut {
+    const FftArgs* a;
+    int64_t off;
+    float Sx = 0.f, Sy = 0.f, inv = 0.f, hdt = 0.f;
+    __device__ __forceinline__ void operator()(int i, float2 pf) const {
+        if (i >= a->N) return;
         const int64_t e = off + i;
-        const float2 pf = buf[i];
-        const float x = a.X[e], y = a.Y[e], z = a.Z[e];
+        const float x = a->X[e], y = a->Y[e], z = a->Z[e];
         // B^a = 1/2 (G S^a - (W s^a)_i) dt + noise part; f = s x (B^y, -B^x, 0)
-        const float Bx = 0.5f * (G * S.x - pf.x * inv) * dt + a.Bnx[e];
-        const float By = 0.5f * (G * S.y - pf.y * inv) * dt + a.Bny[e];
-        const float fx = z * Bx, fy = z * By, fz = -(x * Bx + y * By);
-        a.oX[e] = x + fx;
-        a.oY[e] = y + fy;
-        a.oZ[e] = z + fz;
-        a.oHx[e] = fmaf(0.5f, fx, x);
-        a.oHy[e] = fmaf(0.5f, fy, y);
-        a.oHz[e] = fmaf(0.5f, fz, z);
+        const float Bx = fmaf(fmaf(a->G, Sx, -__fmul_rn(pf.x, inv)), hdt, a->Bnx[e]);
+        const float By = fmaf(fmaf(a->G, Sy, -__fmul_rn(pf.y, inv)), hdt, a->Bny[e]);
+        const float fx = __fmul_rn(z, Bx), fy = __fmul_rn(z, By);
+        const float fz = -fmaf(x, Bx, __fmul_rn(y, By));
+        a->oX[e] = __fadd_rn(x, fx);
+        a->oY[e] = __fadd_rn(y, fy);
+        a->oZ[e] = __fadd_rn(z, fz);
+        a->oHx[e] = fmaf(0.5f, fx, x);
+        a->oHy[e] = fmaf(0.5f, fy, y);
+        a->oHz[e] = fmaf(0.5f, fz, z);
     }
-}
+};
 
-__global__ void __launch_bounds__(FT, 1) k_fft_corr(const FftArgs a) {
-    extern __shared__ float2 buf[];
-    __shared__ float scratch[32];
-    const int64_t m = blockIdx.x, off = m * a.N;
-    const int64_t t1 = *a.d_t + 1;
-    const float2 S = load_state(buf, a.X + off, a.Y + off, a, scratch);
-    __syncthreads();
-    circulant_conv(buf, a);
-    const float inv = 1.0f / (float)a.P, G = a.G, dt = a.dt;
+// Heun corrector and renormalisation at site i; sums of the new state.
+struct CorrOut {
+    const FftArgs* a;
+    int64_t off;
+    float Sx = 0.f, Sy = 0.f, inv = 0.f, hdt = 0.f;
     float sx = 0.f, sy = 0.f, sz = 0.f;
     unsigned bad = 0;
-    for (int64_t i = threadIdx.x; i < a.N; i += FT) {
+    __device__ __forceinline__ void operator()(int i, float2 pf) {
+        if (i >= a->N) return;
         const int64_t e = off + i;
-        const float2 pf = buf[i];
-        const float x = a.X[e], y = a.Y[e], z = a.Z[e];
-        const float Bx = 0.5f * (G * S.x - pf.x * inv) * dt + a.Bnx[e];
-        const float By = 0.5f * (G * S.y - pf.y * inv) * dt + a.Bny[e];
+        const float x = a->X[e], y = a->Y[e], z = a->Z[e];
+        const float Bx = fmaf(fmaf(a->G, Sx, -__fmul_rn(pf.x, inv)), hdt, a->Bnx[e]);
+        const float By = fmaf(fmaf(a->G, Sy, -__fmul_rn(pf.y, inv)), hdt, a->Bny[e]);
         // s' = h + f(s~)/2, then |s'| = sqrt(3)
-        float nx = fmaf(0.5f, z * Bx, a.Hx[e]);
-        float ny = fmaf(0.5f, z * By, a.Hy[e]);
-        float nz = fmaf(-0.5f, x * Bx + y * By, a.Hz[e]);
-        if (a.renorm) {
-            const float s = sqrtf(3.0f / (nx * nx + ny * ny + nz * nz));
-            nx *= s;
-            ny *= s;
-            nz *= s;
+        float nx = fmaf(0.5f, __fmul_rn(z, Bx), a->Hx[e]);
+        float ny = fmaf(0.5f, __fmul_rn(z, By), a->Hy[e]);
+        float nz = fmaf(-0.5f, fmaf(x, Bx, __fmul_rn(y, By)), a->Hz[e]);
+        if (a->renorm) {
+            const float s = sqrtf(3.0f / fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz))));
+            nx = __fmul_rn(nx, s);
+            ny = __fmul_rn(ny, s);
+            nz = __fmul_rn(nz, s);
         }
         if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) ++bad;
-        a.oX[e] = nx;
-        a.oY[e] = ny;
-        a.oZ[e] = nz;
+        a->oX[e] = nx;
+        a->oY[e] = ny;
+        a->oZ[e] = nz;
         sx += nx;
         sy += ny;
         sz += nz;
     }
-    const float Sx = block_sum(sx, scratch), Sy = block_sum(sy, scratch), Sz = block_sum(sz, scratch);
-    const unsigned nb = __reduce_add_sync(0xffffffffu, bad);
+};
+
+__global__ void __launch_bounds__(FT, 1) k_fft_pred(const __grid_constant__ FftArgs a) {
+    extern __shared__ float2 buf[];
+    __shared__ float scratch[32];
+    const int64_t off = (int64_t)blockIdx.x * a.N;
+    StateIn in{a.X + off, a.Y + off, (int)a.N};
+    PredOut out{&a, off};
+    out.inv = 1.0f / (float)a.P;
+    out.hdt = 0.5f * a.dt;
+    auto first = [&]() {
+        if (a.nst == 1)
+            for (int p = threadIdx.x; p < a.N; p += FT) in(p);   // sums only (tiny P)
+        out.Sx = block_sum(in.sx, scratch);
+        out.Sy = block_sum(in.sy, scratch);
+        in.sx = in.sy = 0.f;
+    };
+    circulant_io(buf, a, in, out, first, [] {});
+}
+
+__global__ void __launch_bounds__(FT, 1) k_fft_corr(const __grid_constant__ FftArgs a) {
+    extern __shared__ float2 buf[];
+    __shared__ float scratch[32];
+    const int64_t m = blockIdx.x, off = m * a.N;
+    const int64_t t1 = *a.d_t + 1;
+    StateIn in{a.X + off, a.Y + off, (int)a.N};
+    CorrOut out{&a, off};
+    out.inv = 1.0f / (float)a.P;
+    out.hdt = 0.5f * a.dt;
+    auto first = [&]() {
+        if (a.nst == 1)
+            for (int p = threadIdx.x; p < a.N; p += FT) in(p);
+        out.Sx = block_sum(in.sx, scratch);
+        out.Sy = block_sum(in.sy, scratch);
+        in.sx = in.sy = 0.f;
+    };
+    circulant_io(buf, a, in, out, first, [] {});
+    const float Sx = block_sum(out.sx, scratch), Sy = block_sum(out.sy, scratch), Sz = block_sum(out.sz, scratch);
+    const unsigned nb = __reduce_add_sync(0xffffffffu, out.bad);
     if ((threadIdx.x & 31) == 0 && nb) atomicAdd(&a.flags[FLAG_NONFINITE], (unsigned long long)nb);
     if (threadIdx.x == 0) {
         if (t1 > a.n_window) {
@@ -309,51 +401,85 @@ __global__ void __launch_bounds__(FT, 1) k_fft_corr(const FftArgs a) {
 // frequency, (a_k, b_k) the FP32 Box-Muller pair of Philox counter (m, t, k, 2);
 // the transform returns Y_j in natural order, chi^x_j = Re Y_j, chi^y_j = Im Y_j.
 // Writes the noise part of the field increment, sqrt(G dt) xi^a - sqrt(dt) chi^a_j,
-// xi^a the collective normals of counter (m, t, N, 0).
-__global__ void __launch_bounds__(FT, 1) k_fft_noise(const FftArgs a, const float* nscale, const int32_t* nfreq,
-                                                     uint64_t seed, int64_t m0, float sgdt, float sdt, float* Bnx,
-                                                     float* Bny) {
+// xi^a the collective normals of counter (m, t, N, 0). The draws are made in the
+// first inverse stage and the noise part written by the last one.
+struct NoiseIn {
+    const float* nscale;
+    const int32_t* nfreq;
+    uint64_t seed;
+    uint32_t m, t;
+    __device__ __forceinline__ float2 operator()(int p) const {
+        float ga, gb;
+        normal2_f32(seed, m, t, (uint32_t)__ldg(&nfreq[p]), ga, gb, STREAM_CIRCULANT);
+        const float sc = __ldg(&nscale[p]);
+        return make_float2(__fmul_rn(sc, ga), __fmul_rn(sc, gb));
+    }
+};
+struct NoiseOut {
+    float *Bnx, *Bny;
+    int N;
+    float nx0, ny0, sdt;
+    __device__ __forceinline__ void operator()(int j, float2 y) const {
+        if (j >= N) return;
+        Bnx[j] = fmaf(-sdt, y.x, nx0);
+        Bny[j] = fmaf(-sdt, y.y, ny0);
+    }
+};
+
+__global__ void __launch_bounds__(FT, 1) k_fft_noise(const __grid_constant__ FftArgs a, const float* nscale,
+                                                     const int32_t* nfreq, uint64_t seed, int64_t m0, float sgdt,
+                                                     float sdt, float* Bnx, float* Bny) {
     extern __shared__ float2 buf[];
     const int64_t m = blockIdx.x, off = m * a.N;
     const uint32_t t = (uint32_t)(*a.d_t), mg = (uint32_t)(m0 + m);
     const Tw tw = load_twiddles(buf, a);
-    for (int64_t p = threadIdx.x; p < a.P; p += FT) {
-        float ga, gb;
-        normal2_f32(seed, mg, t, (uint32_t)__ldg(&nfreq[p]), ga, gb, STREAM_CIRCULANT);
-        const float sc = __ldg(&nscale[p]);
-        buf[p] = make_float2(__fmul_rn(sc, ga), __fmul_rn(sc, gb));
-    }
     float xi_x, xi_y;
     normal2_f32(seed, mg, t, (uint32_t)a.N, xi_x, xi_y);
-    const float nx0 = __fmul_rn(sgdt, xi_x), ny0 = __fmul_rn(sgdt, xi_y);
+    NoiseIn in{nscale, nfreq, seed, mg, t};
+    NoiseOut out{Bnx + off, Bny + off, (int)a.N, __fmul_rn(sgdt, xi_x), __fmul_rn(sgdt, xi_y), sdt};
+    SmemLd sld{buf};
+    SmemSt sst{buf};
+    const int P = (int)a.P, nst = a.nst;
     __syncthreads();
-    inverse_dit(buf, a, tw);
-    for (int64_t j = threadIdx.x; j < a.N; j += FT) {
-        const float2 y = buf[j];
-        Bnx[off + j] = fmaf(-sdt, y.x, nx0);
-        Bny[off + j] = fmaf(-sdt, y.y, ny0);
+    // unnormalised inverse transform, digit-reversed input -> natural order
+    int mm = 1;
+    for (int s = nst - 1; s >= 0; --s) {
+        if (s == nst - 1 && s == 0) stage_any<true>(a.radix[s], P, mm, tw, in, out);
+        else if (s == nst - 1) stage_any<true>(a.radix[s], P, mm, tw, in, sst);
+        else if (s == 0) stage_any<true>(a.radix[s], P, mm, tw, sld, out);
+        else stage_any<true>(a.radix[s], P, mm, tw, sld, sst);
+        mm *= a.radix[s];
+        __syncthreads();
     }
 }
 
 // W s for caller vectors: vectors 2b and 2b+1 share one complex transform.
-__global__ void __launch_bounds__(FT, 1) k_fft_field(const FftArgs a) {
+struct FieldIn {
+    const double *v0, *v1;   // v1 NULL for an odd last vector
+    int N;
+    __device__ __forceinline__ float2 operator()(int p) const {
+        if (p >= N) return make_float2(0.f, 0.f);
+        return make_float2((float)v0[p], v1 ? (float)v1[p] : 0.f);
+    }
+};
+struct FieldOut {
+    double *o0, *o1;
+    int N;
+    double inv;
+    __device__ __forceinline__ void operator()(int p, float2 v) const {
+        if (p >= N) return;
+        o0[p] = (double)v.x * inv;
+        if (o1) o1[p] = (double)v.y * inv;
+    }
+};
+
+__global__ void __launch_bounds__(FT, 1) k_fft_field(const __grid_constant__ FftArgs a) {
     extern __shared__ float2 buf[];
     const int64_t k0 = 2 * (int64_t)blockIdx.x, k1 = k0 + 1;
-    for (int64_t i = threadIdx.x; i < a.P; i += FT) {
-        float2 v = make_float2(0.f, 0.f);
-        if (i < a.N) {
-            v.x = (float)a.field_in[k0 * a.N + i];
-            if (k1 < a.K) v.y = (float)a.field_in[k1 * a.N + i];
-        }
-        buf[i] = v;
-    }
-    __syncthreads();
-    circulant_conv(buf, a);
-    const double inv = 1.0 / (double)a.P;
-    for (int64_t i = threadIdx.x; i < a.N; i += FT) {
-        a.field_out[k0 * a.N + i] = (double)buf[i].x * inv;
-        if (k1 < a.K) a.field_out[k1 * a.N + i] = (double)buf[i].y * inv;
-    }
+    const bool two = k1 < a.K;
+    FieldIn in{a.field_in + k0 * a.N, two ? a.field_in + k1 * a.N : nullptr, (int)a.N};
+    FieldOut out{a.field_out + k0 * a.N, two ? a.field_out + k1 * a.N : nullptr, (int)a.N, 1.0 / (double)a.P};
+    circulant_io(buf, a, in, out, [] {}, [] {});
 }
 
 // exp(-2 pi i n / P), accurate to FP32 rounding (FP64 sincospi).
