@@ -40,10 +40,9 @@ struct FftArgs {
     float G, dt;
     int renorm;
     const float *X, *Y, *Z;              // PRED: s; CORR: s~
-    const float *Hx, *Hy, *Hz;           // CORR
+    const float *X0, *Y0, *Z0;           // CORR: s, the state before the step
     const float *Bnx, *Bny;              // noise part of the field increment
     float *oX, *oY, *oZ;                 // PRED: s~; CORR: s'
-    float *oHx, *oHy, *oHz;              // PRED
     double* mom;                         // CORR: window sums [M][5]
     int64_t* d_t;
     int64_t* d_count;
@@ -296,9 +295,6 @@ struct PredOut {
         a->oX[e] = __fadd_rn(x, fx);
         a->oY[e] = __fadd_rn(y, fy);
         a->oZ[e] = __fadd_rn(z, fz);
-        a->oHx[e] = fmaf(0.5f, fx, x);
-        a->oHy[e] = fmaf(0.5f, fy, y);
-        a->oHz[e] = fmaf(0.5f, fz, z);
     }
 };
 
@@ -315,10 +311,13 @@ struct CorrOut {
         const float x = a->X[e], y = a->Y[e], z = a->Z[e];
         const float Bx = fmaf(fmaf(a->G, Sx, -__fmul_rn(pf.x, inv)), hdt, a->Bnx[e]);
         const float By = fmaf(fmaf(a->G, Sy, -__fmul_rn(pf.y, inv)), hdt, a->Bny[e]);
-        // s' = h + f(s~)/2, then |s'| = sqrt(3)
-        float nx = fmaf(0.5f, __fmul_rn(z, Bx), a->Hx[e]);
-        float ny = fmaf(0.5f, __fmul_rn(z, By), a->Hy[e]);
-        float nz = fmaf(-0.5f, fmaf(x, Bx, __fmul_rn(y, By)), a->Hz[e]);
+        // s' = (s + s~)/2 + f(s~)/2, then |s'| = sqrt(3)
+        const float hx = __fmul_rn(0.5f, __fadd_rn(a->X0[e], x));
+        const float hy = __fmul_rn(0.5f, __fadd_rn(a->Y0[e], y));
+        const float hz = __fmul_rn(0.5f, __fadd_rn(a->Z0[e], z));
+        float nx = fmaf(0.5f, __fmul_rn(z, Bx), hx);
+        float ny = fmaf(0.5f, __fmul_rn(z, By), hy);
+        float nz = fmaf(-0.5f, fmaf(x, Bx, __fmul_rn(y, By)), hz);
         if (a->renorm) {
             const float s = sqrtf(3.0f / fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz))));
             nx = __fmul_rn(nx, s);
@@ -622,7 +621,6 @@ int fft_predict(twa_ctx* c) {
     a.X = t->X; a.Y = t->Y; a.Z = t->Z;
     a.Bnx = t->Bx; a.Bny = t->By;
     a.oX = t->Xp; a.oY = t->Yp; a.oZ = t->Zp;
-    a.oHx = t->Hx; a.oHy = t->Hy; a.oHz = t->Hz;
     k_fft_pred<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(a);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
@@ -632,7 +630,7 @@ int fft_correct(twa_ctx* c) {
     TcState* t = c->tc;
     FftArgs a = base_args(c);
     a.X = t->Xp; a.Y = t->Yp; a.Z = t->Zp;
-    a.Hx = t->Hx; a.Hy = t->Hy; a.Hz = t->Hz;
+    a.X0 = t->X; a.Y0 = t->Y; a.Z0 = t->Z;
     a.Bnx = t->Bx; a.Bny = t->By;
     a.oX = t->X; a.oY = t->Y; a.oZ = t->Z;
     a.mom = c->mom;

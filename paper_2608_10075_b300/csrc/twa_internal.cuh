@@ -40,7 +40,6 @@ struct TcState {
     __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
     float *X = nullptr, *Y = nullptr, *Z = nullptr;       // state [M][N]
     float *Xp = nullptr, *Yp = nullptr, *Zp = nullptr;    // predictor
-    float *Hx = nullptr, *Hy = nullptr, *Hz = nullptr;    // s + f(s)/2
     float *Bx = nullptr, *By = nullptr;                   // noise part of the field increment
     __nv_bfloat16 *Shi = nullptr, *Slo = nullptr;         // images of s   [2M][ldk]
     __nv_bfloat16 *Phi = nullptr, *Plo = nullptr;         // images of s~  [2M][ldk]

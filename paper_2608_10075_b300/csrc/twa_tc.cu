@@ -201,10 +201,9 @@ struct TcArgs {
     float G, dt, sgdt, sdt;
     int renorm;
     const float *X, *Y, *Z;           // PRED: s; CORR: s~
-    const float *Hx, *Hy, *Hz;        // CORR: s + f(s)/2
+    const float *X0, *Y0, *Z0;        // CORR: s, the state before the step
     const float *Bnx, *Bny;           // PRED, CORR: noise part of the field increment
     float *oX, *oY, *oZ;              // PRED: s~; CORR: s'
-    float *oHx, *oHy, *oHz;           // PRED
     float *oBnx, *oBny;               // LETA
     __nv_bfloat16 *oHi, *oLo;         // images of the output state
     const float* XI;                  // LETA: collective normals [M][2]
@@ -529,26 +528,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                             const float Byv = fmaf(fmaf(Gm, sS[2 * jl + 1], -pv[2 * jj + 1]), hdt, args.Bny[e]);
                             const int64_t r0 = (2 * m) * args.ldk + i;
                             if constexpr (EM == MODE_PRED) {
-                                // f = s x (B^y, -B^x, 0); s~ = s + f; h = s + f/2
+                                // f = s x (B^y, -B^x, 0); s~ = s + f
                                 const float fx = __fmul_rn(z, Bxv), fy = __fmul_rn(z, Byv);
                                 const float fz = -fmaf(x, Bxv, __fmul_rn(y, Byv));
                                 const float xp = __fadd_rn(x, fx), yp = __fadd_rn(y, fy), zp = __fadd_rn(z, fz);
                                 args.oX[e] = xp;
                                 args.oY[e] = yp;
                                 args.oZ[e] = zp;
-                                args.oHx[e] = fmaf(0.5f, fx, x);
-                                args.oHy[e] = fmaf(0.5f, fy, y);
-                                args.oHz[e] = fmaf(0.5f, fz, z);
                                 split_store(args.oHi, args.oLo, r0, xp, WITH_LO);
                                 split_store(args.oHi, args.oLo, r0 + args.ldk, yp, WITH_LO);
                                 rx[jj] = xp;
                                 ry[jj] = yp;
                                 rz[jj] = zp;
                             } else {
-                                // corrector: s' = h + f(s~)/2, then |s'| = sqrt(3)
-                                float nx = fmaf(0.5f, __fmul_rn(z, Bxv), args.Hx[e]);
-                                float ny = fmaf(0.5f, __fmul_rn(z, Byv), args.Hy[e]);
-                                float nz = fmaf(-0.5f, fmaf(x, Bxv, __fmul_rn(y, Byv)), args.Hz[e]);
+                                // corrector: s' = s + (f(s) + f(s~))/2 = (s + s~)/2 + f(s~)/2,
+                                // then |s'| = sqrt(3)
+                                const float hx = __fmul_rn(0.5f, __fadd_rn(args.X0[e], x));
+                                const float hy = __fmul_rn(0.5f, __fadd_rn(args.Y0[e], y));
+                                const float hz = __fmul_rn(0.5f, __fadd_rn(args.Z0[e], z));
+                                float nx = fmaf(0.5f, __fmul_rn(z, Bxv), hx);
+                                float ny = fmaf(0.5f, __fmul_rn(z, Byv), hy);
+                                float nz = fmaf(-0.5f, fmaf(x, Bxv, __fmul_rn(y, Byv)), hz);
                                 if (args.renorm) {
                                     const float s = sqrtf(3.0f / fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz))));
                                     nx = __fmul_rn(nx, s);
@@ -1011,7 +1011,7 @@ int tc_alloc(twa_ctx* c) {
     TcState* t = c->tc;
     t->M = c->M;
     const size_t mn = (size_t)c->M * c->N;
-    float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Hx, &t->Hy, &t->Hz, &t->Bx, &t->By};
+    float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Bx, &t->By};
     for (auto p : f)
         if (cudaMalloc(p, sizeof(float) * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc state");
     const size_t ni = sizeof(__nv_bfloat16) * 2 * (size_t)c->M * t->ldk;
@@ -1035,7 +1035,7 @@ void tc_free_run(twa_ctx* c) {
     TcState* t = c->tc;
     if (!t) return;
     mix_free(t);
-    float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Hx, &t->Hy, &t->Hz, &t->Bx, &t->By, &t->Bx1,
+    float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Bx, &t->By, &t->Bx1,
                    &t->By1, &t->XI, &t->part, &t->partp};
     for (auto p : f) {
         if (*p) cudaFree(*p);
@@ -1287,12 +1287,11 @@ int mix_build(twa_ctx* c) {
         pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z;
         pa.Bnx = bx; pa.Bny = by;
         pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
-        pa.oHx = t->Hx; pa.oHy = t->Hy; pa.oHz = t->Hz;
         pa.oHi = t->Phi; pa.oLo = t->Plo;
         pa.part_in = t->part; pa.part_out = t->partp;
         TcArgs ca = base_args(c);
         ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp;
-        ca.Hx = t->Hx; ca.Hy = t->Hy; ca.Hz = t->Hz;
+        ca.X0 = t->X; ca.Y0 = t->Y; ca.Z0 = t->Z;
         ca.Bnx = bx; ca.Bny = by;
         ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
         ca.oHi = t->Shi; ca.oLo = t->Slo;
@@ -1546,9 +1545,9 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
         la.flags = pa.flags = ca.flags = lead->d_flags;
         la.XI = t->XI; la.oBnx = t->Bx; la.oBny = t->By;
         pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z; pa.Bnx = t->Bx; pa.Bny = t->By;
-        pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp; pa.oHx = t->Hx; pa.oHy = t->Hy; pa.oHz = t->Hz;
+        pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
         pa.oHi = t->Phi; pa.oLo = t->Plo; pa.part_in = t->part; pa.part_out = t->partp;
-        ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp; ca.Hx = t->Hx; ca.Hy = t->Hy; ca.Hz = t->Hz;
+        ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp; ca.X0 = t->X; ca.Y0 = t->Y; ca.Z0 = t->Z;
         ca.Bnx = t->Bx; ca.Bny = t->By; ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
         ca.oHi = t->Shi; ca.oLo = t->Slo; ca.part_in = t->partp; ca.part_out = t->part;
         lg[p].maps = TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmE};
