@@ -30,6 +30,10 @@ constexpr int FT = 1024;                 // threads per CTA
 constexpr int64_t FFT_MAX_P = 28000;     // P complex FP32 values in shared memory (219 KB)
 constexpr int TW_LO = 128;               // two-level twiddles: w^n = hi[n / 128] lo[n % 128]
 constexpr int64_t TW_HI_MAX = (FFT_MAX_P + TW_LO - 1) / TW_LO;
+// lo entry k is stored at k + k / 16: the strided lookups n = j * step of the
+// middle stages (step a multiple of 16 or 32) then fall on distinct banks
+constexpr int TW_LO_PADDED = TW_LO + TW_LO / 16;
+__host__ __device__ constexpr int lo_slot(int k) { return k + (k >> 4); }
 
 struct FftArgs {
     int64_t N, M, P;
@@ -113,7 +117,7 @@ __device__ __forceinline__ void dft(float2* a) {
 struct Tw {
     const float2* hi;
     const float2* lo;
-    __device__ __forceinline__ float2 operator[](int64_t n) const { return cmul(hi[n >> 7], lo[n & (TW_LO - 1)]); }
+    __device__ __forceinline__ float2 operator[](int n) const { return cmul(hi[n >> 7], lo[lo_slot(n & (TW_LO - 1))]); }
 };
 
 // One stage over butterflies of radix R and stride m (span L = m R): DIF applies
@@ -205,7 +209,7 @@ __device__ Tw load_twiddles(float2* buf, const FftArgs& a) {
     float2* thi = buf + a.P;
     float2* tlo = thi + TW_HI_MAX;
     for (int64_t k = threadIdx.x; k * TW_LO < a.P; k += FT) thi[k] = a.tw[k * TW_LO];
-    for (int j = threadIdx.x; j < TW_LO; j += FT) tlo[j] = (j < a.P) ? a.tw[j] : make_float2(1.f, 0.f);
+    for (int j = threadIdx.x; j < TW_LO; j += FT) tlo[lo_slot(j)] = (j < a.P) ? a.tw[j] : make_float2(1.f, 0.f);
     return Tw{thi, tlo};
 }
 
@@ -559,7 +563,7 @@ FftArgs base_args(twa_ctx* c) {
 }
 
 // shared memory of one FFT CTA: the transform and the two twiddle tables
-size_t smem_bytes(int64_t P) { return sizeof(float2) * (size_t)(P + TW_HI_MAX + TW_LO); }
+size_t smem_bytes(int64_t P) { return sizeof(float2) * (size_t)(P + TW_HI_MAX + TW_LO_PADDED); }
 
 int set_smem(twa_ctx* c, const void* kern) {
     TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
