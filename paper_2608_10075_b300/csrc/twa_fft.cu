@@ -130,13 +130,23 @@ struct Tw {
 template <int R, bool INV, typename LD, typename ST>
 __device__ __forceinline__ void stage_io(int P, int m, const Tw tw, LD& ld, ST& st) {
     const int L = m * R, step = P / L, nb = P / R;   // P <= FFT_MAX_P: 32-bit indices
+    // butterfly u = b m + j; advancing u by FT advances (b, j) by (db, dj), with
+    // one carry: no integer division inside the loop
+    const int db = FT / m, dj = FT - db * m;
+    int b = (int)threadIdx.x / m, j = (int)threadIdx.x - b * m;
     for (int u = threadIdx.x; u < nb; u += FT) {
-        const int b = u / m, j = u - b * m, base = b * L + j;
+        const int jc = j, base = b * L + j;
+        b += db;
+        j += dj;
+        if (j >= m) {
+            j -= m;
+            ++b;
+        }
         float2 a[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) a[q] = ld(base + q * m);
         float2 w[R];
-        w[1] = tw[j * step];
+        w[1] = tw[jc * step];
 #pragma unroll
         for (int k = 2; k < R; ++k) w[k] = cmul(w[k - 1], w[1]);
         if (!INV) {
