@@ -716,27 +716,47 @@ __global__ void k_noise_tc(__nv_bfloat16* E, float* XI, int64_t M, int64_t N, in
     }
 }
 
-// Closing kernel: S^a from the corrector's partial sums (FP32, fixed order), the
-// FP64 window moments, and the step counter (last block).
+// S^a of trajectory m in FP64 from the per-row-tile partial sums, one warp per
+// trajectory: lane l adds tiles l, l + 32, ... in order, then a butterfly over
+// the lanes (a fixed order, so every run gives the same bits). All lanes
+// receive the sums.
+__device__ __forceinline__ void warp_tile_sums(const float* part, int64_t M, int64_t n_rt, int64_t m, int lane,
+                                               double& sx, double& sy, double& sz) {
+    sx = sy = sz = 0.0;
+    for (int64_t r = lane; r < n_rt; r += 32) {
+        const float4 v = *(const float4*)(part + (r * M + m) * 4);
+        sx += v.x;
+        sy += v.y;
+        sz += v.z;
+    }
+    for (int o = 16; o; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+}
+
+// Window moments S^z, A, A^2, A S^z, (S^z)^2 of one trajectory (A = |S^x + i S^y|^2 / 4).
+__device__ __forceinline__ void add_moments(double* mm, double sx, double sy, double sz) {
+    const double A = 0.25 * (sx * sx + sy * sy);
+    mm[0] += sz;
+    mm[1] += A;
+    mm[2] += A * A;
+    mm[3] += A * sz;
+    mm[4] += sz * sz;
+}
+
+// Closing kernel: S^a from the corrector's partial sums (one warp per
+// trajectory), the FP64 window moments, and the step counter (last block).
 __global__ void k_close_tc(const float* part, int64_t M, int64_t n_rt, double* mom, int64_t* d_t, int64_t n_window,
                            int64_t* d_count, unsigned long long* flags) {
-    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t t1 = *d_t + 1;
-    if (m < M && t1 > n_window) {
-        double sx = 0, sy = 0, sz = 0;
-        for (int64_t r = 0; r < n_rt; ++r) {
-            const float4 v = *(const float4*)(part + (r * M + m) * 4);
-            sx += v.x;
-            sy += v.y;
-            sz += v.z;
-        }
-        const double A = 0.25 * (sx * sx + sy * sy);
-        double* mm = mom + 5 * m;
-        mm[0] += sz;
-        mm[1] += A;
-        mm[2] += A * A;
-        mm[3] += A * sz;
-        mm[4] += sz * sz;
+    if (m < M && t1 > n_window) {   // warp-uniform
+        double sx, sy, sz;
+        warp_tile_sums(part, M, n_rt, m, lane, sx, sy, sz);
+        if (lane == 0) add_moments(mom + 5 * m, sx, sy, sz);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -796,26 +816,15 @@ __global__ void k_noise_group(const StepDesc* sd, const int64_t* start, int n) {
 
 // Window moments of every problem (start = prefix of M); counters advance later.
 __global__ void k_close_group(const StepDesc* sd, const int64_t* start, int n) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;   // one warp per trajectory
     if (e >= start[n]) return;
     const int p = find_problem(start, n, e);
     const StepDesc& d = sd[p];
     const int64_t m = e - start[p];
     if (*d.d_t + 1 <= d.n_window) return;
-    double sx = 0, sy = 0, sz = 0;
-    for (int64_t r = 0; r < d.n_rt; ++r) {
-        const float4 v = *(const float4*)(d.part + (r * d.M + m) * 4);
-        sx += v.x;
-        sy += v.y;
-        sz += v.z;
-    }
-    const double A = 0.25 * (sx * sx + sy * sy);
-    double* mm = d.mom + 5 * m;
-    mm[0] += sz;
-    mm[1] += A;
-    mm[2] += A * A;
-    mm[3] += A * sz;
-    mm[4] += sz * sz;
+    double sx, sy, sz;
+    warp_tile_sums(d.part, d.M, d.n_rt, m, threadIdx.x & 31, sx, sy, sz);
+    if ((threadIdx.x & 31) == 0) add_moments(d.mom + 5 * m, sx, sy, sz);
 }
 
 __global__ void k_advance_group(const StepDesc* sd, int n) {
@@ -1438,7 +1447,7 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
     }
     {
         ProfScope p(c, TWA_PROF_CLOSE);
-        k_close_tc<<<nblk(M, 256), 256, 0, c->stream>>>(ts->part, M, ts->n_rt, c->mom, c->d_t, c->n_window,
+        k_close_tc<<<nblk(32 * M, 256), 256, 0, c->stream>>>(ts->part, M, ts->n_rt, c->mom, c->d_t, c->n_window,
                                                         c->d_count, c->d_flags);
     }
     TWA_CUDA(c, cudaGetLastError());
@@ -1601,7 +1610,7 @@ int tc_batch_step(twa_ctx* lead, TcBatch* b) {
     rc = b->x3 ? launch_cfg<MODE_CORR, 3>(lead, none, b->flag_args, Group{b->cg, b->tstart, b->n}, b->tiles)
                : launch_cfg<MODE_CORR, 1>(lead, none, b->flag_args, Group{b->cg, b->tstart, b->n}, b->tiles);
     if (rc) return rc;
-    k_close_group<<<nblk(b->traj, 256), 256, 0, lead->stream>>>(b->sd, b->mstart, b->n);
+    k_close_group<<<nblk(32 * b->traj, 256), 256, 0, lead->stream>>>(b->sd, b->mstart, b->n);
     k_advance_group<<<nblk(b->n, 128), 128, 0, lead->stream>>>(b->sd, b->n);
     TWA_CUDA(lead, cudaGetLastError());
     return TWA_OK;
