@@ -74,9 +74,11 @@ int time_batch(std::vector<twa_ctx*>& ctx, int steps, float* ms) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    rc = twa::tc_batch_step(lead, b);   // untimed: first launch of this configuration
+    // the contexts sit at step 0 (trials run between snapshot and restore)
+    rc = twa::tc_batch_prime(lead, b, 0);
+    if (!rc) rc = twa::tc_batch_step(lead, b, 0);   // untimed: first launch of this configuration
     cudaEventRecord(e0, lead->stream);
-    for (int s = 0; s < steps && !rc; ++s) rc = twa::tc_batch_step(lead, b);
+    for (int s = 1; s <= steps && !rc; ++s) rc = twa::tc_batch_step(lead, b, s);
     cudaEventRecord(e1, lead->stream);
     cudaEventSynchronize(e1);
     cudaEventElapsedTime(ms, e0, e1);
@@ -114,36 +116,51 @@ int autotune(std::vector<twa_ctx*>& ctx, int* bn, int* kc) {
     return set_tiles_all(ctx, *bn, *kc);
 }
 
-// Run `reps` steps of the running points as replays of one captured step.
-int run_stage(std::vector<twa_ctx*>& active, int64_t reps, cudaStream_t cap) {
+// Run steps t0 .. t0 + reps - 1 of the running points as replays of the
+// captured step of each parity. At t0 = 0 the noise part of the first step is
+// computed first; later stages find it in place (the previous stage's last step
+// computed it for every point, the finished ones included).
+int run_stage(std::vector<twa_ctx*>& active, int64_t t0, int64_t reps, cudaStream_t cap) {
     twa_ctx* lead = active[0];
     twa::TcBatch* b = nullptr;
     int rc = twa::tc_batch_build(active.data(), (int)active.size(), lead, &b);
     if (rc) return rc;
+    if (t0 == 0 && (rc = twa::tc_batch_prime(lead, b, 0))) {
+        twa::tc_batch_free(b);
+        return rc;
+    }
     cudaStream_t saved = lead->stream;
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
+    cudaGraph_t g[2] = {nullptr, nullptr};
+    cudaGraphExec_t ge[2] = {nullptr, nullptr};
     lead->stream = cap;
-    bool graph = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    if (graph) {
-        rc = twa::tc_batch_step(lead, b);
-        graph = cudaStreamEndCapture(cap, &g) == cudaSuccess && rc == TWA_OK &&
-                cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    bool graph = true;
+    for (int k = 0; k < 2 && graph; ++k) {
+        const int64_t t = t0 + k;
+        graph = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (graph) {
+            rc = twa::tc_batch_step(lead, b, t);
+            graph = cudaStreamEndCapture(cap, &g[k]) == cudaSuccess && rc == TWA_OK &&
+                    cudaGraphInstantiate(&ge[k], g[k], 0) == cudaSuccess;
+        }
     }
     lead->stream = saved;
     cudaGetLastError();
     rc = TWA_OK;
     for (int64_t s = 0; s < reps && rc == TWA_OK; ++s) {
+        const int64_t t = t0 + s;
         if (graph) {
-            if (cudaGraphLaunch(ge, lead->stream) != cudaSuccess) rc = twa::set_error(lead, TWA_ECUDA, "cudaGraphLaunch");
+            if (cudaGraphLaunch(ge[(t - t0) & 1], lead->stream) != cudaSuccess)
+                rc = twa::set_error(lead, TWA_ECUDA, "cudaGraphLaunch");
         } else {
-            rc = twa::tc_batch_step(lead, b);   // capture unavailable: launch directly
+            rc = twa::tc_batch_step(lead, b, t);   // capture unavailable: launch directly
         }
     }
     if (cudaStreamSynchronize(lead->stream) != cudaSuccess && rc == TWA_OK)
         rc = twa::set_error(lead, TWA_ECUDA, "batch stage failed");
-    if (ge) cudaGraphExecDestroy(ge);
-    if (g) cudaGraphDestroy(g);
+    for (int k = 0; k < 2; ++k) {
+        if (ge[k]) cudaGraphExecDestroy(ge[k]);
+        if (g[k]) cudaGraphDestroy(g[k]);
+    }
     twa::tc_batch_free(b);
     return rc;
 }
@@ -213,7 +230,7 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
         std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return pts[a].N > pts[b].N; });
         std::vector<twa_ctx*> active;
         for (int p : idx) active.push_back(ctx[p]);
-        if ((rc = run_stage(active, end - done, cap))) {
+        if ((rc = run_stage(active, done, end - done, cap))) {
             set_error(nullptr, rc, active[0]->err);
             cudaStreamDestroy(cap);
             return cleanup(rc);

@@ -262,7 +262,8 @@ int tc_set_extra_matrix(twa_ctx* c, int slot, const double* A64);   // slot 0 or
 // batches of contexts advanced by grouped launches (twa_tc.cu)
 struct TcBatch;
 int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out);
-int tc_batch_step(twa_ctx* lead, TcBatch* b);   // one step of every context: 6 launches
+int tc_batch_prime(twa_ctx* lead, TcBatch* b, int64_t t);   // noise part of the batch's first step t
+int tc_batch_step(twa_ctx* lead, TcBatch* b, int64_t t);    // step t of every context: 5 launches
 void tc_batch_free(TcBatch* b);
 int tc_set_tiles(twa_ctx* c, int bn, int kc);
 // twa_fft.cu

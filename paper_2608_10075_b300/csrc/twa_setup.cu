@@ -178,8 +178,9 @@ __global__ void k_lanczos_update(double* y, const double* v, const double* vprev
     }
 }
 
-// Sturm-count bisection on the Lanczos tridiagonal for its extreme eigenvalues.
-// The recurrence is cut at the first beta below tol (an invariant subspace).
+// Number of eigenvalues of the leading k x k Lanczos tridiagonal below x (Sturm
+// sequence of the LDL^T pivots). The recurrence is cut at the first beta below
+// tol (an invariant subspace) by the caller.
 __device__ int sturm_count(const double* a, const double* b, int k, double x) {
     int cnt = 0;
     double d = 1.0;
@@ -192,32 +193,53 @@ __device__ int sturm_count(const double* a, const double* b, int k, double x) {
     return cnt;
 }
 
-__global__ void k_tridiag_extremes(const double* a, const double* b, int kmax, double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double amax = 0.0;
-    for (int j = 0; j < kmax; ++j) amax = fmax(amax, fabs(a[j]));
-    int k = kmax;
-    for (int j = 0; j < kmax - 1; ++j)
-        if (b[j] <= 1e-12 * fmax(amax, 1e-300)) { k = j + 1; break; }
-    double lo = INFINITY, hi = -INFINITY;
-    for (int j = 0; j < k; ++j) {
-        const double r = (j > 0 ? fabs(b[j - 1]) : 0.0) + (j < k - 1 ? fabs(b[j]) : 0.0);
-        lo = fmin(lo, a[j] - r);
-        hi = fmax(hi, a[j] + r);
+// Extreme eigenvalues of the tridiagonal by multisection of Sturm counts: in
+// each round the block's threads evaluate the count at as many interior points
+// of the bracket, which then shrinks to the sub-interval where the count first
+// reaches the target (1 for the smallest eigenvalue, k for the largest): a
+// factor blockDim + 1 per round, so 8 rounds reach FP64 resolution.
+__global__ void __launch_bounds__(1024) k_tridiag_extremes(const double* a, const double* b, int kmax,
+                                                           double* out) {
+    __shared__ int s_k, s_first;
+    __shared__ double s_lo, s_hi;
+    if (threadIdx.x == 0) {
+        double amax = 0.0;
+        for (int j = 0; j < kmax; ++j) amax = fmax(amax, fabs(a[j]));
+        int k = kmax;
+        for (int j = 0; j < kmax - 1; ++j)
+            if (b[j] <= 1e-12 * fmax(amax, 1e-300)) { k = j + 1; break; }
+        double lo = INFINITY, hi = -INFINITY;   // Gershgorin bracket
+        for (int j = 0; j < k; ++j) {
+            const double r = (j > 0 ? fabs(b[j - 1]) : 0.0) + (j < k - 1 ? fabs(b[j]) : 0.0);
+            lo = fmin(lo, a[j] - r);
+            hi = fmax(hi, a[j] + r);
+        }
+        s_k = k;
+        s_lo = lo;
+        s_hi = hi;
     }
-    // smallest: largest x with count(x) == 0
-    double l = lo, h = hi;
-    for (int it = 0; it < 200; ++it) {
-        const double m = 0.5 * (l + h);
-        if (sturm_count(a, b, k, m) >= 1) h = m; else l = m;
+    __syncthreads();
+    const int k = s_k;
+    const double T1 = (double)(blockDim.x + 1);
+    for (int which = 0; which < 2; ++which) {
+        const int target = (which == 0) ? 1 : k;
+        double l = s_lo, h = s_hi;
+        for (int round = 0; round < 8; ++round) {
+            const double x = l + (h - l) * (double)(threadIdx.x + 1) / T1;
+            if (threadIdx.x == 0) s_first = blockDim.x;
+            __syncthreads();
+            if (sturm_count(a, b, k, x) >= target) atomicMin(&s_first, (int)threadIdx.x);
+            __syncthreads();
+            const int f = s_first;
+            // the count reaches the target in (x_{f-1}, x_f], x_{-1} = l, x_T = h
+            const double nl = (f == 0) ? l : l + (h - l) * (double)f / T1;
+            const double nh = (f == (int)blockDim.x) ? h : l + (h - l) * (double)(f + 1) / T1;
+            l = nl;
+            h = nh;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[which == 0 ? 1 : 0] = 0.5 * (l + h);
     }
-    out[1] = 0.5 * (l + h);
-    l = lo; h = hi;
-    for (int it = 0; it < 200; ++it) {
-        const double m = 0.5 * (l + h);
-        if (sturm_count(a, b, k, m) >= k) h = m; else l = m;
-    }
-    out[0] = 0.5 * (l + h);
 }
 
 __global__ void k_rescale(double* v, int64_t N, const double* nrm2) {
@@ -301,7 +323,7 @@ int setup_pump(twa_ctx* c) {
         k_lanczos_update<<<1, 1024, 0, st>>>(y, vc, vp, vn, al, be, j, N);
         double* t = vp; vp = vc; vc = vn; vn = t;
     }
-    k_tridiag_extremes<<<1, 1, 0, st>>>(al, be, kmax, ext);
+    k_tridiag_extremes<<<1, 1024, 0, st>>>(al, be, kmax, ext);
     TWA_CUDA(c, cudaGetLastError());
     double e2[2];
     TWA_CUDA(c, cudaMemcpyAsync(e2, ext, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));

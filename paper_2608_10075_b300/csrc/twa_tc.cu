@@ -795,8 +795,8 @@ __device__ __forceinline__ int find_problem(const int64_t* start, int n, int64_t
     return lo;
 }
 
-// Noise of every problem's current step (start = prefix of M (N + 1)).
-__global__ void k_noise_group(const StepDesc* sd, const int64_t* start, int n) {
+// Noise of every problem's step *d_t + toff (start = prefix of M (N + 1)).
+__global__ void k_noise_group(const StepDesc* sd, const int64_t* start, int n, int64_t toff) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= start[n]) return;
     const int p = find_problem(start, n, e);
@@ -804,7 +804,7 @@ __global__ void k_noise_group(const StepDesc* sd, const int64_t* start, int n) {
     const int64_t el = e - start[p], NP = d.N + 1;
     const int64_t m = el / NP, i = el - m * NP;
     float gx, gy;
-    normal2_f32(d.seed, (uint32_t)(d.m0 + m), (uint32_t)(*d.d_t), (uint32_t)i, gx, gy);
+    normal2_f32(d.seed, (uint32_t)(d.m0 + m), (uint32_t)(*d.d_t + toff), (uint32_t)i, gx, gy);
     if (i < d.N) {
         d.E[(2 * m) * d.ldk + i] = __float2bfloat16_rn(gx);
         d.E[(2 * m + 1) * d.ldk + i] = __float2bfloat16_rn(gy);
@@ -1148,26 +1148,32 @@ int tc_init_state(twa_ctx* c) {
 // so the triangular L.eta needs no launch of its own and fills the tails of the
 // two W.s launches.
 struct MixPlan {
-    GroupDesc* desc = nullptr;                // [parity of t][launch][W problem, L.eta problem]
-    int64_t* start = nullptr;                 // {0, W tiles, W tiles + L.eta tiles}
+    int nprob = 0;                            // 3 x problems: predictor, corrector, L.eta blocks
+    GroupDesc* desc = nullptr;                // [parity of t][predictor | corrector | L.eta][problem]
+    int64_t* start = nullptr;                 // [nprob + 1] first flat tile of each problem
+    int64_t* lstart = nullptr;                // [problems + 1] tile prefix within the L.eta block
     int32_t* list[2] = {nullptr, nullptr};    // per launch: flat tiles, CTA after CTA
     int32_t* first[2] = {nullptr, nullptr};   // per launch: [ctas + 1] offsets into list
     int ctas[2] = {0, 0};
     int64_t tiles[2] = {0, 0};
     double flops[2] = {0.0, 0.0};             // algorithmic tensor-core FLOPs per launch
-    double leta_flops = 0.0, w_flops = 0.0;   // of a standalone L.eta or W.s launch
+    double leta_flops = 0.0, w_flops = 0.0;   // of all L.eta tiles / all W.s tiles of one stage
+    int64_t leta_tiles = 0;                   // tiles of the L.eta block
     std::vector<GroupDesc> host;              // host copy of desc
 };
 
 namespace {
 
-void mix_free(TcState* t) {
-    MixPlan* p = t->mix;
+void mix_plan_free(MixPlan* p) {
     if (!p) return;
-    void* q[] = {p->desc, p->start, p->list[0], p->list[1], p->first[0], p->first[1]};
+    void* q[] = {p->desc, p->start, p->lstart, p->list[0], p->list[1], p->first[0], p->first[1]};
     for (void* x : q)
         if (x) cudaFree(x);
     delete p;
+}
+
+void mix_free(TcState* t) {
+    mix_plan_free(t->mix);
     t->mix = nullptr;
     t->bn_ready = -1;
 }
@@ -1207,127 +1213,171 @@ int64_t lpt_schedule(std::vector<std::pair<int64_t, int32_t>> jobs, int ctas, st
     return span;
 }
 
-int mix_build(twa_ctx* c) {
-    TcState* t = c->tc;
-    const int64_t M = c->M, N = c->N, MN = M * N;
-    const int bn = t->bn, bk = t->kc == 0 ? KCfg<0>::BK : KCfg<1>::BK;
-    const int ntw = t->terms, ntl = t->terms == 3 ? 2 : 1;
-    const int64_t nct = (2 * M + bn - 1) / bn, nk = (N + bk - 1) / bk;
-    const int64_t Tw = t->n_rt * nct, Tl = Tw;
-    if (Tw + Tl > INT32_MAX) return set_error(c, TWA_EUNSUPPORTED, "dense step: too many tiles");
-    if (!t->Bx1 && (cudaMalloc(&t->Bx1, sizeof(float) * MN) != cudaSuccess ||
-                    cudaMalloc(&t->By1, sizeof(float) * MN) != cudaSuccess))
-        return set_error(c, TWA_ENOMEM, "cudaMalloc noise part");
+// Descriptor table and the two launches' tile schedules of the dense step for
+// n problems advanced together (n = 1: one context; n > 1: a batched scan). Per
+// parity of the step index, the table holds the W.s + predictor problems, the
+// W.s~ + corrector problems and the L.eta problems of step t + 1; launch 1 runs
+// the predictor tiles and the longest L.eta tiles, launch 2 the corrector tiles
+// and the rest, each placed on the CTAs by longest-first list scheduling.
+int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
+    const TcState* t0 = cs[0]->tc;
+    const int bn = t0->bn, bk = t0->kc == 0 ? KCfg<0>::BK : KCfg<1>::BK;
+    const int ntw = t0->terms, ntl = t0->terms == 3 ? 2 : 1;
+    const int nprob = 3 * n;
+    p->nprob = nprob;
+    // flat tile ranges: [W.s + predictor of 0..n-1][W.s~ + corrector][L.eta]
+    std::vector<int64_t> st(nprob + 1, 0), nct(n), nk(n);
+    for (int q = 0; q < n; ++q) {
+        const TcState* t = cs[q]->tc;
+        nct[q] = (2 * cs[q]->M + bn - 1) / bn;
+        nk[q] = (cs[q]->N + bk - 1) / bk;
+        const int64_t T = t->n_rt * nct[q];
+        st[q + 1] = T;
+        st[n + q + 1] = T;
+        st[2 * n + q + 1] = T;
+    }
+    for (int k = 0; k < nprob; ++k) st[k + 1] += st[k];
+    if (st[nprob] > INT32_MAX) return set_error(ec, TWA_EUNSUPPORTED, "dense step: too many tiles");
+    for (int q = 0; q < n; ++q) {
+        TcState* t = cs[q]->tc;
+        const size_t mn = sizeof(float) * cs[q]->M * cs[q]->N;
+        if (!t->Bx1 && (cudaMalloc(&t->Bx1, mn) != cudaSuccess || cudaMalloc(&t->By1, mn) != cudaSuccess))
+            return set_error(ec, TWA_ENOMEM, "cudaMalloc noise part");
+    }
 
     // tile costs in K stages x products; algorithmic FLOPs per tile
-    auto rows_of = [&](int64_t rt) { return std::min<int64_t>(BM, N - rt * BM); };
-    auto cols_of = [&](int64_t ct) { return (double)std::min<int64_t>(bn, 2 * M - ct * bn); };
-    std::vector<std::pair<int64_t, int32_t>> wjobs, ljobs;
-    std::vector<double> fl(Tw + Tl);
-    for (int64_t x = 0; x < Tw; ++x) {
-        const int64_t rt = x / nct, ct = x - rt * nct;
-        wjobs.push_back({nk * ntw, (int32_t)x});
-        fl[x] = 2.0 * rows_of(rt) * (double)N * cols_of(ct) * ntw;
-    }
-    for (int64_t x = 0; x < Tl; ++x) {
-        const int64_t rt = t->n_rt - 1 - x / nct, ct = x % nct;   // the kernel's L.eta tile order
-        const int64_t k1 = std::min<int64_t>((rt * BM + BM + bk - 1) / bk, nk);
-        ljobs.push_back({k1 * ntl, (int32_t)(Tw + x)});
-        const double r0 = (double)(rt * BM), r1 = r0 + rows_of(rt);
-        fl[Tw + x] = 2.0 * ((r1 * (r1 + 1) - r0 * (r0 + 1)) / 2.0) * cols_of(ct) * ntl;   // lower triangle
+    std::vector<std::pair<int64_t, int32_t>> pjobs, cjobs, ljobs;
+    std::vector<double> fl(st[nprob]);
+    for (int q = 0; q < n; ++q) {
+        const int64_t N = cs[q]->N, M = cs[q]->M, n_rt = cs[q]->tc->n_rt;
+        auto rows_of = [&](int64_t rt) { return std::min<int64_t>(BM, N - rt * BM); };
+        auto cols_of = [&](int64_t ct) { return (double)std::min<int64_t>(bn, 2 * M - ct * bn); };
+        for (int64_t x = 0; x < st[q + 1] - st[q]; ++x) {
+            const int64_t rt = x / nct[q], ct = x - rt * nct[q];
+            const double f = 2.0 * rows_of(rt) * (double)N * cols_of(ct) * ntw;
+            pjobs.push_back({nk[q] * ntw, (int32_t)(st[q] + x)});
+            cjobs.push_back({nk[q] * ntw, (int32_t)(st[n + q] + x)});
+            fl[st[q] + x] = fl[st[n + q] + x] = f;
+            // the kernel hands out L.eta row tiles longest first
+            const int64_t lrt = n_rt - 1 - rt;
+            const int64_t k1 = std::min<int64_t>((lrt * BM + BM + bk - 1) / bk, nk[q]);
+            const double r0 = (double)(lrt * BM), r1 = r0 + rows_of(lrt);
+            ljobs.push_back({k1 * ntl, (int32_t)(st[2 * n + q] + x)});
+            fl[st[2 * n + q] + x] = 2.0 * ((r1 * (r1 + 1) - r0 * (r0 + 1)) / 2.0) * cols_of(ct) * ntl;   // triangle
+        }
     }
     std::stable_sort(ljobs.begin(), ljobs.end(),
                      [](const std::pair<int64_t, int32_t>& a, const std::pair<int64_t, int32_t>& b) {
                          return a.first > b.first;
                      });
     // the predictor's launch takes the kl longest L.eta tiles, the corrector's the rest
-    auto ctas_for = [&](int64_t n) { return (int)std::min<int64_t>(n, t->num_sms); };
+    const int sms = t0->num_sms;
+    auto ctas_for = [&](int64_t k) { return (int)std::min<int64_t>(k, sms); };
+    const int64_t Tl = (int64_t)ljobs.size();
     auto span_of = [&](int64_t kl) {
-        std::vector<std::pair<int64_t, int32_t>> a(wjobs), b(wjobs);
+        std::vector<std::pair<int64_t, int32_t>> a(pjobs), b(cjobs);
         a.insert(a.end(), ljobs.begin(), ljobs.begin() + kl);
         b.insert(b.end(), ljobs.begin() + kl, ljobs.end());
         return lpt_schedule(a, ctas_for((int64_t)a.size()), nullptr, nullptr) +
                lpt_schedule(b, ctas_for((int64_t)b.size()), nullptr, nullptr);
     };
-    const int64_t stride = std::max<int64_t>(1, Tl / 256);
+    // coarse search over 32 split points, then a finer one around the best
     int64_t best_k = 0, best = span_of(0);
-    for (int64_t kl = stride; kl <= Tl; kl += stride) {
-        const int64_t s = span_of(kl);
-        if (s < best) best = s, best_k = kl;
-    }
+    auto scan = [&](int64_t lo, int64_t hi, int64_t stride) {
+        for (int64_t kl = lo; kl <= hi; kl += stride) {
+            const int64_t s = span_of(kl);
+            if (s < best) best = s, best_k = kl;
+        }
+    };
+    const int64_t coarse = std::max<int64_t>(1, Tl / 32);
+    scan(coarse, Tl, coarse);
+    const int64_t fine = std::max<int64_t>(1, coarse / 16);
+    scan(std::max<int64_t>(0, best_k - coarse), std::min<int64_t>(Tl, best_k + coarse), fine);
 
-    MixPlan* p = new MixPlan();
-    t->mix = p;
     std::vector<int32_t> lists[2], firsts[2];
-    std::vector<int> seen(Tw + Tl, 0);
+    std::vector<int> seen(st[nprob], 0);
     for (int L = 0; L < 2; ++L) {
-        std::vector<std::pair<int64_t, int32_t>> jobs(wjobs);
+        std::vector<std::pair<int64_t, int32_t>> jobs(L == 0 ? pjobs : cjobs);
         if (L == 0) jobs.insert(jobs.end(), ljobs.begin(), ljobs.begin() + best_k);
         else jobs.insert(jobs.end(), ljobs.begin() + best_k, ljobs.end());
         p->ctas[L] = ctas_for((int64_t)jobs.size());
         p->tiles[L] = (int64_t)jobs.size();
         lpt_schedule(jobs, p->ctas[L], &lists[L], &firsts[L]);
+        // each CTA walks its tiles in flat order: a problem's tiles stay together
+        // (fewer descriptor switches, W rows reused while in L2)
+        for (int c = 0; c < p->ctas[L]; ++c)
+            std::sort(lists[L].begin() + firsts[L][c], lists[L].begin() + firsts[L][c + 1]);
         for (int32_t x : lists[L]) {
             p->flops[L] += fl[x];
-            seen[x] += (x < Tw) ? 1 : 2;
+            ++seen[x];
         }
     }
-    for (int64_t x = Tl; x-- > 0;) p->leta_flops += fl[Tw + x];
-    for (int64_t x = Tw; x-- > 0;) p->w_flops += fl[x];
-    // every W tile in both launches, every L.eta tile in exactly one
-    for (int64_t x = 0; x < Tw + Tl; ++x)
-        if (seen[x] != 2) return set_error(c, TWA_EUNSUPPORTED, "dense step: internal error in the tile schedule");
+    for (int64_t x = st[2 * n]; x < st[nprob]; ++x) p->leta_flops += fl[x];
+    p->leta_tiles = st[nprob] - st[2 * n];
+    for (int64_t x = 0; x < st[n]; ++x) p->w_flops += fl[x];
+    // every tile in exactly one launch
+    for (int64_t x = 0; x < st[nprob]; ++x)
+        if (seen[x] != 1) return set_error(ec, TWA_EUNSUPPORTED, "dense step: internal error in the tile schedule");
 
-    // descriptors: [parity][launch][problem]
-    const TcMaps lm{t->tmLhi, t->tmLlo, t->tmE, t->tmE};
-    const TcMaps pm{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo};
-    const TcMaps cm{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo};
-    std::vector<GroupDesc> d(8);
+    // descriptors: [parity of t][predictor | corrector | L.eta][problem]
+    std::vector<GroupDesc> d(2 * nprob);
     for (int par = 0; par < 2; ++par) {
-        float* bx = par ? t->Bx1 : t->Bx;   // noise part of step t (this parity)
-        float* by = par ? t->By1 : t->By;
-        float* nx = par ? t->Bx : t->Bx1;   // ... and of step t + 1
-        float* ny = par ? t->By : t->By1;
-        TcArgs la = base_args(c);
-        la.XI = t->XI;
-        la.oBnx = nx;
-        la.oBny = ny;
-        TcArgs pa = base_args(c);
-        pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z;
-        pa.Bnx = bx; pa.Bny = by;
-        pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
-        pa.oHi = t->Phi; pa.oLo = t->Plo;
-        pa.part_in = t->part; pa.part_out = t->partp;
-        TcArgs ca = base_args(c);
-        ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp;
-        ca.X0 = t->X; ca.Y0 = t->Y; ca.Z0 = t->Z;
-        ca.Bnx = bx; ca.Bny = by;
-        ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
-        ca.oHi = t->Shi; ca.oLo = t->Slo;
-        ca.part_in = t->partp; ca.part_out = t->part;
-        GroupDesc* g = &d[4 * par];
-        g[0] = GroupDesc{pm, pa, MODE_PRED};
-        g[1] = GroupDesc{lm, la, MODE_LETA};
-        g[2] = GroupDesc{cm, ca, MODE_CORR};
-        g[3] = GroupDesc{lm, la, MODE_LETA};
+        for (int q = 0; q < n; ++q) {
+            twa_ctx* c = cs[q];
+            TcState* t = c->tc;
+            float* bx = par ? t->Bx1 : t->Bx;   // noise part of step t (this parity)
+            float* by = par ? t->By1 : t->By;
+            float* nx = par ? t->Bx : t->Bx1;   // ... and of step t + 1
+            float* ny = par ? t->By : t->By1;
+            TcArgs la = base_args(c), pa = base_args(c), ca = base_args(c);
+            la.flags = pa.flags = ca.flags = ec->d_flags;
+            la.XI = t->XI;
+            la.oBnx = nx;
+            la.oBny = ny;
+            pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z;
+            pa.Bnx = bx; pa.Bny = by;
+            pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
+            pa.oHi = t->Phi; pa.oLo = t->Plo;
+            pa.part_in = t->part; pa.part_out = t->partp;
+            ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp;
+            ca.X0 = t->X; ca.Y0 = t->Y; ca.Z0 = t->Z;
+            ca.Bnx = bx; ca.Bny = by;
+            ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
+            ca.oHi = t->Shi; ca.oLo = t->Slo;
+            ca.part_in = t->partp; ca.part_out = t->part;
+            GroupDesc* g = &d[par * nprob];
+            g[q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo}, pa, MODE_PRED};
+            g[n + q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo}, ca, MODE_CORR};
+            g[2 * n + q] = GroupDesc{TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmE}, la, MODE_LETA};
+        }
     }
     p->host = d;
-    const int64_t st[3] = {0, Tw, Tw + Tl};
-    bool ok = cudaMalloc(&p->desc, sizeof(GroupDesc) * 8) == cudaSuccess &&
-              cudaMalloc(&p->start, sizeof(st)) == cudaSuccess;
+    std::vector<int64_t> lst(n + 1);
+    for (int q = 0; q <= n; ++q) lst[q] = st[2 * n + q] - st[2 * n];
+    bool ok = cudaMalloc(&p->desc, sizeof(GroupDesc) * d.size()) == cudaSuccess &&
+              cudaMalloc(&p->start, sizeof(int64_t) * st.size()) == cudaSuccess &&
+              cudaMalloc(&p->lstart, sizeof(int64_t) * lst.size()) == cudaSuccess;
     for (int L = 0; L < 2 && ok; ++L)
         ok = cudaMalloc(&p->list[L], sizeof(int32_t) * lists[L].size()) == cudaSuccess &&
              cudaMalloc(&p->first[L], sizeof(int32_t) * firsts[L].size()) == cudaSuccess;
-    if (!ok) return set_error(c, TWA_ENOMEM, "cudaMalloc dense step plan");
-    ok = cudaMemcpy(p->desc, d.data(), sizeof(GroupDesc) * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(p->start, st, sizeof(st), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) return set_error(ec, TWA_ENOMEM, "cudaMalloc dense step plan");
+    ok = cudaMemcpy(p->desc, d.data(), sizeof(GroupDesc) * d.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->start, st.data(), sizeof(int64_t) * st.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->lstart, lst.data(), sizeof(int64_t) * lst.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     for (int L = 0; L < 2 && ok; ++L)
         ok = cudaMemcpy(p->list[L], lists[L].data(), sizeof(int32_t) * lists[L].size(), cudaMemcpyHostToDevice) ==
                  cudaSuccess &&
              cudaMemcpy(p->first[L], firsts[L].data(), sizeof(int32_t) * firsts[L].size(),
                         cudaMemcpyHostToDevice) == cudaSuccess;
-    if (!ok) return set_error(c, TWA_ECUDA, "dense step plan upload failed");
+    if (!ok) return set_error(ec, TWA_ECUDA, "dense step plan upload failed");
     return TWA_OK;
+}
+
+int mix_build(twa_ctx* c) {
+    MixPlan* p = new MixPlan();
+    c->tc->mix = p;
+    twa_ctx* cs[1] = {c};
+    return mix_plan_build(cs, 1, c, p);
 }
 
 }  // namespace
@@ -1415,7 +1465,7 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         // the same tiles as four separate launches: noise, L.eta, W.s + predictor,
         // W.s~ + corrector (bit-identical results)
         if ((rc = noise_part_alone(c, t))) return rc;
-        const GroupDesc* h = mp->host.data() + 4 * (t & 1);
+        const GroupDesc* h = mp->host.data() + 3 * (t & 1);   // predictor, corrector, L.eta
         {
             ProfScope p(c, TWA_PROF_PREDICT, mp->w_flops);
             rc = x3 ? launch_cfg<MODE_PRED, 3>(c, h[0].maps, h[0].args)
@@ -1424,8 +1474,8 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         if (rc) return rc;
         {
             ProfScope p(c, TWA_PROF_CORRECT, mp->w_flops);
-            rc = x3 ? launch_cfg<MODE_CORR, 3>(c, h[2].maps, h[2].args)
-                    : launch_cfg<MODE_CORR, 1>(c, h[2].maps, h[2].args);
+            rc = x3 ? launch_cfg<MODE_CORR, 3>(c, h[1].maps, h[1].args)
+                    : launch_cfg<MODE_CORR, 1>(c, h[1].maps, h[1].args);
         }
         if (rc) return rc;
     } else {
@@ -1436,9 +1486,9 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         }
         const TcMaps none{};
         const TcArgs fa = base_args(c);   // flags of the launch
-        const GroupDesc* dp = mp->desc + 4 * (t & 1);
+        const GroupDesc* dp = mp->desc + mp->nprob * (t & 1);
         for (int L = 0; L < 2; ++L) {
-            const Group g{dp + 2 * L, mp->start, 2, mp->list[L], mp->first[L], mp->ctas[L]};
+            const Group g{dp, mp->start, mp->nprob, mp->list[L], mp->first[L], mp->ctas[L]};
             ProfScope p(c, L == 0 ? TWA_PROF_PREDICT : TWA_PROF_CORRECT, mp->flops[L]);
             rc = x3 ? launch_cfg<MODE_MIX, 3>(c, none, fa, g, mp->tiles[L])
                     : launch_cfg<MODE_MIX, 1>(c, none, fa, g, mp->tiles[L]);
@@ -1519,16 +1569,17 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
 struct TcBatch {
     int n = 0;
     bool x3 = true;
-    int64_t tiles = 0, noise_elems = 0, traj = 0;
-    GroupDesc *lg = nullptr, *pg = nullptr, *cg = nullptr;   // device descriptor tables
+    int64_t noise_elems = 0, traj = 0;
+    MixPlan* mix = nullptr;   // the mixed launches of all problems
     StepDesc* sd = nullptr;
-    int64_t *tstart = nullptr, *nstart = nullptr, *mstart = nullptr;
+    int64_t *nstart = nullptr, *mstart = nullptr;
     TcArgs flag_args{};
 };
 
 void tc_batch_free(TcBatch* b) {
     if (!b) return;
-    void* p[] = {b->lg, b->pg, b->cg, b->sd, b->tstart, b->nstart, b->mstart};
+    mix_plan_free(b->mix);
+    void* p[] = {b->sd, b->nstart, b->mstart};
     for (void* q : p)
         if (q) cudaFree(q);
     delete b;
@@ -1539,9 +1590,8 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
     TcBatch* b = new TcBatch();
     b->n = n;
     b->x3 = lead->tc->terms == 3;
-    std::vector<GroupDesc> lg(n), pg(n), cg(n);
     std::vector<StepDesc> sd(n);
-    std::vector<int64_t> ts(n + 1, 0), ns(n + 1, 0), ms(n + 1, 0);
+    std::vector<int64_t> ns(n + 1, 0), ms(n + 1, 0);
     for (int p = 0; p < n; ++p) {
         twa_ctx* c = ctxs[p];
         TcState* t = c->tc;
@@ -1549,44 +1599,25 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
             tc_batch_free(b);
             return set_error(lead, TWA_EINVAL, "batch: contexts differ in precision or tiles, or have no trajectories");
         }
-        t->bn_ready = -1;   // the batch steps use the noise-part buffer of even steps
-        TcArgs la = base_args(c), pa = base_args(c), ca = base_args(c);
-        la.flags = pa.flags = ca.flags = lead->d_flags;
-        la.XI = t->XI; la.oBnx = t->Bx; la.oBny = t->By;
-        pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z; pa.Bnx = t->Bx; pa.Bny = t->By;
-        pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
-        pa.oHi = t->Phi; pa.oLo = t->Plo; pa.part_in = t->part; pa.part_out = t->partp;
-        ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp; ca.X0 = t->X; ca.Y0 = t->Y; ca.Z0 = t->Z;
-        ca.Bnx = t->Bx; ca.Bny = t->By; ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;
-        ca.oHi = t->Shi; ca.oLo = t->Slo; ca.part_in = t->partp; ca.part_out = t->part;
-        lg[p].maps = TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmE};
-        pg[p].maps = TcMaps{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo};
-        cg[p].maps = TcMaps{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo};
-        lg[p].args = la;
-        pg[p].args = pa;
-        cg[p].args = ca;
+        t->bn_ready = -1;   // the batch writes the noise-part buffers of its contexts
         sd[p] = StepDesc{t->E, t->XI, t->part, c->mom, c->d_t, c->d_count, c->M, c->N, t->ldk, t->n_rt,
                          c->n_window, c->opts.traj_offset, c->seed};
-        ts[p + 1] = ts[p] + t->n_rt * ((2 * c->M + t->bn - 1) / t->bn);
         ns[p + 1] = ns[p] + c->M * (c->N + 1);
         ms[p + 1] = ms[p] + c->M;
     }
-    b->tiles = ts[n];
     b->noise_elems = ns[n];
     b->traj = ms[n];
     b->flag_args = base_args(lead);
-    bool ok = cudaMalloc(&b->lg, sizeof(GroupDesc) * n) == cudaSuccess &&
-              cudaMalloc(&b->pg, sizeof(GroupDesc) * n) == cudaSuccess &&
-              cudaMalloc(&b->cg, sizeof(GroupDesc) * n) == cudaSuccess &&
-              cudaMalloc(&b->sd, sizeof(StepDesc) * n) == cudaSuccess &&
-              cudaMalloc(&b->tstart, sizeof(int64_t) * (n + 1)) == cudaSuccess &&
+    b->mix = new MixPlan();
+    int rc = mix_plan_build(ctxs, n, lead, b->mix);
+    if (rc) {
+        tc_batch_free(b);
+        return rc;
+    }
+    bool ok = cudaMalloc(&b->sd, sizeof(StepDesc) * n) == cudaSuccess &&
               cudaMalloc(&b->nstart, sizeof(int64_t) * (n + 1)) == cudaSuccess &&
               cudaMalloc(&b->mstart, sizeof(int64_t) * (n + 1)) == cudaSuccess;
-    ok = ok && cudaMemcpy(b->lg, lg.data(), sizeof(GroupDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(b->pg, pg.data(), sizeof(GroupDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(b->cg, cg.data(), sizeof(GroupDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(b->sd, sd.data(), sizeof(StepDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(b->tstart, ts.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+    ok = ok && cudaMemcpy(b->sd, sd.data(), sizeof(StepDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(b->nstart, ns.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(b->mstart, ms.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
@@ -1597,19 +1628,36 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
     return TWA_OK;
 }
 
-int tc_batch_step(twa_ctx* lead, TcBatch* b) {
+// Noise of step t and its noise part for every problem (one grouped L.eta
+// launch), into the buffers of t's parity: the first step of a batch.
+int tc_batch_prime(twa_ctx* lead, TcBatch* b, int64_t t) {
+    MixPlan* mp = b->mix;
+    const int n = b->n;
+    k_noise_group<<<nblk(b->noise_elems, 256), 256, 0, lead->stream>>>(b->sd, b->nstart, n, 0);
+    // the L.eta descriptors of the other parity write the buffers of t's parity
+    const GroupDesc* ld = mp->desc + mp->nprob * ((t & 1) ^ 1) + 2 * n;
     const TcMaps none{};
-    int rc;
-    k_noise_group<<<nblk(b->noise_elems, 256), 256, 0, lead->stream>>>(b->sd, b->nstart, b->n);
-    rc = b->x3 ? launch_cfg<MODE_LETA, 2>(lead, none, b->flag_args, Group{b->lg, b->tstart, b->n}, b->tiles)
-               : launch_cfg<MODE_LETA, 1>(lead, none, b->flag_args, Group{b->lg, b->tstart, b->n}, b->tiles);
+    const Group g{ld, mp->lstart, n};
+    const int rc = b->x3 ? launch_cfg<MODE_LETA, 2>(lead, none, b->flag_args, g, mp->leta_tiles)
+                         : launch_cfg<MODE_LETA, 1>(lead, none, b->flag_args, g, mp->leta_tiles);
     if (rc) return rc;
-    rc = b->x3 ? launch_cfg<MODE_PRED, 3>(lead, none, b->flag_args, Group{b->pg, b->tstart, b->n}, b->tiles)
-               : launch_cfg<MODE_PRED, 1>(lead, none, b->flag_args, Group{b->pg, b->tstart, b->n}, b->tiles);
-    if (rc) return rc;
-    rc = b->x3 ? launch_cfg<MODE_CORR, 3>(lead, none, b->flag_args, Group{b->cg, b->tstart, b->n}, b->tiles)
-               : launch_cfg<MODE_CORR, 1>(lead, none, b->flag_args, Group{b->cg, b->tstart, b->n}, b->tiles);
-    if (rc) return rc;
+    TWA_CUDA(lead, cudaGetLastError());
+    return TWA_OK;
+}
+
+// Step t of every problem (its noise part already in place): noise of step t + 1,
+// the two mixed launches, window moments, counters.
+int tc_batch_step(twa_ctx* lead, TcBatch* b, int64_t t) {
+    MixPlan* mp = b->mix;
+    const TcMaps none{};
+    k_noise_group<<<nblk(b->noise_elems, 256), 256, 0, lead->stream>>>(b->sd, b->nstart, b->n, 1);
+    const GroupDesc* dp = mp->desc + mp->nprob * (t & 1);
+    for (int L = 0; L < 2; ++L) {
+        const Group g{dp, mp->start, mp->nprob, mp->list[L], mp->first[L], mp->ctas[L]};
+        const int rc = b->x3 ? launch_cfg<MODE_MIX, 3>(lead, none, b->flag_args, g, mp->tiles[L])
+                             : launch_cfg<MODE_MIX, 1>(lead, none, b->flag_args, g, mp->tiles[L]);
+        if (rc) return rc;
+    }
     k_close_group<<<nblk(32 * b->traj, 256), 256, 0, lead->stream>>>(b->sd, b->mstart, b->n);
     k_advance_group<<<nblk(b->n, 128), 128, 0, lead->stream>>>(b->sd, b->n);
     TWA_CUDA(lead, cudaGetLastError());
