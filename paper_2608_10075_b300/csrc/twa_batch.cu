@@ -6,7 +6,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "twa_internal.cuh"
@@ -189,15 +191,59 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
         return rc;
     };
     int rc;
-    for (int p = 0; p < n; ++p) {
-        twa_opts op = o;
-        op.window_start = pts[p].window_start;
-        rc = twa_init(&ctx[p], pts[p].N, pts[p].alpha, pts[p].w, pts[p].Gamma, pts[p].dt, seed, &op);
-        if (rc) return cleanup(rc);   // message stays in twa_last_error(NULL)
-        if ((rc = twa_run(ctx[p], M, 0))) {
-            set_error(nullptr, rc, ctx[p]->err);
-            return cleanup(rc);
+    // Set-up (pump matrix, Cholesky factor, Lanczos bounds, initial state) is a
+    // chain of small dependent kernels per point: the points are set up from
+    // several host threads, each on a stream of its own, so that the chains
+    // overlap on the GPU. Afterwards every context works on the caller's stream.
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const int nw = n < 16 ? n : 16;
+        std::vector<cudaStream_t> streams(nw, nullptr);
+        std::vector<int> rcs(n, TWA_OK);
+        std::vector<std::string> errs(n);
+        bool ok = true;
+        for (int w = 0; w < nw && ok; ++w)
+            ok = cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) {
+            std::atomic<int> next{0};
+            auto worker = [&](int w) {
+                cudaSetDevice(dev);
+                for (int p; (p = next.fetch_add(1)) < n;) {
+                    twa_opts op = o;
+                    op.window_start = pts[p].window_start;
+                    op.stream = streams[w];
+                    int r = twa_init(&ctx[p], pts[p].N, pts[p].alpha, pts[p].w, pts[p].Gamma, pts[p].dt, seed, &op);
+                    if (r) {
+                        rcs[p] = r;
+                        errs[p] = twa_last_error(nullptr);
+                        continue;
+                    }
+                    r = twa_run(ctx[p], M, 0);
+                    if (!r && cudaStreamSynchronize(streams[w]) != cudaSuccess) r = TWA_ECUDA;
+                    if (r) {
+                        rcs[p] = r;
+                        errs[p] = ctx[p]->err;
+                    }
+                }
+            };
+            std::vector<std::thread> pool;
+            for (int w = 0; w < nw; ++w) pool.emplace_back(worker, w);
+            for (auto& th : pool) th.join();
         }
+        for (int p = 0; p < n; ++p)
+            if (ctx[p]) ctx[p]->stream = (cudaStream_t)o.stream;
+        for (cudaStream_t st : streams)
+            if (st) cudaStreamDestroy(st);
+        if (!ok) {
+            set_error(nullptr, TWA_ECUDA, "twa_batch_run: cudaStreamCreate");
+            return cleanup(TWA_ECUDA);
+        }
+        for (int p = 0; p < n; ++p)
+            if (rcs[p]) {
+                set_error(nullptr, rcs[p], errs[p]);
+                return cleanup(rcs[p]);
+            }
     }
     twa_ctx* lead = ctx[0];
     int bn = lead->tc->bn, kc = lead->tc->kc;

@@ -32,6 +32,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <atomic>
 #include <functional>
 #include <queue>
 #include <type_traits>
@@ -877,15 +878,16 @@ __global__ void k_widen(const float* a, double* b, int64_t n) {
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // resolved once (thread-safe initialisation of a local static)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -910,10 +912,10 @@ int make_map(twa_ctx* c, CUtensorMap* map, const void* base, int64_t rows, int64
 template <int MODE, int NT, int BN, int KC>
 int launch_one(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_tiles, const Group& grp) {
     auto kern = k_tc<MODE, NT, BN, KC>;
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};   // contexts may be set up from several host threads
+    if (!attr.load()) {
         TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<BN, KC>::SMEM));
-        attr = true;
+        attr.store(true);
     }
     const int64_t g = grp.sched ? grp.ctas : (n_tiles < c->tc->num_sms ? n_tiles : c->tc->num_sms);
     kern<<<(unsigned)g, NTHREADS, Geo<BN, KC>::SMEM, c->stream>>>(maps, a, grp);
