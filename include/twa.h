@@ -256,20 +256,25 @@ typedef struct twa_point {
 /* Run many parameter points of uneven N together (spec pattern 2, e.g. a
  * phase-diagram scan) and return each point's observables in out[0..n-1].
  *
- * Every point gets its own pump matrix, Cholesky factor and M trajectories (seed
+ * Every point gets its own pump matrix, Cholesky factor and M trajectories (set
+ * up concurrently from several host threads, each on its own stream; seed
  * and opts as for twa_init; opts->precision must be TWA_PREC_BF16 or
  * TWA_PREC_BF16X3, opts->window_start is replaced by each point's, and every
- * point runs the dense route with the Cholesky noise draw). Each step of
- * all points still running is one grouped persistent launch per kernel class:
- * the tensor-core tiles of all points form one list, largest problems first,
- * walked by one CTA per SM; the step is captured once per set of running points
- * as a CUDA graph and replayed. Points with fewer steps drop out as they finish.
+ * point runs the dense route with the Cholesky noise draw). A step of all
+ * points still running is the single-context step done for all of them at
+ * once: noise of the next step, one persistent launch with every point's W.s +
+ * predictor tiles and part of the L.eta tiles of the next step, one with the
+ * W.s~ + corrector tiles and the rest (tiles placed on one CTA per SM by
+ * longest-first list scheduling), window moments. The step is captured per
+ * set of running points and parity of the step index as CUDA graphs and
+ * replayed. Points with fewer steps drop out as they finish.
  * The results equal those of running every point alone with twa_run.
  *
  * Tile shapes: unless TWA_TC_BN / TWA_TC_KC are set in the environment, a
  * built-in autotuner times the compiled configurations on a few steps of the
- * batch (the state is saved and restored around the trials) and keeps the
- * fastest. tiles: NULL or int[2] receiving the chosen (BN, K-stage config).
+ * points that run in the stage with the most work (steps x N^2 of the points
+ * still running; the state is saved and restored around the trials) and keeps
+ * the fastest. tiles: NULL or int[2] receiving the chosen (BN, K-stage config).
  * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (FP64 precision), plus those of twa_init
  * and twa_sync. Synchronises. */
 TWA_API int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,

@@ -104,7 +104,7 @@ int autotune(std::vector<twa_ctx*>& ctx, int* bn, int* kc) {
         int rc = set_tiles_all(ctx, cd[0], cd[1]);
         if (rc) return rc;
         float ms = 0.f;
-        if ((rc = time_batch(ctx, 3, &ms))) return rc;
+        if ((rc = time_batch(ctx, 5, &ms))) return rc;
         if (ms < best) {
             best = ms;
             *bn = cd[0];
@@ -248,7 +248,26 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
     twa_ctx* lead = ctx[0];
     int bn = lead->tc->bn, kc = lead->tc->kc;
     if (!getenv("TWA_TC_BN") && !getenv("TWA_TC_KC")) {
-        if ((rc = autotune(ctx, &bn, &kc))) {
+        // tune on the points of the stage with the most work (steps x N^2 of the
+        // points still running), which dominates the run
+        std::vector<int64_t> cuts;
+        for (int p = 0; p < n; ++p) cuts.push_back(pts[p].steps);
+        std::sort(cuts.begin(), cuts.end());
+        int64_t prev = 0, best_end = cuts.back();
+        double best_work = -1.0;
+        for (int64_t end : cuts) {
+            if (end == prev) continue;
+            double w = 0.0;
+            for (int p = 0; p < n; ++p)
+                if (pts[p].steps >= end) w += (double)pts[p].N * (double)pts[p].N;
+            w *= (double)(end - prev);
+            if (w > best_work) best_work = w, best_end = end;
+            prev = end;
+        }
+        std::vector<twa_ctx*> trial;
+        for (int p = 0; p < n; ++p)
+            if (pts[p].steps >= best_end) trial.push_back(ctx[p]);
+        if ((rc = autotune(trial, &bn, &kc)) || (rc = set_tiles_all(ctx, bn, kc))) {
             set_error(nullptr, rc, lead->err);
             return cleanup(rc);
         }
