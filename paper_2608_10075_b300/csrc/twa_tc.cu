@@ -16,11 +16,13 @@
 // in FP32 and rounded to BF16 once, so L.eta needs the two terms of L only.
 //
 // Kernel structure: persistent CTAs (at most one per SM) walk a static list of
-// (row tile, trajectory tile) pairs, strided or from a host-built schedule. Warp 0 streams K tiles through a ring of
-// shared-memory stages with TMA, running ahead across tile boundaries; warp 1
-// issues the MMAs into one of two TMEM accumulators; warps 2-5 run the epilogue
-// of the previous tile from the other accumulator, so epilogue and main loop
-// overlap. Every wait on an mbarrier is bounded in time and reports a timeout.
+// (row tile, trajectory tile) pairs, strided or from a host-built schedule.
+// Warp 0 streams K tiles through a ring of shared-memory stages with TMA,
+// running ahead across tile boundaries; warp 1 issues the MMAs into one of two
+// TMEM accumulators; warps 2-9 run the epilogue of the previous tile from the
+// other accumulator (two warps per TMEM lane quadrant, each on half of the
+// columns), so epilogue and main loop overlap. Every wait on an mbarrier is
+// bounded in time and reports a timeout.
 //
 // A step t is: noise of step t + 1; one launch with the tiles of W.s and the
 // Heun predictor plus part of the L.eta tiles of step t + 1 (-> noise part of
@@ -47,7 +49,10 @@ namespace twa {
 namespace {
 
 constexpr int BM = TC_BM;
-constexpr int NTHREADS = 192;                           // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+// warp 0 TMA, warp 1 MMA, warps 2.. epilogue: two per TMEM lane quadrant, each
+// draining half of the accumulator columns (twice the loads in flight of one)
+constexpr int EPI_WARPS = 8, EPI_THREADS = 32 * EPI_WARPS;
+constexpr int NTHREADS = 64 + EPI_THREADS;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 
 // MODE_MIX: tiles of several modes in one launch, each problem's mode and term
@@ -185,7 +190,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS) : "memory"); }
 
 __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t off, float v, bool with_lo) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -436,7 +441,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
         const int q = warp & 3;              // TMEM lane quadrant of this warp
-        const int et = threadIdx.x - 64;     // 0..127
+        const int half = (warp - 2) >> 2;    // which half of the accumulator columns
+        const int et = threadIdx.x - 64;     // 0 .. EPI_THREADS - 1
         int it = 0;
         for (int64_t k = 0; k < n_mine; ++k, ++it) {
             const int64_t t = tile_of(k);
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             const bool site_ok = i < args.N;
             epi_sync();                                   // smem of the previous tile is free
             if (md == MODE_PRED || md == MODE_CORR) {
-                for (int j = et; j < NTRAJ; j += 128) {
+                for (int j = et; j < NTRAJ; j += EPI_THREADS) {
                     const int64_t m = m0 + j;
                     float sx = 0.f, sy = 0.f;
                     if (m < M) {
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                     sS[2 * j + 1] = sy;
                 }
             } else if (md == MODE_LETA) {
-                for (int j = et; j < NTRAJ; j += 128) {
+                for (int j = et; j < NTRAJ; j += EPI_THREADS) {
                     const int64_t m = m0 + j;
                     sS[2 * j] = (m < M) ? args.XI[2 * m] : 0.f;
                     sS[2 * j + 1] = (m < M) ? args.XI[2 * m + 1] : 0.f;
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             auto run_tile = [&](auto em_tag) {
                 constexpr int EM = decltype(em_tag)::value;
                 constexpr bool WITH_LO = (NT == 3);   // images of the W.s operand: hi + lo
-                for (int c = 0; c < BN / 16; ++c) {
+                for (int c = half * (BN / 32); c < (half + 1) * (BN / 32); ++c) {
                     float pv[16];
                     tmem_ld16(trow + 16 * c, pv);
                     tmem_ld_wait();
@@ -609,7 +615,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             // (md is the same for the four epilogue warps: they walk the same tiles)
             if (md == MODE_PRED || md == MODE_CORR) {
                 epi_sync();   // every epilogue thread, live or not
-                for (int j = et; j < NTRAJ; j += 128) {
+                for (int j = et; j < NTRAJ; j += EPI_THREADS) {
                     const int64_t m = m0 + j;
                     if (!live || m >= M) continue;
                     float4 o;
