@@ -37,9 +37,10 @@ def _linear_samples(means):
     return {"Sz": Sz, "SpSm": A + 0.5 * Sz, "G2num": A2 + 2 * ASz - Sz / 3 + 0.5 * Sz2 - 4.0 / 3.0 * A}
 
 
-def _run(N, alpha, w, G, dt, steps, M, t0, precision, route="dense"):
+def _run(N, alpha, w, G, dt, steps, M, t0, precision, route="dense", noise="cholesky"):
     t = time.perf_counter()
-    with twa.TWA(N, alpha, w, G, dt, seed=0, precision=precision, window_start=t0, ws_route=route) as g:
+    with twa.TWA(N, alpha, w, G, dt, seed=0, precision=precision, window_start=t0, ws_route=route,
+                 noise_route=noise) as g:
         g.run(M, steps)
         obs = g.observables()
         means = g.moments()
@@ -57,9 +58,13 @@ def precision_study(args):
         line = {"study": "precision", "N": N, "alpha": alpha, "w": w, "dt": dt, "steps": steps,
                 "M_ref": args.M_ref, "stability": ref_obs["stability"], "w_tilde": ref_obs["w_tilde"],
                 "fp64": {k: [ref_obs[k], ref_obs[k + "_se"]] for k in KEYS}, "fp64_seconds": ref_t}
-        for name, prec, route in (("bf16", "bf16", "dense"), ("bf16x3", "bf16x3", "dense"),
-                                  ("bf16x3_fft", "bf16x3", "fft")):
-            obs, means, secs = _run(N, alpha, w, G, dt, steps, args.M_ref, t0, prec, route)
+        # the circulant draw has the same noise law but other per-trajectory values,
+        # so only its unpaired difference (diff_over_se) measures its error
+        for name, prec, route, noise in (("bf16", "bf16", "dense", "cholesky"),
+                                         ("bf16x3", "bf16x3", "dense", "cholesky"),
+                                         ("bf16x3_fft", "bf16x3", "fft", "cholesky"),
+                                         ("fft_circulant_noise", "bf16x3", "fft", "circulant")):
+            obs, means, secs = _run(N, alpha, w, G, dt, steps, args.M_ref, t0, prec, route, noise)
             s = _linear_samples(means)
             paired = {}
             for k in ("Sz", "SpSm", "G2num"):
