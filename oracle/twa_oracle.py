@@ -40,8 +40,9 @@ Readings where the paper is silent (each is also listed in the design notes):
   Box-Muller: r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2) -> (x, y).
 * Initial s^z is a parameter (+1 excited as in the paper, -1 ground).
 * Window: the state after completed step t (time t dt) is one sample when
-  t > round(t0 / dt), t0 the window start; each trajectory's window mean is one
-  sample of the ensemble; g2 is the ratio of ensemble means with a
+  t > round(t0 / dt), t0 the window start, and (t - round(t0 / dt)) is a
+  multiple of the sample stride (1: every step); each trajectory's window mean
+  is one sample of the ensemble; g2 is the ratio of ensemble means with a
   block-jackknife standard error.
 """
 import math
@@ -161,12 +162,14 @@ class TWAOracle:
     """
 
     def __init__(self, N, alpha, w, Gamma, dt, seed, M, m0=0, init_sz=-1.0,
-                 window_start=0.0, renormalize=True, L=None, W=None):
+                 window_start=0.0, renormalize=True, L=None, W=None, sample_stride=1):
         self.N, self.alpha, self.w, self.Gamma, self.dt = int(N), float(alpha), float(w), float(Gamma), float(dt)
         self.seed, self.M, self.m0 = int(seed), int(M), int(m0)
         self.window_start = float(window_start)
-        # samples are taken after completed step t for t > n_w, n_w = round(t0 / dt)
+        # samples are taken after completed step t for t > n_w, n_w = round(t0 / dt),
+        # every sample_stride-th step: t = n_w + stride, n_w + 2 stride, ...
         self.n_window = int(math.floor(self.window_start / self.dt + 0.5))
+        self.sample_stride = max(1, int(sample_stride))
         self.renormalize = bool(renormalize)
         self.W = pump_matrix(self.N, self.alpha, self.w) if W is None else np.asarray(W, dtype=np.float64)
         self.L = noise_factor(self.N, self.alpha, self.w) if L is None else np.asarray(L, dtype=np.float64)
@@ -229,7 +232,7 @@ class TWAOracle:
             nx, ny, nz = nx * scale, ny * scale, nz * scale
         self.sx, self.sy, self.sz = nx, ny, nz
         self.t = t + 1
-        if self.t > self.n_window:
+        if self.t > self.n_window and (self.t - self.n_window) % self.sample_stride == 0:
             self.accumulate()
 
     def accumulate(self):

@@ -139,7 +139,7 @@ class TWATangent(TWAOracle):
         self.sx, self.sy, self.sz = new
         self.tx, self.ty, self.tz = tnew
         self.t = t + 1
-        if self.t > self.n_window:
+        if self.t > self.n_window and (self.t - self.n_window) % self.sample_stride == 0:
             self.accumulate()
 
     def accumulate(self):

@@ -289,3 +289,29 @@ def test_g2_jackknife_on_known_law():
     assert 0.7 < np.mean(ses) / spread < 1.4
     # g2 = (130 + 0 - 0 + 2.5 - 40/3) / 10^2 for these means
     assert abs(np.mean(vals) - (130 + 2.5 - 40.0 / 3.0) / 100.0) < 4 * spread / math.sqrt(60)
+
+
+def test_sample_stride_takes_every_kth_step_of_the_window():
+    # Same trajectories (same seed and counters): with stride k the window mean is
+    # the mean of the states after steps n_w + k, n_w + 2k, ... <= T.
+    N, M, steps, nw, k, dt = 5, 7, 23, 4, 3, 0.01
+    states = {}
+
+    class Record(TWAOracle):
+        def step(self):
+            super().step()
+            states[self.t] = (self.sx.sum(1), self.sy.sum(1), self.sz.sum(1))
+
+    a = Record(N, 1.0, 3.0, 1.0, dt, 9, M, window_start=nw * dt)
+    a.run(steps)
+    b = TWAOracle(N, 1.0, 3.0, 1.0, dt, 9, M, window_start=nw * dt, sample_stride=k)
+    b.run(steps)
+    picks = [t for t in sorted(states) if t > nw and (t - nw) % k == 0]
+    assert picks == list(range(nw + k, steps + 1, k)) and b.count == len(picks)
+    assert np.array_equal(a.sx, b.sx)
+    Sz = np.mean([states[t][2] for t in picks], axis=0)
+    A = np.mean([0.25 * (states[t][0] ** 2 + states[t][1] ** 2) for t in picks], axis=0)
+    assert np.allclose(b.window_means()[:, 0], Sz, rtol=1e-13, atol=1e-12)
+    assert np.allclose(b.window_means()[:, 1], A, rtol=1e-13, atol=1e-12)
+    # stride 1 is every step of the window
+    assert a.count == steps - nw
