@@ -77,7 +77,8 @@ typedef struct twa_opts {
     int    precision;       /* TWA_PREC_*; default TWA_PREC_FP64                      */
     int    init_state;      /* initial s^z: -1 ground (default) or +1 excited         */
     double window_start;    /* t0: the state after step t is averaged when
-                               t > round(t0 / dt); default 0 (every step)             */
+                               t > round(t0 / dt) (and the stride below divides
+                               t - round(t0 / dt)); default 0                         */
     int    renormalize;     /* 1 (default): rescale every spin to sqrt(3) each step   */
     int    clip_negative;   /* 0 (default): non-positive Cholesky pivot -> TWA_ENOTPSD;
                                1: zero that column of L and carry on (reported)        */
@@ -93,6 +94,9 @@ typedef struct twa_opts {
                                TWA_NOISE_CIRCULANT (FFT of the circulant embedding;
                                needs ws_route = TWA_ROUTE_FFT). The two draws have the
                                same law and different per-trajectory values.       */
+    int64_t sample_stride;  /* window samples every sample_stride-th step: the states
+                               after steps n_w + k, n_w + 2k, ... with n_w =
+                               round(t0 / dt); 0 or 1 (default): every step        */
 } twa_opts;
 
 #define TWA_ROUTE_DENSE 0   /* tensor-core contraction with the dense W          */

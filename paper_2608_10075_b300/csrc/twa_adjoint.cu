@@ -560,7 +560,8 @@ struct Adjoint {
             }
             int rc;
             if ((rc = step(t, a, az, b, bz, 0))) return rc;
-            if (t + 1 > c->n_window) k_a_moments<<<nb(M, 256), 256, 0, c->stream>>>(tSn, mom, M);
+            if (window_sample(t + 1, c->n_window, c->n_stride))
+                k_a_moments<<<nb(M, 256), 256, 0, c->stream>>>(tSn, mom, M);
             std::swap(a, b);
             std::swap(az, bz);
         }
@@ -594,8 +595,8 @@ struct Adjoint {
                 TWA_CUDA(c, cudaMemsetAsync(sumbt, 0, sizeof(double) * 2 * M, c->stream));
                 TWA_CUDA(c, cudaMemsetAsync(sumb, 0, sizeof(double) * 2 * M, c->stream));
                 k_b1<T><<<g2, AT, 0, c->stream>>>(lxy, lz, sxy, sz, sxt, szt, P, Pt, Q, xi, S, St, Sn, obj,
-                                                  (t + 1 > c->n_window) ? 1 : 0, luxy, luz, btxy, gtxy, gtz, sumbt, M,
-                                                  N, G, dt, c->opts.renormalize);
+                                                  window_sample(t + 1, c->n_window, c->n_stride) ? 1 : 0, luxy, luz,
+                                                  btxy, gtxy, gtz, sumbt, M, N, G, dt, c->opts.renormalize);
                 if ((rc = contract(0, btxy, Wbt))) return rc;
                 k_b2<T><<<g2, AT, 0, c->stream>>>(luxy, luz, gtxy, gtz, Wbt, sumbt, btxy, sxy, sz, P, Pt, Q, xi, S,
                                                   bxy, lpxy, lpz, sumb, gpart, M, N, G, dt, c->w);
@@ -625,7 +626,7 @@ int run_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
     a.C = r->checkpoint > 0 ? r->checkpoint : 64;
     if (a.C > a.steps) a.C = a.steps;
     a.nck = (a.steps + a.C - 1) / a.C;
-    a.nsamp = a.steps - c->n_window;
+    a.nsamp = a.steps > c->n_window ? (a.steps - c->n_window) / c->n_stride : 0;
     a.want_alpha = r->want_alpha != 0;
     if (a.nsamp < 1) return set_error(c, TWA_ESTATE, "twa_grad: no step inside the averaging window");
     int rc;

@@ -151,6 +151,7 @@ int twa_opts_default(twa_opts* o) {
     o->renormalize = 1;
     o->clip_negative = 0;
     o->stream = nullptr;
+    o->sample_stride = 1;
     return TWA_OK;
 }
 
@@ -177,6 +178,8 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         return set_error(nullptr, TWA_EINVAL, "twa_init: ws_route must be TWA_ROUTE_DENSE or TWA_ROUTE_FFT");
     if (o.ws_route == TWA_ROUTE_FFT && o.precision == TWA_PREC_FP64)
         return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the FFT route runs with the BF16 precisions only");
+    if (o.sample_stride < 0 || o.sample_stride > MAX_COUNTER)
+        return set_error(nullptr, TWA_EINVAL, "twa_init: sample_stride must be in [0, 2^32-1]");
     if (o.noise_route != TWA_NOISE_CHOLESKY && o.noise_route != TWA_NOISE_CIRCULANT)
         return set_error(nullptr, TWA_EINVAL, "twa_init: noise_route must be TWA_NOISE_CHOLESKY or TWA_NOISE_CIRCULANT");
     if (o.noise_route == TWA_NOISE_CIRCULANT && o.ws_route != TWA_ROUTE_FFT)
@@ -193,6 +196,7 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
     c->opts = o;
     c->stream = (cudaStream_t)o.stream;
     c->n_window = (int64_t)floor(o.window_start / dt + 0.5);
+    c->n_stride = o.sample_stride > 1 ? o.sample_stride : 1;
     int rc = TWA_OK;
     auto fail = [&](int code) {
         g_init_error = c->err;

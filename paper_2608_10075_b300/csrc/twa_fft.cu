@@ -50,7 +50,7 @@ struct FftArgs {
     double* mom;                         // CORR: window sums [M][5]
     int64_t* d_t;
     int64_t* d_count;
-    int64_t n_window;
+    int64_t n_window, n_stride;
     unsigned long long* flags;
     const double* field_in;              // FIELD: [K][N]
     double* field_out;
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_corr(const __grid_constant__ FftA
     const unsigned nb = __reduce_add_sync(0xffffffffu, out.bad);
     if ((threadIdx.x & 31) == 0 && nb) atomicAdd(&a.flags[FLAG_NONFINITE], (unsigned long long)nb);
     if (threadIdx.x == 0) {
-        if (t1 > a.n_window) {
+        if (window_sample(t1, a.n_window, a.n_stride)) {
             // window moments S^z, A, A^2, A S^z, (S^z)^2 with A = ((S^x)^2 + (S^y)^2) / 4
             const double dx = Sx, dy = Sy, dz = Sz;
             const double A = 0.25 * (dx * dx + dy * dy);
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_corr(const __grid_constant__ FftA
         const unsigned long long done = atomicAdd(&a.flags[FLAG_DONE], 1ull);
         if (done == gridDim.x - 1) {   // last trajectory of the step: advance the counter
             a.flags[FLAG_DONE] = 0ull;
-            if (t1 > a.n_window) *a.d_count += 1;
+            if (window_sample(t1, a.n_window, a.n_stride)) *a.d_count += 1;
             __threadfence();
             *a.d_t = t1;
         }
@@ -651,6 +651,7 @@ int fft_correct(twa_ctx* c) {
     a.d_t = c->d_t;
     a.d_count = c->d_count;
     a.n_window = c->n_window;
+    a.n_stride = c->n_stride;
     k_fft_corr<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(a);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;

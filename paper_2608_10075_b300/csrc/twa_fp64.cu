@@ -194,10 +194,12 @@ __global__ void k_correct_f64(const double* xyp, const double* zp, const double*
 // step count exceeds n_window, and the step counter increment by the last
 // block to finish (all blocks have read the counter by then).
 __global__ void k_close_f64(const double* xy, const double* z, double* S, double* mom, int64_t M, int64_t N,
-                            int64_t* d_t, int64_t n_window, int64_t* d_count, unsigned long long* flags) {
+                            int64_t* d_t, int64_t n_window, int64_t n_stride, int64_t* d_count,
+                            unsigned long long* flags) {
     const int64_t m = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     const int64_t t1 = *d_t + 1;
+    const bool sample = window_sample(t1, n_window, n_stride);
     if (m < M) {
         double sx = 0, sy = 0, sz = 0;
         for (int64_t i = lane; i < N; i += 32) {
@@ -214,7 +216,7 @@ __global__ void k_close_f64(const double* xy, const double* z, double* S, double
             S[4 * m] = sx;
             S[4 * m + 1] = sy;
             S[4 * m + 2] = sz;
-            if (t1 > n_window) {
+            if (sample) {
                 const double A = 0.25 * (sx * sx + sy * sy);
                 double* mm = mom + 5 * m;
                 mm[0] += sz;
@@ -231,7 +233,7 @@ __global__ void k_close_f64(const double* xy, const double* z, double* S, double
         const unsigned long long done = atomicAdd(&flags[FLAG_DONE], 1ull);
         if (done == gridDim.x - 1) {
             flags[FLAG_DONE] = 0ull;
-            if (t1 > n_window) *d_count += 1;
+            if (sample) *d_count += 1;
             __threadfence();
             *d_t = t1;
         }
@@ -326,7 +328,7 @@ int f64_run(twa_ctx* c, int64_t steps) {
         {
             ProfScope p(c, TWA_PROF_CLOSE);
             k_close_f64<<<blocks_for(M, 8), 256, 0, st>>>(c->xy, c->z, c->S, c->mom, M, N, c->d_t, c->n_window,
-                                                           c->d_count, c->d_flags);
+                                                           c->n_stride, c->d_count, c->d_flags);
         }
     }
     TWA_CUDA(c, cudaGetLastError());

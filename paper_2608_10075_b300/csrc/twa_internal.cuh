@@ -97,7 +97,8 @@ struct twa_ctx {
     // run state
     int64_t M = 0;           // 0 until the first run / set_state
     int64_t steps = 0;       // completed steps (host mirror of d_t)
-    int64_t n_window = 0;    // samples after step t are taken when t > n_window
+    int64_t n_window = 0;    // samples after step t are taken when t > n_window ...
+    int64_t n_stride = 1;    // ... and n_stride divides t - n_window
     int64_t* d_t = nullptr;  // device step counter
     unsigned long long* d_flags = nullptr;
     double* mom = nullptr;   // [M][5] window sums (FP64)
@@ -186,6 +187,11 @@ __host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_
 constexpr uint32_t STREAM_NOISE = 0;
 constexpr uint32_t STREAM_INIT = 1;
 constexpr uint32_t STREAM_CIRCULANT = 2;   // circulant noise draw: counter (m, t, frequency k, 2)
+
+// The state after step t1 is a window sample (the averaging window of Sec. S1).
+__host__ __device__ __forceinline__ bool window_sample(int64_t t1, int64_t n_window, int64_t stride) {
+    return t1 > n_window && (t1 - n_window) % stride == 0;
+}
 
 // Two FP64 standard normals from one Philox call: 53-bit uniforms
 // u = (k + 1/2) 2^-53 from words (0,1) and (2,3), then Box-Muller.

@@ -758,11 +758,12 @@ __device__ __forceinline__ void add_moments(double* mm, double sx, double sy, do
 // Closing kernel: S^a from the corrector's partial sums (one warp per
 // trajectory), the FP64 window moments, and the step counter (last block).
 __global__ void k_close_tc(const float* part, int64_t M, int64_t n_rt, double* mom, int64_t* d_t, int64_t n_window,
-                           int64_t* d_count, unsigned long long* flags) {
+                           int64_t n_stride, int64_t* d_count, unsigned long long* flags) {
     const int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t t1 = *d_t + 1;
-    if (m < M && t1 > n_window) {   // warp-uniform
+    const bool sample = window_sample(t1, n_window, n_stride);
+    if (m < M && sample) {   // warp-uniform
         double sx, sy, sz;
         warp_tile_sums(part, M, n_rt, m, lane, sx, sy, sz);
         if (lane == 0) add_moments(mom + 5 * m, sx, sy, sz);
@@ -773,7 +774,7 @@ __global__ void k_close_tc(const float* part, int64_t M, int64_t n_rt, double* m
         const unsigned long long done = atomicAdd(&flags[FLAG_DONE], 1ull);
         if (done == gridDim.x - 1) {
             flags[FLAG_DONE] = 0ull;
-            if (t1 > n_window) *d_count += 1;
+            if (sample) *d_count += 1;
             __threadfence();
             *d_t = t1;
         }
@@ -790,7 +791,7 @@ struct StepDesc {
     double* mom;
     int64_t* d_t;
     int64_t* d_count;
-    int64_t M, N, ldk, n_rt, n_window, m0;
+    int64_t M, N, ldk, n_rt, n_window, n_stride, m0;
     uint64_t seed;
 };
 
@@ -830,7 +831,7 @@ __global__ void k_close_group(const StepDesc* sd, const int64_t* start, int n) {
     const int p = find_problem(start, n, e);
     const StepDesc& d = sd[p];
     const int64_t m = e - start[p];
-    if (*d.d_t + 1 <= d.n_window) return;
+    if (!window_sample(*d.d_t + 1, d.n_window, d.n_stride)) return;
     double sx, sy, sz;
     warp_tile_sums(d.part, d.M, d.n_rt, m, threadIdx.x & 31, sx, sy, sz);
     if ((threadIdx.x & 31) == 0) add_moments(d.mom + 5 * m, sx, sy, sz);
@@ -840,7 +841,7 @@ __global__ void k_advance_group(const StepDesc* sd, int n) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t t1 = *sd[p].d_t + 1;
-    if (t1 > sd[p].n_window) *sd[p].d_count += 1;
+    if (window_sample(t1, sd[p].n_window, sd[p].n_stride)) *sd[p].d_count += 1;
     *sd[p].d_t = t1;
 }
 
@@ -1508,7 +1509,7 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
     {
         ProfScope p(c, TWA_PROF_CLOSE);
         k_close_tc<<<nblk(32 * M, 256), 256, 0, c->stream>>>(ts->part, M, ts->n_rt, c->mom, c->d_t, c->n_window,
-                                                        c->d_count, c->d_flags);
+                                                             c->n_stride, c->d_count, c->d_flags);
     }
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
@@ -1611,7 +1612,7 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
         }
         t->bn_ready = -1;   // the batch writes the noise-part buffers of its contexts
         sd[p] = StepDesc{t->E, t->XI, t->part, c->mom, c->d_t, c->d_count, c->M, c->N, t->ldk, t->n_rt,
-                         c->n_window, c->opts.traj_offset, c->seed};
+                         c->n_window, c->n_stride, c->opts.traj_offset, c->seed};
         ns[p + 1] = ns[p] + c->M * (c->N + 1);
         ms[p + 1] = ms[p] + c->M;
     }

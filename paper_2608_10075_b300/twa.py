@@ -28,7 +28,8 @@ class TWAError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("init_state", ctypes.c_int), ("window_start", ctypes.c_double),
                 ("renormalize", ctypes.c_int), ("clip_negative", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("traj_offset", ctypes.c_int64), ("ws_route", ctypes.c_int), ("noise_route", ctypes.c_int)]
+                ("traj_offset", ctypes.c_int64), ("ws_route", ctypes.c_int), ("noise_route", ctypes.c_int),
+                ("sample_stride", ctypes.c_int64)]
 
 
 ROUTE = {"dense": 0, "fft": 1}
@@ -143,7 +144,7 @@ class TWA:
 
     def __init__(self, N, alpha, w, Gamma, dt, seed=0, precision="fp64", init_state=-1, window_start=0.0,
                  renormalize=True, clip_negative=False, stream=None, traj_offset=0, ws_route="dense",
-                 noise_route="cholesky"):
+                 noise_route="cholesky", sample_stride=1):
         L = lib()
         o = Opts()
         L.twa_opts_default(ctypes.byref(o))
@@ -156,6 +157,7 @@ class TWA:
         o.traj_offset = int(traj_offset)
         o.ws_route = ROUTE[ws_route] if isinstance(ws_route, str) else int(ws_route)
         o.noise_route = NOISE[noise_route] if isinstance(noise_route, str) else int(noise_route)
+        o.sample_stride = int(sample_stride)
         self._stream = stream
         h = ctypes.c_void_p()
         a = float(alpha)

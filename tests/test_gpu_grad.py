@@ -36,6 +36,23 @@ def test_fp64_adjoint_equals_oracle_tangent(objective, theta, col):
     assert np.max(np.abs(r["per_traj"][:, col] - per)) <= 1e-7 * max(np.max(np.abs(per)), 1e-6)
 
 
+@pytest.mark.parametrize("objective", ["SpSm", "g2"])
+def test_fp64_adjoint_with_sample_stride_equals_oracle_tangent(objective):
+    # window samples every 4th step (steps 19, 23, ..., 59): the objective and its
+    # derivatives are those of the strided window
+    twa = _twa()
+    N, alpha, w, G, dt, M, steps, t0, k = 16, 1.0, 8.0, 1.0, 2e-3, 24, 59, 0.03, 4
+    for theta, key in (("w", "dJ_dw"), ("alpha", "dJ_dalpha")):
+        o = TWATangent(N, alpha, w, G, dt, 0, M, theta, window_start=t0, sample_stride=k)
+        o.run(steps)
+        J, dJ, _ = o.derivative(objective)
+        with twa.TWA(N, alpha, w, G, dt, seed=0, precision="fp64", window_start=t0, sample_stride=k) as g:
+            r = g.grad(objective, M, steps, checkpoint=16)
+        assert o.count == (steps - 15) // k
+        assert abs(r["J"] - J) <= 1e-9 * abs(J)
+        assert abs(r[key] - dJ) <= 1e-8 * max(abs(dJ), 1e-6), (theta, r[key], dJ)
+
+
 def test_checkpoint_stride_does_not_change_the_gradient():
     twa = _twa()
     res = []

@@ -99,3 +99,29 @@ def test_profile_standalone_noise_factor_after_set_state():
     assert p["noise_factor"][1] == 1 and p["noise"][1] == 4 and p["predict"][1] == 3
     N, M = 300, 130
     assert abs(p["noise_factor"][2] - 2.0 * (N * (N + 1) / 2) * 2 * M * 2) <= 1e-9 * p["noise_factor"][2]
+
+
+@pytest.mark.parametrize("prec,route,noise", [("fp64", "dense", "cholesky"), ("bf16x3", "dense", "cholesky"),
+                                              ("bf16", "dense", "cholesky"), ("bf16x3", "fft", "circulant")])
+def test_sample_stride_selects_every_kth_window_step(prec, route, noise):
+    # window start n_w = 2, stride 3, 11 steps: samples after steps 5, 8, 11. The
+    # library's window means must be the means of the collective moments of the
+    # states read back after exactly those steps.
+    from paper_2608_10075_b300 import twa
+    N, M, steps, nw, k, dt = 50, 8, 11, 2, 3, 1e-3
+    acc, n = np.zeros((M, 5)), 0
+    with twa.TWA(N, 1.0, 8.0, 1.0, dt, seed=6, precision=prec, window_start=nw * dt, ws_route=route,
+                 noise_route=noise, sample_stride=k) as g:
+        for t in range(1, steps + 1):
+            g.run(M, 1)
+            if t > nw and (t - nw) % k == 0:
+                x, y, z = g.get_state()
+                Sx, Sy, Sz = x.sum(1), y.sum(1), z.sum(1)
+                A = 0.25 * (Sx * Sx + Sy * Sy)
+                acc += np.stack([Sz, A, A * A, A * Sz, Sz * Sz], axis=1)
+                n += 1
+        mom = g.moments()
+        assert g.observables()["samples"] == n == 3
+    # FP64 path: the same sums; mixed paths: FP32 state summed in a different order
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert np.allclose(mom, acc / n, rtol=tol, atol=tol * np.abs(acc / n).max())
