@@ -73,6 +73,18 @@ extern "C" {
 
 typedef struct twa_ctx twa_ctx;   /* opaque, owned by the library */
 
+/* Caller-supplied device allocator (e.g. a framework's caching allocator), so
+   that a context's device memory comes from the caller's pool. alloc returns
+   `bytes` of device memory usable in work ordered on `stream` (a cudaStream_t;
+   NULL = legacy default stream), or NULL on failure; free releases a pointer
+   that alloc returned, for reuse after the work already ordered on `stream`.
+   `user` is the twa_opts.alloc_user pointer. The memory must be aligned to
+   256 bytes as cudaMalloc's is (the tensor maps of the tensor-core path need
+   16). Both are called from the thread that calls into the library (for
+   twa_batch_run: from its set-up threads too, so they must be thread-safe). */
+typedef void* (*twa_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*twa_free_fn)(void* ptr, void* stream, void* user);
+
 typedef struct twa_opts {
     int    precision;       /* TWA_PREC_*; default TWA_PREC_FP64                      */
     int    init_state;      /* initial s^z: -1 ground (default) or +1 excited         */
@@ -97,6 +109,15 @@ typedef struct twa_opts {
     int64_t sample_stride;  /* window samples every sample_stride-th step: the states
                                after steps n_w + k, n_w + 2k, ... with n_w =
                                round(t0 / dt); 0 or 1 (default): every step        */
+    twa_alloc_fn alloc;     /* NULL (default): the library allocates with cudaMalloc
+                               (buffers that live with the context) and
+                               cudaMallocAsync (scratch of one call). Non-NULL,
+                               with `free`: every device allocation of the context
+                               and of the calls made on it goes through alloc/free
+                               instead (the context-less twa_reduce_moments keeps
+                               the library's allocator)                           */
+    twa_free_fn free;
+    void*  alloc_user;      /* passed through to alloc and free                   */
 } twa_opts;
 
 #define TWA_ROUTE_DENSE 0   /* tensor-core contraction with the dense W          */

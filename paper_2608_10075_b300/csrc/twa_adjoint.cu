@@ -469,13 +469,13 @@ struct Adjoint {
 
     template <typename U>
     int alloc(U** p, size_t n) {
-        if (cudaMalloc(p, sizeof(U) * n) != cudaSuccess) return set_error(c, TWA_ENOMEM, "twa_grad: cudaMalloc");
+        if (dev_malloc(c, p, sizeof(U) * n) != cudaSuccess) return set_error(c, TWA_ENOMEM, "twa_grad: device allocation");
         owned.push_back(*p);
         return TWA_OK;
     }
     ~Adjoint() {
         cudaStreamSynchronize(c->stream);
-        for (void* p : owned) cudaFree(p);
+        for (void* p : owned) dev_free(c, p);
     }
 
     int contract(int which, const T* in, T* out) {

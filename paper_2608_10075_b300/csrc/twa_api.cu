@@ -8,6 +8,43 @@
 
 #include "twa_internal.cuh"
 
+
+namespace twa {
+
+cudaError_t dev_malloc(twa_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    if (c && c->opts.alloc && c->opts.free) {
+        *p = c->opts.alloc(bytes, (void*)c->stream, c->opts.alloc_user);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+void dev_free(twa_ctx* c, void* p) {
+    if (!p) return;
+    if (c && c->opts.alloc && c->opts.free) c->opts.free(p, (void*)c->stream, c->opts.alloc_user);
+    else cudaFree(p);
+}
+
+cudaError_t dev_malloc_async(twa_ctx* c, void** p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    if (c && c->opts.alloc && c->opts.free) {
+        *p = c->opts.alloc(bytes, (void*)st, c->opts.alloc_user);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+void dev_free_async(twa_ctx* c, void* p, cudaStream_t st) {
+    if (!p) return;
+    if (c && c->opts.alloc && c->opts.free) c->opts.free(p, (void*)st, c->opts.alloc_user);
+    else cudaFreeAsync(p, st);
+}
+
+}  // namespace twa
+
 namespace {
 thread_local std::string g_init_error;
 constexpr int64_t MAX_N = 60000;          // W and L in FP64 take 2 N^2 8 B (57.6 GB at the limit)
@@ -42,7 +79,7 @@ __global__ void k_window_means(const double* mom, const int64_t* cnt, double* ou
 int free_run_buffers(twa_ctx* c) {
     twa::f64_free(c);
     if (c->tc) twa::tc_free_run(c);
-    if (c->mom) cudaFree(c->mom);
+    twa::dev_free(c, c->mom);
     c->mom = nullptr;
     return TWA_OK;
 }
@@ -50,9 +87,9 @@ int free_run_buffers(twa_ctx* c) {
 // Fix M, allocate the trajectory buffers and zero the window sums.
 int fix_M(twa_ctx* c, int64_t M) {
     c->M = M;
-    if (cudaMalloc(&c->mom, sizeof(double) * 5 * M) != cudaSuccess) {
+    if (twa::dev_malloc(c, &c->mom, sizeof(double) * 5 * M) != cudaSuccess) {
         c->M = 0;
-        return set_error(c, TWA_ENOMEM, "cudaMalloc window sums");
+        return set_error(c, TWA_ENOMEM, "device window sums");
     }
     TWA_CUDA(c, cudaMemsetAsync(c->mom, 0, sizeof(double) * 5 * M, c->stream));
     int rc = use_tc(c) ? twa::tc_alloc(c) : twa::f64_alloc(c);
@@ -178,6 +215,8 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         return set_error(nullptr, TWA_EINVAL, "twa_init: ws_route must be TWA_ROUTE_DENSE or TWA_ROUTE_FFT");
     if (o.ws_route == TWA_ROUTE_FFT && o.precision == TWA_PREC_FP64)
         return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the FFT route runs with the BF16 precisions only");
+    if ((o.alloc == nullptr) != (o.free == nullptr))
+        return set_error(nullptr, TWA_EINVAL, "twa_init: give both alloc and free, or neither");
     if (o.sample_stride < 0 || o.sample_stride > MAX_COUNTER)
         return set_error(nullptr, TWA_EINVAL, "twa_init: sample_stride must be in [0, 2^32-1]");
     if (o.noise_route != TWA_NOISE_CHOLESKY && o.noise_route != TWA_NOISE_CIRCULANT)
@@ -208,10 +247,11 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         twa::cuda_check(c, e, "cudaGetDevice");
         return fail(TWA_ECUDA);
     }
-    if (cudaMalloc(&c->W64, sizeof(double) * N * N) != cudaSuccess ||
-        cudaMalloc(&c->L64, sizeof(double) * N * N) != cudaSuccess ||
-        cudaMalloc(&c->d_t, sizeof(int64_t)) != cudaSuccess || cudaMalloc(&c->d_count, sizeof(int64_t)) != cudaSuccess ||
-        cudaMalloc(&c->d_flags, sizeof(unsigned long long) * twa::FLAG_COUNT) != cudaSuccess) {
+    if (twa::dev_malloc(c, &c->W64, sizeof(double) * N * N) != cudaSuccess ||
+        twa::dev_malloc(c, &c->L64, sizeof(double) * N * N) != cudaSuccess ||
+        twa::dev_malloc(c, &c->d_t, sizeof(int64_t)) != cudaSuccess ||
+        twa::dev_malloc(c, &c->d_count, sizeof(int64_t)) != cudaSuccess ||
+        twa::dev_malloc(c, &c->d_flags, sizeof(unsigned long long) * twa::FLAG_COUNT) != cudaSuccess) {
         set_error(c, TWA_ENOMEM, "twa_init: device allocation failed");
         return fail(TWA_ENOMEM);
     }
@@ -291,7 +331,7 @@ int twa_get_state(twa_ctx* c, double* sx, double* sy, double* sz, int on_device)
     if (use_tc(c)) {
         double *dx = sx, *dy = sy, *dz = sz, *tmp = nullptr;
         if (!on_device) {
-            TWA_CUDA(c, cudaMallocAsync(&tmp, 3 * row * M, c->stream));
+            TWA_CUDA(c, twa::dev_malloc_async(c, &tmp, 3 * row * M, c->stream));
             dx = tmp;
             dy = tmp + M * N;
             dz = tmp + 2 * M * N;
@@ -302,7 +342,7 @@ int twa_get_state(twa_ctx* c, double* sx, double* sy, double* sz, int on_device)
             TWA_CUDA(c, cudaMemcpyAsync(sx, dx, row * M, cudaMemcpyDeviceToHost, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(sy, dy, row * M, cudaMemcpyDeviceToHost, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(sz, dz, row * M, cudaMemcpyDeviceToHost, c->stream));
-            TWA_CUDA(c, cudaFreeAsync(tmp, c->stream));
+            twa::dev_free_async(c, tmp, c->stream);
         }
     } else {
         const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -325,7 +365,7 @@ int twa_set_state(twa_ctx* c, int64_t M, const double* sx, const double* sy, con
         const double *dx = sx, *dy = sy, *dz = sz;
         double* tmp = nullptr;
         if (!on_device) {
-            TWA_CUDA(c, cudaMallocAsync(&tmp, 3 * row * M, c->stream));
+            TWA_CUDA(c, twa::dev_malloc_async(c, &tmp, 3 * row * M, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(tmp, sx, row * M, cudaMemcpyHostToDevice, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(tmp + M * N, sy, row * M, cudaMemcpyHostToDevice, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(tmp + 2 * M * N, sz, row * M, cudaMemcpyHostToDevice, c->stream));
@@ -334,7 +374,7 @@ int twa_set_state(twa_ctx* c, int64_t M, const double* sx, const double* sy, con
             dz = tmp + 2 * M * N;
         }
         rc = twa::tc_set_state(c, dx, dy, dz);
-        if (tmp) cudaFreeAsync(tmp, c->stream);
+        twa::dev_free_async(c, tmp, c->stream);
         if (rc) return rc;
     } else {
         const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -356,12 +396,12 @@ int twa_get_moments(twa_ctx* c, double* out, int on_device) {
     if (cnt == 0) return set_error(c, TWA_ESTATE, "twa_get_moments: no step inside the averaging window yet");
     const int64_t n = 5 * c->M;
     double* dst = out;
-    if (!on_device) TWA_CUDA(c, cudaMallocAsync(&dst, sizeof(double) * n, c->stream));
+    if (!on_device) TWA_CUDA(c, twa::dev_malloc_async(c, &dst, sizeof(double) * n, c->stream));
     k_window_means<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->mom, c->d_count, dst, n);
     TWA_CUDA(c, cudaGetLastError());
     if (!on_device) {
         TWA_CUDA(c, cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
-        TWA_CUDA(c, cudaFreeAsync(dst, c->stream));
+        twa::dev_free_async(c, dst, c->stream);
     }
     return check_device_flags(c);
 }
@@ -469,8 +509,7 @@ void twa_destroy(twa_ctx* c) {
     if (c->tc) twa::tc_free(c);
     twa::fft_free(c);
     void* p[] = {c->W64, c->L64, c->d_t, c->d_count, c->d_flags};
-    for (void* q : p)
-        if (q) cudaFree(q);
+    for (void* q : p) twa::dev_free(c, q);
     delete c;
 }
 

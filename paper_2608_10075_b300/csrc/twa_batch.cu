@@ -25,9 +25,10 @@ struct Snapshot {
 
 int snapshot(twa_ctx* c, Snapshot& s) {
     const size_t mn = sizeof(float) * c->M * c->N;
-    if (cudaMalloc(&s.X, mn) != cudaSuccess || cudaMalloc(&s.Y, mn) != cudaSuccess ||
-        cudaMalloc(&s.Z, mn) != cudaSuccess || cudaMalloc(&s.mom, sizeof(double) * 5 * c->M) != cudaSuccess)
-        return twa::set_error(c, TWA_ENOMEM, "batch autotuner: cudaMalloc snapshot");
+    if (twa::dev_malloc(c, &s.X, mn) != cudaSuccess || twa::dev_malloc(c, &s.Y, mn) != cudaSuccess ||
+        twa::dev_malloc(c, &s.Z, mn) != cudaSuccess ||
+        twa::dev_malloc(c, &s.mom, sizeof(double) * 5 * c->M) != cudaSuccess)
+        return twa::set_error(c, TWA_ENOMEM, "batch autotuner: device allocation of the snapshot");
     twa::TcState* t = c->tc;
     TWA_CUDA(c, cudaMemcpyAsync(s.X, t->X, mn, cudaMemcpyDeviceToDevice, c->stream));
     TWA_CUDA(c, cudaMemcpyAsync(s.Y, t->Y, mn, cudaMemcpyDeviceToDevice, c->stream));
@@ -51,10 +52,10 @@ int restore(twa_ctx* c, Snapshot& s) {
     int rc = twa::tc_state_changed(c);   // images and partial sums of the restored state
     if (rc) return rc;
     TWA_CUDA(c, cudaStreamSynchronize(c->stream));
-    cudaFree(s.X);
-    cudaFree(s.Y);
-    cudaFree(s.Z);
-    cudaFree(s.mom);
+    twa::dev_free(c, s.X);
+    twa::dev_free(c, s.Y);
+    twa::dev_free(c, s.Z);
+    twa::dev_free(c, s.mom);
     s = Snapshot();
     return TWA_OK;
 }
@@ -212,7 +213,9 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
                 for (int p; (p = next.fetch_add(1)) < n;) {
                     twa_opts op = o;
                     op.window_start = pts[p].window_start;
-                    op.stream = streams[w];
+                    // a caller's allocator may tie its blocks to the stream they were
+                    // allocated on: then every point is set up on the caller's stream
+                    op.stream = o.alloc ? o.stream : streams[w];
                     int r = twa_init(&ctx[p], pts[p].N, pts[p].alpha, pts[p].w, pts[p].Gamma, pts[p].dt, seed, &op);
                     if (r) {
                         rcs[p] = r;

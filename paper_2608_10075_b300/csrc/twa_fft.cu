@@ -599,11 +599,12 @@ int fft_prepare(twa_ctx* c) {
     while (v % 3 == 0) { f->radix[f->nst++] = 3; v /= 3; }
     while (v % 5 == 0) { f->radix[f->nst++] = 5; v /= 5; }
     double* cseq = nullptr;
-    if (cudaMalloc(&f->lam, sizeof(float) * P) != cudaSuccess || cudaMalloc(&f->tw, sizeof(float2) * P) != cudaSuccess ||
-        cudaMalloc(&f->nscale, sizeof(float) * P) != cudaSuccess ||
-        cudaMalloc(&f->nfreq, sizeof(int32_t) * P) != cudaSuccess ||
-        cudaMallocAsync(&cseq, sizeof(double) * (P / 2 + 1), c->stream) != cudaSuccess)
-        return set_error(c, TWA_ENOMEM, "cudaMalloc FFT plan");
+    if (dev_malloc(c, &f->lam, sizeof(float) * P) != cudaSuccess ||
+        dev_malloc(c, &f->tw, sizeof(float2) * P) != cudaSuccess ||
+        dev_malloc(c, &f->nscale, sizeof(float) * P) != cudaSuccess ||
+        dev_malloc(c, &f->nfreq, sizeof(int32_t) * P) != cudaSuccess ||
+        dev_malloc_async(c, &cseq, sizeof(double) * (P / 2 + 1), c->stream) != cudaSuccess)
+        return set_error(c, TWA_ENOMEM, "device allocation of the FFT plan");
     RadixPlan rp{};
     rp.nst = f->nst;
     for (int s = 0; s < f->nst; ++s) rp.radix[s] = f->radix[s];
@@ -612,7 +613,7 @@ int fft_prepare(twa_ctx* c) {
     k_fft_sequence<<<(unsigned)((P / 2 + 256) / 256), 256, 0, c->stream>>>(cseq, P, c->alpha, c->w);
     k_fft_lambda<<<g, 256, 0, c->stream>>>(f->lam, f->nscale, f->nfreq, cseq, P, rp);
     TWA_CUDA(c, cudaGetLastError());
-    TWA_CUDA(c, cudaFreeAsync(cseq, c->stream));
+    dev_free_async(c, cseq, c->stream);
     int rc;
     if ((rc = set_smem(c, (const void*)k_fft_pred)) || (rc = set_smem(c, (const void*)k_fft_corr)) ||
         (rc = set_smem(c, (const void*)k_fft_field)) || (rc = set_smem(c, (const void*)k_fft_noise)))
@@ -623,8 +624,7 @@ int fft_prepare(twa_ctx* c) {
 void fft_free(twa_ctx* c) {
     if (!c->fft) return;
     void* p[] = {c->fft->lam, c->fft->tw, c->fft->nscale, c->fft->nfreq};
-    for (void* q : p)
-        if (q) cudaFree(q);
+    for (void* q : p) dev_free(c, q);
     delete c->fft;
     c->fft = nullptr;
 }

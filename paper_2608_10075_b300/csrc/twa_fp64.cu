@@ -256,20 +256,20 @@ int f64_alloc(twa_ctx* c) {
     double** bufs2[] = {&c->xy, &c->xyp, &c->hxy, &c->eta, &c->pf};
     double** bufs1[] = {&c->z, &c->zp, &c->hz};
     for (auto b : bufs2)
-        if (cudaMalloc(b, sizeof(double) * 2 * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc state");
+        if (dev_malloc(c, b, sizeof(double) * 2 * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device state");
     for (auto b : bufs1)
-        if (cudaMalloc(b, sizeof(double) * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc state");
-    if (cudaMalloc(&c->xi, sizeof(double) * 2 * c->M) != cudaSuccess ||
-        cudaMalloc(&c->S, sizeof(double) * 4 * c->M) != cudaSuccess ||
-        cudaMalloc(&c->Sp, sizeof(double) * 4 * c->M) != cudaSuccess)
-        return set_error(c, TWA_ENOMEM, "cudaMalloc state");
+        if (dev_malloc(c, b, sizeof(double) * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device state");
+    if (dev_malloc(c, &c->xi, sizeof(double) * 2 * c->M) != cudaSuccess ||
+        dev_malloc(c, &c->S, sizeof(double) * 4 * c->M) != cudaSuccess ||
+        dev_malloc(c, &c->Sp, sizeof(double) * 4 * c->M) != cudaSuccess)
+        return set_error(c, TWA_ENOMEM, "device state");
     return TWA_OK;
 }
 
 void f64_free(twa_ctx* c) {
     double** all[] = {&c->xy, &c->xyp, &c->hxy, &c->eta, &c->pf, &c->z, &c->zp, &c->hz, &c->xi, &c->S, &c->Sp};
     for (auto b : all) {
-        if (*b) cudaFree(*b);
+        dev_free(c, *b);
         *b = nullptr;
     }
 }

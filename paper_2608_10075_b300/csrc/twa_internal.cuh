@@ -231,6 +231,24 @@ __device__ __forceinline__ void init_signs(uint64_t seed, uint32_t m, uint32_t i
 }
 
 // ---------------------------------------------------------------------------
+// Device memory of a context: through the caller's allocator when twa_opts
+// names one, else cudaMalloc / cudaFree for buffers that live with the context
+// and cudaMallocAsync / cudaFreeAsync (ordered on `st`) for scratch of one call.
+// A request of 0 bytes gives NULL and succeeds.
+cudaError_t dev_malloc(twa_ctx* c, void** p, size_t bytes);
+void dev_free(twa_ctx* c, void* p);
+cudaError_t dev_malloc_async(twa_ctx* c, void** p, size_t bytes, cudaStream_t st);
+void dev_free_async(twa_ctx* c, void* p, cudaStream_t st);
+template <class T>
+cudaError_t dev_malloc(twa_ctx* c, T** p, size_t bytes) {
+    return dev_malloc(c, reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+cudaError_t dev_malloc_async(twa_ctx* c, T** p, size_t bytes, cudaStream_t st) {
+    return dev_malloc_async(c, reinterpret_cast<void**>(p), bytes, st);
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // twa_setup.cu
 int setup_pump(twa_ctx* c);                      // W64, L64, pivots, spectrum

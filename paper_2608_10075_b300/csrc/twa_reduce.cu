@@ -127,14 +127,14 @@ __global__ void __launch_bounds__(RT) k_observables(const double* mom, const int
 
 int reduce_observables(twa_ctx* c, twa_obs* o) {
     double* d = nullptr;
-    TWA_CUDA(c, cudaMallocAsync(&d, 8 * sizeof(double), c->stream));
+    TWA_CUDA(c, dev_malloc_async(c, &d, 8 * sizeof(double), c->stream));
     k_observables<<<1, RT, 0, c->stream>>>(c->mom, c->d_count, c->M, d);
     TWA_CUDA(c, cudaGetLastError());
     double h[8];
     int64_t cnt = 0;
     TWA_CUDA(c, cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     TWA_CUDA(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
-    TWA_CUDA(c, cudaFreeAsync(d, c->stream));
+    dev_free_async(c, d, c->stream);
     TWA_CUDA(c, cudaStreamSynchronize(c->stream));
     o->Sz = h[0];
     o->Sz_se = h[1];

@@ -264,7 +264,7 @@ int setup_pump(twa_ctx* c) {
     TWA_CUDA(c, cudaGetLastError());
 
     double* piv = nullptr;
-    TWA_CUDA(c, cudaMallocAsync(&piv, sizeof(double) * (N + 8), st));
+    TWA_CUDA(c, dev_malloc_async(c, &piv, sizeof(double) * (N + 8), st));
     c->clipped = 0;
     if (c->w == 0.0 || c->alpha == 0.0 || isinf(c->alpha)) {
         const int mode = (c->w == 0.0) ? 2 : (c->alpha == 0.0 ? 0 : 1);
@@ -295,7 +295,7 @@ int setup_pump(twa_ctx* c) {
         if (fl[FLAG_NOTPSD] > 0) {
             c->clipped = (int64_t)fl[FLAG_NOTPSD];
             if (!c->opts.clip_negative) {
-                cudaFreeAsync(piv, st);
+                dev_free_async(c, piv, st);
                 return set_error(c, TWA_ENOTPSD,
                                  "pump matrix not positive definite: pivot " +
                                      std::to_string((long long)fl[FLAG_NOTPSD_IDX] - 1) + " <= 0 (" +
@@ -310,7 +310,7 @@ int setup_pump(twa_ctx* c) {
     // space is taken large (the full space for N <= 1024)
     const int kmax = (int)(N < 1024 ? N : 1024);
     double* lz = nullptr;
-    TWA_CUDA(c, cudaMallocAsync(&lz, sizeof(double) * (4 * N + 2 * kmax + 8), st));
+    TWA_CUDA(c, dev_malloc_async(c, &lz, sizeof(double) * (4 * N + 2 * kmax + 8), st));
     double *v0 = lz, *v1 = lz + N, *v2 = lz + 2 * N, *y = lz + 3 * N;
     double *al = lz + 4 * N, *be = al + kmax, *ext = be + kmax;
     k_lanczos_start<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(v1, N);
@@ -330,8 +330,8 @@ int setup_pump(twa_ctx* c) {
     TWA_CUDA(c, cudaStreamSynchronize(st));
     c->w_max = e2[0];
     c->w_min = e2[1];
-    cudaFreeAsync(lz, st);
-    cudaFreeAsync(piv, st);
+    dev_free_async(c, lz, st);
+    dev_free_async(c, piv, st);
     TWA_CUDA(c, cudaStreamSynchronize(st));
     return TWA_OK;
 }

@@ -1019,7 +1019,7 @@ int tc_prepare(twa_ctx* c) {
     const size_t nb = sizeof(__nv_bfloat16) * (size_t)c->N * t->ldk;
     __nv_bfloat16** m4[] = {&t->Whi, &t->Wlo, &t->Lhi, &t->Llo};
     for (auto p : m4)
-        if (cudaMalloc(p, nb) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc BF16 images");
+        if (dev_malloc(c, p, nb) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device BF16 images");
     const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
     k_split_matrix<<<g, 256, 0, c->stream>>>(c->W64, c->N, t->ldk, t->Whi, t->Wlo);
     k_split_matrix<<<g, 256, 0, c->stream>>>(c->L64, c->N, t->ldk, t->Lhi, t->Llo);
@@ -1033,17 +1033,17 @@ int tc_alloc(twa_ctx* c) {
     const size_t mn = (size_t)c->M * c->N;
     float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Bx, &t->By};
     for (auto p : f)
-        if (cudaMalloc(p, sizeof(float) * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc state");
+        if (dev_malloc(c, p, sizeof(float) * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device state");
     const size_t ni = sizeof(__nv_bfloat16) * 2 * (size_t)c->M * t->ldk;
     __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E};
     for (auto p : b) {
-        if (cudaMalloc(p, ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "cudaMalloc images");
+        if (dev_malloc(c, p, ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device images");
         TWA_CUDA(c, cudaMemsetAsync(*p, 0, ni, c->stream));
     }
-    if (cudaMalloc(&t->XI, sizeof(float) * 2 * c->M) != cudaSuccess ||
-        cudaMalloc(&t->part, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess ||
-        cudaMalloc(&t->partp, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess)
-        return set_error(c, TWA_ENOMEM, "cudaMalloc sums");
+    if (dev_malloc(c, &t->XI, sizeof(float) * 2 * c->M) != cudaSuccess ||
+        dev_malloc(c, &t->part, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess ||
+        dev_malloc(c, &t->partp, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess)
+        return set_error(c, TWA_ENOMEM, "device sums");
     return make_state_maps(c);
 }
 
@@ -1058,12 +1058,12 @@ void tc_free_run(twa_ctx* c) {
     float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Bx, &t->By, &t->Bx1,
                    &t->By1, &t->XI, &t->part, &t->partp};
     for (auto p : f) {
-        if (*p) cudaFree(*p);
+        dev_free(c, *p);
         *p = nullptr;
     }
     __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E};
     for (auto p : b) {
-        if (*p) cudaFree(*p);
+        dev_free(c, *p);
         *p = nullptr;
     }
 }
@@ -1073,8 +1073,8 @@ int tc_set_extra_matrix(twa_ctx* c, int slot, const double* A64) {
     if (slot < 0 || slot > 1) return set_error(c, TWA_EINVAL, "tc_set_extra_matrix: slot");
     const size_t nb = sizeof(__nv_bfloat16) * (size_t)c->N * t->ldk;
     if (!t->Xhi[slot]) {
-        if (cudaMalloc(&t->Xhi[slot], nb) != cudaSuccess || cudaMalloc(&t->Xlo[slot], nb) != cudaSuccess)
-            return set_error(c, TWA_ENOMEM, "cudaMalloc extra matrix images");
+        if (dev_malloc(c, &t->Xhi[slot], nb) != cudaSuccess || dev_malloc(c, &t->Xlo[slot], nb) != cudaSuccess)
+            return set_error(c, TWA_ENOMEM, "device extra matrix images");
     }
     const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
     k_split_matrix<<<g, 256, 0, c->stream>>>(A64, c->N, t->ldk, t->Xhi[slot], t->Xlo[slot]);
@@ -1088,12 +1088,12 @@ int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t 
     TcState* t = c->tc;
     int rc;
     if (t->vec_rows != K) {
-        if (t->Vhi) cudaFree(t->Vhi);
-        if (t->Vlo) cudaFree(t->Vlo);
+        dev_free(c, t->Vhi);
+        dev_free(c, t->Vlo);
         const size_t ni = sizeof(__nv_bfloat16) * (size_t)K * t->ldk;
         t->Vhi = t->Vlo = nullptr;
-        if (cudaMalloc(&t->Vhi, ni) != cudaSuccess || cudaMalloc(&t->Vlo, ni) != cudaSuccess)
-            return set_error(c, TWA_ENOMEM, "cudaMalloc vector images");
+        if (dev_malloc(c, &t->Vhi, ni) != cudaSuccess || dev_malloc(c, &t->Vlo, ni) != cudaSuccess)
+            return set_error(c, TWA_ENOMEM, "device vector images");
         TWA_CUDA(c, cudaMemsetAsync(t->Vhi, 0, ni, c->stream));
         TWA_CUDA(c, cudaMemsetAsync(t->Vlo, 0, ni, c->stream));
         if ((rc = make_map(c, &t->tmVhi, t->Vhi, K, c->N, t->ldk, t->bn, t->kc))) return rc;
@@ -1119,11 +1119,9 @@ void tc_free(twa_ctx* c) {
     if (!t) return;
     tc_free_run(c);
     void* extra[] = {t->Xhi[0], t->Xhi[1], t->Xlo[0], t->Xlo[1], t->Vhi, t->Vlo};
-    for (void* p : extra)
-        if (p) cudaFree(p);
+    for (void* p : extra) dev_free(c, p);
     void* all[] = {t->Whi, t->Wlo, t->Lhi, t->Llo};
-    for (void* p : all)
-        if (p) cudaFree(p);
+    for (void* p : all) dev_free(c, p);
     delete t;
     c->tc = nullptr;
 }
@@ -1171,6 +1169,7 @@ struct MixPlan {
     double leta_flops = 0.0, w_flops = 0.0;   // of all L.eta tiles / all W.s tiles of one stage
     int64_t leta_tiles = 0;                   // tiles of the L.eta block
     std::vector<GroupDesc> host;              // host copy of desc
+    twa_ctx* owner = nullptr;                 // whose allocator the tables came from
 };
 
 namespace {
@@ -1178,8 +1177,7 @@ namespace {
 void mix_plan_free(MixPlan* p) {
     if (!p) return;
     void* q[] = {p->desc, p->start, p->lstart, p->list[0], p->list[1], p->first[0], p->first[1]};
-    for (void* x : q)
-        if (x) cudaFree(x);
+    for (void* x : q) dev_free(p->owner, x);
     delete p;
 }
 
@@ -1252,8 +1250,8 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
     for (int q = 0; q < n; ++q) {
         TcState* t = cs[q]->tc;
         const size_t mn = sizeof(float) * cs[q]->M * cs[q]->N;
-        if (!t->Bx1 && (cudaMalloc(&t->Bx1, mn) != cudaSuccess || cudaMalloc(&t->By1, mn) != cudaSuccess))
-            return set_error(ec, TWA_ENOMEM, "cudaMalloc noise part");
+        if (!t->Bx1 && (dev_malloc(cs[q], &t->Bx1, mn) != cudaSuccess || dev_malloc(cs[q], &t->By1, mn) != cudaSuccess))
+            return set_error(ec, TWA_ENOMEM, "device noise part");
     }
 
     // tile costs in K stages x products; algorithmic FLOPs per tile
@@ -1365,13 +1363,14 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
     p->host = d;
     std::vector<int64_t> lst(n + 1);
     for (int q = 0; q <= n; ++q) lst[q] = st[2 * n + q] - st[2 * n];
-    bool ok = cudaMalloc(&p->desc, sizeof(GroupDesc) * d.size()) == cudaSuccess &&
-              cudaMalloc(&p->start, sizeof(int64_t) * st.size()) == cudaSuccess &&
-              cudaMalloc(&p->lstart, sizeof(int64_t) * lst.size()) == cudaSuccess;
+    p->owner = ec;
+    bool ok = dev_malloc(ec, &p->desc, sizeof(GroupDesc) * d.size()) == cudaSuccess &&
+              dev_malloc(ec, &p->start, sizeof(int64_t) * st.size()) == cudaSuccess &&
+              dev_malloc(ec, &p->lstart, sizeof(int64_t) * lst.size()) == cudaSuccess;
     for (int L = 0; L < 2 && ok; ++L)
-        ok = cudaMalloc(&p->list[L], sizeof(int32_t) * lists[L].size()) == cudaSuccess &&
-             cudaMalloc(&p->first[L], sizeof(int32_t) * firsts[L].size()) == cudaSuccess;
-    if (!ok) return set_error(ec, TWA_ENOMEM, "cudaMalloc dense step plan");
+        ok = dev_malloc(ec, &p->list[L], sizeof(int32_t) * lists[L].size()) == cudaSuccess &&
+             dev_malloc(ec, &p->first[L], sizeof(int32_t) * firsts[L].size()) == cudaSuccess;
+    if (!ok) return set_error(ec, TWA_ENOMEM, "device allocation of the dense step plan");
     ok = cudaMemcpy(p->desc, d.data(), sizeof(GroupDesc) * d.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(p->start, st.data(), sizeof(int64_t) * st.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(p->lstart, lst.data(), sizeof(int64_t) * lst.size(), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -1549,9 +1548,9 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
     float* out = nullptr;
     const size_t ni = sizeof(__nv_bfloat16) * (size_t)K * ldk;
-    TWA_CUDA(c, cudaMallocAsync(&hi, ni, c->stream));
-    TWA_CUDA(c, cudaMallocAsync(&lo, ni, c->stream));
-    TWA_CUDA(c, cudaMallocAsync(&out, sizeof(float) * K * N, c->stream));
+    TWA_CUDA(c, dev_malloc_async(c, &hi, ni, c->stream));
+    TWA_CUDA(c, dev_malloc_async(c, &lo, ni, c->stream));
+    TWA_CUDA(c, dev_malloc_async(c, &out, sizeof(float) * K * N, c->stream));
     TWA_CUDA(c, cudaMemsetAsync(hi, 0, ni, c->stream));
     TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
     k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo);
@@ -1567,9 +1566,9 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     rc = (t->terms == 3) ? launch_cfg<MODE_FIELD, 3>(c, fm, fa) : launch_cfg<MODE_FIELD, 1>(c, fm, fa);
     if (rc) return rc;
     k_widen<<<nblk(K * N, 256), 256, 0, c->stream>>>(out, P, K * N);
-    cudaFreeAsync(hi, c->stream);
-    cudaFreeAsync(lo, c->stream);
-    cudaFreeAsync(out, c->stream);
+    dev_free_async(c, hi, c->stream);
+    dev_free_async(c, lo, c->stream);
+    dev_free_async(c, out, c->stream);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }
@@ -1585,20 +1584,21 @@ struct TcBatch {
     StepDesc* sd = nullptr;
     int64_t *nstart = nullptr, *mstart = nullptr;
     TcArgs flag_args{};
+    twa_ctx* owner = nullptr;   // whose allocator the tables came from
 };
 
 void tc_batch_free(TcBatch* b) {
     if (!b) return;
     mix_plan_free(b->mix);
     void* p[] = {b->sd, b->nstart, b->mstart};
-    for (void* q : p)
-        if (q) cudaFree(q);
+    for (void* q : p) dev_free(b->owner, q);
     delete b;
 }
 
 int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
     *out = nullptr;
     TcBatch* b = new TcBatch();
+    b->owner = lead;
     b->n = n;
     b->x3 = lead->tc->terms == 3;
     std::vector<StepDesc> sd(n);
@@ -1625,9 +1625,9 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
         tc_batch_free(b);
         return rc;
     }
-    bool ok = cudaMalloc(&b->sd, sizeof(StepDesc) * n) == cudaSuccess &&
-              cudaMalloc(&b->nstart, sizeof(int64_t) * (n + 1)) == cudaSuccess &&
-              cudaMalloc(&b->mstart, sizeof(int64_t) * (n + 1)) == cudaSuccess;
+    bool ok = dev_malloc(lead, &b->sd, sizeof(StepDesc) * n) == cudaSuccess &&
+              dev_malloc(lead, &b->nstart, sizeof(int64_t) * (n + 1)) == cudaSuccess &&
+              dev_malloc(lead, &b->mstart, sizeof(int64_t) * (n + 1)) == cudaSuccess;
     ok = ok && cudaMemcpy(b->sd, sd.data(), sizeof(StepDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(b->nstart, ns.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(b->mstart, ms.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess;

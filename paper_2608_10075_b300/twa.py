@@ -25,11 +25,46 @@ class TWAError(RuntimeError):
         self.name = ERRORS.get(code, "?")
 
 
+# twa_alloc_fn / twa_free_fn of include/twa.h
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("init_state", ctypes.c_int), ("window_start", ctypes.c_double),
                 ("renormalize", ctypes.c_int), ("clip_negative", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("traj_offset", ctypes.c_int64), ("ws_route", ctypes.c_int), ("noise_route", ctypes.c_int),
-                ("sample_stride", ctypes.c_int64)]
+                ("sample_stride", ctypes.c_int64), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", ctypes.c_void_p)]
+
+
+def torch_allocator():
+    """(alloc, free) C callbacks that take a context's device memory from
+    torch's caching allocator, on the stream the library passes. Keep the
+    returned pair alive as long as the context (TWA does that itself)."""
+    import torch
+
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(alloc), FREE_FN(free)
+
+
+def _allocator(allocator):
+    """None, "torch", or a pair (alloc(nbytes, stream) -> int, free(ptr, stream))."""
+    if allocator is None:
+        return None
+    if allocator == "torch":
+        return torch_allocator()
+    a, f = allocator
+    return (ALLOC_FN(lambda n, s, u: a(int(n), int(s or 0)) or None),
+            FREE_FN(lambda p, s, u: f(int(p), int(s or 0))))
 
 
 ROUTE = {"dense": 0, "fft": 1}
@@ -144,7 +179,7 @@ class TWA:
 
     def __init__(self, N, alpha, w, Gamma, dt, seed=0, precision="fp64", init_state=-1, window_start=0.0,
                  renormalize=True, clip_negative=False, stream=None, traj_offset=0, ws_route="dense",
-                 noise_route="cholesky", sample_stride=1):
+                 noise_route="cholesky", sample_stride=1, allocator=None):
         L = lib()
         o = Opts()
         L.twa_opts_default(ctypes.byref(o))
@@ -158,6 +193,10 @@ class TWA:
         o.ws_route = ROUTE[ws_route] if isinstance(ws_route, str) else int(ws_route)
         o.noise_route = NOISE[noise_route] if isinstance(noise_route, str) else int(noise_route)
         o.sample_stride = int(sample_stride)
+        # device memory from the caller's allocator (kept alive with the context)
+        self._alloc = _allocator(allocator)
+        if self._alloc is not None:
+            o.alloc, o.free = self._alloc
         self._stream = stream
         h = ctypes.c_void_p()
         a = float(alpha)
@@ -285,7 +324,7 @@ def reduce_moments(means, N):
     return o.as_dict()
 
 
-def batch_run(points, M, seed=0, precision="bf16x3", stream=None):
+def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None):
     """twa_batch_run: points = list of dicts with N, alpha, w, Gamma, dt, steps,
     window_start. Returns (list of observables dicts, (BN, K-stage config))."""
     arr = (Point * len(points))()
@@ -296,6 +335,9 @@ def batch_run(points, M, seed=0, precision="bf16x3", stream=None):
     lib().twa_opts_default(ctypes.byref(o))
     o.precision = PRECISION[precision]
     o.stream = _stream_handle(stream)
+    alloc = _allocator(allocator)
+    if alloc is not None:
+        o.alloc, o.free = alloc
     out = (Obs * len(points))()
     tiles = (ctypes.c_int * 2)()
     rc = lib().twa_batch_run(ctypes.cast(arr, ctypes.c_void_p), len(points), int(M), int(seed) & (2 ** 64 - 1),

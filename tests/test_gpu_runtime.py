@@ -125,3 +125,73 @@ def test_sample_stride_selects_every_kth_window_step(prec, route, noise):
     # FP64 path: the same sums; mixed paths: FP32 state summed in a different order
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert np.allclose(mom, acc / n, rtol=tol, atol=tol * np.abs(acc / n).max())
+
+
+def _count_allocator():
+    """(alloc, free) over torch's caching allocator that record every pointer."""
+    import torch
+    live, log = {}, {"alloc": 0, "free": 0, "bad_free": 0}
+
+    def alloc(nbytes, stream):
+        p = torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+        live[p] = nbytes
+        log["alloc"] += 1
+        return p
+
+    def free(ptr, stream):
+        if live.pop(ptr, None) is None:
+            log["bad_free"] += 1
+        log["free"] += 1
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return (alloc, free), live, log
+
+
+@pytest.mark.parametrize("prec,route,noise", [("fp64", "dense", "cholesky"), ("bf16x3", "dense", "cholesky"),
+                                              ("bf16x3", "fft", "circulant")])
+def test_caller_allocator_gives_the_same_results_and_frees_everything(prec, route, noise):
+    # all device memory of the context and of its calls from the caller's
+    # allocator (here torch's caching allocator): same bits as the library's own
+    # allocator, every block handed back exactly once by twa_destroy
+    import torch
+    from paper_2608_10075_b300 import twa
+    N, M, steps = 130, 40, 7
+    kw = dict(seed=5, precision=prec, window_start=0.002, ws_route=route, noise_route=noise)
+    with twa.TWA(N, 1.0, 12.0, 1.0, 1e-3, **kw) as g:
+        g.run(M, steps)
+        ref = g.get_state()
+        ref_obs = g.observables()
+    base = torch.cuda.memory_allocated()
+    pair, live, log = _count_allocator()
+    with twa.TWA(N, 1.0, 12.0, 1.0, 1e-3, allocator=pair, **kw) as g:
+        g.run(M, steps)
+        st = g.get_state()
+        obs = g.observables()
+        assert torch.cuda.memory_allocated() - base >= sum(live.values()) >= 2 * 8 * N * N   # W, L in FP64
+    for a, b in zip(ref, st):
+        assert np.array_equal(a, b)
+    for k in ("Sz", "SpSm", "G2num", "g2"):
+        assert obs[k] == ref_obs[k]
+    assert log["alloc"] > 0 and log["alloc"] == log["free"] and log["bad_free"] == 0 and not live
+    assert torch.cuda.memory_allocated() == base
+
+
+def test_caller_allocator_in_gradients_and_batches():
+    import torch
+    from paper_2608_10075_b300 import twa
+    base = torch.cuda.memory_allocated()
+    pair, live, log = _count_allocator()
+    with twa.TWA(40, 0.8, 10.0, 1.0, 1e-3, seed=2, precision="fp64", window_start=0.01, allocator=pair) as g:
+        r1 = g.grad("g2", 24, 30, checkpoint=7)
+    with twa.TWA(40, 0.8, 10.0, 1.0, 1e-3, seed=2, precision="fp64", window_start=0.01) as g:
+        r0 = g.grad("g2", 24, 30, checkpoint=7)
+    assert r1["dJ_dw"] == r0["dJ_dw"] and r1["dJ_dalpha"] == r0["dJ_dalpha"]
+    pts = [dict(N=100, alpha=1.5, w=25.0, Gamma=1.0, dt=5e-4, steps=9, window_start=0.001),
+           dict(N=37, alpha=1.0, w=3.0, Gamma=1.0, dt=1e-3, steps=6, window_start=0.002)]
+    a, _ = twa.batch_run(pts, 16, seed=3, allocator=pair)
+    b, _ = twa.batch_run(pts, 16, seed=3)
+    for x, y in zip(a, b):
+        for k in ("Sz", "SpSm", "G2num", "g2"):
+            assert x[k] == y[k]
+    assert log["alloc"] == log["free"] and log["bad_free"] == 0 and not live
+    assert torch.cuda.memory_allocated() == base
