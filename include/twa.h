@@ -70,6 +70,11 @@ extern "C" {
 #define TWA_PREC_FP64    0   /* FP64 everywhere (SIMT DFMA)                              */
 #define TWA_PREC_BF16    1   /* tcgen05 BF16 x BF16 -> FP32, one term, FP32 state        */
 #define TWA_PREC_BF16X3  2   /* tcgen05 split hi+lo: hi*hi + hi*lo + lo*hi, FP32 state   */
+#define TWA_PREC_TF32    3   /* tcgen05 TF32 x TF32 -> FP32, one term, FP32 state; W, L,
+                                s and eta rounded to TF32 (11 significant bits, relative
+                                error 2^-11 against 2^-8 for BF16). Dense and FFT routes
+                                of twa_init / twa_run / twa_field; not twa_grad,
+                                twa_batch_run or the extra-matrix contractions        */
 
 typedef struct twa_ctx twa_ctx;   /* opaque, owned by the library */
 
@@ -218,8 +223,8 @@ TWA_API int twa_get_moments(twa_ctx* ctx, double* out, int on_device);
 
 /* Pump-field contraction of Eq. S1, P[k][i] = sum_j w_ij s[k][j], for K
  * caller vectors s (device, [K][N] doubles) into P (device, [K][N] doubles),
- * computed with the context's precision path (FP64, or the BF16 images of W
- * and an hi/lo split of s with FP32 accumulation). Enqueued on the context's
+ * computed with the context's precision path (FP64; the BF16 images of W
+ * and an hi/lo split of s, or their TF32 images, with FP32 accumulation). Enqueued on the context's
  * stream. Errors: TWA_EINVAL (NULL, K < 1). */
 TWA_API int twa_field(twa_ctx* ctx, const double* s, double* P, int64_t K);
 
@@ -245,8 +250,8 @@ typedef struct twa_grad_out {
 } twa_grad_out;
 
 /* Pathwise gradient of a steady-state objective with respect to the pump
- * prefactor w and exponent alpha of Eq. 2 at fixed noise (spec pattern 3:
- * not in the paper, which computes no derivatives).
+ * prefactor w and exponent alpha of Eq. 2 at fixed noise (an extension: the
+ * paper computes no derivatives).
  *
  * Runs its own forward pass of `steps` stochastic-Heun steps from the initial
  * state (the same trajectories twa_run would produce: same seed, counters and
@@ -265,7 +270,8 @@ typedef struct twa_grad_out {
  * their standard deviation / sqrt(M) the returned SE. Synchronises.
  * Errors: TWA_EINVAL (NULL, M < 1, steps < 1), TWA_ESTATE (no step inside the
  * window), TWA_EUNSUPPORTED (want_alpha with alpha = 0 or inf, w = 0, a
- * context with noise_route = TWA_NOISE_CIRCULANT), TWA_ENOMEM, TWA_ECUDA,
+ * context with noise_route = TWA_NOISE_CIRCULANT or precision = TWA_PREC_TF32),
+ * TWA_ENOMEM, TWA_ECUDA,
  * TWA_ENONFINITE. */
 TWA_API int twa_grad(twa_ctx* ctx, const twa_grad_req* req, twa_grad_out* out, double* per_traj);
 
@@ -278,8 +284,7 @@ typedef struct twa_point {
     double  window_start;   /* averaging window start time (as twa_opts)           */
 } twa_point;
 
-/* Run many parameter points of uneven N together (spec pattern 2, e.g. a
- * phase-diagram scan) and return each point's observables in out[0..n-1].
+/* Run many parameter points of uneven N together (e.g. a phase-diagram scan) and return each point's observables in out[0..n-1].
  *
  * Every point gets its own pump matrix, Cholesky factor and M trajectories (set
  * up concurrently from several host threads, each on its own stream; seed

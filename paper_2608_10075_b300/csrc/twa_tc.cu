@@ -61,36 +61,51 @@ constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 // count read from its group descriptor.
 enum Mode { MODE_FIELD = 0, MODE_LETA = 1, MODE_PRED = 2, MODE_CORR = 3, MODE_MIX = 4 };
 
-// K-stage configurations: K tile width, swizzle and ring depth.
+// K-stage configurations: K tile width (elements), element size, swizzle and ring
+// depth. KC = 2 is the TF32 precision mode: FP32 containers holding TF32 values,
+// kind::tf32 MMAs (K = 8 per instruction, the same 32 bytes of a row as 16 BF16).
 template <int KC>
 struct KCfg;
 template <>
 struct KCfg<0> {   // 64 BF16 = 128 B rows, SWIZZLE_128B, two stages
-    static constexpr int BK = 64, STAGES = 2;
+    static constexpr int BK = 64, STAGES = 2, ESZ = 2;
+    static constexpr bool TF32 = false;
     static constexpr uint64_t LAYOUT = 2;   // descriptor layout code of SWIZZLE_128B
     static constexpr uint32_t SBO = 1024;   // 8 rows x 128 B
 };
 template <>
 struct KCfg<1> {   // 32 BF16 = 64 B rows, SWIZZLE_64B, four stages
-    static constexpr int BK = 32, STAGES = 4;
+    static constexpr int BK = 32, STAGES = 4, ESZ = 2;
+    static constexpr bool TF32 = false;
     static constexpr uint64_t LAYOUT = 4;   // SWIZZLE_64B
     static constexpr uint32_t SBO = 512;    // 8 rows x 64 B
 };
+template <>
+struct KCfg<2> {   // 16 TF32 = 64 B rows, SWIZZLE_64B, four stages
+    static constexpr int BK = 16, STAGES = 4, ESZ = 4;
+    static constexpr bool TF32 = true;
+    static constexpr uint64_t LAYOUT = 4;
+    static constexpr uint32_t SBO = 512;
+};
+inline int kcfg_bk(int kc) { return kc == 0 ? KCfg<0>::BK : kc == 1 ? KCfg<1>::BK : KCfg<2>::BK; }
 
 template <int BN, int KC>
 struct Geo {
     static constexpr int BK = KCfg<KC>::BK, STAGES = KCfg<KC>::STAGES;
-    static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int A_BYTES = BM * BK * KCfg<KC>::ESZ;
+    static constexpr int B_BYTES = BN * BK * KCfg<KC>::ESZ;
+    static constexpr int MMAS = BK * KCfg<KC>::ESZ / 32;   // MMAs per stage: 32 bytes of K each
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int TILES = STAGES * STAGE_BYTES;
     static constexpr int NTRAJ = BN / 2;
     static constexpr int EXTRA = (2 * STAGES + 4) * 8 + 16 + NTRAJ * 2 * 4 * 2 + 4 * NTRAJ * 3 * 4;
     static constexpr int SMEM = TILES + EXTRA + 1024;
     static constexpr uint32_t NCOLS = (2 * BN <= 256) ? 256 : 512;
-    // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits
-    // 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+    // instruction descriptor: D = F32 (bits 4-5 = 1), A and B format at bits 7-9 and
+    // 10-12 (kind::f16: BF16 = 1; kind::tf32: TF32 = 2), both K-major, N >> 3 at
+    // bits 17-22, M >> 4 at bits 24-28.
+    static constexpr uint32_t FMT = KCfg<KC>::TF32 ? 2u : 1u;
+    static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(BM >> 4) << 24);
 };
 
@@ -162,12 +177,21 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
            ((uint64_t)1 << 46) | (KCfg<KC>::LAYOUT << 61);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+template <bool TF32>
+__device__ __forceinline__ void mma_issue(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    if constexpr (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -198,6 +222,21 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[off] = h;
     if (with_lo) lo[off] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// v rounded to TF32 (10 explicit mantissa bits, nearest, ties away), in FP32.
+__device__ __forceinline__ float to_tf32(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// Operand image entry `off` of value v: BF16 hi (+ lo) or, in the TF32 mode, one
+// TF32 value in an FP32 container (the storage of `hi` then holds floats).
+__device__ __forceinline__ void image_store(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t off, float v, bool with_lo,
+                                            bool tf32) {
+    if (tf32) reinterpret_cast<float*>(hi)[off] = to_tf32(v);
+    else split_store(hi, lo, off, v, with_lo);
 }
 
 struct TcMaps {
@@ -244,6 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                                                    const Group grp) {
     using G_ = Geo<BN, KC>;
     constexpr int BK = G_::BK, STAGES = G_::STAGES, NTRAJ = G_::NTRAJ;
+    constexpr bool TFM = KCfg<KC>::TF32;   // TF32 mode: kind::tf32 MMAs, FP32-container images
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* tiles = smem;
@@ -417,15 +457,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                     const uint32_t a0 = smem_u32(tiles + stage * G_::STAGE_BYTES);
                     const uint32_t a1 = a0 + G_::A_BYTES, b0 = a0 + 2 * G_::A_BYTES, b1 = b0 + G_::B_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint32_t ko = kk * 32;   // 16 BF16 = 32 B along the swizzled row
-                        mma_bf16(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b0 + ko), G_::IDESC,
+                    for (int kk = 0; kk < G_::MMAS; ++kk) {
+                        const uint32_t ko = kk * 32;   // 16 BF16 or 8 TF32 = 32 B along the swizzled row
+                        mma_issue<TFM>(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b0 + ko), G_::IDESC,
                                  (kt > 0 || kk > 0) ? 1u : 0u);
                         if (nt == 3) {
-                            mma_bf16(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b1 + ko), G_::IDESC, 1u);
-                            mma_bf16(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
+                            mma_issue<TFM>(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b1 + ko), G_::IDESC, 1u);
+                            mma_issue<TFM>(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
                         }
-                        if (nt == 2) mma_bf16(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
+                        if (nt == 2) mma_issue<TFM>(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
                     }
                     mma_commit(&empty[stage]);
                     if (++stage == STAGES) {
@@ -544,8 +584,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                                 args.oX[e] = xp;
                                 args.oY[e] = yp;
                                 args.oZ[e] = zp;
-                                split_store(args.oHi, args.oLo, r0, xp, WITH_LO);
-                                split_store(args.oHi, args.oLo, r0 + args.ldk, yp, WITH_LO);
+                                image_store(args.oHi, args.oLo, r0, xp, WITH_LO, TFM);
+                                image_store(args.oHi, args.oLo, r0 + args.ldk, yp, WITH_LO, TFM);
                                 rx[jj] = xp;
                                 ry[jj] = yp;
                                 rz[jj] = zp;
@@ -568,8 +608,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                                 args.oX[e] = nx;
                                 args.oY[e] = ny;
                                 args.oZ[e] = nz;
-                                split_store(args.oHi, args.oLo, r0, nx, WITH_LO);
-                                split_store(args.oHi, args.oLo, r0 + args.ldk, ny, WITH_LO);
+                                image_store(args.oHi, args.oLo, r0, nx, WITH_LO, TFM);
+                                image_store(args.oHi, args.oLo, r0 + args.ldk, ny, WITH_LO, TFM);
                                 rx[jj] = nx;
                                 ry[jj] = ny;
                                 rz[jj] = nz;
@@ -643,11 +683,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
 // ---------------------------------------------------------------------------
 // elementwise kernels of the mixed path
 
-__global__ void k_split_matrix(const double* src, int64_t N, int64_t ldk, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+__global__ void k_split_matrix(const double* src, int64_t N, int64_t ldk, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                               int tf32) {
     const int64_t n2 = N * ldk;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / ldk, k = e - r * ldk;
         const float v = (k < N) ? (float)src[r * N + k] : 0.f;
+        if (tf32) {   // one TF32 image in an FP32 container
+            reinterpret_cast<float*>(hi)[e] = to_tf32(v);
+            continue;
+        }
         // hi = bf16(v), lo = bf16(v - hi): the pair carries ~16 significant bits
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         hi[e] = h;
@@ -656,7 +701,7 @@ __global__ void k_split_matrix(const double* src, int64_t N, int64_t ldk, __nv_b
 }
 
 __global__ void k_init_tc(float* X, float* Y, float* Z, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t M, int64_t N,
-                          int64_t ldk, uint64_t seed, float init_sz, int64_t m0) {
+                          int64_t ldk, uint64_t seed, float init_sz, int64_t m0, int tf32) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= M * N) return;
     const int64_t m = e / N, i = e - m * N;
@@ -665,6 +710,11 @@ __global__ void k_init_tc(float* X, float* Y, float* Z, __nv_bfloat16* hi, __nv_
     X[e] = (float)sx;
     Y[e] = (float)sy;
     Z[e] = init_sz;
+    if (tf32) {   // +-1 is exact in TF32
+        reinterpret_cast<float*>(hi)[(2 * m) * ldk + i] = (float)sx;
+        reinterpret_cast<float*>(hi)[(2 * m + 1) * ldk + i] = (float)sy;
+        return;
+    }
     hi[(2 * m) * ldk + i] = __float2bfloat16_rn((float)sx);
     hi[(2 * m + 1) * ldk + i] = __float2bfloat16_rn((float)sy);
     lo[(2 * m) * ldk + i] = __float2bfloat16_rn(0.f);
@@ -673,12 +723,12 @@ __global__ void k_init_tc(float* X, float* Y, float* Z, __nv_bfloat16* hi, __nv_
 
 // Images of an arbitrary FP32 state (after set_state).
 __global__ void k_images_tc(const float* X, const float* Y, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t M,
-                            int64_t N, int64_t ldk) {
+                            int64_t N, int64_t ldk, int tf32) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= M * N) return;
     const int64_t m = e / N, i = e - m * N;
-    split_store(hi, lo, (2 * m) * ldk + i, X[e], true);
-    split_store(hi, lo, (2 * m + 1) * ldk + i, Y[e], true);
+    image_store(hi, lo, (2 * m) * ldk + i, X[e], true, tf32);
+    image_store(hi, lo, (2 * m + 1) * ldk + i, Y[e], true, tf32);
 }
 
 // part[r][m] = sums over sites [128 r, 128 r + 128) of (x, y, z); one warp per (r, m).
@@ -705,10 +755,11 @@ __global__ void k_part_tc(const float* X, const float* Y, const float* Z, float*
     if (lane == 0) *(float4*)(part + (r * M + m) * 4) = make_float4(sx, sy, sz, 0.f);
 }
 
-// Noise of step t = *d_t + toff: eta (FP32 Box-Muller, rounded to BF16) into the
-// B-operand image rows 2m / 2m+1, and the collective pair xi (site index N) into XI.
+// Noise of step t = *d_t + toff: eta (FP32 Box-Muller, rounded to BF16, or to TF32
+// in an FP32 container) into the B-operand image rows 2m / 2m+1, and the
+// collective pair xi (site index N) into XI.
 __global__ void k_noise_tc(__nv_bfloat16* E, float* XI, int64_t M, int64_t N, int64_t ldk, uint64_t seed,
-                           const int64_t* d_t, int64_t toff, int64_t m0) {
+                           const int64_t* d_t, int64_t toff, int64_t m0, int tf32) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t NP = N + 1;
     if (e >= M * NP) return;
@@ -717,8 +768,8 @@ __global__ void k_noise_tc(__nv_bfloat16* E, float* XI, int64_t M, int64_t N, in
     float gx, gy;
     normal2_f32(seed, (uint32_t)(m0 + m), t, (uint32_t)i, gx, gy);
     if (i < N) {
-        E[(2 * m) * ldk + i] = __float2bfloat16_rn(gx);
-        E[(2 * m + 1) * ldk + i] = __float2bfloat16_rn(gy);
+        image_store(E, nullptr, (2 * m) * ldk + i, gx, false, tf32);
+        image_store(E, nullptr, (2 * m + 1) * ldk + i, gy, false, tf32);
     } else {
         XI[2 * m] = gx;
         XI[2 * m + 1] = gy;
@@ -864,11 +915,11 @@ __global__ void k_f64_to_f32_rows(const double* x, const double* y, const double
 }
 
 __global__ void k_split_vectors(const double* s, int64_t K, int64_t N, int64_t ldk, __nv_bfloat16* hi,
-                                __nv_bfloat16* lo) {
+                                __nv_bfloat16* lo, int tf32) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= K * N) return;
     const int64_t r = e / N, k = e - r * N;
-    split_store(hi, lo, r * ldk + k, (float)s[e], true);
+    image_store(hi, lo, r * ldk + k, (float)s[e], true, tf32);
 }
 
 __global__ void k_split_vectors_f32(const float* s, int64_t K, int64_t N, int64_t ldk, __nv_bfloat16* hi,
@@ -900,18 +951,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor map: inner dimension K (extent kext, row pitch ldk elements),
-// outer dimension rows; box (K tile) x box_rows with the K configuration's
-// swizzle. Reads outside the extents return zeros.
+// 2-D tensor map of an operand image (BF16, or FP32 containers in the TF32
+// configuration): inner dimension K (extent kext, row pitch ldk elements), outer
+// dimension rows; box (K tile) x box_rows with the K configuration's swizzle.
+// Reads outside the extents return zeros.
 int make_map(twa_ctx* c, CUtensorMap* map, const void* base, int64_t rows, int64_t kext, int64_t ldk, int box_rows,
              int kc) {
     auto fn = encode_fn();
     if (!fn) return set_error(c, TWA_ECUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {(cuuint64_t)kext, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ldk * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)(kc == 0 ? KCfg<0>::BK : KCfg<1>::BK), (cuuint32_t)box_rows};
+    const bool f32 = kc == 2;
+    cuuint64_t strides[1] = {(cuuint64_t)(ldk * (f32 ? 4 : 2))};
+    cuuint32_t box[2] = {(cuuint32_t)kcfg_bk(kc), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+    CUresult r = fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, kc == 0 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(c, TWA_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -946,6 +1000,7 @@ int launch_cfg(twa_ctx* c, const TcMaps& maps, const TcArgs& a, const Group& grp
     TWA_TC_CASE(192, 1)
     TWA_TC_CASE(128, 0)
     TWA_TC_CASE(128, 1)
+    TWA_TC_CASE(256, 2)
 #undef TWA_TC_CASE
     return set_error(c, TWA_EUNSUPPORTED, "tensor-core tile configuration not compiled");
 }
@@ -976,10 +1031,12 @@ int make_state_maps(twa_ctx* c) {
     TcState* t = c->tc;
     int rc;
     const int64_t R = 2 * c->M;
+    // TF32 keeps no lo images: the lo maps alias the hi images (never read, NT = 1)
+    const bool tf = t->kc == 2;
     if ((rc = make_map(c, &t->tmShi, t->Shi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmSlo, t->Slo, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmSlo, tf ? t->Shi : t->Slo, R, c->N, t->ldk, t->bn, t->kc))) return rc;
     if ((rc = make_map(c, &t->tmPhi, t->Phi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmPlo, t->Plo, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmPlo, tf ? t->Phi : t->Plo, R, c->N, t->ldk, t->bn, t->kc))) return rc;
     if ((rc = make_map(c, &t->tmE, t->E, R, c->N, t->ldk, t->bn, t->kc))) return rc;
     return TWA_OK;
 }
@@ -987,10 +1044,11 @@ int make_state_maps(twa_ctx* c) {
 int make_matrix_maps(twa_ctx* c) {
     TcState* t = c->tc;
     int rc;
+    const bool tf = t->kc == 2;
     if ((rc = make_map(c, &t->tmWhi, t->Whi, c->N, c->N, t->ldk, BM, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmWlo, t->Wlo, c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmWlo, tf ? t->Whi : t->Wlo, c->N, c->N, t->ldk, BM, t->kc))) return rc;
     if ((rc = make_map(c, &t->tmLhi, t->Lhi, c->N, c->N, t->ldk, BM, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmLlo, t->Llo, c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmLlo, tf ? t->Lhi : t->Llo, c->N, c->N, t->ldk, BM, t->kc))) return rc;
     return TWA_OK;
 }
 
@@ -1002,27 +1060,31 @@ int tc_prepare(twa_ctx* c) {
     t->N = c->N;
     t->ldk = (c->N + 7) / 8 * 8;
     t->n_rt = (c->N + BM - 1) / BM;
-    t->terms = (c->opts.precision == TWA_PREC_BF16) ? 1 : 3;
+    t->terms = (c->opts.precision == TWA_PREC_BF16X3) ? 3 : 1;
     // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1}.
     // Default measured fastest at N = 10^4, M = 1024: 256-wide tiles, four 32-wide
-    // K stages (SWIZZLE_64B).
-    t->bn = env_int("TWA_TC_BN", 256);
-    t->kc = env_int("TWA_TC_KC", 1);
+    // K stages (SWIZZLE_64B). The TF32 precision has one configuration: 256-wide
+    // tiles, four 16-wide FP32 K stages (KC = 2).
+    const bool tf32 = c->opts.precision == TWA_PREC_TF32;
+    if (tf32 && (getenv("TWA_TC_BN") || getenv("TWA_TC_KC")))
+        return set_error(c, TWA_EINVAL, "TWA_TC_BN / TWA_TC_KC do not apply to the TF32 precision");
+    t->bn = tf32 ? 256 : env_int("TWA_TC_BN", 256);
+    t->kc = tf32 ? 2 : env_int("TWA_TC_KC", 1);
     // TWA_SEPARATE_LETA=1: dense step as separate noise, L.eta, predictor and
     // corrector launches instead of the two mixed launches (same results)
     t->separate_leta = env_int("TWA_SEPARATE_LETA", 0) != 0;
-    if (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1))
+    if (!tf32 && (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1)))
         return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0 or 1");
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
         t->num_sms = sms;
-    const size_t nb = sizeof(__nv_bfloat16) * (size_t)c->N * t->ldk;
-    __nv_bfloat16** m4[] = {&t->Whi, &t->Wlo, &t->Lhi, &t->Llo};
-    for (auto p : m4)
-        if (dev_malloc(c, p, nb) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device BF16 images");
+    const size_t nb = (size_t)(tf32 ? 4 : 2) * c->N * t->ldk;
+    __nv_bfloat16** m4[] = {&t->Whi, &t->Lhi, &t->Wlo, &t->Llo};
+    for (int k = 0; k < (tf32 ? 2 : 4); ++k)
+        if (dev_malloc(c, m4[k], nb) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device operand images");
     const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
-    k_split_matrix<<<g, 256, 0, c->stream>>>(c->W64, c->N, t->ldk, t->Whi, t->Wlo);
-    k_split_matrix<<<g, 256, 0, c->stream>>>(c->L64, c->N, t->ldk, t->Lhi, t->Llo);
+    k_split_matrix<<<g, 256, 0, c->stream>>>(c->W64, c->N, t->ldk, t->Whi, t->Wlo, tf32);
+    k_split_matrix<<<g, 256, 0, c->stream>>>(c->L64, c->N, t->ldk, t->Lhi, t->Llo, tf32);
     TWA_CUDA(c, cudaGetLastError());
     return make_matrix_maps(c);
 }
@@ -1034,11 +1096,12 @@ int tc_alloc(twa_ctx* c) {
     float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Bx, &t->By};
     for (auto p : f)
         if (dev_malloc(c, p, sizeof(float) * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device state");
-    const size_t ni = sizeof(__nv_bfloat16) * 2 * (size_t)c->M * t->ldk;
-    __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E};
-    for (auto p : b) {
-        if (dev_malloc(c, p, ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device images");
-        TWA_CUDA(c, cudaMemsetAsync(*p, 0, ni, c->stream));
+    const bool tf32 = t->kc == 2;   // FP32 containers, no lo images
+    const size_t ni = (size_t)(tf32 ? 4 : 2) * 2 * (size_t)c->M * t->ldk;
+    __nv_bfloat16** b[] = {&t->Shi, &t->Phi, &t->E, &t->Slo, &t->Plo};
+    for (int k = 0; k < (tf32 ? 3 : 5); ++k) {
+        if (dev_malloc(c, b[k], ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device images");
+        TWA_CUDA(c, cudaMemsetAsync(*b[k], 0, ni, c->stream));
     }
     if (dev_malloc(c, &t->XI, sizeof(float) * 2 * c->M) != cudaSuccess ||
         dev_malloc(c, &t->part, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess ||
@@ -1071,13 +1134,14 @@ void tc_free_run(twa_ctx* c) {
 int tc_set_extra_matrix(twa_ctx* c, int slot, const double* A64) {
     TcState* t = c->tc;
     if (slot < 0 || slot > 1) return set_error(c, TWA_EINVAL, "tc_set_extra_matrix: slot");
+    if (t->kc == 2) return set_error(c, TWA_EUNSUPPORTED, "extra matrices run on the BF16 precisions");
     const size_t nb = sizeof(__nv_bfloat16) * (size_t)c->N * t->ldk;
     if (!t->Xhi[slot]) {
         if (dev_malloc(c, &t->Xhi[slot], nb) != cudaSuccess || dev_malloc(c, &t->Xlo[slot], nb) != cudaSuccess)
             return set_error(c, TWA_ENOMEM, "device extra matrix images");
     }
     const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
-    k_split_matrix<<<g, 256, 0, c->stream>>>(A64, c->N, t->ldk, t->Xhi[slot], t->Xlo[slot]);
+    k_split_matrix<<<g, 256, 0, c->stream>>>(A64, c->N, t->ldk, t->Xhi[slot], t->Xlo[slot], 0);
     TWA_CUDA(c, cudaGetLastError());
     int rc;
     if ((rc = make_map(c, &t->tmXhi[slot], t->Xhi[slot], c->N, c->N, t->ldk, BM, t->kc))) return rc;
@@ -1087,6 +1151,7 @@ int tc_set_extra_matrix(twa_ctx* c, int slot, const double* A64) {
 int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t K) {
     TcState* t = c->tc;
     int rc;
+    if (t->kc == 2) return set_error(c, TWA_EUNSUPPORTED, "FP32 contractions run on the BF16 precisions");
     if (t->vec_rows != K) {
         dev_free(c, t->Vhi);
         dev_free(c, t->Vlo);
@@ -1130,7 +1195,7 @@ int tc_state_changed(twa_ctx* c) {
     TcState* t = c->tc;
     t->bn_ready = -1;
     const int64_t MN = c->M * c->N;
-    k_images_tc<<<nblk(MN, 256), 256, 0, c->stream>>>(t->X, t->Y, t->Shi, t->Slo, c->M, c->N, t->ldk);
+    k_images_tc<<<nblk(MN, 256), 256, 0, c->stream>>>(t->X, t->Y, t->Shi, t->Slo, c->M, c->N, t->ldk, t->kc == 2);
     k_part_tc<<<nblk(t->n_rt * c->M, 8), 256, 0, c->stream>>>(t->X, t->Y, t->Z, t->part, c->M, c->N, t->n_rt);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
@@ -1141,7 +1206,7 @@ int tc_init_state(twa_ctx* c) {
     t->bn_ready = -1;
     k_init_tc<<<nblk(c->M * c->N, 256), 256, 0, c->stream>>>(t->X, t->Y, t->Z, t->Shi, t->Slo, c->M, c->N, t->ldk,
                                                             c->seed, (float)c->opts.init_state,
-                                                            c->opts.traj_offset);
+                                                            c->opts.traj_offset, t->kc == 2);
     TWA_CUDA(c, cudaGetLastError());
     k_part_tc<<<nblk(t->n_rt * c->M, 8), 256, 0, c->stream>>>(t->X, t->Y, t->Z, t->part, c->M, c->N, t->n_rt);
     TWA_CUDA(c, cudaGetLastError());
@@ -1230,7 +1295,7 @@ int64_t lpt_schedule(std::vector<std::pair<int64_t, int32_t>> jobs, int ctas, st
 // and the rest, each placed on the CTAs by longest-first list scheduling.
 int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
     const TcState* t0 = cs[0]->tc;
-    const int bn = t0->bn, bk = t0->kc == 0 ? KCfg<0>::BK : KCfg<1>::BK;
+    const int bn = t0->bn, bk = kcfg_bk(t0->kc);
     const int ntw = t0->terms, ntl = t0->terms == 3 ? 2 : 1;
     const int nprob = 3 * n;
     p->nprob = nprob;
@@ -1402,7 +1467,7 @@ int noise_part_alone(twa_ctx* c, int64_t t) {
     {
         ProfScope p(c, TWA_PROF_NOISE);
         k_noise_tc<<<nblk(c->M * (c->N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, c->M, c->N, ts->ldk, c->seed,
-                                                                        c->d_t, 0, c->opts.traj_offset);
+                                                                        c->d_t, 0, c->opts.traj_offset, ts->kc == 2);
     }
     TcArgs la = base_args(c);
     la.XI = ts->XI;
@@ -1447,7 +1512,8 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
             {
                 ProfScope p(c, TWA_PROF_NOISE);
                 k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, M, N, ts->ldk, c->seed,
-                                                                         c->d_t, 0, c->opts.traj_offset);
+                                                                         c->d_t, 0, c->opts.traj_offset,
+                                                                         ts->kc == 2);
             }
             TcArgs la = base_args(c);
             la.XI = ts->XI;
@@ -1492,7 +1558,7 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         {
             ProfScope p(c, TWA_PROF_NOISE);   // noise of step t + 1 (L.eta tiles below)
             k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, M, N, ts->ldk, c->seed, c->d_t,
-                                                                     1, c->opts.traj_offset);
+                                                                     1, c->opts.traj_offset, ts->kc == 2);
         }
         const TcMaps none{};
         const TcArgs fa = base_args(c);   // flags of the launch
@@ -1547,19 +1613,20 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     const int64_t N = c->N, ldk = t->ldk;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
     float* out = nullptr;
-    const size_t ni = sizeof(__nv_bfloat16) * (size_t)K * ldk;
+    const bool tf32 = t->kc == 2;   // one FP32-container image, no lo image
+    const size_t ni = (size_t)(tf32 ? 4 : 2) * K * ldk;
     TWA_CUDA(c, dev_malloc_async(c, &hi, ni, c->stream));
-    TWA_CUDA(c, dev_malloc_async(c, &lo, ni, c->stream));
+    if (!tf32) TWA_CUDA(c, dev_malloc_async(c, &lo, ni, c->stream));
     TWA_CUDA(c, dev_malloc_async(c, &out, sizeof(float) * K * N, c->stream));
     TWA_CUDA(c, cudaMemsetAsync(hi, 0, ni, c->stream));
-    TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
-    k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo);
+    if (!tf32) TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
+    k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo, tf32);
     TcMaps fm{};
     fm.a0 = t->tmWhi;
     fm.a1 = t->tmWlo;
     int rc;
     if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &fm.b1, lo, K, N, ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &fm.b1, tf32 ? hi : lo, K, N, ldk, t->bn, t->kc))) return rc;
     TcArgs fa = base_args(c);
     fa.n_vec = K;
     fa.field_out = out;
