@@ -323,6 +323,11 @@ def run_ours(args, rank, world, dist):
         # W.s by FFT and the pump noise from the same circulant embedding: no contraction left
         side["fft_route_circulant_noise"] = side_run(CFG["precision"], "fft", min(K, 300), 3, noise="circulant")
         side["fft_route_circulant_noise"]["speedup_vs_dense"] = side["fft_route_circulant_noise"]["value"] / value
+        # the dense route in the other tensor-core precisions (one-term BF16, TF32)
+        for prec in ("bf16", "tf32"):
+            if prec != CFG["precision"]:
+                side["dense_" + prec] = side_run(prec, "dense", min(K, 300), 3)
+                side["dense_" + prec]["speedup_vs_main"] = side["dense_" + prec]["value"] / value
         side["fp64_gpu"] = side_run("fp64", "dense", 2, 1)
         side["fp64_gpu"]["mixed_speedup"] = value / side["fp64_gpu"]["value"]
 

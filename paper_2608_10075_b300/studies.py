@@ -5,7 +5,8 @@
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
-path and on the mixed paths (BF16, BF16X3, BF16X3 with the FFT pump field);
+path and on the mixed paths (BF16, TF32, BF16X3, BF16X3 with the FFT pump
+field);
 each observable is reported with its standard error and, per mixed path, the
 paired difference to FP64 (mean over trajectories of the per-trajectory
 difference, and its standard error), which isolates the arithmetic error from
@@ -52,7 +53,7 @@ def precision_study(args):
     N, w, G, dt = c["N"], c["w"], c["Gamma"], c["dt"]
     steps = args.steps or int(round(c["T"] / dt))
     t0 = steps * dt - c["window"]
-    for alpha in c["alphas"]:
+    for alpha in (args.alphas or c["alphas"]):
         ref_obs, ref_means, ref_t = _run(N, alpha, w, G, dt, steps, args.M_ref, t0, "fp64")
         ref_s = _linear_samples(ref_means)
         line = {"study": "precision", "N": N, "alpha": alpha, "w": w, "dt": dt, "steps": steps,
@@ -61,6 +62,7 @@ def precision_study(args):
         # the circulant draw has the same noise law but other per-trajectory values,
         # so only its unpaired difference (diff_over_se) measures its error
         for name, prec, route, noise in (("bf16", "bf16", "dense", "cholesky"),
+                                         ("tf32", "tf32", "dense", "cholesky"),
                                          ("bf16x3", "bf16x3", "dense", "cholesky"),
                                          ("bf16x3_fft", "bf16x3", "fft", "cholesky"),
                                          ("fft_circulant_noise", "bf16x3", "fft", "circulant")):
@@ -188,6 +190,7 @@ def main():
     p.add_argument("--M-ref", type=int, default=512)
     p.add_argument("--M-full", type=int, default=MIXED_N1024["M"])
     p.add_argument("--steps", type=int, default=0)
+    p.add_argument("--alphas", type=float, nargs="*", default=None, help="a subset of the study's exponents")
     q = sub.add_parser("gradients")
     q.add_argument("--M", type=int, default=ADJOINT_N1024["M"])
     q.add_argument("--steps", type=int, default=0)
