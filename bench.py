@@ -323,8 +323,9 @@ def run_ours(args, rank, world, dist):
         # W.s by FFT and the pump noise from the same circulant embedding: no contraction left
         side["fft_route_circulant_noise"] = side_run(CFG["precision"], "fft", min(K, 300), 3, noise="circulant")
         side["fft_route_circulant_noise"]["speedup_vs_dense"] = side["fft_route_circulant_noise"]["value"] / value
-        # the dense route in the other tensor-core precisions (one-term BF16, TF32)
-        for prec in ("bf16", "tf32"):
+        # the dense route in the other tensor-core precisions (one-term BF16, TF32,
+        # and the FP32-accurate TF32 split)
+        for prec in ("bf16", "tf32", "fp32"):
             if prec != CFG["precision"]:
                 side["dense_" + prec] = side_run(prec, "dense", min(K, 300), 3)
                 side["dense_" + prec]["speedup_vs_main"] = side["dense_" + prec]["value"] / value

@@ -75,6 +75,12 @@ extern "C" {
                                 error 2^-11 against 2^-8 for BF16). Dense and FFT routes
                                 of twa_init / twa_run / twa_field; not twa_grad,
                                 twa_batch_run or the extra-matrix contractions        */
+#define TWA_PREC_FP32    4   /* FP32-accurate contractions on tcgen05: every operand
+                                (W, L, s, eta) split into TF32 hi = tf32(v) and lo =
+                                tf32(v - hi), products hi*hi + hi*lo + lo*hi with FP32
+                                accumulation (about 2^-22 relative per product, the
+                                order of an FP32 product), FP32 state. Same coverage
+                                as TWA_PREC_TF32                                      */
 
 typedef struct twa_ctx twa_ctx;   /* opaque, owned by the library */
 
@@ -224,7 +230,8 @@ TWA_API int twa_get_moments(twa_ctx* ctx, double* out, int on_device);
 /* Pump-field contraction of Eq. S1, P[k][i] = sum_j w_ij s[k][j], for K
  * caller vectors s (device, [K][N] doubles) into P (device, [K][N] doubles),
  * computed with the context's precision path (FP64; the BF16 images of W
- * and an hi/lo split of s, or their TF32 images, with FP32 accumulation). Enqueued on the context's
+ * and an hi/lo split of s, or their TF32 images or TF32 hi/lo splits, with
+ * FP32 accumulation). Enqueued on the context's
  * stream. Errors: TWA_EINVAL (NULL, K < 1). */
 TWA_API int twa_field(twa_ctx* ctx, const double* s, double* P, int64_t K);
 
@@ -270,7 +277,8 @@ typedef struct twa_grad_out {
  * their standard deviation / sqrt(M) the returned SE. Synchronises.
  * Errors: TWA_EINVAL (NULL, M < 1, steps < 1), TWA_ESTATE (no step inside the
  * window), TWA_EUNSUPPORTED (want_alpha with alpha = 0 or inf, w = 0, a
- * context with noise_route = TWA_NOISE_CIRCULANT or precision = TWA_PREC_TF32),
+ * context with noise_route = TWA_NOISE_CIRCULANT or precision = TWA_PREC_TF32
+ * or TWA_PREC_FP32),
  * TWA_ENOMEM, TWA_ECUDA,
  * TWA_ENONFINITE. */
 TWA_API int twa_grad(twa_ctx* ctx, const twa_grad_req* req, twa_grad_out* out, double* per_traj);
@@ -354,7 +362,7 @@ TWA_API int twa_profile(twa_ctx* ctx, int enable);
  * in ms, the number of launches and the summed algorithmic tensor-core FLOPs
  * of the dense mixed-precision contractions (2 x multiply-adds of the defined
  * product over its nonzero entries -- all of W, the lower triangle of L --
- * times the BF16 products per entry; 0 for other classes) since profiling
+ * times the tensor-core products per entry; 0 for other classes) since profiling
  * started, and clear the record. Each array holds TWA_PROF_KINDS entries and
  * may be NULL. */
 TWA_API int twa_profile_read(twa_ctx* ctx, double* ms, int64_t* launches, double* flops);

@@ -204,7 +204,7 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
     if (!(w >= 0.0) || isinf(w)) return set_error(nullptr, TWA_EINVAL, "twa_init: w must be finite and >= 0");
     if (!(Gamma >= 0.0) || isinf(Gamma)) return set_error(nullptr, TWA_EINVAL, "twa_init: Gamma must be finite and >= 0");
     if (!(dt > 0.0) || isinf(dt)) return set_error(nullptr, TWA_EINVAL, "twa_init: dt must be finite and > 0");
-    if (o.precision < TWA_PREC_FP64 || o.precision > TWA_PREC_TF32)
+    if (o.precision < TWA_PREC_FP64 || o.precision > TWA_PREC_FP32)
         return set_error(nullptr, TWA_EINVAL, "twa_init: unknown precision");
     if (o.init_state != -1 && o.init_state != 1) return set_error(nullptr, TWA_EINVAL, "twa_init: init_state must be +-1");
     if (!(o.window_start >= 0.0) || isinf(o.window_start))
@@ -421,7 +421,7 @@ int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
     if (c->opts.traj_offset + r->M - 1 > MAX_COUNTER)
         return set_error(c, TWA_EINVAL, "twa_grad: traj_offset + M exceeds the 32-bit trajectory counter");
     if (!(c->w > 0.0)) return set_error(c, TWA_EUNSUPPORTED, "twa_grad: needs w > 0");
-    if (c->opts.precision == TWA_PREC_TF32)
+    if (c->opts.precision == TWA_PREC_TF32 || c->opts.precision == TWA_PREC_FP32)
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: runs on the FP64, BF16 and BF16X3 precisions");
     if (c->opts.noise_route != TWA_NOISE_CHOLESKY)
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: differentiates the Cholesky noise draw only");

@@ -34,7 +34,7 @@ constexpr int TC_BK = 64;
 // Buffers of the mixed-precision path (twa_tc.cu, twa_fft.cu).
 struct TcState {
     int64_t M = 0, N = 0, ldk = 0, n_rt = 0;
-    int terms = 3;                               // 1 (BF16) or 3 (BF16X3)
+    int terms = 3;                               // 1 (BF16, TF32) or 3 (BF16X3, FP32)
     int bn = 256, kc = 0;                        // tile width and K-stage configuration
     int num_sms = 148;
     __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
@@ -44,10 +44,11 @@ struct TcState {
     __nv_bfloat16 *Shi = nullptr, *Slo = nullptr;         // images of s   [2M][ldk]
     __nv_bfloat16 *Phi = nullptr, *Plo = nullptr;         // images of s~  [2M][ldk]
     __nv_bfloat16* E = nullptr;                           // eta           [2M][ldk]
+    __nv_bfloat16* Elo = nullptr;                         // lo image of eta (FP32 mode only)
     float* XI = nullptr;                                  // [M][2]
     float* part = nullptr;                                // [n_rt][M][4] sums of s
     float* partp = nullptr;                               // [n_rt][M][4] sums of s~
-    CUtensorMap tmWhi, tmWlo, tmLhi, tmLlo, tmShi, tmSlo, tmPhi, tmPlo, tmE;
+    CUtensorMap tmWhi, tmWlo, tmLhi, tmLlo, tmShi, tmSlo, tmPhi, tmPlo, tmE, tmElo;
     // extra N x N operands (the adjoint's dW/dalpha and dL/dalpha), hi/lo images
     __nv_bfloat16 *Xhi[2] = {nullptr, nullptr}, *Xlo[2] = {nullptr, nullptr};
     CUtensorMap tmXhi[2], tmXlo[2];

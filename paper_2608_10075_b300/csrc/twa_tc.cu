@@ -14,6 +14,10 @@
 // Precision modes: BF16 (one term, hi*hi) or BF16X3 (hi*hi + hi*lo + lo*hi,
 // hi = bf16(v), lo = bf16(v - hi)), FP32 accumulation. The noise eta is drawn
 // in FP32 and rounded to BF16 once, so L.eta needs the two terms of L only.
+// TF32 (kind::tf32, one term, operands rounded to TF32 in FP32 containers) and
+// FP32 (the same split as BF16X3 with hi = tf32(v), lo = tf32(v - hi): about
+// 22 significant bits, FP32-accurate contractions; eta split as well, so L.eta
+// has three terms) run on a 16-wide FP32 K stage.
 //
 // Kernel structure: persistent CTAs (at most one per SM) walk a static list of
 // (row tile, trajectory tile) pairs, strided or from a host-built schedule.
@@ -88,6 +92,9 @@ struct KCfg<2> {   // 16 TF32 = 64 B rows, SWIZZLE_64B, four stages
     static constexpr uint32_t SBO = 512;
 };
 inline int kcfg_bk(int kc) { return kc == 0 ? KCfg<0>::BK : kc == 1 ? KCfg<1>::BK : KCfg<2>::BK; }
+// products per L.eta entry: one term, two (L hi + lo against the single BF16 eta
+// of BF16X3) or three (FP32 mode: eta split into TF32 hi + lo as well)
+inline int leta_terms(const TcState* t) { return t->terms == 3 ? (t->kc == 2 ? 3 : 2) : 1; }
 
 template <int BN, int KC>
 struct Geo {
@@ -231,12 +238,18 @@ __device__ __forceinline__ float to_tf32(float v) {
     return __uint_as_float(r);
 }
 
-// Operand image entry `off` of value v: BF16 hi (+ lo) or, in the TF32 mode, one
-// TF32 value in an FP32 container (the storage of `hi` then holds floats).
+// Operand image entry `off` of value v: BF16 hi (+ lo) or, in the TF32 and FP32
+// modes, TF32 values in FP32 containers (the storage of `hi` and `lo` then holds
+// floats): hi = tf32(v) and, where a lo image exists, lo = tf32(v - hi).
 __device__ __forceinline__ void image_store(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t off, float v, bool with_lo,
                                             bool tf32) {
-    if (tf32) reinterpret_cast<float*>(hi)[off] = to_tf32(v);
-    else split_store(hi, lo, off, v, with_lo);
+    if (tf32) {
+        const float h = to_tf32(v);
+        reinterpret_cast<float*>(hi)[off] = h;
+        if (with_lo && lo) reinterpret_cast<float*>(lo)[off] = to_tf32(v - h);
+    } else {
+        split_store(hi, lo, off, v, with_lo);
+    }
 }
 
 struct TcMaps {
@@ -326,9 +339,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             tl = t - grp.start[lo];
             if (MODE == MODE_MIX) {
                 // W.s tiles take the template's term count, L.eta tiles one term
-                // fewer (their noise operand is a single BF16 value)
+                // fewer when their noise operand is a single BF16 value (in the
+                // FP32 mode eta has a lo image too)
                 md = grp.desc[lo].mode;
-                nt = (md == MODE_LETA) ? (NT == 3 ? 2 : 1) : NT;
+                nt = (md == MODE_LETA) ? (NT == 3 ? (TFM ? 3 : 2) : 1) : NT;
             }
         }
         const int64_t nct = (ap->n_vec + BN - 1) / BN;
@@ -689,8 +703,10 @@ __global__ void k_split_matrix(const double* src, int64_t N, int64_t ldk, __nv_b
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / ldk, k = e - r * ldk;
         const float v = (k < N) ? (float)src[r * N + k] : 0.f;
-        if (tf32) {   // one TF32 image in an FP32 container
-            reinterpret_cast<float*>(hi)[e] = to_tf32(v);
+        if (tf32) {   // TF32 images in FP32 containers: hi, and lo where it exists
+            const float h = to_tf32(v);
+            reinterpret_cast<float*>(hi)[e] = h;
+            if (lo) reinterpret_cast<float*>(lo)[e] = to_tf32(v - h);
             continue;
         }
         // hi = bf16(v), lo = bf16(v - hi): the pair carries ~16 significant bits
@@ -713,6 +729,10 @@ __global__ void k_init_tc(float* X, float* Y, float* Z, __nv_bfloat16* hi, __nv_
     if (tf32) {   // +-1 is exact in TF32
         reinterpret_cast<float*>(hi)[(2 * m) * ldk + i] = (float)sx;
         reinterpret_cast<float*>(hi)[(2 * m + 1) * ldk + i] = (float)sy;
+        if (lo) {
+            reinterpret_cast<float*>(lo)[(2 * m) * ldk + i] = 0.f;
+            reinterpret_cast<float*>(lo)[(2 * m + 1) * ldk + i] = 0.f;
+        }
         return;
     }
     hi[(2 * m) * ldk + i] = __float2bfloat16_rn((float)sx);
@@ -756,10 +776,10 @@ __global__ void k_part_tc(const float* X, const float* Y, const float* Z, float*
 }
 
 // Noise of step t = *d_t + toff: eta (FP32 Box-Muller, rounded to BF16, or to TF32
-// in an FP32 container) into the B-operand image rows 2m / 2m+1, and the
-// collective pair xi (site index N) into XI.
-__global__ void k_noise_tc(__nv_bfloat16* E, float* XI, int64_t M, int64_t N, int64_t ldk, uint64_t seed,
-                           const int64_t* d_t, int64_t toff, int64_t m0, int tf32) {
+// in an FP32 container, with a TF32 lo image Elo in the FP32 mode) into the
+// B-operand image rows 2m / 2m+1, and the collective pair xi (site index N) into XI.
+__global__ void k_noise_tc(__nv_bfloat16* E, __nv_bfloat16* Elo, float* XI, int64_t M, int64_t N, int64_t ldk,
+                           uint64_t seed, const int64_t* d_t, int64_t toff, int64_t m0, int tf32) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t NP = N + 1;
     if (e >= M * NP) return;
@@ -768,8 +788,8 @@ __global__ void k_noise_tc(__nv_bfloat16* E, float* XI, int64_t M, int64_t N, in
     float gx, gy;
     normal2_f32(seed, (uint32_t)(m0 + m), t, (uint32_t)i, gx, gy);
     if (i < N) {
-        image_store(E, nullptr, (2 * m) * ldk + i, gx, false, tf32);
-        image_store(E, nullptr, (2 * m + 1) * ldk + i, gy, false, tf32);
+        image_store(E, Elo, (2 * m) * ldk + i, gx, Elo != nullptr, tf32);
+        image_store(E, Elo, (2 * m + 1) * ldk + i, gy, Elo != nullptr, tf32);
     } else {
         XI[2 * m] = gx;
         XI[2 * m + 1] = gy;
@@ -1005,6 +1025,16 @@ int launch_cfg(twa_ctx* c, const TcMaps& maps, const TcArgs& a, const Group& grp
     return set_error(c, TWA_EUNSUPPORTED, "tensor-core tile configuration not compiled");
 }
 
+// Standalone L.eta launch with the context's term count (two terms of L against
+// the BF16 eta in BF16X3, three in FP32 where eta has a lo image, else one).
+int launch_leta(twa_ctx* c, const TcMaps& m, const TcArgs& a) {
+    switch (leta_terms(c->tc)) {
+        case 3: return launch_cfg<MODE_LETA, 3>(c, m, a);
+        case 2: return launch_cfg<MODE_LETA, 2>(c, m, a);
+        default: return launch_cfg<MODE_LETA, 1>(c, m, a);
+    }
+}
+
 TcArgs base_args(twa_ctx* c) {
     TcState* t = c->tc;
     TcArgs a{};
@@ -1031,24 +1061,24 @@ int make_state_maps(twa_ctx* c) {
     TcState* t = c->tc;
     int rc;
     const int64_t R = 2 * c->M;
-    // TF32 keeps no lo images: the lo maps alias the hi images (never read, NT = 1)
-    const bool tf = t->kc == 2;
+    // where no lo image is kept (TF32; eta outside the FP32 mode) the lo map
+    // aliases the hi image: it is never read (one term)
     if ((rc = make_map(c, &t->tmShi, t->Shi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmSlo, tf ? t->Shi : t->Slo, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmSlo, t->Slo ? t->Slo : t->Shi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
     if ((rc = make_map(c, &t->tmPhi, t->Phi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmPlo, tf ? t->Phi : t->Plo, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmPlo, t->Plo ? t->Plo : t->Phi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
     if ((rc = make_map(c, &t->tmE, t->E, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmElo, t->Elo ? t->Elo : t->E, R, c->N, t->ldk, t->bn, t->kc))) return rc;
     return TWA_OK;
 }
 
 int make_matrix_maps(twa_ctx* c) {
     TcState* t = c->tc;
     int rc;
-    const bool tf = t->kc == 2;
     if ((rc = make_map(c, &t->tmWhi, t->Whi, c->N, c->N, t->ldk, BM, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmWlo, tf ? t->Whi : t->Wlo, c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmWlo, t->Wlo ? t->Wlo : t->Whi, c->N, c->N, t->ldk, BM, t->kc))) return rc;
     if ((rc = make_map(c, &t->tmLhi, t->Lhi, c->N, c->N, t->ldk, BM, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmLlo, tf ? t->Lhi : t->Llo, c->N, c->N, t->ldk, BM, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmLlo, t->Llo ? t->Llo : t->Lhi, c->N, c->N, t->ldk, BM, t->kc))) return rc;
     return TWA_OK;
 }
 
@@ -1060,14 +1090,14 @@ int tc_prepare(twa_ctx* c) {
     t->N = c->N;
     t->ldk = (c->N + 7) / 8 * 8;
     t->n_rt = (c->N + BM - 1) / BM;
-    t->terms = (c->opts.precision == TWA_PREC_BF16X3) ? 3 : 1;
+    t->terms = (c->opts.precision == TWA_PREC_BF16X3 || c->opts.precision == TWA_PREC_FP32) ? 3 : 1;
     // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1}.
     // Default measured fastest at N = 10^4, M = 1024: 256-wide tiles, four 32-wide
-    // K stages (SWIZZLE_64B). The TF32 precision has one configuration: 256-wide
-    // tiles, four 16-wide FP32 K stages (KC = 2).
-    const bool tf32 = c->opts.precision == TWA_PREC_TF32;
+    // K stages (SWIZZLE_64B). The TF32 and FP32 precisions have one configuration:
+    // 256-wide tiles, four 16-wide FP32 K stages (KC = 2).
+    const bool tf32 = c->opts.precision == TWA_PREC_TF32 || c->opts.precision == TWA_PREC_FP32;
     if (tf32 && (getenv("TWA_TC_BN") || getenv("TWA_TC_KC")))
-        return set_error(c, TWA_EINVAL, "TWA_TC_BN / TWA_TC_KC do not apply to the TF32 precision");
+        return set_error(c, TWA_EINVAL, "TWA_TC_BN / TWA_TC_KC do not apply to the TF32 and FP32 precisions");
     t->bn = tf32 ? 256 : env_int("TWA_TC_BN", 256);
     t->kc = tf32 ? 2 : env_int("TWA_TC_KC", 1);
     // TWA_SEPARATE_LETA=1: dense step as separate noise, L.eta, predictor and
@@ -1080,7 +1110,7 @@ int tc_prepare(twa_ctx* c) {
         t->num_sms = sms;
     const size_t nb = (size_t)(tf32 ? 4 : 2) * c->N * t->ldk;
     __nv_bfloat16** m4[] = {&t->Whi, &t->Lhi, &t->Wlo, &t->Llo};
-    for (int k = 0; k < (tf32 ? 2 : 4); ++k)
+    for (int k = 0; k < (tf32 && t->terms == 1 ? 2 : 4); ++k)
         if (dev_malloc(c, m4[k], nb) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device operand images");
     const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
     k_split_matrix<<<g, 256, 0, c->stream>>>(c->W64, c->N, t->ldk, t->Whi, t->Wlo, tf32);
@@ -1096,10 +1126,13 @@ int tc_alloc(twa_ctx* c) {
     float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Bx, &t->By};
     for (auto p : f)
         if (dev_malloc(c, p, sizeof(float) * mn) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device state");
-    const bool tf32 = t->kc == 2;   // FP32 containers, no lo images
+    // FP32 containers in the TF32 and FP32 modes; lo images of s and s~ except in
+    // TF32, and of eta in FP32 only
+    const bool tf32 = t->kc == 2;
     const size_t ni = (size_t)(tf32 ? 4 : 2) * 2 * (size_t)c->M * t->ldk;
-    __nv_bfloat16** b[] = {&t->Shi, &t->Phi, &t->E, &t->Slo, &t->Plo};
-    for (int k = 0; k < (tf32 ? 3 : 5); ++k) {
+    __nv_bfloat16** b[] = {&t->Shi, &t->Phi, &t->E, &t->Slo, &t->Plo, &t->Elo};
+    const int nimg = !tf32 ? 5 : t->terms == 3 ? 6 : 3;
+    for (int k = 0; k < nimg; ++k) {
         if (dev_malloc(c, b[k], ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device images");
         TWA_CUDA(c, cudaMemsetAsync(*b[k], 0, ni, c->stream));
     }
@@ -1124,7 +1157,7 @@ void tc_free_run(twa_ctx* c) {
         dev_free(c, *p);
         *p = nullptr;
     }
-    __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E};
+    __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E, &t->Elo};
     for (auto p : b) {
         dev_free(c, *p);
         *p = nullptr;
@@ -1296,7 +1329,7 @@ int64_t lpt_schedule(std::vector<std::pair<int64_t, int32_t>> jobs, int ctas, st
 int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
     const TcState* t0 = cs[0]->tc;
     const int bn = t0->bn, bk = kcfg_bk(t0->kc);
-    const int ntw = t0->terms, ntl = t0->terms == 3 ? 2 : 1;
+    const int ntw = t0->terms, ntl = leta_terms(t0);
     const int nprob = 3 * n;
     p->nprob = nprob;
     // flat tile ranges: [W.s + predictor of 0..n-1][W.s~ + corrector][L.eta]
@@ -1422,7 +1455,7 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
             GroupDesc* g = &d[par * nprob];
             g[q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo}, pa, MODE_PRED};
             g[n + q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo}, ca, MODE_CORR};
-            g[2 * n + q] = GroupDesc{TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmE}, la, MODE_LETA};
+            g[2 * n + q] = GroupDesc{TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmElo}, la, MODE_LETA};
         }
     }
     p->host = d;
@@ -1466,16 +1499,16 @@ int noise_part_alone(twa_ctx* c, int64_t t) {
     TcState* ts = c->tc;
     {
         ProfScope p(c, TWA_PROF_NOISE);
-        k_noise_tc<<<nblk(c->M * (c->N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, c->M, c->N, ts->ldk, c->seed,
+        k_noise_tc<<<nblk(c->M * (c->N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->Elo, ts->XI, c->M, c->N, ts->ldk, c->seed,
                                                                         c->d_t, 0, c->opts.traj_offset, ts->kc == 2);
     }
     TcArgs la = base_args(c);
     la.XI = ts->XI;
     la.oBnx = (t & 1) ? ts->Bx1 : ts->Bx;
     la.oBny = (t & 1) ? ts->By1 : ts->By;
-    const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmE};
+    const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmElo};
     ProfScope p(c, TWA_PROF_NOISE_FACTOR, ts->mix->leta_flops);
-    return ts->terms == 3 ? launch_cfg<MODE_LETA, 2>(c, lm, la) : launch_cfg<MODE_LETA, 1>(c, lm, la);
+    return launch_leta(c, lm, la);
 }
 }  // namespace
 
@@ -1511,7 +1544,7 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         } else {
             {
                 ProfScope p(c, TWA_PROF_NOISE);
-                k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, M, N, ts->ldk, c->seed,
+                k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->Elo, ts->XI, M, N, ts->ldk, c->seed,
                                                                          c->d_t, 0, c->opts.traj_offset,
                                                                          ts->kc == 2);
             }
@@ -1519,9 +1552,9 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
             la.XI = ts->XI;
             la.oBnx = ts->Bx;
             la.oBny = ts->By;
-            const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmE};
+            const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmElo};
             ProfScope p(c, TWA_PROF_NOISE_FACTOR);
-            rc = x3 ? launch_cfg<MODE_LETA, 2>(c, lm, la) : launch_cfg<MODE_LETA, 1>(c, lm, la);
+            rc = launch_leta(c, lm, la);
         }
         if (rc) return rc;
         {
@@ -1557,7 +1590,7 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
     } else {
         {
             ProfScope p(c, TWA_PROF_NOISE);   // noise of step t + 1 (L.eta tiles below)
-            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->XI, M, N, ts->ldk, c->seed, c->d_t,
+            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->Elo, ts->XI, M, N, ts->ldk, c->seed, c->d_t,
                                                                      1, c->opts.traj_offset, ts->kc == 2);
         }
         const TcMaps none{};
@@ -1613,20 +1646,21 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     const int64_t N = c->N, ldk = t->ldk;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
     float* out = nullptr;
-    const bool tf32 = t->kc == 2;   // one FP32-container image, no lo image
+    const bool tf32 = t->kc == 2;   // FP32 containers; no lo image in the TF32 mode
+    const bool with_lo = !(tf32 && t->terms == 1);
     const size_t ni = (size_t)(tf32 ? 4 : 2) * K * ldk;
     TWA_CUDA(c, dev_malloc_async(c, &hi, ni, c->stream));
-    if (!tf32) TWA_CUDA(c, dev_malloc_async(c, &lo, ni, c->stream));
+    if (with_lo) TWA_CUDA(c, dev_malloc_async(c, &lo, ni, c->stream));
     TWA_CUDA(c, dev_malloc_async(c, &out, sizeof(float) * K * N, c->stream));
     TWA_CUDA(c, cudaMemsetAsync(hi, 0, ni, c->stream));
-    if (!tf32) TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
+    if (with_lo) TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
     k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo, tf32);
     TcMaps fm{};
     fm.a0 = t->tmWhi;
     fm.a1 = t->tmWlo;
     int rc;
     if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &fm.b1, tf32 ? hi : lo, K, N, ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &fm.b1, with_lo ? lo : hi, K, N, ldk, t->bn, t->kc))) return rc;
     TcArgs fa = base_args(c);
     fa.n_vec = K;
     fa.field_out = out;

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libtwa.so")
 TWA_OK = 0
 ERRORS = {-1: "TWA_EINVAL", -2: "TWA_ENOTPSD", -3: "TWA_ENOMEM", -4: "TWA_ECUDA", -5: "TWA_ETIMEOUT",
           -6: "TWA_ENONFINITE", -7: "TWA_ESTATE", -8: "TWA_EUNSUPPORTED"}
-PRECISION = {"fp64": 0, "bf16": 1, "bf16x3": 2, "tf32": 3}
+PRECISION = {"fp64": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "fp32": 4}
 
 
 class TWAError(RuntimeError):

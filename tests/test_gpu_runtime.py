@@ -26,7 +26,7 @@ def _run(prec, steps, graph, N=200, M=70, offset=0, traj=None):
             os.environ["TWA_NO_GRAPH"] = old
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32"])
 @pytest.mark.parametrize("N,M,steps", [(200, 70, 9), (300, 130, 6), (37, 5, 5)])
 def test_mixed_launches_equal_separate_launches(prec, N, M, steps):
     # L.eta tiles of step t + 1 inside the launches of step t, scheduled by the

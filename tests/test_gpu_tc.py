@@ -8,8 +8,9 @@ so each product w s is off by at most ~3 * 2^-18 |w s| (plus 2^-24 from the
 FP32 rounding of W), and the FP32 sum over N terms adds N 2^-24 sum |w s| in
 the worst case. Single-term BF16 is off by ~2 * 2^-9 |w s| per product, and
 the TF32 mode (operands rounded to nearest TF32, 2^-11 relative, products
-exact and summed in FP32) by ~2 * 2^-11 |w s|. The tests use these bounds with
-a factor of two of margin.
+exact and summed in FP32) by ~2 * 2^-11 |w s|. The FP32 mode is BF16X3's split
+with TF32 halves: residual and dropped lo*lo term 2^-22 each, so ~3 * 2^-22
+|w s| per product. The tests use these bounds with a factor of two of margin.
 
 Trajectories. The mixed path rounds its normals to BF16 (relative 2^-9), so a
 trajectory only stays close to the oracle's for a few steps; beyond that the
@@ -44,6 +45,8 @@ def _field_check(prec, N, K, alpha, w, seed=2):
         bound = 2.0 * (3 * 2.0 ** -18 + 2.0 ** -24 + N * 2.0 ** -24) * absref
     elif prec == "tf32":
         bound = 2.0 * (2 * 2.0 ** -11 + N * 2.0 ** -24) * absref
+    elif prec == "fp32":
+        bound = 2.0 * (3 * 2.0 ** -22 + 2.0 ** -24 + N * 2.0 ** -24) * absref
     else:
         bound = 2.0 * (2 * 2.0 ** -9 + N * 2.0 ** -24) * absref
     err = np.abs(P - ref)
@@ -51,7 +54,7 @@ def _field_check(prec, N, K, alpha, w, seed=2):
     return float(np.max(err / absref))
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32"])
 @pytest.mark.parametrize("N,K", [(16, 8), (300, 600), (129, 257), (1024, 512)])
 def test_field_contraction_bound(prec, N, K):
     # several 128-site row tiles and 256-row column tiles, with ragged tails
@@ -66,7 +69,26 @@ def test_field_bf16x3_is_much_better_than_bf16():
     assert e3 < et < e1   # 16, 11 and 8 significant bits
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
+def test_fp32_mode_resolves_22_bits():
+    # alpha = inf: W = w I, so every output is one product w s and the sum adds
+    # only exact zeros; w = 150 is exact in every format. The FP32 split keeps
+    # s to 2^-22 (+ 2^-24 from FP64 -> FP32 and the accumulator's rounding),
+    # the BF16 split only to 2^-18.
+    import torch
+    twa = _twa()
+    N, K, w = 300, 600, 150.0
+    rng = np.random.default_rng(9)
+    s = rng.choice([-1.0, 1.0], size=(K, N)) * rng.uniform(0.2, 1.7, size=(K, N))
+    err = {}
+    for prec in ("fp32", "bf16x3"):
+        with twa.TWA(N, math.inf, w, 1.0, 1e-4, precision=prec) as g:
+            P = g.field(torch.tensor(s, device="cuda")).cpu().numpy()
+        err[prec] = float(np.max(np.abs(P - w * s) / np.abs(w * s)))
+    assert err["fp32"] <= 2.0 * (2.0 ** -22 + 2.0 ** -23 + 2.0 ** -24), err
+    assert err["bf16x3"] > 2.0 * err["fp32"], err
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32"])
 def test_initial_state_is_exact(prec):
     twa = _twa()
     N, M = 300, 200
@@ -77,12 +99,14 @@ def test_initial_state_is_exact(prec):
     assert np.array_equal(gx, o.sx) and np.array_equal(gy, o.sy) and np.array_equal(gz, o.sz)
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-2), ("bf16", 3e-2), ("tf32", 1e-2)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-2), ("bf16", 3e-2), ("tf32", 1e-2), ("fp32", 1e-4)])
 @pytest.mark.parametrize("N,M", [(300, 200), (128, 128), (45, 3)])
 def test_trajectories_track_oracle_for_a_few_steps(prec, tol, N, M):
     # Here the noise increment per site is sqrt(w dt) eta ~ 0.13 eta; rounding eta
     # to BF16 moves it by up to 2^-9 |eta|, i.e. ~1e-3 per step at |eta| ~ 4 in
-    # the tail of 6e4 draws, so three steps stay within ~1e-2 of the oracle.
+    # the tail of 6e4 draws, so three steps stay within ~1e-2 of the oracle. The
+    # FP32 mode keeps eta to 2^-22; what is left is the FP32 Box-Muller (32-bit
+    # uniforms: ~1e-5 on the largest of 6e4 normals) and FP32 state arithmetic.
     twa = _twa()
     alpha, w, G, dt = 1.0, 8.0, 1.0, 2e-3
     o = TWAOracle(N, alpha, w, G, dt, 11, M)
@@ -97,7 +121,7 @@ def test_trajectories_track_oracle_for_a_few_steps(prec, tol, N, M):
             assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 5e-6
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32"])
 def test_ensemble_observables_within_3se(prec):
     # N = 256, alpha = 1, w = 32, M = 512, dt = 1e-3, T = 1, window (0.5, 1]
     N, alpha, w, G, dt, M, T, t0 = 256, 1.0, 32.0, 1.0, 1e-3, 512, 1.0, 0.5
@@ -150,42 +174,44 @@ def test_full_size_sampled_field():
             assert abs(P[k, i] - ref) <= bound, (i, k, P[k, i], ref)
 
 
-def test_tf32_full_size_sampled_trajectories_and_fft_route():
-    # the TF32 configuration (kind::tf32 MMAs, FP32-container images, 16-wide K
-    # stages) at N = 10^4, M = 1024 on the dense route and on the FFT route
-    # (whose L.eta runs on the same kernel); three trajectories by the oracle
+def test_tf32_fp32_full_size_sampled_trajectories_and_fft_route():
+    # the 16-wide FP32 K-stage configuration (kind::tf32 MMAs, FP32-container
+    # images) at N = 10^4, M = 1024: TF32 (one term) and FP32 (three terms, eta
+    # split too) on the dense route and on the FFT route (whose L.eta runs on the
+    # same kernel); three trajectories by the oracle
     twa = _twa()
     N, alpha, w, G, dt, M = 10000, 1.0, 5000.0, 1.0, 2e-5, 1024
+    tol = {"tf32": 1e-2, "fp32": 1e-4}
     st = {}
-    for route in ("dense", "fft"):
-        with twa.TWA(N, alpha, w, G, dt, seed=0, precision="tf32", ws_route=route) as g:
-            g.run(M, 2)
-            st[route] = g.get_state()
+    for prec in tol:
+        for route in ("dense", "fft"):
+            with twa.TWA(N, alpha, w, G, dt, seed=0, precision=prec, ws_route=route) as g:
+                g.run(M, 2)
+                st[prec, route] = g.get_state()
     W = pump_matrix(N, alpha, w)
     L = np.linalg.cholesky(W)
-    for route in ("dense", "fft"):
-        gx, gy, gz = st[route]
+    for gx, gy, gz in st.values():
         assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 5e-6
     for m in (0, 517, 1023):
         o = TWAOracle(N, alpha, w, G, dt, 0, 1, m0=m, W=W, L=L)
         o.run(2)
-        for route in ("dense", "fft"):
-            gx, gy, gz = st[route]
+        for (prec, route), (gx, gy, gz) in st.items():
             err = max(np.max(np.abs(gx[m] - o.sx[0])), np.max(np.abs(gy[m] - o.sy[0])),
                       np.max(np.abs(gz[m] - o.sz[0])))
-            assert err < 1e-2, (route, m, err)
+            assert err < tol[prec], (prec, route, m, err)
 
 
-def test_tf32_rejects_what_it_does_not_cover(monkeypatch):
+@pytest.mark.parametrize("prec", ["tf32", "fp32"])
+def test_tf32_modes_reject_what_they_do_not_cover(prec, monkeypatch):
     twa = _twa()
-    with twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="tf32") as g:
+    with twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision=prec) as g:
         with pytest.raises(twa.TWAError) as e:
             g.grad("SpSm", 8, 4)
         assert e.value.name == "TWA_EUNSUPPORTED"
     with pytest.raises(twa.TWAError) as e:
-        twa.batch_run([dict(N=32, alpha=1.0, w=4.0, Gamma=1.0, dt=1e-3, steps=4)], 8, precision="tf32")
+        twa.batch_run([dict(N=32, alpha=1.0, w=4.0, Gamma=1.0, dt=1e-3, steps=4)], 8, precision=prec)
     assert e.value.name == "TWA_EUNSUPPORTED"
     monkeypatch.setenv("TWA_TC_BN", "128")
     with pytest.raises(twa.TWAError) as e:
-        twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="tf32")
+        twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision=prec)
     assert e.value.name == "TWA_EINVAL"
