@@ -5,8 +5,8 @@
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
-path and on the mixed paths (BF16, TF32, BF16X3, BF16X3 with the FFT pump
-field);
+path and on the mixed paths (BF16, TF32, BF16X3, FP32 from a TF32 split,
+BF16X3 with the FFT pump field);
 each observable is reported with its standard error and, per mixed path, the
 paired difference to FP64 (mean over trajectories of the per-trajectory
 difference, and its standard error), which isolates the arithmetic error from
@@ -64,6 +64,7 @@ def precision_study(args):
         for name, prec, route, noise in (("bf16", "bf16", "dense", "cholesky"),
                                          ("tf32", "tf32", "dense", "cholesky"),
                                          ("bf16x3", "bf16x3", "dense", "cholesky"),
+                                         ("fp32", "fp32", "dense", "cholesky"),
                                          ("bf16x3_fft", "bf16x3", "fft", "cholesky"),
                                          ("fft_circulant_noise", "bf16x3", "fft", "circulant")):
             obs, means, secs = _run(N, alpha, w, G, dt, steps, args.M_ref, t0, prec, route, noise)
