@@ -27,7 +27,11 @@ Readings where the paper is silent (each is also listed in the design notes):
 
 * Integrator: stochastic Heun (predictor/corrector, Stratonovich sense, the
   same noise in both stages) followed by renormalising every spin to length
-  sqrt(3); the paper's own semi-implicit scheme is not reproduced.
+  sqrt(3). Option: the semi-implicit midpoint scheme the paper cites for its
+  own runs (Mentink et al., J. Phys.: Condens. Matter 22, 176001 (2010)),
+  written with the effective field of Sec. S1, ds_i = s_i x b_i: a predictor
+  s~ = s + ((s + s~)/2) x b(s), then s' = s + ((s + s')/2) x b((s + s~)/2),
+  each an exact rotation; the same noise in both stages.
 * Noise: chi = L eta with L L^T = W (Cholesky, lower triangular); alpha = 0 uses
   the exact rank-one factor L[:, 0] = sqrt(w); alpha = inf uses sqrt(w) I.
   Per step the increments are sqrt(Gamma dt) xi_hat (collective, one per
@@ -153,7 +157,8 @@ def spectrum(N, alpha, w):
 
 
 class TWAOracle:
-    """Stochastic-Heun integration of Eq. (S1) for trajectories m0 .. m0+M-1.
+    """Stochastic-Heun (or semi-implicit midpoint) integration of Eq. (S1) for
+    trajectories m0 .. m0+M-1.
 
     State arrays ``sx, sy, sz`` have shape (M, N): row = trajectory, column =
     site. ``t`` counts completed steps; the Philox counter uses the global
@@ -162,7 +167,7 @@ class TWAOracle:
     """
 
     def __init__(self, N, alpha, w, Gamma, dt, seed, M, m0=0, init_sz=-1.0,
-                 window_start=0.0, renormalize=True, L=None, W=None, sample_stride=1):
+                 window_start=0.0, renormalize=True, L=None, W=None, sample_stride=1, integrator="heun"):
         self.N, self.alpha, self.w, self.Gamma, self.dt = int(N), float(alpha), float(w), float(Gamma), float(dt)
         self.seed, self.M, self.m0 = int(seed), int(M), int(m0)
         self.window_start = float(window_start)
@@ -171,6 +176,9 @@ class TWAOracle:
         self.n_window = int(math.floor(self.window_start / self.dt + 0.5))
         self.sample_stride = max(1, int(sample_stride))
         self.renormalize = bool(renormalize)
+        if integrator not in ("heun", "midpoint"):
+            raise ValueError("integrator must be 'heun' or 'midpoint'")
+        self.integrator = integrator
         self.W = pump_matrix(self.N, self.alpha, self.w) if W is None else np.asarray(W, dtype=np.float64)
         self.L = noise_factor(self.N, self.alpha, self.w) if L is None else np.asarray(L, dtype=np.float64)
         mm = (self.m0 + np.arange(self.M, dtype=np.uint64))[:, None]
@@ -207,6 +215,31 @@ class TWAOracle:
             - (dxi_x * sx + dxi_y * sy) + (dchi_x * sx + dchi_y * sy)
         return dx, dy, dz
 
+    def field(self, sx, sy, sz, dxi_x, dxi_y, dchi_x, dchi_y):
+        """Effective field of Sec. S1 integrated over dt, b_i = (B^y_i, -B^x_i, 0),
+        so that the increment of Eq. (S1) is s_i x b_i, with
+        B^a_i = 1/2 (Gamma S^a - sum_j w_ij s^a_j) dt + xi^a dt - chi_i^a dt."""
+        G, dt = self.Gamma, self.dt
+        Bx = 0.5 * (G * sx.sum(axis=1, keepdims=True) - sx @ self.W.T) * dt + dxi_x - dchi_x
+        By = 0.5 * (G * sy.sum(axis=1, keepdims=True) - sy @ self.W.T) * dt + dxi_y - dchi_y
+        return By, -Bx, np.zeros_like(Bx)
+
+    @staticmethod
+    def cayley(sx, sy, sz, bx, by, bz):
+        """The s' solving s' = s + ((s + s') / 2) x b for every spin.
+
+        With K the cross-product matrix of b (K v = b x v, so v x b = -K v) the
+        equation is (I + K/2) s' = (I - K/2) s, solved spin by spin."""
+        b = np.stack(np.broadcast_arrays(bx, by, bz), axis=-1)
+        K = np.zeros(b.shape + (3,))
+        K[..., 0, 1], K[..., 0, 2] = -b[..., 2], b[..., 1]
+        K[..., 1, 0], K[..., 1, 2] = b[..., 2], -b[..., 0]
+        K[..., 2, 0], K[..., 2, 1] = -b[..., 1], b[..., 0]
+        eye = np.eye(3)
+        v = np.stack(np.broadcast_arrays(sx, sy, sz), axis=-1)[..., None]
+        out = np.linalg.solve(eye + 0.5 * K, (eye - 0.5 * K) @ v)[..., 0]
+        return out[..., 0], out[..., 1], out[..., 2]
+
     def noise_increments(self, t):
         """Integrated noises of step t: xi^a dt with variance Gamma dt (one per
         trajectory and component, shape (M, 1)) and chi_i^a dt = sqrt(dt) (L eta^a)_i
@@ -223,10 +256,18 @@ class TWAOracle:
         t = self.t
         dxi_x, dxi_y, dchi_x, dchi_y = self.noise_increments(t)
         sx, sy, sz = self.sx, self.sy, self.sz
-        fx, fy, fz = self.increment(sx, sy, sz, dxi_x, dxi_y, dchi_x, dchi_y)
-        px, py, pz = sx + fx, sy + fy, sz + fz        # predictor
-        gx, gy, gz = self.increment(px, py, pz, dxi_x, dxi_y, dchi_x, dchi_y)
-        nx, ny, nz = sx + 0.5 * (fx + gx), sy + 0.5 * (fy + gy), sz + 0.5 * (fz + gz)
+        if self.integrator == "heun":
+            fx, fy, fz = self.increment(sx, sy, sz, dxi_x, dxi_y, dchi_x, dchi_y)
+            px, py, pz = sx + fx, sy + fy, sz + fz        # predictor
+            gx, gy, gz = self.increment(px, py, pz, dxi_x, dxi_y, dchi_x, dchi_y)
+            nx, ny, nz = sx + 0.5 * (fx + gx), sy + 0.5 * (fy + gy), sz + 0.5 * (fz + gz)
+        else:
+            # semi-implicit midpoint: predictor with the field at s, corrector with
+            # the field at the midpoint of s and the predictor
+            b0 = self.field(sx, sy, sz, dxi_x, dxi_y, dchi_x, dchi_y)
+            px, py, pz = self.cayley(sx, sy, sz, *b0)
+            b1 = self.field(0.5 * (sx + px), 0.5 * (sy + py), 0.5 * (sz + pz), dxi_x, dxi_y, dchi_x, dchi_y)
+            nx, ny, nz = self.cayley(sx, sy, sz, *b1)
         if self.renormalize:
             scale = math.sqrt(3.0) / np.sqrt(nx * nx + ny * ny + nz * nz)
             nx, ny, nz = nx * scale, ny * scale, nz * scale
