@@ -296,9 +296,9 @@ def run_ours(args, rank, world, dist):
     ctx.close()
 
     # ---- beside the dense route: the FFT route and the plain FP64 GPU path ----
-    def side_run(precision, route, steps, warm, noise="cholesky"):
+    def side_run(precision, route, steps, warm, noise="cholesky", integrator="heun"):
         g = twa.TWA(N, CFG["alpha"], CFG["w"], CFG["Gamma"], CFG["dt"], seed=0, precision=precision,
-                    stream=stream, traj_offset=rank * M, ws_route=route, noise_route=noise)
+                    stream=stream, traj_offset=rank * M, ws_route=route, noise_route=noise, integrator=integrator)
         g.run(M, warm)
         g.sync()
         torch.cuda.synchronize()
@@ -329,6 +329,9 @@ def run_ours(args, rank, world, dist):
             if prec != CFG["precision"]:
                 side["dense_" + prec] = side_run(prec, "dense", min(K, 300), 3)
                 side["dense_" + prec]["speedup_vs_main"] = side["dense_" + prec]["value"] / value
+        # the paper's semi-implicit midpoint integrator in place of Heun
+        side["dense_midpoint"] = side_run(CFG["precision"], "dense", min(K, 300), 3, integrator="midpoint")
+        side["dense_midpoint"]["speedup_vs_main"] = side["dense_midpoint"]["value"] / value
         side["fp64_gpu"] = side_run("fp64", "dense", 2, 1)
         side["fp64_gpu"]["mixed_speedup"] = value / side["fp64_gpu"]["value"]
 

@@ -111,7 +111,7 @@ typedef struct twa_opts {
                                offsets and reproduce the unsharded run exactly     */
     int    ws_route;        /* pump field sum_j w_ij s_j: TWA_ROUTE_DENSE (default,
                                any W) or TWA_ROUTE_FFT (uses that Eq. 2 is Toeplitz;
-                               BF16 modes only, 2N - 2 <= 28000)                   */
+                               tensor-core precisions only, 2N - 2 <= 28000)       */
     int    noise_route;     /* draw of the pump noise chi (covariance w_ij dt, Sec. S1):
                                TWA_NOISE_CHOLESKY (default: chi = L eta) or
                                TWA_NOISE_CIRCULANT (FFT of the circulant embedding;
@@ -129,7 +129,25 @@ typedef struct twa_opts {
                                the library's allocator)                           */
     twa_free_fn free;
     void*  alloc_user;      /* passed through to alloc and free                   */
+    int    integrator;      /* TWA_INT_HEUN (default) or TWA_INT_MIDPOINT          */
 } twa_opts;
+
+/* Integrators of Eq. S1, written with its effective field: ds_i = s_i x b_i,
+   b_i = (B^y_i, -B^x_i, 0) over one step, B^a_i = 1/2 (Gamma S^a - sum_j w_ij
+   s^a_j) dt + sqrt(Gamma dt) xi^a - sqrt(dt) (L eta^a)_i, the same noise in
+   both stages of a step.
+   HEUN: s~ = s + s x b(s), s' = s + (s x b(s) + s~ x b(s~)) / 2 (stochastic
+   Heun, Stratonovich), then |s_i| = sqrt(3) if renormalize is set.
+   MIDPOINT: the semi-implicit scheme the paper uses (Mentink et al., J. Phys.:
+   Condens. Matter 22, 176001 (2010)): s~ solves s~ = s + ((s + s~)/2) x b(s),
+   s' solves s' = s + ((s + s')/2) x b((s + s~)/2); each stage is an exact
+   rotation, m = (s + s x c + (s.c) c) / (1 + |c|^2) with c = b/2 and s' = 2m - s,
+   so |s_i| is kept without renormalisation (renormalize still removes the
+   rounding drift). The corrector field is that of the midpoint state, whose
+   images the predictor hands to the second contraction. Dense route only; not
+   twa_grad or twa_batch_run.                                                  */
+#define TWA_INT_HEUN     0
+#define TWA_INT_MIDPOINT 1
 
 #define TWA_ROUTE_DENSE 0   /* tensor-core contraction with the dense W          */
 #define TWA_ROUTE_FFT   1   /* circulant-embedding FFT convolution, FP32         */
@@ -277,8 +295,8 @@ typedef struct twa_grad_out {
  * their standard deviation / sqrt(M) the returned SE. Synchronises.
  * Errors: TWA_EINVAL (NULL, M < 1, steps < 1), TWA_ESTATE (no step inside the
  * window), TWA_EUNSUPPORTED (want_alpha with alpha = 0 or inf, w = 0, a
- * context with noise_route = TWA_NOISE_CIRCULANT or precision = TWA_PREC_TF32
- * or TWA_PREC_FP32),
+ * context with noise_route = TWA_NOISE_CIRCULANT, precision = TWA_PREC_TF32
+ * or TWA_PREC_FP32, or integrator = TWA_INT_MIDPOINT),
  * TWA_ENOMEM, TWA_ECUDA,
  * TWA_ENONFINITE. */
 TWA_API int twa_grad(twa_ctx* ctx, const twa_grad_req* req, twa_grad_out* out, double* per_traj);
@@ -313,8 +331,9 @@ typedef struct twa_point {
  * points that run in the stage with the most work (steps x N^2 of the points
  * still running; the state is saved and restored around the trials) and keeps
  * the fastest. tiles: NULL or int[2] receiving the chosen (BN, K-stage config).
- * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (FP64 precision), plus those of twa_init
- * and twa_sync. Synchronises. */
+ * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (a precision other than BF16 and
+ * BF16X3, or the midpoint integrator), plus those of twa_init and twa_sync.
+ * Synchronises. */
 TWA_API int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,
                           twa_obs* out, int* tiles);
 

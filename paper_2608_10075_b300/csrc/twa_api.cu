@@ -219,6 +219,10 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         return set_error(nullptr, TWA_EINVAL, "twa_init: give both alloc and free, or neither");
     if (o.sample_stride < 0 || o.sample_stride > MAX_COUNTER)
         return set_error(nullptr, TWA_EINVAL, "twa_init: sample_stride must be in [0, 2^32-1]");
+    if (o.integrator != TWA_INT_HEUN && o.integrator != TWA_INT_MIDPOINT)
+        return set_error(nullptr, TWA_EINVAL, "twa_init: integrator must be TWA_INT_HEUN or TWA_INT_MIDPOINT");
+    if (o.integrator == TWA_INT_MIDPOINT && o.ws_route == TWA_ROUTE_FFT)
+        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the midpoint integrator runs on the dense route");
     if (o.noise_route != TWA_NOISE_CHOLESKY && o.noise_route != TWA_NOISE_CIRCULANT)
         return set_error(nullptr, TWA_EINVAL, "twa_init: noise_route must be TWA_NOISE_CHOLESKY or TWA_NOISE_CIRCULANT");
     if (o.noise_route == TWA_NOISE_CIRCULANT && o.ws_route != TWA_ROUTE_FFT)
@@ -423,6 +427,8 @@ int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
     if (!(c->w > 0.0)) return set_error(c, TWA_EUNSUPPORTED, "twa_grad: needs w > 0");
     if (c->opts.precision == TWA_PREC_TF32 || c->opts.precision == TWA_PREC_FP32)
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: runs on the FP64, BF16 and BF16X3 precisions");
+    if (c->opts.integrator != TWA_INT_HEUN)
+        return set_error(c, TWA_EUNSUPPORTED, "twa_grad: differentiates the Heun integrator only");
     if (c->opts.noise_route != TWA_NOISE_CHOLESKY)
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: differentiates the Cholesky noise draw only");
     if (r->want_alpha && (c->alpha == 0.0 || isinf(c->alpha)))

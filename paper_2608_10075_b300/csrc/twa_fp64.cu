@@ -189,6 +189,73 @@ __global__ void k_correct_f64(const double* xyp, const double* zp, const double*
     z[e] = nz;
 }
 
+// Midpoint m = (s + s')/2 of the implicit-midpoint rotation s' = s + m x b with
+// b = (B^y, -B^x, 0) (Mentink et al. 2010): with c = b/2, m - m x c = s gives
+// m = (s + s x c + (s.c) c) / (1 + |c|^2), where s x c = (z B^x, z B^y,
+// -(x B^x + y B^y)) / 2 and s.c = (x B^y - y B^x) / 2.
+__device__ __forceinline__ void mid_rotation_f64(double x, double y, double z, double Bx, double By, double& mx,
+                                                 double& my, double& mz) {
+    const double hx = 0.5 * Bx, hy = 0.5 * By;
+    const double sc = x * hy - y * hx;
+    const double inv = 1.0 / (1.0 + hx * hx + hy * hy);
+    mx = (x + z * hx + sc * hy) * inv;
+    my = (y + z * hy - sc * hx) * inv;
+    mz = (z - (x * hx + y * hy)) * inv;
+}
+
+// Midpoint-scheme predictor: the same field increment as k_predict_f64; writes
+// the midpoint state (s + s~)/2 of the predictor rotation (the corrector's field
+// is evaluated there) and the noise part over the L.eta buffer.
+__global__ void k_predict_mid_f64(const double* xy, const double* z, const double* pf, double* q, const double* xi,
+                                  const double* S, double* xym, double* zm, int64_t M, int64_t N, double G,
+                                  double dt) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= M * N) return;
+    const int64_t m = e / N, i = e - m * N;
+    const int64_t rx = (2 * m) * N + i, ry = rx + N;
+    const double sg = sqrt(G * dt), sd = sqrt(dt);
+    const double x = xy[rx], y = xy[ry], zz = z[e];
+    const double bnx = sg * xi[2 * m] - sd * q[rx];
+    const double bny = sg * xi[2 * m + 1] - sd * q[ry];
+    const double Bx = 0.5 * (G * S[4 * m] - pf[rx]) * dt + bnx;
+    const double By = 0.5 * (G * S[4 * m + 1] - pf[ry]) * dt + bny;
+    double mx, my, mz;
+    mid_rotation_f64(x, y, zz, Bx, By, mx, my, mz);
+    xym[rx] = mx;
+    xym[ry] = my;
+    zm[e] = mz;
+    q[rx] = bnx;
+    q[ry] = bny;
+}
+
+// Midpoint-scheme corrector: field at the midpoint state (pf = W m, Sm its sums)
+// with the same noise, s' = 2 m' - s of the rotation from s, optional rescaling
+// to |s_i| = sqrt(3) (the rotation keeps it up to rounding). In place on xy, z.
+__global__ void k_correct_mid_f64(const double* pf, const double* bn, const double* Sm, double* xy, double* z,
+                                  int64_t M, int64_t N, double G, double dt, int renorm,
+                                  unsigned long long* flags) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= M * N) return;
+    const int64_t m = e / N, i = e - m * N;
+    const int64_t rx = (2 * m) * N + i, ry = rx + N;
+    const double x = xy[rx], y = xy[ry], zz = z[e];
+    const double Bx = 0.5 * (G * Sm[4 * m] - pf[rx]) * dt + bn[rx];
+    const double By = 0.5 * (G * Sm[4 * m + 1] - pf[ry]) * dt + bn[ry];
+    double mx, my, mz;
+    mid_rotation_f64(x, y, zz, Bx, By, mx, my, mz);
+    double nx = 2.0 * mx - x, ny = 2.0 * my - y, nz = 2.0 * mz - zz;
+    if (renorm) {
+        const double s = sqrt(3.0) / sqrt(nx * nx + ny * ny + nz * nz);
+        nx *= s;
+        ny *= s;
+        nz *= s;
+    }
+    if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicAdd(&flags[FLAG_NONFINITE], 1ull);
+    xy[rx] = nx;
+    xy[ry] = ny;
+    z[e] = nz;
+}
+
 // Closing kernel of a step: collective sums of the new state, window moments
 // S^z, A, A^2, A S^z, (S^z)^2 with A = ((S^x)^2 + (S^y)^2)/4 when the completed
 // step count exceeds n_window, and the step counter increment by the last
@@ -307,10 +374,16 @@ int f64_run(twa_ctx* c, int64_t steps) {
             ProfScope p(c, TWA_PROF_GEMM64);
             gemm_f64(c->W64, N, c->xy, N, c->pf, N, N, 2 * M, N, 1.0, 0.0, false, false, st);
         }
+        const bool mid = c->opts.integrator == TWA_INT_MIDPOINT;
         {
+            // xyp, zp: the predictor s~ (Heun) or the midpoint (s + s~)/2 (midpoint scheme)
             ProfScope p(c, TWA_PROF_ELEM64);
-            k_predict_f64<<<gMN, 256, 0, st>>>(c->xy, c->z, c->pf, c->eta, c->xi, c->S, c->xyp, c->zp, c->hxy,
-                                               c->hz, M, N, c->Gamma, c->dt);
+            if (mid)
+                k_predict_mid_f64<<<gMN, 256, 0, st>>>(c->xy, c->z, c->pf, c->eta, c->xi, c->S, c->xyp, c->zp, M, N,
+                                                       c->Gamma, c->dt);
+            else
+                k_predict_f64<<<gMN, 256, 0, st>>>(c->xy, c->z, c->pf, c->eta, c->xi, c->S, c->xyp, c->zp, c->hxy,
+                                                   c->hz, M, N, c->Gamma, c->dt);
         }
         {
             ProfScope p(c, TWA_PROF_ELEM64);
@@ -322,8 +395,12 @@ int f64_run(twa_ctx* c, int64_t steps) {
         }
         {
             ProfScope p(c, TWA_PROF_ELEM64);
-            k_correct_f64<<<gMN, 256, 0, st>>>(c->xyp, c->zp, c->pf, c->eta, c->Sp, c->hxy, c->hz, c->xy, c->z,
-                                               M, N, c->Gamma, c->dt, c->opts.renormalize, c->d_flags);
+            if (mid)
+                k_correct_mid_f64<<<gMN, 256, 0, st>>>(c->pf, c->eta, c->Sp, c->xy, c->z, M, N, c->Gamma, c->dt,
+                                                       c->opts.renormalize, c->d_flags);
+            else
+                k_correct_f64<<<gMN, 256, 0, st>>>(c->xyp, c->zp, c->pf, c->eta, c->Sp, c->hxy, c->hz, c->xy,
+                                                   c->z, M, N, c->Gamma, c->dt, c->opts.renormalize, c->d_flags);
         }
         {
             ProfScope p(c, TWA_PROF_CLOSE);

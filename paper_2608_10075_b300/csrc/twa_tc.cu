@@ -231,6 +231,21 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
     if (with_lo) lo[off] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// Midpoint m = (s + s')/2 of the implicit-midpoint rotation s' = s + m x b, b =
+// (B^y, -B^x, 0) (Mentink et al. 2010): with c = b/2, m - m x c = s gives
+// m = (s + s x c + (s.c) c) / (1 + |c|^2), s x c = (z B^x, z B^y, -(x B^x +
+// y B^y)) / 2, s.c = (x B^y - y B^x) / 2. Every rounding written out, so that
+// each kernel instantiation gives the same bits.
+__device__ __forceinline__ void mid_rotation_f32(float x, float y, float z, float Bx, float By, float& mx, float& my,
+                                                 float& mz) {
+    const float hx = __fmul_rn(0.5f, Bx), hy = __fmul_rn(0.5f, By);
+    const float sc = fmaf(x, hy, -__fmul_rn(y, hx));
+    const float inv = __frcp_rn(fmaf(hx, hx, fmaf(hy, hy, 1.0f)));
+    mx = __fmul_rn(fmaf(sc, hy, fmaf(z, hx, x)), inv);
+    my = __fmul_rn(fmaf(-sc, hx, fmaf(z, hy, y)), inv);
+    mz = __fmul_rn(fmaf(-x, hx, fmaf(-y, hy, z)), inv);
+}
+
 // v rounded to TF32 (10 explicit mantissa bits, nearest, ties away), in FP32.
 __device__ __forceinline__ float to_tf32(float v) {
     uint32_t r;
@@ -260,12 +275,14 @@ struct TcArgs {
     int64_t N, M, ldk, n_rt, n_vec;   // n_vec: B rows (2M, or K vectors in the field mode)
     float G, dt, sgdt, sdt;
     int renorm;
-    const float *X, *Y, *Z;           // PRED: s; CORR: s~
+    int integ;                        // TWA_INT_HEUN or TWA_INT_MIDPOINT
+    const float *X, *Y, *Z;           // PRED: s; CORR: s~ (midpoint scheme: s)
     const float *X0, *Y0, *Z0;        // CORR: s, the state before the step
     const float *Bnx, *Bny;           // PRED, CORR: noise part of the field increment
-    float *oX, *oY, *oZ;              // PRED: s~; CORR: s'
+    float *oX, *oY, *oZ;              // PRED: s~ (not written by the midpoint scheme); CORR: s'
     float *oBnx, *oBny;               // LETA
-    __nv_bfloat16 *oHi, *oLo;         // images of the output state
+    __nv_bfloat16 *oHi, *oLo;         // images of the output state (midpoint scheme's
+                                      // predictor: of the midpoint (s + s~)/2)
     const float* XI;                  // LETA: collective normals [M][2]
     const float* part_in;             // sums of the input state, [n_rt][M][4]
     float* part_out;                  // sums of the output state
@@ -591,27 +608,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                             const float Byv = fmaf(fmaf(Gm, sS[2 * jl + 1], -pv[2 * jj + 1]), hdt, args.Bny[e]);
                             const int64_t r0 = (2 * m) * args.ldk + i;
                             if constexpr (EM == MODE_PRED) {
-                                // f = s x (B^y, -B^x, 0); s~ = s + f
-                                const float fx = __fmul_rn(z, Bxv), fy = __fmul_rn(z, Byv);
-                                const float fz = -fmaf(x, Bxv, __fmul_rn(y, Byv));
-                                const float xp = __fadd_rn(x, fx), yp = __fadd_rn(y, fy), zp = __fadd_rn(z, fz);
-                                args.oX[e] = xp;
-                                args.oY[e] = yp;
-                                args.oZ[e] = zp;
+                                float xp, yp, zp;
+                                if (args.integ == TWA_INT_MIDPOINT) {
+                                    // the corrector's field point (s + s~)/2; only its
+                                    // images and sums are needed
+                                    mid_rotation_f32(x, y, z, Bxv, Byv, xp, yp, zp);
+                                } else {
+                                    // f = s x (B^y, -B^x, 0); s~ = s + f
+                                    const float fx = __fmul_rn(z, Bxv), fy = __fmul_rn(z, Byv);
+                                    const float fz = -fmaf(x, Bxv, __fmul_rn(y, Byv));
+                                    xp = __fadd_rn(x, fx);
+                                    yp = __fadd_rn(y, fy);
+                                    zp = __fadd_rn(z, fz);
+                                    args.oX[e] = xp;
+                                    args.oY[e] = yp;
+                                    args.oZ[e] = zp;
+                                }
                                 image_store(args.oHi, args.oLo, r0, xp, WITH_LO, TFM);
                                 image_store(args.oHi, args.oLo, r0 + args.ldk, yp, WITH_LO, TFM);
                                 rx[jj] = xp;
                                 ry[jj] = yp;
                                 rz[jj] = zp;
                             } else {
-                                // corrector: s' = s + (f(s) + f(s~))/2 = (s + s~)/2 + f(s~)/2,
-                                // then |s'| = sqrt(3)
-                                const float hx = __fmul_rn(0.5f, __fadd_rn(args.X0[e], x));
-                                const float hy = __fmul_rn(0.5f, __fadd_rn(args.Y0[e], y));
-                                const float hz = __fmul_rn(0.5f, __fadd_rn(args.Z0[e], z));
-                                float nx = fmaf(0.5f, __fmul_rn(z, Bxv), hx);
-                                float ny = fmaf(0.5f, __fmul_rn(z, Byv), hy);
-                                float nz = fmaf(-0.5f, fmaf(x, Bxv, __fmul_rn(y, Byv)), hz);
+                                float nx, ny, nz;
+                                if (args.integ == TWA_INT_MIDPOINT) {
+                                    // (x, y, z) = s; field of the midpoint state:
+                                    // s' = 2 m - s of the rotation from s
+                                    float mx, my, mz;
+                                    mid_rotation_f32(x, y, z, Bxv, Byv, mx, my, mz);
+                                    nx = fmaf(2.0f, mx, -x);
+                                    ny = fmaf(2.0f, my, -y);
+                                    nz = fmaf(2.0f, mz, -z);
+                                } else {
+                                    // corrector: s' = s + (f(s) + f(s~))/2 = (s + s~)/2 + f(s~)/2,
+                                    // then |s'| = sqrt(3)
+                                    const float hx = __fmul_rn(0.5f, __fadd_rn(args.X0[e], x));
+                                    const float hy = __fmul_rn(0.5f, __fadd_rn(args.Y0[e], y));
+                                    const float hz = __fmul_rn(0.5f, __fadd_rn(args.Z0[e], z));
+                                    nx = fmaf(0.5f, __fmul_rn(z, Bxv), hx);
+                                    ny = fmaf(0.5f, __fmul_rn(z, Byv), hy);
+                                    nz = fmaf(-0.5f, fmaf(x, Bxv, __fmul_rn(y, Byv)), hz);
+                                }
                                 if (args.renorm) {
                                     const float s = sqrtf(3.0f / fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz))));
                                     nx = __fmul_rn(nx, s);
@@ -1048,6 +1085,7 @@ TcArgs base_args(twa_ctx* c) {
     a.sgdt = (float)sqrt(c->Gamma * c->dt);
     a.sdt = (float)sqrt(c->dt);
     a.renorm = c->opts.renormalize;
+    a.integ = c->opts.integrator;
     a.flags = c->d_flags;
     return a;
 }
@@ -1446,7 +1484,9 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
             pa.oX = t->Xp; pa.oY = t->Yp; pa.oZ = t->Zp;
             pa.oHi = t->Phi; pa.oLo = t->Plo;
             pa.part_in = t->part; pa.part_out = t->partp;
-            ca.X = t->Xp; ca.Y = t->Yp; ca.Z = t->Zp;
+            // the midpoint scheme's corrector rotates s itself (in place)
+            const bool mid = c->opts.integrator == TWA_INT_MIDPOINT;
+            ca.X = mid ? t->X : t->Xp; ca.Y = mid ? t->Y : t->Yp; ca.Z = mid ? t->Z : t->Zp;
             ca.X0 = t->X; ca.Y0 = t->Y; ca.Z0 = t->Z;
             ca.Bnx = bx; ca.Bny = by;
             ca.oX = t->X; ca.oY = t->Y; ca.oZ = t->Z;

@@ -35,7 +35,7 @@ class Opts(ctypes.Structure):
                 ("renormalize", ctypes.c_int), ("clip_negative", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("traj_offset", ctypes.c_int64), ("ws_route", ctypes.c_int), ("noise_route", ctypes.c_int),
                 ("sample_stride", ctypes.c_int64), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p)]
+                ("alloc_user", ctypes.c_void_p), ("integrator", ctypes.c_int)]
 
 
 def torch_allocator():
@@ -69,6 +69,7 @@ def _allocator(allocator):
 
 ROUTE = {"dense": 0, "fft": 1}
 NOISE = {"cholesky": 0, "circulant": 1}
+INTEGRATOR = {"heun": 0, "midpoint": 1}
 
 
 class Obs(ctypes.Structure):
@@ -179,7 +180,7 @@ class TWA:
 
     def __init__(self, N, alpha, w, Gamma, dt, seed=0, precision="fp64", init_state=-1, window_start=0.0,
                  renormalize=True, clip_negative=False, stream=None, traj_offset=0, ws_route="dense",
-                 noise_route="cholesky", sample_stride=1, allocator=None):
+                 noise_route="cholesky", sample_stride=1, allocator=None, integrator="heun"):
         L = lib()
         o = Opts()
         L.twa_opts_default(ctypes.byref(o))
@@ -193,6 +194,7 @@ class TWA:
         o.ws_route = ROUTE[ws_route] if isinstance(ws_route, str) else int(ws_route)
         o.noise_route = NOISE[noise_route] if isinstance(noise_route, str) else int(noise_route)
         o.sample_stride = int(sample_stride)
+        o.integrator = INTEGRATOR[integrator] if isinstance(integrator, str) else int(integrator)
         # device memory from the caller's allocator (kept alive with the context)
         self._alloc = _allocator(allocator)
         if self._alloc is not None:
@@ -324,7 +326,7 @@ def reduce_moments(means, N):
     return o.as_dict()
 
 
-def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None):
+def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None, integrator="heun"):
     """twa_batch_run: points = list of dicts with N, alpha, w, Gamma, dt, steps,
     window_start. Returns (list of observables dicts, (BN, K-stage config))."""
     arr = (Point * len(points))()
@@ -334,6 +336,7 @@ def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None
     o = Opts()
     lib().twa_opts_default(ctypes.byref(o))
     o.precision = PRECISION[precision]
+    o.integrator = INTEGRATOR[integrator]
     o.stream = _stream_handle(stream)
     alloc = _allocator(allocator)
     if alloc is not None:
