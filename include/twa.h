@@ -144,8 +144,9 @@ typedef struct twa_opts {
    rotation, m = (s + s x c + (s.c) c) / (1 + |c|^2) with c = b/2 and s' = 2m - s,
    so |s_i| is kept without renormalisation (renormalize still removes the
    rounding drift). The corrector field is that of the midpoint state, whose
-   images the predictor hands to the second contraction. Dense route only; not
-   twa_grad or twa_batch_run.                                                  */
+   images the predictor hands to the second contraction (on the FFT route, the
+   midpoint state is the second transform's input). twa_run on both routes and
+   twa_batch_run; not twa_grad.                                                */
 #define TWA_INT_HEUN     0
 #define TWA_INT_MIDPOINT 1
 
@@ -332,8 +333,7 @@ typedef struct twa_point {
  * still running; the state is saved and restored around the trials) and keeps
  * the fastest. tiles: NULL or int[2] receiving the chosen (BN, K-stage config).
  * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (a precision other than BF16 and
- * BF16X3, or the midpoint integrator), plus those of twa_init and twa_sync.
- * Synchronises. */
+ * BF16X3), plus those of twa_init and twa_sync. Synchronises. */
 TWA_API int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,
                           twa_obs* out, int* tiles);
 

@@ -221,8 +221,6 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         return set_error(nullptr, TWA_EINVAL, "twa_init: sample_stride must be in [0, 2^32-1]");
     if (o.integrator != TWA_INT_HEUN && o.integrator != TWA_INT_MIDPOINT)
         return set_error(nullptr, TWA_EINVAL, "twa_init: integrator must be TWA_INT_HEUN or TWA_INT_MIDPOINT");
-    if (o.integrator == TWA_INT_MIDPOINT && o.ws_route == TWA_ROUTE_FFT)
-        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the midpoint integrator runs on the dense route");
     if (o.noise_route != TWA_NOISE_CHOLESKY && o.noise_route != TWA_NOISE_CIRCULANT)
         return set_error(nullptr, TWA_EINVAL, "twa_init: noise_route must be TWA_NOISE_CHOLESKY or TWA_NOISE_CIRCULANT");
     if (o.noise_route == TWA_NOISE_CIRCULANT && o.ws_route != TWA_ROUTE_FFT)

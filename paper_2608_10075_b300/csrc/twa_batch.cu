@@ -181,8 +181,6 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
     if (opts) o = *opts;
     if (o.precision != TWA_PREC_BF16 && o.precision != TWA_PREC_BF16X3)
         return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: batches run on the BF16 precision paths");
-    if (o.integrator != TWA_INT_HEUN)
-        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: batches run the Heun integrator");
     o.ws_route = TWA_ROUTE_DENSE;
     o.noise_route = TWA_NOISE_CHOLESKY;
     for (int p = 0; p < n; ++p)

@@ -43,10 +43,11 @@ struct FftArgs {
     const float2* tw;
     float G, dt;
     int renorm;
-    const float *X, *Y, *Z;              // PRED: s; CORR: s~
+    int integ;                           // TWA_INT_HEUN or TWA_INT_MIDPOINT
+    const float *X, *Y, *Z;              // PRED: s; CORR: s~ (midpoint scheme: the midpoint state)
     const float *X0, *Y0, *Z0;           // CORR: s, the state before the step
     const float *Bnx, *Bny;              // noise part of the field increment
-    float *oX, *oY, *oZ;                 // PRED: s~; CORR: s'
+    float *oX, *oY, *oZ;                 // PRED: s~ (midpoint scheme: (s + s~)/2); CORR: s'
     double* mom;                         // CORR: window sums [M][5]
     int64_t* d_t;
     int64_t* d_count;
@@ -292,7 +293,8 @@ struct StateIn {
     }
 };
 
-// Heun predictor at site i from P (W s)_i (Eq. S1; every rounding spelled out).
+// Predictor at site i from P (W s)_i (Eq. S1; every rounding spelled out): Heun's
+// s~, or the midpoint state of the semi-implicit scheme's predictor rotation.
 struct PredOut {
     const FftArgs* a;
     int64_t off;
@@ -304,6 +306,14 @@ struct PredOut {
         // B^a = 1/2 (G S^a - (W s^a)_i) dt + noise part; f = s x (B^y, -B^x, 0)
         const float Bx = fmaf(fmaf(a->G, Sx, -__fmul_rn(pf.x, inv)), hdt, a->Bnx[e]);
         const float By = fmaf(fmaf(a->G, Sy, -__fmul_rn(pf.y, inv)), hdt, a->Bny[e]);
+        if (a->integ == TWA_INT_MIDPOINT) {
+            float mx, my, mz;
+            mid_rotation_f32(x, y, z, Bx, By, mx, my, mz);
+            a->oX[e] = mx;
+            a->oY[e] = my;
+            a->oZ[e] = mz;
+            return;
+        }
         const float fx = __fmul_rn(z, Bx), fy = __fmul_rn(z, By);
         const float fz = -fmaf(x, Bx, __fmul_rn(y, By));
         a->oX[e] = __fadd_rn(x, fx);
@@ -312,7 +322,8 @@ struct PredOut {
     }
 };
 
-// Heun corrector and renormalisation at site i; sums of the new state.
+// Corrector and renormalisation at site i; sums of the new state. Heun: from s~
+// (X) and s (X0); midpoint scheme: the field of the midpoint state (X) rotates s.
 struct CorrOut {
     const FftArgs* a;
     int64_t off;
@@ -325,13 +336,24 @@ struct CorrOut {
         const float x = a->X[e], y = a->Y[e], z = a->Z[e];
         const float Bx = fmaf(fmaf(a->G, Sx, -__fmul_rn(pf.x, inv)), hdt, a->Bnx[e]);
         const float By = fmaf(fmaf(a->G, Sy, -__fmul_rn(pf.y, inv)), hdt, a->Bny[e]);
-        // s' = (s + s~)/2 + f(s~)/2, then |s'| = sqrt(3)
-        const float hx = __fmul_rn(0.5f, __fadd_rn(a->X0[e], x));
-        const float hy = __fmul_rn(0.5f, __fadd_rn(a->Y0[e], y));
-        const float hz = __fmul_rn(0.5f, __fadd_rn(a->Z0[e], z));
-        float nx = fmaf(0.5f, __fmul_rn(z, Bx), hx);
-        float ny = fmaf(0.5f, __fmul_rn(z, By), hy);
-        float nz = fmaf(-0.5f, fmaf(x, Bx, __fmul_rn(y, By)), hz);
+        float nx, ny, nz;
+        if (a->integ == TWA_INT_MIDPOINT) {
+            // s' = 2 m - s of the rotation of s by the midpoint field
+            const float s0x = a->X0[e], s0y = a->Y0[e], s0z = a->Z0[e];
+            float mx, my, mz;
+            mid_rotation_f32(s0x, s0y, s0z, Bx, By, mx, my, mz);
+            nx = fmaf(2.0f, mx, -s0x);
+            ny = fmaf(2.0f, my, -s0y);
+            nz = fmaf(2.0f, mz, -s0z);
+        } else {
+            // s' = (s + s~)/2 + f(s~)/2, then |s'| = sqrt(3)
+            const float hx = __fmul_rn(0.5f, __fadd_rn(a->X0[e], x));
+            const float hy = __fmul_rn(0.5f, __fadd_rn(a->Y0[e], y));
+            const float hz = __fmul_rn(0.5f, __fadd_rn(a->Z0[e], z));
+            nx = fmaf(0.5f, __fmul_rn(z, Bx), hx);
+            ny = fmaf(0.5f, __fmul_rn(z, By), hy);
+            nz = fmaf(-0.5f, fmaf(x, Bx, __fmul_rn(y, By)), hz);
+        }
         if (a->renorm) {
             const float s = sqrtf(3.0f / fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz))));
             nx = __fmul_rn(nx, s);
@@ -568,6 +590,7 @@ FftArgs base_args(twa_ctx* c) {
     a.G = (float)c->Gamma;
     a.dt = (float)c->dt;
     a.renorm = c->opts.renormalize;
+    a.integ = c->opts.integrator;
     a.flags = c->d_flags;
     return a;
 }

@@ -231,21 +231,6 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
     if (with_lo) lo[off] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// Midpoint m = (s + s')/2 of the implicit-midpoint rotation s' = s + m x b, b =
-// (B^y, -B^x, 0) (Mentink et al. 2010): with c = b/2, m - m x c = s gives
-// m = (s + s x c + (s.c) c) / (1 + |c|^2), s x c = (z B^x, z B^y, -(x B^x +
-// y B^y)) / 2, s.c = (x B^y - y B^x) / 2. Every rounding written out, so that
-// each kernel instantiation gives the same bits.
-__device__ __forceinline__ void mid_rotation_f32(float x, float y, float z, float Bx, float By, float& mx, float& my,
-                                                 float& mz) {
-    const float hx = __fmul_rn(0.5f, Bx), hy = __fmul_rn(0.5f, By);
-    const float sc = fmaf(x, hy, -__fmul_rn(y, hx));
-    const float inv = __frcp_rn(fmaf(hx, hx, fmaf(hy, hy, 1.0f)));
-    mx = __fmul_rn(fmaf(sc, hy, fmaf(z, hx, x)), inv);
-    my = __fmul_rn(fmaf(-sc, hx, fmaf(z, hy, y)), inv);
-    mz = __fmul_rn(fmaf(-x, hx, fmaf(-y, hy, z)), inv);
-}
-
 // v rounded to TF32 (10 explicit mantissa bits, nearest, ties away), in FP32.
 __device__ __forceinline__ float to_tf32(float v) {
     uint32_t r;

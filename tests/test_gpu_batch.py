@@ -24,10 +24,10 @@ POINTS = [
 ]
 
 
-def _alone(p, M, seed):
+def _alone(p, M, seed, integrator="heun"):
     from paper_2608_10075_b300 import twa
     with twa.TWA(p["N"], p["alpha"], p["w"], p["Gamma"], p["dt"], seed=seed, precision="bf16x3",
-                 window_start=p["window_start"]) as g:
+                 window_start=p["window_start"], integrator=integrator) as g:
         g.run(M, p["steps"])
         return g.observables()
 
@@ -56,6 +56,19 @@ def test_batch_equals_points_run_alone(tiles):
         for k in ("Sz", "SpSm", "G2num", "g2", "Sz_se", "g2_se"):
             assert abs(r[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (p, k, r[k], ref[k])
         assert math.isfinite(r["w_max"]) and r["nonfinite"] == 0
+
+
+def test_batch_with_the_midpoint_integrator_equals_points_run_alone():
+    # the midpoint scheme's descriptors (corrector rotating s in place, predictor
+    # writing the midpoint images) inside one batched plan
+    from paper_2608_10075_b300 import twa
+    M, seed = 64, 7
+    res, _ = twa.batch_run(POINTS, M, seed=seed, integrator="midpoint")
+    for p, r in zip(POINTS, res):
+        ref = _alone(p, M, seed, integrator="midpoint")
+        for k in ("Sz", "SpSm", "G2num", "g2", "Sz_se", "g2_se"):
+            assert abs(r[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (p, k, r[k], ref[k])
+        assert r["nonfinite"] == 0
 
 
 def test_batch_rejects_fp64():

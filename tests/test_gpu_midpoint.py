@@ -123,11 +123,32 @@ def test_full_size_sampled_trajectories():
         assert err < 1e-2, (m, err)
 
 
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-2), ("fp32", 1e-3)])
+@pytest.mark.parametrize("noise", ["cholesky", "circulant"])
+def test_fft_route(prec, tol, noise):
+    # W.s by the circulant FFT, the midpoint state as the second transform's input
+    twa = _twa()
+    N, M, alpha, w, G, dt = 300, 40, 1.0, 8.0, 1.0, 2e-3
+    if noise == "cholesky":
+        o = TWAOracle(N, alpha, w, G, dt, 11, M, integrator="midpoint")
+    else:
+        from oracle.circulant import TWAOracleCirculant
+        o = TWAOracleCirculant(N, alpha, w, G, dt, 11, M, integrator="midpoint")
+    with twa.TWA(N, alpha, w, G, dt, seed=11, precision=prec, ws_route="fft", noise_route=noise,
+                 integrator="midpoint") as g:
+        for _ in range(3):
+            o.run(1)
+            g.run(M, 1)
+            assert _err(g, o) < tol
+    with twa.TWA(N, alpha, w, G, dt, seed=11, precision=prec, ws_route="fft", noise_route=noise,
+                 integrator="midpoint", renormalize=False) as g:
+        g.run(M, 100)
+        gx, gy, gz = g.get_state()
+    assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 1e-4
+
+
 def test_rejections():
     twa = _twa()
-    with pytest.raises(twa.TWAError) as e:
-        twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="bf16x3", ws_route="fft", integrator="midpoint")
-    assert e.value.name == "TWA_EUNSUPPORTED"
     with pytest.raises(twa.TWAError) as e:
         twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, integrator=2)
     assert e.value.name == "TWA_EINVAL"
@@ -135,6 +156,3 @@ def test_rejections():
         with pytest.raises(twa.TWAError) as e:
             g.grad("SpSm", 8, 4)
         assert e.value.name == "TWA_EUNSUPPORTED"
-    with pytest.raises(twa.TWAError) as e:
-        twa.batch_run([dict(N=32, alpha=1.0, w=4.0, Gamma=1.0, dt=1e-3, steps=4)], 8, integrator="midpoint")
-    assert e.value.name == "TWA_EUNSUPPORTED"
