@@ -1674,29 +1674,34 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     const bool tf32 = t->kc == 2;   // FP32 containers; no lo image in the TF32 mode
     const bool with_lo = !(tf32 && t->terms == 1);
     const size_t ni = (size_t)(tf32 ? 4 : 2) * K * ldk;
-    TWA_CUDA(c, dev_malloc_async(c, &hi, ni, c->stream));
-    if (with_lo) TWA_CUDA(c, dev_malloc_async(c, &lo, ni, c->stream));
-    TWA_CUDA(c, dev_malloc_async(c, &out, sizeof(float) * K * N, c->stream));
-    TWA_CUDA(c, cudaMemsetAsync(hi, 0, ni, c->stream));
-    if (with_lo) TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
-    k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo, tf32);
-    TcMaps fm{};
-    fm.a0 = t->tmWhi;
-    fm.a1 = t->tmWlo;
-    int rc;
-    if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &fm.b1, with_lo ? lo : hi, K, N, ldk, t->bn, t->kc))) return rc;
-    TcArgs fa = base_args(c);
-    fa.n_vec = K;
-    fa.field_out = out;
-    rc = (t->terms == 3) ? launch_cfg<MODE_FIELD, 3>(c, fm, fa) : launch_cfg<MODE_FIELD, 1>(c, fm, fa);
-    if (rc) return rc;
-    k_widen<<<nblk(K * N, 256), 256, 0, c->stream>>>(out, P, K * N);
+    // scratch of this call, released (stream-ordered) on every exit below
+    auto run = [&]() -> int {
+        TWA_CUDA(c, dev_malloc_async(c, &hi, ni, c->stream));
+        if (with_lo) TWA_CUDA(c, dev_malloc_async(c, &lo, ni, c->stream));
+        TWA_CUDA(c, dev_malloc_async(c, &out, sizeof(float) * K * N, c->stream));
+        TWA_CUDA(c, cudaMemsetAsync(hi, 0, ni, c->stream));
+        if (with_lo) TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
+        k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo, tf32);
+        TcMaps fm{};
+        fm.a0 = t->tmWhi;
+        fm.a1 = t->tmWlo;
+        int rc;
+        if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, t->bn, t->kc))) return rc;
+        if ((rc = make_map(c, &fm.b1, with_lo ? lo : hi, K, N, ldk, t->bn, t->kc))) return rc;
+        TcArgs fa = base_args(c);
+        fa.n_vec = K;
+        fa.field_out = out;
+        rc = (t->terms == 3) ? launch_cfg<MODE_FIELD, 3>(c, fm, fa) : launch_cfg<MODE_FIELD, 1>(c, fm, fa);
+        if (rc) return rc;
+        k_widen<<<nblk(K * N, 256), 256, 0, c->stream>>>(out, P, K * N);
+        TWA_CUDA(c, cudaGetLastError());
+        return TWA_OK;
+    };
+    const int rc = run();
     dev_free_async(c, hi, c->stream);
     dev_free_async(c, lo, c->stream);
     dev_free_async(c, out, c->stream);
-    TWA_CUDA(c, cudaGetLastError());
-    return TWA_OK;
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
