@@ -78,6 +78,15 @@ def test_init_rejects_bad_options():
         twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=7)
     assert e.value.code == -1
     with pytest.raises(twa.TWAError) as e:
+        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=5)          # one past TWA_PREC_FP32
+    assert e.value.code == -1 and "precision" in str(e.value)
+    with pytest.raises(twa.TWAError) as e:
+        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, integrator=2)
+    assert e.value.code == -1 and "integrator" in str(e.value)
+    with pytest.raises(twa.TWAError) as e:
+        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, integrator=-1)
+    assert e.value.code == -1
+    with pytest.raises(twa.TWAError) as e:
         twa.TWA(4, 1.0, 1.0, 1.0, 0.1, init_state=0)
     assert e.value.code == -1
     with pytest.raises(twa.TWAError) as e:
@@ -90,6 +99,23 @@ def test_init_rejects_bad_options():
     with pytest.raises(twa.TWAError) as e:
         twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision="bf16x3", noise_route="circulant")
     assert e.value.name == "TWA_EUNSUPPORTED"
+
+
+def test_precision_and_integrator_constants_match_the_header():
+    # the binding's names are the header's values
+    import re
+    hdr = open(os.path.join(os.path.dirname(twa.LIB_PATH), "..", "include", "twa.h")).read()
+    val = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (TWA_\w+)\s+(-?\d+)", hdr)}
+    assert twa.PRECISION == {"fp64": val["TWA_PREC_FP64"], "bf16": val["TWA_PREC_BF16"],
+                             "bf16x3": val["TWA_PREC_BF16X3"], "tf32": val["TWA_PREC_TF32"],
+                             "fp32": val["TWA_PREC_FP32"]}
+    assert twa.INTEGRATOR == {"heun": val["TWA_INT_HEUN"], "midpoint": val["TWA_INT_MIDPOINT"]}
+    import ctypes
+    o = twa.Opts()
+    ctypes.memset(ctypes.byref(o), 0xFF, ctypes.sizeof(o))   # the defaults overwrite every byte
+    twa.lib().twa_opts_default(ctypes.byref(o))
+    assert o.integrator == val["TWA_INT_HEUN"] and o.precision == val["TWA_PREC_FP64"]
+    assert o.sample_stride == 1 and not o.alloc and not o.free
 
 
 def test_null_context_calls_are_rejected():
