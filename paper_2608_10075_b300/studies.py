@@ -2,6 +2,7 @@
 
     python -m paper_2608_10075_b300.studies precision [--M-ref 512] [--steps S]
     python -m paper_2608_10075_b300.studies gradients [--M 2048] [--steps S]
+    python -m paper_2608_10075_b300.studies phase [--Ns 100] [--alphas 0.5 1 2] [--T 5]
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
@@ -11,6 +12,13 @@ each observable is reported with its standard error and, per mixed path, the
 paired difference to FP64 (mean over trajectories of the per-trajectory
 difference, and its standard error), which isolates the arithmetic error from
 the sampling noise.
+
+phase: the phase-diagram workflow on the batched scan. For every (N, alpha) the
+pump prefactor is set from a target w~ = w_max / (Gamma N) (main text, "Observables
+and method"): one calibration batch at w = 1 gives each point's w_max, which is
+linear in w, so w = w~ Gamma N / w_max(w = 1). Ten w~ per (N, alpha), log-spaced,
+run as one batch; each (N, alpha) reports g2(w~), <S+S->/N and the minimum of g2
+with the w~ where it falls.
 
 gradients: N = 1024, alpha = 1, w = N Gamma / 4, dt = 1e-4, T = 2, window
 (1, 2], checkpoints every 64 steps. twa_grad (BF16X3) gives d<S+S->/dw,
@@ -180,6 +188,62 @@ def scan_study(args):
     print(json.dumps(line), flush=True)
 
 
+def phase_grid(Ns, alphas, wts, T, window, dt_scale, w_max_unit):
+    """Points of the phase scan: w = w~ Gamma N / w_max(w = 1) for each target w~,
+    dt = dt_scale / (Gamma N), T / dt steps, averaging over the last `window`."""
+    pts = []
+    for N in Ns:
+        dt = dt_scale / N
+        steps = max(1, int(round(T / dt)))
+        for a in alphas:
+            for wt in wts:
+                pts.append(dict(N=N, alpha=a, w=wt * N / w_max_unit[(N, a)], Gamma=1.0, dt=dt, steps=steps,
+                                window_start=max(0.0, steps * dt - window), wt=wt))
+    return pts
+
+
+def phase_lines(pts, res):
+    """One summary per (N, alpha): the g2 and <S+S->/N curves over w~ and the
+    minimum of g2."""
+    out = {}
+    for p, r in zip(pts, res):
+        d = out.setdefault((p["N"], p["alpha"]), {"study": "phase", "N": p["N"], "alpha": p["alpha"], "wt": [],
+                                                  "wt_lib": [], "g2": [], "g2_se": [], "SpSm_over_N": [],
+                                                  "sigma_z": [], "stability": []})
+        d["wt"].append(p["wt"])
+        d["wt_lib"].append(r["w_tilde"])
+        d["g2"].append(r["g2"])
+        d["g2_se"].append(r["g2_se"])
+        d["SpSm_over_N"].append(r["SpSm"] / p["N"])
+        d["sigma_z"].append(r["sigma_z"])
+        d["stability"].append(r["stability"])
+    for d in out.values():
+        k = min(range(len(d["g2"])), key=lambda j: d["g2"][j])
+        d["g2_min"], d["g2_min_se"], d["wt_at_min"] = d["g2"][k], d["g2_se"][k], d["wt"][k]
+        # superradiant: <S+S-> above N, the independent-emitter value
+        d["superradiant_wt"] = [wt for wt, x in zip(d["wt"], d["SpSm_over_N"]) if x > 1.0]
+    return list(out.values())
+
+
+def phase_study(args, runner=None):
+    runner = runner or twa.batch_run
+    Ns, alphas = args.Ns, args.alphas
+    wts = list(np.logspace(math.log10(args.wt_min), math.log10(args.wt_max), args.n_wt))
+    cal = [dict(N=N, alpha=a, w=1.0, Gamma=1.0, dt=args.dt_scale / N, steps=1, window_start=0.0)
+           for N in Ns for a in alphas]
+    res, _ = runner(cal, 8, seed=0, precision=args.precision)
+    w_max_unit = {(p["N"], p["alpha"]): r["w_max"] for p, r in zip(cal, res)}
+    pts = phase_grid(Ns, alphas, wts, args.T, args.window, args.dt_scale, w_max_unit)
+    t = time.perf_counter()
+    res, tiles = runner([{k: v for k, v in p.items() if k != "wt"} for p in pts], args.M, seed=0,
+                        precision=args.precision)
+    secs = time.perf_counter() - t
+    for d in phase_lines(pts, res):
+        d.update(M=args.M, T=args.T, window=args.window, dt=args.dt_scale / d["N"], precision=args.precision,
+                 batch_seconds=secs, points_in_batch=len(pts), tiles=list(tiles))
+        print(json.dumps(d), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -192,12 +256,25 @@ def main():
     p.add_argument("--M-full", type=int, default=MIXED_N1024["M"])
     p.add_argument("--steps", type=int, default=0)
     p.add_argument("--alphas", type=float, nargs="*", default=None, help="a subset of the study's exponents")
+    f = sub.add_parser("phase")
+    f.add_argument("--Ns", type=int, nargs="+", default=[100])
+    f.add_argument("--alphas", type=float, nargs="+", default=[0.5, 1.0, 2.0])
+    f.add_argument("--n-wt", type=int, default=10)
+    f.add_argument("--wt-min", type=float, default=0.1)
+    f.add_argument("--wt-max", type=float, default=10.0)
+    f.add_argument("--M", type=int, default=256)
+    f.add_argument("--T", type=float, default=5.0, help="horizon in 1/Gamma")
+    f.add_argument("--window", type=float, default=2.5, help="averaging window at the end of the run, 1/Gamma")
+    f.add_argument("--dt-scale", type=float, default=0.02, help="dt = dt_scale / (Gamma N)")
+    f.add_argument("--precision", default="bf16x3")
     q = sub.add_parser("gradients")
     q.add_argument("--M", type=int, default=ADJOINT_N1024["M"])
     q.add_argument("--steps", type=int, default=0)
     a = ap.parse_args()
     if a.cmd == "precision":
         precision_study(a)
+    elif a.cmd == "phase":
+        phase_study(a)
     elif a.cmd == "scan":
         scan_study(a)
     else:
