@@ -2,7 +2,7 @@
 
     python -m paper_2608_10075_b300.studies precision [--M-ref 512] [--steps S]
     python -m paper_2608_10075_b300.studies gradients [--M 2048] [--steps S]
-    python -m paper_2608_10075_b300.studies phase [--Ns 100] [--alphas 0.5 1 2] [--T 5]
+    python -m paper_2608_10075_b300.studies phase [--Ns 100] [--alphas 0.5 1 2] [--T 15]
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
@@ -16,9 +16,11 @@ the sampling noise.
 phase: the phase-diagram workflow on the batched scan. For every (N, alpha) the
 pump prefactor is set from a target w~ = w_max / (Gamma N) (main text, "Observables
 and method"): one calibration batch at w = 1 gives each point's w_max, which is
-linear in w, so w = w~ Gamma N / w_max(w = 1). Ten w~ per (N, alpha), log-spaced,
-run as one batch; each (N, alpha) reports g2(w~), <S+S->/N and the minimum of g2
-with the w~ where it falls.
+linear in w, so w = w~ Gamma N / w_max(w = 1). By default the g2_min protocol of
+the main text: ten equally spaced w~ in [1/10, 1] per (N, alpha), a preparation
+time of 10 / Gamma and an average over the following 5 / Gamma, all points run as
+one batch; each (N, alpha) reports g2(w~), <S+S->/N and the minimum of g2 with the
+w~ where it falls (--spacing log and a wider range show the thermal side too).
 
 gradients: N = 1024, alpha = 1, w = N Gamma / 4, dt = 1e-4, T = 2, window
 (1, 2], checkpoints every 64 steps. twa_grad (BF16X3) gives d<S+S->/dw,
@@ -228,7 +230,10 @@ def phase_lines(pts, res):
 def phase_study(args, runner=None):
     runner = runner or twa.batch_run
     Ns, alphas = args.Ns, args.alphas
-    wts = list(np.logspace(math.log10(args.wt_min), math.log10(args.wt_max), args.n_wt))
+    if args.spacing == "log":
+        wts = list(np.logspace(math.log10(args.wt_min), math.log10(args.wt_max), args.n_wt))
+    else:
+        wts = list(np.linspace(args.wt_min, args.wt_max, args.n_wt))
     cal = [dict(N=N, alpha=a, w=1.0, Gamma=1.0, dt=args.dt_scale / N, steps=1, window_start=0.0)
            for N in Ns for a in alphas]
     res, _ = runner(cal, 8, seed=0, precision=args.precision)
@@ -261,10 +266,11 @@ def main():
     f.add_argument("--alphas", type=float, nargs="+", default=[0.5, 1.0, 2.0])
     f.add_argument("--n-wt", type=int, default=10)
     f.add_argument("--wt-min", type=float, default=0.1)
-    f.add_argument("--wt-max", type=float, default=10.0)
+    f.add_argument("--wt-max", type=float, default=1.0)
+    f.add_argument("--spacing", choices=["linear", "log"], default="linear")
     f.add_argument("--M", type=int, default=256)
-    f.add_argument("--T", type=float, default=5.0, help="horizon in 1/Gamma")
-    f.add_argument("--window", type=float, default=2.5, help="averaging window at the end of the run, 1/Gamma")
+    f.add_argument("--T", type=float, default=15.0, help="horizon in 1/Gamma")
+    f.add_argument("--window", type=float, default=5.0, help="averaging window at the end of the run, 1/Gamma")
     f.add_argument("--dt-scale", type=float, default=0.02, help="dt = dt_scale / (Gamma N)")
     f.add_argument("--precision", default="bf16x3")
     q = sub.add_parser("gradients")

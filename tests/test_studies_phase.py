@@ -25,7 +25,7 @@ def _fake_runner(calls):
 
 def test_phase_study_sets_w_from_the_target_and_finds_the_minimum(capsys):
     args = argparse.Namespace(Ns=[100, 300], alphas=[0.5, 1.0], n_wt=21, wt_min=0.1, wt_max=10.0, M=64, T=1.0,
-                              window=0.5, dt_scale=0.02, precision="bf16x3")
+                              window=0.5, dt_scale=0.02, precision="bf16x3", spacing="log")
     calls = []
     studies.phase_study(args, runner=_fake_runner(calls))
     cal, grid = calls[0][0], calls[1][0]
@@ -41,3 +41,14 @@ def test_phase_study_sets_w_from_the_target_and_finds_the_minimum(capsys):
         j = int(np.argmin([(math.log10(w) - 0.3 * d["alpha"]) ** 2 for w in wts]))
         assert d["wt_at_min"] == d["wt"][j] and d["g2_min"] == min(d["g2"])
         assert d["superradiant_wt"] == [w for w in d["wt"] if 2.0 * w > 1.0]
+
+
+def test_phase_study_default_protocol_is_ten_equally_spaced_values(capsys):
+    # ten equally spaced w~ in [1/10, 1]
+    args = argparse.Namespace(Ns=[100], alphas=[0.7], n_wt=10, wt_min=0.1, wt_max=1.0, M=8, T=15.0, window=5.0,
+                              dt_scale=0.02, precision="bf16x3", spacing="linear")
+    calls = []
+    studies.phase_study(args, runner=_fake_runner(calls))
+    d = __import__("json").loads(capsys.readouterr().out.strip())
+    assert np.allclose(d["wt"], np.arange(1, 11) / 10.0, rtol=1e-12)
+    assert all(abs(p["window_start"] - 10.0) < 1e-9 for p in calls[1][0])
