@@ -82,55 +82,70 @@ def recorded_traffic(kernel_file, summary):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms, from before
+    the warm-up to the end of the run; mark() notes the sample index at a point
+    of the run and stats(a, b) summarises the samples between two marks."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, interval_ms=50):
         self.idx = device_index
+        self.interval = interval_ms
         self.proc = None
         self.lines = []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, ValueError):
             self.proc = None
+        return self
 
     def _read(self):
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
 
+    def mark(self):
+        # let the sampler catch up with the work just finished
+        time.sleep(2.5 * self.interval / 1000.0)
+        return len(self.lines)
+
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+
+    def stats(self, a=0, b=None):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm, smax, power, reasons = [], [], [], set()
+        for ln in self.lines[a:b]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
             try:
                 sm.append(float(f[1]))
                 smax.append(float(f[2]))
+                power.append(float(f[3]))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
+            for n, v in zip(self.NAMES, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm),
+                "interval_ms": self.interval}
 
 
 def contraction_flops(N, M, terms_w=3, terms_l=2):
@@ -200,8 +215,53 @@ def run_reference(args, rank, world):
     return 0
 
 
-def run_ours(args, rank, world, dist):
+def algorithmic_flops(N, M, lib_flops, launches, terms_w, terms_l):
+    """Algorithmic contraction FLOPs of the predictor or corrector launches:
+    one W.s (2 N^2 per column, 2M columns) each plus their share of the L.eta
+    tiles of the next step, counted once (no split-precision multiplier). The
+    library reports executed products (terms_w per W entry, terms_l per L
+    entry); the L.eta share is what remains after the W part."""
+    w_exec = 2.0 * N * N * 2 * M * terms_w * launches
+    l_exec = lib_flops - w_exec
+    return 2.0 * N * N * 2 * M * launches + l_exec / terms_l
+
+
+def precision_check(twa, stream, rank, M_sub=128, steps=200):
+    """The metric's qualifier on a subset of the ensemble: BF16X3 and the FP64
+    GPU path on the same trajectories and seeds, `steps` steps, window over the
+    second half; unpaired differences in units of the combined standard error,
+    and the paired per-trajectory difference with its standard error."""
+    import math
+
     import numpy as np
+    N = CFG["N"]
+    t0 = (steps // 2) * CFG["dt"]
+    obs, smp = {}, {}
+    for prec in (CFG["precision"], "fp64"):
+        with twa.TWA(N, CFG["alpha"], CFG["w"], CFG["Gamma"], CFG["dt"], seed=0, precision=prec, stream=stream,
+                     traj_offset=rank * CFG["M"], window_start=t0) as g:
+            g.run(M_sub, steps)
+            obs[prec] = g.observables()
+            Sz, A, A2, ASz, Sz2 = g.moments().T
+            smp[prec] = {"Sz": Sz, "SpSm": A + 0.5 * Sz, "G2num": A2 + 2 * ASz - Sz / 3 + 0.5 * Sz2 - 4.0 / 3.0 * A}
+    a, b = obs[CFG["precision"]], obs["fp64"]
+    out = {"trajectories": M_sub, "steps": steps, "window_steps": steps - steps // 2, "observables": {}}
+    worst = 0.0
+    for k in ("Sz", "SpSm", "G2num", "g2"):
+        se = math.hypot(a[k + "_se"], b[k + "_se"])
+        r = {"mixed": a[k], "fp64": b[k], "diff_in_se": (a[k] - b[k]) / se}
+        if k in smp["fp64"]:
+            d = smp[CFG["precision"]][k] - smp["fp64"][k]
+            r["paired_diff"] = float(np.mean(d))
+            r["paired_se"] = float(np.std(d, ddof=1) / math.sqrt(M_sub))
+        worst = max(worst, abs(r["diff_in_se"]))
+        out["observables"][k] = r
+    out["max_abs_diff_in_se"] = worst
+    out["within_3se"] = worst <= 3.0
+    return out
+
+
+def run_ours(args, rank, world, dist):
     import torch
 
     from paper_2608_10075_b300 import twa
@@ -211,6 +271,7 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     N, M = CFG["N"], CFG["M"]
     K, Wm = args.steps, args.warmup
+    clocks = ClockSampler(local).start()
     ctx = twa.TWA(N, CFG["alpha"], CFG["w"], CFG["Gamma"], CFG["dt"], seed=0, precision=CFG["precision"],
                   window_start=0.0, stream=stream, traj_offset=rank * M)
     ctx.run(M, 0)
@@ -222,10 +283,9 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
 
     # ---- timed region: K steps, device-resident inputs ----
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier()
     torch.cuda.synchronize()
+    c0 = clocks.mark()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -234,7 +294,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
+    c1 = clocks.mark()
     ctx.sync()
     if dist is not None:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -242,31 +302,40 @@ def run_ours(args, rank, world, dist):
         ms = float(t.item())
     value = N * M * world * K / (ms * 1e-3)
 
-    # ---- per-kernel times on the launching stream (separate pass) ----
-    kp = min(K, 50)
+    # ---- per-kernel times on the launching stream (separate pass, same K) ----
+    kp = max(K, 20)
+    c2 = clocks.mark()
     ctx.profile(True)
     ctx.run(M, kp)
     prof = ctx.profile_read()
     ctx.profile(False)
+    c3 = clocks.mark()
     step_kernel_ms = sum(v[0] for v in prof.values()) / max(kp, 1)
-    terms_w = 3 if CFG["precision"] == "bf16x3" else 1
-    terms_l = 2 if CFG["precision"] == "bf16x3" else 1
+    terms_w = {"bf16x3": 3, "fp32": 3}.get(CFG["precision"], 1)
+    terms_l = {"bf16x3": 2, "fp32": 3}.get(CFG["precision"], 1)
     flops = contraction_flops(N, M, terms_w, terms_l)
-    # the library reports the algorithmic FLOPs of each launch it timed: the
+    # the library reports the executed FLOPs of each launch it timed: the
     # predictor and corrector launches of step t also carry L.eta tiles of t + 1
     lib_flops = sum(prof[k][2] for k in flops)
-    # predictor + corrector launches: W twice per step, plus the L.eta tiles when
-    # they ride along (mixed launches); standalone L.eta launches: L once each
     in_mixed = prof["predict"][2] + prof["correct"][2] - kp * (flops["predict"] + flops["correct"])
     assert min(abs(in_mixed), abs(in_mixed - kp * flops["noise_factor"])) <= 1e-6 * lib_flops, in_mixed
     assert abs(prof["noise_factor"][2] - prof["noise_factor"][1] * flops["noise_factor"]) <= 1e-6 * lib_flops
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     dominant = max((k for k in flops if prof[k][1]), key=lambda k: prof[k][0])
-    d_ms = prof[dominant][0] / max(prof[dominant][1], 1)
-    d_flops = prof[dominant][2] / max(prof[dominant][1], 1)
-    achieved = d_flops / (d_ms * 1e-3) / 1e12
-    contraction_tflops = lib_flops / (sum(prof[k][0] for k in flops) * 1e-3) / 1e12
+    n_dom = max(prof[dominant][1], 1)
+    d_ms_prof = prof[dominant][0] / n_dom
+    # the dominant kernel's time in the timed region: its share of the step in
+    # the profiled pass applied to the timed step (launch gaps included, so the
+    # per-step kernel times add up to ms_per_step)
+    share = prof[dominant][0] / kp / step_kernel_ms
+    launches_per_step = prof[dominant][1] / kp
+    d_ms = (ms / K) * share / launches_per_step
+    d_exec = prof[dominant][2] / n_dom
+    d_algo = algorithmic_flops(N, M, prof[dominant][2], n_dom, terms_w, terms_l) / n_dom
+    achieved = d_algo / (d_ms * 1e-3) / 1e12
+    executed_tflops = d_exec / (d_ms * 1e-3) / 1e12
+    step_algo = (2 * 2.0 * N * N * 2 * M + 2.0 * N * (N + 1) / 2.0 * 2 * M)   # W.s twice + L.eta once
     traffic = recorded_traffic("twa_tc.cu", "tc_mix_%s_n10000.md" % dominant)
     kernel_name = {"predict": "k_tc<MIX> (W.s + Heun predictor, with L.eta tiles of step t+1)",
                    "correct": "k_tc<MIX> (W.s~ + Heun corrector, with L.eta tiles of step t+1)",
@@ -281,7 +350,7 @@ def run_ours(args, rank, world, dist):
     t0 = time.perf_counter()
     ctx.set_state(*(x.numpy() for x in xs))          # host -> device, pinned
     ctx.run(M, K)
-    mom = ctx.moments()                               # device -> host
+    ctx.moments()                                     # device -> host
     obs = ctx.observables()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
@@ -293,6 +362,22 @@ def run_ours(args, rank, world, dist):
     h2d = 3 * 8 * M * N
     d2h = mom_bytes + 160
 
+    # ---- sustained: a seconds-long block of steps under the power limit ----
+    sustained = None
+    if not args.no_side:
+        ks = args.sustained_steps
+        c4 = clocks.mark()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ctx.run(M, ks)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        s_ms = a0.elapsed_time(a1)
+        c5 = clocks.mark()
+        sustained = {"value": N * M * world * ks / (s_ms * 1e-3), "ms_per_step": s_ms / ks, "steps": ks,
+                     "seconds": s_ms * 1e-3, "clocks": clocks.stats(c4, c5),
+                     "all_contractions_algorithmic_tflops": step_algo / (s_ms / ks * 1e-3) / 1e12}
     ctx.close()
 
     # ---- beside the dense route: the FFT route and the plain FP64 GPU path ----
@@ -334,6 +419,10 @@ def run_ours(args, rank, world, dist):
         side["dense_midpoint"]["speedup_vs_main"] = side["dense_midpoint"]["value"] / value
         side["fp64_gpu"] = side_run("fp64", "dense", 2, 1)
         side["fp64_gpu"]["mixed_speedup"] = value / side["fp64_gpu"]["value"]
+    qualifier = None
+    if not args.no_precision_check:
+        qualifier = precision_check(twa, stream, rank)
+    clocks.stop()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -346,24 +435,31 @@ def run_ours(args, rank, world, dist):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3", "data": "synthetic",
+            "dtype": CFG["precision"], "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "M_per_gpu": M, "alpha": CFG["alpha"], "w": CFG["w"],
                        "Gamma": CFG["Gamma"], "dt": CFG["dt"], "precision": CFG["precision"],
                        "parallelism": "trajectory shards, no data-path collective" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2: W and L BF16 hi+lo images 600 MB, state 0.9 GB"},
+                       "l2": "inputs larger than L2: W and L BF16 hi+lo images 800 MB, state 0.9 GB"},
             "roofline": {"bound": "tensor", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s bf16_tflops_sustained" % peak_src,
-                         "kernel_ms": d_ms, "flops_per_launch": d_flops,
-                         "all_contractions_tflops": contraction_tflops,
-                         "all_contractions_frac": contraction_tflops / peak,
-                         "kernel_ms_per_step": {k: v[0] / max(kp, 1) for k, v in prof.items() if v[1]},
-                         "step_kernel_ms": step_kernel_ms},
+                         "work": "algorithmic: 2 N^2 per column for W.s, 2 per nonzero of L for L.eta, "
+                                 "counted once (no split-precision multiplier)",
+                         "kernel_ms": d_ms, "kernel_ms_profile_pass": d_ms_prof,
+                         "algorithmic_flops_per_launch": d_algo, "executed_flops_per_launch": d_exec,
+                         "tensor_pipe_tflops": executed_tflops, "tensor_pipe_frac": executed_tflops / peak,
+                         "step_algorithmic_tflops": step_algo / (ms / K * 1e-3) / 1e12,
+                         "step_algorithmic_frac": step_algo / (ms / K * 1e-3) / 1e12 / peak,
+                         "kernel_ms_per_step_profile_pass": {k: v[0] / max(kp, 1) for k, v in prof.items() if v[1]},
+                         "step_kernel_ms_profile_pass": step_kernel_ms,
+                         "profile_pass_clocks": clocks.stats(c2, c3)},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                     "note": "set_state from pinned host FP64 buffers, K steps, moments and observables to host"},
             "gpu_launches": 4 * K,   # per step: noise, predictor launch, corrector launch, close
-            "clocks": clk,
+            "clocks": clocks.stats(c0, c1),
+            "sustained": sustained,
+            "precision_check": qualifier,
             "observables": {k: obs[k] for k in ("sigma_z", "SpSm", "g2", "w_tilde", "stability", "nonfinite")},
         }
         line.update(side)
@@ -378,7 +474,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-side", action="store_true", help="skip the FFT-route and FP64-GPU legs")
+    ap.add_argument("--no-side", action="store_true", help="skip the FFT-route, FP64-GPU and sustained legs")
+    ap.add_argument("--no-precision-check", action="store_true",
+                    help="skip the mixed-vs-FP64 comparison on a 128-trajectory subset")
+    ap.add_argument("--sustained-steps", type=int, default=2500,
+                    help="steps of the seconds-long sustained leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -104,7 +104,10 @@ typedef struct twa_opts {
                                t - round(t0 / dt)); default 0                         */
     int    renormalize;     /* 1 (default): rescale every spin to sqrt(3) each step   */
     int    clip_negative;   /* 0 (default): non-positive Cholesky pivot -> TWA_ENOTPSD;
-                               1: zero that column of L and carry on (reported)        */
+                               1: zero that column of L and carry on. This zeroes
+                               pivots during the factorisation; it does not clip
+                               eigenvalues of W. twa_obs reports the count
+                               (clipped) and ||W - L L^T||_F / ||W||_F            */
     void*  stream;          /* cudaStream_t for all work; NULL = default stream       */
     int64_t traj_offset;    /* global index of trajectory 0 in the Philox counter
                                (default 0): shards of one ensemble use disjoint
@@ -195,6 +198,8 @@ typedef struct twa_obs {
     double min_pivot;           /* smallest Cholesky pivot L_ii^2               */
     int64_t clipped;            /* columns of L zeroed by clip_negative         */
     int64_t nonfinite;          /* spin components found non-finite             */
+    double factor_residual;     /* ||W - L L^T||_F / ||W||_F when clip_negative
+                                   zeroed columns (else 0, not computed)        */
 } twa_obs;
 
 /* Fill *opts with the defaults listed above. Returns TWA_EINVAL if opts is NULL. */
@@ -254,6 +259,26 @@ TWA_API int twa_get_moments(twa_ctx* ctx, double* out, int on_device);
  * stream. Errors: TWA_EINVAL (NULL, K < 1). */
 TWA_API int twa_field(twa_ctx* ctx, const double* s, double* P, int64_t K);
 
+/* matrices of twa_contract */
+#define TWA_MAT_W 0         /* the pump matrix w_ij of Eq. 2                     */
+#define TWA_MAT_L 1         /* its noise factor L (L L^T = W, lower triangular)  */
+
+/* The contractions of one step alone, P[k][i] = sum_j A_ij s[k][j] for K caller
+ * vectors (device, [K][N] doubles) into P (device, [K][N] doubles), with A the
+ * pump matrix (TWA_MAT_W: the pump field sum_j w_ij s_j of Eq. S1, the same
+ * result as twa_field) or the noise factor (TWA_MAT_L: the correlated noise
+ * chi = L eta of Sec. S1 before its sqrt(dt) scaling), in the arithmetic the
+ * context's step uses for it:
+ *  - FP64: DFMA (the K range of L stops at the diagonal);
+ *  - BF16X3: W hi/lo against an hi/lo split of s (three products), or L hi/lo
+ *    against s rounded once to BF16 (two products), FP32 accumulation;
+ *  - BF16: one product of BF16 images; TF32: one product of TF32 images;
+ *  - FP32: TF32 hi/lo splits of both operands (three products).
+ * On the FFT route TWA_MAT_W runs the FFT convolution, TWA_MAT_L the dense
+ * tensor-core contraction. Enqueued on the context's stream.
+ * Errors: TWA_EINVAL (NULL, unknown matrix, K < 1). */
+TWA_API int twa_contract(twa_ctx* ctx, int matrix, const double* s, double* P, int64_t K);
+
 /* objectives of twa_grad */
 #define TWA_OBJ_SPSM 0      /* <S+S->, window and ensemble mean, normal ordered */
 #define TWA_OBJ_G2   1      /* g2 = <S+S+S-S-> / <S+S->^2                      */
@@ -309,6 +334,8 @@ typedef struct twa_point {
     double  Gamma, dt;      /* collective decay, time step                         */
     int64_t steps;          /* steps to run from the discrete-Wigner start          */
     double  window_start;   /* averaging window start time (as twa_opts)           */
+    double* means;          /* NULL, or a host array [M][5] that receives the point's
+                               per-trajectory window means (twa_get_moments order) */
 } twa_point;
 
 /* Run many parameter points of uneven N together (e.g. a phase-diagram scan) and return each point's observables in out[0..n-1].
@@ -325,7 +352,8 @@ typedef struct twa_point {
  * longest-first list scheduling), window moments. The step is captured per
  * set of running points and parity of the step index as CUDA graphs and
  * replayed. Points with fewer steps drop out as they finish.
- * The results equal those of running every point alone with twa_run.
+ * The results equal those of running every point alone with twa_run. A point
+ * whose `means` is not NULL also gets its per-trajectory window means there.
  *
  * Tile shapes: unless TWA_TC_BN / TWA_TC_KC are set in the environment, a
  * built-in autotuner times the compiled configurations on a few steps of the
@@ -360,17 +388,32 @@ TWA_API int twa_reduce_moments(const double* means, int64_t M, int64_t N, twa_ob
  * means, the sample count and the results in one file-scope __device__ array of
  * 16 + 5 * TWA_NOALLOC_MAX_M doubles (about 2.6 MB), which every GPU that loads
  * libtwa holds until the process exits.
- *  - The first call on a device looks up that array's device address
- *    (cudaGetSymbolAddress) with the device current; make that first call before
- *    any stream capture. Later calls on the device reuse the address.
- *  - Work runs on the legacy default stream and the call returns once the
- *    results are on the host. It calls no cudaMalloc, cudaFree or other
- *    allocating routine.
+ *  - Every call looks up that array's device address (cudaGetSymbolAddress) in
+ *    the CUDA context current on the calling thread, so it stays right after
+ *    cudaDeviceReset and in a context the caller created. The first call in a
+ *    context also loads the library's device code into it; make that first
+ *    call before any stream capture.
+ *  - Work runs on the legacy default stream with synchronous copies, and the
+ *    call returns once the results are on the host. So each call synchronises
+ *    with every blocking stream of the device, and no call may overlap a
+ *    stream capture in cudaStreamCaptureModeGlobal on any thread (that capture
+ *    would be invalidated, or the call would fail). It calls no cudaMalloc,
+ *    cudaFree or other allocating routine.
  *  - Every call on a device shares the one array and rewrites the count, the
  *    means and the results it uses; calls that overlap on the GPU (from several
  *    host threads) race and must be serialised by the caller.
  * Errors: TWA_EINVAL (NULL, M < 1, N < 1, M > TWA_NOALLOC_MAX_M), TWA_ECUDA. */
 TWA_API int twa_reduce_moments_noalloc(const double* means, int64_t M, int64_t N, twa_obs* out);
+
+/* Check of the device-side timeout path, without any fault (the paper has no
+ * counterpart). Enqueues on the context's stream one bounded wait -- the
+ * routine every tensor-core kernel uses on its shared-memory mbarriers -- on a
+ * barrier that nothing completes, with a limit of limit_us microseconds. The
+ * wait gives up, records a timeout on the context and returns; the next call
+ * that synchronises (twa_sync, twa_observables, ...) returns TWA_ETIMEOUT, as it
+ * would after a real wait ran out. The record stays: such a context should be
+ * destroyed. Errors: TWA_EINVAL (NULL, limit_us outside [1, 10^7]). */
+TWA_API int twa_wait_probe(twa_ctx* ctx, int64_t limit_us);
 
 /* Start (enable = 1) or stop (0) timing every kernel the context launches with
  * a pair of CUDA events recorded on its stream around the launch. Recording

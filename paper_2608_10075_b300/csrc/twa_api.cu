@@ -62,7 +62,8 @@ int set_error(twa_ctx* c, int code, const std::string& msg) {
 }
 
 int cuda_check(twa_ctx* c, cudaError_t e, const char* what) {
-    return set_error(c, TWA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return set_error(c, e == cudaErrorMemoryAllocation ? TWA_ENOMEM : TWA_ECUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 }  // namespace twa
@@ -194,6 +195,7 @@ int twa_opts_default(twa_opts* o) {
 
 int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, double dt, uint64_t seed,
              const twa_opts* opts) {
+    twa::NvtxRange range("twa_init");
     if (!out) return set_error(nullptr, TWA_EINVAL, "twa_init: out is NULL");
     *out = nullptr;
     twa_opts o;
@@ -263,9 +265,15 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         set_error(c, TWA_ECUDA, "twa_init: cudaMemsetAsync failed");
         return fail(TWA_ECUDA);
     }
-    if ((rc = twa::setup_pump(c))) return fail(rc);
-    if (use_tc(c) && (rc = twa::tc_prepare(c))) return fail(rc);
-    if (o.ws_route == TWA_ROUTE_FFT && (rc = twa::fft_prepare(c))) return fail(rc);
+    {
+        twa::NvtxRange r1("twa_init: pump matrix, Cholesky factor, spectrum");
+        if ((rc = twa::setup_pump(c))) return fail(rc);
+    }
+    {
+        twa::NvtxRange r2("twa_init: operand images, FFT plan");
+        if (use_tc(c) && (rc = twa::tc_prepare(c))) return fail(rc);
+        if (o.ws_route == TWA_ROUTE_FFT && (rc = twa::fft_prepare(c))) return fail(rc);
+    }
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         twa::cuda_check(c, e, "twa_init");
@@ -276,6 +284,7 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
 }
 
 int twa_run(twa_ctx* c, int64_t M, int64_t steps) {
+    twa::NvtxRange range("twa_run: step block");
     if (!c) return set_error(nullptr, TWA_EINVAL, "twa_run: ctx is NULL");
     if (M < 1 || M > (int64_t)1 << 30) return set_error(c, TWA_EINVAL, "twa_run: M must be in [1, 2^30]");
     if (steps < 0) return set_error(c, TWA_EINVAL, "twa_run: steps must be >= 0");
@@ -302,6 +311,7 @@ int twa_sync(twa_ctx* c) {
 }
 
 int twa_observables(twa_ctx* c, twa_obs* out) {
+    twa::NvtxRange range("twa_observables: ensemble reduction");
     if (!c || !out) return set_error(c, TWA_EINVAL, "twa_observables: NULL argument");
     if (c->M == 0) return set_error(c, TWA_ESTATE, "twa_observables: no trajectories yet");
     int rc = check_device_flags(c);
@@ -319,6 +329,7 @@ int twa_observables(twa_ctx* c, twa_obs* out) {
     out->stability = fmax(c->Gamma * (double)c->N, c->w_max) * c->dt;
     out->min_pivot = c->min_pivot;
     out->clipped = c->clipped;
+    out->factor_residual = c->factor_residual;
     unsigned long long fl[twa::FLAG_COUNT];
     TWA_CUDA(c, cudaMemcpy(fl, c->d_flags, sizeof(fl), cudaMemcpyDeviceToHost));
     out->nonfinite = (int64_t)fl[twa::FLAG_NONFINITE];
@@ -331,9 +342,11 @@ int twa_get_state(twa_ctx* c, double* sx, double* sy, double* sz, int on_device)
     const int64_t M = c->M, N = c->N;
     const size_t row = sizeof(double) * N;
     if (use_tc(c)) {
-        double *dx = sx, *dy = sy, *dz = sz, *tmp = nullptr;
+        double *dx = sx, *dy = sy, *dz = sz;
+        twa::Scratch<double> tmp_buf(c, c->stream);
         if (!on_device) {
-            TWA_CUDA(c, twa::dev_malloc_async(c, &tmp, 3 * row * M, c->stream));
+            TWA_CUDA(c, tmp_buf.alloc(3 * row * M));
+            double* tmp = tmp_buf.p;
             dx = tmp;
             dy = tmp + M * N;
             dz = tmp + 2 * M * N;
@@ -344,7 +357,6 @@ int twa_get_state(twa_ctx* c, double* sx, double* sy, double* sz, int on_device)
             TWA_CUDA(c, cudaMemcpyAsync(sx, dx, row * M, cudaMemcpyDeviceToHost, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(sy, dy, row * M, cudaMemcpyDeviceToHost, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(sz, dz, row * M, cudaMemcpyDeviceToHost, c->stream));
-            twa::dev_free_async(c, tmp, c->stream);
         }
     } else {
         const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -365,9 +377,10 @@ int twa_set_state(twa_ctx* c, int64_t M, const double* sx, const double* sy, con
     const size_t row = sizeof(double) * N;
     if (use_tc(c)) {
         const double *dx = sx, *dy = sy, *dz = sz;
-        double* tmp = nullptr;
+        twa::Scratch<double> tmp_buf(c, c->stream);
         if (!on_device) {
-            TWA_CUDA(c, twa::dev_malloc_async(c, &tmp, 3 * row * M, c->stream));
+            TWA_CUDA(c, tmp_buf.alloc(3 * row * M));
+            double* tmp = tmp_buf.p;
             TWA_CUDA(c, cudaMemcpyAsync(tmp, sx, row * M, cudaMemcpyHostToDevice, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(tmp + M * N, sy, row * M, cudaMemcpyHostToDevice, c->stream));
             TWA_CUDA(c, cudaMemcpyAsync(tmp + 2 * M * N, sz, row * M, cudaMemcpyHostToDevice, c->stream));
@@ -376,7 +389,6 @@ int twa_set_state(twa_ctx* c, int64_t M, const double* sx, const double* sy, con
             dz = tmp + 2 * M * N;
         }
         rc = twa::tc_set_state(c, dx, dy, dz);
-        twa::dev_free_async(c, tmp, c->stream);
         if (rc) return rc;
     } else {
         const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -398,12 +410,15 @@ int twa_get_moments(twa_ctx* c, double* out, int on_device) {
     if (cnt == 0) return set_error(c, TWA_ESTATE, "twa_get_moments: no step inside the averaging window yet");
     const int64_t n = 5 * c->M;
     double* dst = out;
-    if (!on_device) TWA_CUDA(c, twa::dev_malloc_async(c, &dst, sizeof(double) * n, c->stream));
+    twa::Scratch<double> dst_buf(c, c->stream);
+    if (!on_device) {
+        TWA_CUDA(c, dst_buf.alloc(sizeof(double) * n));
+        dst = dst_buf.p;
+    }
     k_window_means<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->mom, c->d_count, dst, n);
     TWA_CUDA(c, cudaGetLastError());
     if (!on_device) {
         TWA_CUDA(c, cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
-        twa::dev_free_async(c, dst, c->stream);
     }
     return check_device_flags(c);
 }
@@ -414,7 +429,17 @@ int twa_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     return use_tc(c) ? twa::tc_field(c, s, P, K) : twa::f64_field(c, s, P, K);
 }
 
+int twa_contract(twa_ctx* c, int matrix, const double* s, double* P, int64_t K) {
+    if (!c || !s || !P) return set_error(c, TWA_EINVAL, "twa_contract: NULL argument");
+    if (matrix != TWA_MAT_W && matrix != TWA_MAT_L)
+        return set_error(c, TWA_EINVAL, "twa_contract: matrix must be TWA_MAT_W or TWA_MAT_L");
+    if (K < 1 || K > (int64_t)1 << 30) return set_error(c, TWA_EINVAL, "twa_contract: K must be in [1, 2^30]");
+    const int which = matrix == TWA_MAT_L ? 1 : 0;
+    return use_tc(c) ? twa::tc_field(c, s, P, K, which) : twa::f64_field(c, s, P, K, which);
+}
+
 int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_traj) {
+    twa::NvtxRange range("twa_grad: forward with checkpoints, reverse sweep");
     if (!c || !r || !out) return set_error(c, TWA_EINVAL, "twa_grad: NULL argument");
     if (r->objective != TWA_OBJ_SPSM && r->objective != TWA_OBJ_G2)
         return set_error(c, TWA_EINVAL, "twa_grad: unknown objective");
@@ -438,6 +463,7 @@ int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
 }
 
 int twa_reduce_moments(const double* means, int64_t M, int64_t N, twa_obs* out) {
+    twa::NvtxRange range("twa_reduce_moments");
     if (!means || !out || M < 1 || N < 1) return set_error(nullptr, TWA_EINVAL, "twa_reduce_moments: bad argument");
     twa_ctx tmp;
     tmp.N = N;
@@ -462,6 +488,13 @@ int twa_reduce_moments(const double* means, int64_t M, int64_t N, twa_obs* out) 
     tmp.mom = nullptr;
     tmp.d_count = nullptr;
     return rc;
+}
+
+int twa_wait_probe(twa_ctx* c, int64_t limit_us) {
+    if (!c) return set_error(nullptr, TWA_EINVAL, "twa_wait_probe: ctx is NULL");
+    if (limit_us < 1 || limit_us > 10000000)
+        return set_error(c, TWA_EINVAL, "twa_wait_probe: limit_us must be in [1, 10^7]");
+    return twa::wait_probe(c, limit_us * 1000);
 }
 
 int twa_profile(twa_ctx* c, int enable) {

@@ -16,48 +16,81 @@
 namespace {
 
 // Device copy of a context's trajectories and window sums (autotuning trials
-// advance the state; it is put back afterwards).
+// advance the state; it is put back afterwards). The buffers come from the
+// context's allocator and are returned by release() on every path.
 struct Snapshot {
+    twa_ctx* owner = nullptr;
     float *X = nullptr, *Y = nullptr, *Z = nullptr;
     double* mom = nullptr;
     int64_t t = 0, count = 0;
+    bool taken = false;   // the copies completed: restore() may put them back
+
+    void release() {
+        if (owner) {
+            void* p[] = {X, Y, Z, mom};
+            for (void* q : p) twa::dev_free(owner, q);
+        }
+        X = Y = Z = nullptr;
+        mom = nullptr;
+        taken = false;
+    }
+    Snapshot() = default;
+    Snapshot(const Snapshot&) = delete;
+    Snapshot& operator=(const Snapshot&) = delete;
+    ~Snapshot() { release(); }
 };
 
 int snapshot(twa_ctx* c, Snapshot& s) {
+    s.release();
+    s.owner = c;
     const size_t mn = sizeof(float) * c->M * c->N;
     if (twa::dev_malloc(c, &s.X, mn) != cudaSuccess || twa::dev_malloc(c, &s.Y, mn) != cudaSuccess ||
         twa::dev_malloc(c, &s.Z, mn) != cudaSuccess ||
-        twa::dev_malloc(c, &s.mom, sizeof(double) * 5 * c->M) != cudaSuccess)
+        twa::dev_malloc(c, &s.mom, sizeof(double) * 5 * c->M) != cudaSuccess) {
+        s.release();
         return twa::set_error(c, TWA_ENOMEM, "batch autotuner: device allocation of the snapshot");
+    }
     twa::TcState* t = c->tc;
-    TWA_CUDA(c, cudaMemcpyAsync(s.X, t->X, mn, cudaMemcpyDeviceToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(s.Y, t->Y, mn, cudaMemcpyDeviceToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(s.Z, t->Z, mn, cudaMemcpyDeviceToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(s.mom, c->mom, sizeof(double) * 5 * c->M, cudaMemcpyDeviceToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(&s.t, c->d_t, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(&s.count, c->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    TWA_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaError_t e = cudaMemcpyAsync(s.X, t->X, mn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.Y, t->Y, mn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.Z, t->Z, mn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.mom, c->mom, sizeof(double) * 5 * c->M, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&s.t, c->d_t, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&s.count, c->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(c->stream);   // no copy may still write into the buffers freed below
+        s.release();
+        return twa::cuda_check(c, e, "batch autotuner: snapshot copy");
+    }
+    s.taken = true;
     return TWA_OK;
 }
 
+// Put the snapshot back (and release it).
 int restore(twa_ctx* c, Snapshot& s) {
+    if (!s.taken) {
+        s.release();
+        return TWA_OK;
+    }
     const size_t mn = sizeof(float) * c->M * c->N;
     twa::TcState* t = c->tc;
-    TWA_CUDA(c, cudaMemcpyAsync(t->X, s.X, mn, cudaMemcpyDeviceToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(t->Y, s.Y, mn, cudaMemcpyDeviceToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(t->Z, s.Z, mn, cudaMemcpyDeviceToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(c->mom, s.mom, sizeof(double) * 5 * c->M, cudaMemcpyDeviceToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(c->d_t, &s.t, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
-    TWA_CUDA(c, cudaMemcpyAsync(c->d_count, &s.count, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
-    int rc = twa::tc_state_changed(c);   // images and partial sums of the restored state
-    if (rc) return rc;
-    TWA_CUDA(c, cudaStreamSynchronize(c->stream));
-    twa::dev_free(c, s.X);
-    twa::dev_free(c, s.Y);
-    twa::dev_free(c, s.Z);
-    twa::dev_free(c, s.mom);
-    s = Snapshot();
-    return TWA_OK;
+    cudaError_t e = cudaMemcpyAsync(t->X, s.X, mn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->Y, s.Y, mn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->Z, s.Z, mn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->mom, s.mom, sizeof(double) * 5 * c->M, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_t, &s.t, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_count, &s.count, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+    int rc = (e == cudaSuccess) ? twa::tc_state_changed(c)   // images and partial sums of the restored state
+                                : twa::cuda_check(c, e, "batch autotuner: restore copy");
+    const cudaError_t es = cudaStreamSynchronize(c->stream);
+    if (!rc && es != cudaSuccess) rc = twa::cuda_check(c, es, "batch autotuner: restore");
+    s.release();
+    return rc;
 }
 
 int set_tiles_all(std::vector<twa_ctx*>& ctx, int bn, int kc) {
@@ -92,30 +125,42 @@ int time_batch(std::vector<twa_ctx*>& ctx, int steps, float* ms) {
     return rc;
 }
 
-// Pick the fastest compiled tile configuration for this batch.
+// Pick the fastest compiled tile configuration for this batch. Every context is
+// put back to its snapshot before returning, also when a trial fails.
 int autotune(std::vector<twa_ctx*>& ctx, int* bn, int* kc) {
     const int cand[][2] = {{256, 1}, {192, 1}, {256, 0}, {128, 1}};
     std::vector<Snapshot> snap(ctx.size());
+    const int bn0 = *bn, kc0 = *kc;
+    auto put_back = [&](int rc) {
+        // restore what was snapshotted (a failed trial leaves the state advanced)
+        for (size_t p = 0; p < ctx.size(); ++p) {
+            const int r = restore(ctx[p], snap[p]);
+            if (!rc) rc = r;
+        }
+        return rc;
+    };
     for (size_t p = 0; p < ctx.size(); ++p) {
         int rc = snapshot(ctx[p], snap[p]);
-        if (rc) return rc;
+        if (rc) return put_back(rc);
     }
     float best = INFINITY;
     for (auto& cd : cand) {
         int rc = set_tiles_all(ctx, cd[0], cd[1]);
-        if (rc) return rc;
         float ms = 0.f;
-        if ((rc = time_batch(ctx, 5, &ms))) return rc;
+        if (!rc) rc = time_batch(ctx, 5, &ms);
+        if (rc) {
+            // back to the configuration the contexts had before the trials
+            set_tiles_all(ctx, bn0, kc0);
+            return put_back(rc);
+        }
         if (ms < best) {
             best = ms;
             *bn = cd[0];
             *kc = cd[1];
         }
     }
-    for (size_t p = 0; p < ctx.size(); ++p) {
-        int rc = restore(ctx[p], snap[p]);
-        if (rc) return rc;
-    }
+    const int rc = put_back(TWA_OK);
+    if (rc) return rc;
     return set_tiles_all(ctx, *bn, *kc);
 }
 
@@ -173,6 +218,7 @@ int run_stage(std::vector<twa_ctx*>& active, int64_t t0, int64_t reps, cudaStrea
 extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,
                              twa_obs* out, int* tiles) {
     using twa::set_error;
+    twa::NvtxRange range("twa_batch_run");
     if (!pts || !out || n < 1 || n > 65536) return set_error(nullptr, TWA_EINVAL, "twa_batch_run: bad points or n");
     if (M < 1 || M > (int64_t)1 << 30) return set_error(nullptr, TWA_EINVAL, "twa_batch_run: M must be in [1, 2^30]");
     twa_opts o;
@@ -308,7 +354,8 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
     cudaStreamDestroy(cap);
     for (int p = 0; p < n; ++p) {
         ctx[p]->steps = pts[p].steps;
-        if ((rc = twa_observables(ctx[p], &out[p]))) {
+        if ((rc = twa_observables(ctx[p], &out[p])) ||
+            (pts[p].means && (rc = twa_get_moments(ctx[p], pts[p].means, 0)))) {
             set_error(nullptr, rc, ctx[p]->err);
             return cleanup(rc);
         }

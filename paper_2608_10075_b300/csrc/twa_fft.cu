@@ -621,13 +621,14 @@ int fft_prepare(twa_ctx* c) {
     while (v % 2 == 0) { f->radix[f->nst++] = 2; v /= 2; }
     while (v % 3 == 0) { f->radix[f->nst++] = 3; v /= 3; }
     while (v % 5 == 0) { f->radix[f->nst++] = 5; v /= 5; }
-    double* cseq = nullptr;
+    Scratch<double> cseq_buf(c, c->stream);
     if (dev_malloc(c, &f->lam, sizeof(float) * P) != cudaSuccess ||
         dev_malloc(c, &f->tw, sizeof(float2) * P) != cudaSuccess ||
         dev_malloc(c, &f->nscale, sizeof(float) * P) != cudaSuccess ||
         dev_malloc(c, &f->nfreq, sizeof(int32_t) * P) != cudaSuccess ||
-        dev_malloc_async(c, &cseq, sizeof(double) * (P / 2 + 1), c->stream) != cudaSuccess)
+        cseq_buf.alloc(sizeof(double) * (P / 2 + 1)) != cudaSuccess)
         return set_error(c, TWA_ENOMEM, "device allocation of the FFT plan");
+    double* cseq = cseq_buf.p;
     RadixPlan rp{};
     rp.nst = f->nst;
     for (int s = 0; s < f->nst; ++s) rp.radix[s] = f->radix[s];
@@ -636,7 +637,6 @@ int fft_prepare(twa_ctx* c) {
     k_fft_sequence<<<(unsigned)((P / 2 + 256) / 256), 256, 0, c->stream>>>(cseq, P, c->alpha, c->w);
     k_fft_lambda<<<g, 256, 0, c->stream>>>(f->lam, f->nscale, f->nfreq, cseq, P, rp);
     TWA_CUDA(c, cudaGetLastError());
-    dev_free_async(c, cseq, c->stream);
     int rc;
     if ((rc = set_smem(c, (const void*)k_fft_pred)) || (rc = set_smem(c, (const void*)k_fft_corr)) ||
         (rc = set_smem(c, (const void*)k_fft_field)) || (rc = set_smem(c, (const void*)k_fft_noise)))

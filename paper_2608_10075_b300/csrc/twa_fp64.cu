@@ -412,8 +412,10 @@ int f64_run(twa_ctx* c, int64_t steps) {
     return TWA_OK;
 }
 
-int f64_field(twa_ctx* c, const double* s, double* P, int64_t K) {
-    gemm_f64(c->W64, c->N, s, c->N, P, c->N, c->N, K, c->N, 1.0, 0.0, false, false, c->stream);
+int f64_field(twa_ctx* c, const double* s, double* P, int64_t K, int which) {
+    // L is lower triangular: the K range of each row tile stops at its end
+    gemm_f64(which == 1 ? c->L64 : c->W64, c->N, s, c->N, P, c->N, c->N, K, c->N, 1.0, 0.0, which == 1, false,
+             c->stream);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }

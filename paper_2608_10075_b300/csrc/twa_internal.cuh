@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <vector>
 
@@ -94,6 +96,7 @@ struct twa_ctx {
     double* L64 = nullptr;
     double w_max = 0, w_min = 0, min_pivot = 0;
     int64_t clipped = 0;
+    double factor_residual = 0;   // ||W - L L^T||_F / ||W||_F when columns were clipped, else 0
 
     // run state
     int64_t M = 0;           // 0 until the first run / set_state
@@ -138,6 +141,15 @@ struct twa_ctx {
 };
 
 namespace twa {
+// NVTX range over one phase of a call (set-up, factor, step block, reduction,
+// reverse sweep), for timeline tools; costs nothing when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Brackets one launch with CUDA events on the context's stream when profiling.
 struct ProfScope {
     twa_ctx* c;
@@ -264,6 +276,20 @@ cudaError_t dev_malloc_async(twa_ctx* c, T** p, size_t bytes, cudaStream_t st) {
     return dev_malloc_async(c, reinterpret_cast<void**>(p), bytes, st);
 }
 
+// Scratch buffer of one call, released in stream order on `st` when the scope
+// ends, on the error paths too.
+template <class T>
+struct Scratch {
+    twa_ctx* c;
+    cudaStream_t st;
+    T* p = nullptr;
+    Scratch(twa_ctx* ctx, cudaStream_t s) : c(ctx), st(s) {}
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    cudaError_t alloc(size_t bytes) { return dev_malloc_async(c, &p, bytes, st); }
+    ~Scratch() { dev_free_async(c, p, st); }
+};
+
 // ---------------------------------------------------------------------------
 // host launchers
 // twa_setup.cu
@@ -274,7 +300,8 @@ void f64_free(twa_ctx* c);
 int f64_init_state(twa_ctx* c);
 int f64_run(twa_ctx* c, int64_t steps);
 int f64_state_changed(twa_ctx* c);               // recompute sums after set_state
-int f64_field(twa_ctx* c, const double* s, double* P, int64_t K);
+// which: 0 = W (the pump field), 1 = L (the noise factor)
+int f64_field(twa_ctx* c, const double* s, double* P, int64_t K, int which = 0);
 void gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
               int64_t n_i, int64_t n_n, int64_t K, double alpha, double beta, bool tri_a, bool lower_only,
               cudaStream_t st);
@@ -294,7 +321,7 @@ void tc_steps_done(twa_ctx* c, int64_t t_next);
 int tc_state_changed(twa_ctx* c);
 int tc_get_state(twa_ctx* c, double* sx, double* sy, double* sz);   // device buffers
 int tc_set_state(twa_ctx* c, const double* sx, const double* sy, const double* sz);
-int tc_field(twa_ctx* c, const double* s, double* P, int64_t K);
+int tc_field(twa_ctx* c, const double* s, double* P, int64_t K, int which = 0);
 // out[k] = A in[k] for FP32 device vectors [K][N] with BF16X3 (or BF16) tensor-core
 // contractions; which: 0 = W, 1 = L (lower), 2, 3 = the extra matrices below.
 int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t K);
@@ -306,6 +333,7 @@ int tc_batch_prime(twa_ctx* lead, TcBatch* b, int64_t t);   // noise part of the
 int tc_batch_step(twa_ctx* lead, TcBatch* b, int64_t t);    // step t of every context: 5 launches
 void tc_batch_free(TcBatch* b);
 int tc_set_tiles(twa_ctx* c, int bn, int kc);
+int wait_probe(twa_ctx* c, int64_t limit_ns);    // one bounded wait that runs out (twa_wait_probe)
 // twa_fft.cu
 int fft_prepare(twa_ctx* c);                     // plan, twiddles, spectrum of the embedding
 void fft_free(twa_ctx* c);

@@ -8,7 +8,6 @@
 #include <math.h>
 #include <string.h>
 
-#include <mutex>
 #include <string>
 
 #include "twa_internal.cuh"
@@ -126,15 +125,15 @@ __global__ void __launch_bounds__(RT) k_observables(const double* mom, const int
 }  // namespace
 
 int reduce_observables(twa_ctx* c, twa_obs* o) {
-    double* d = nullptr;
-    TWA_CUDA(c, dev_malloc_async(c, &d, 8 * sizeof(double), c->stream));
+    Scratch<double> d_buf(c, c->stream);
+    TWA_CUDA(c, d_buf.alloc(8 * sizeof(double)));
+    double* d = d_buf.p;
     k_observables<<<1, RT, 0, c->stream>>>(c->mom, c->d_count, c->M, d);
     TWA_CUDA(c, cudaGetLastError());
     double h[8];
     int64_t cnt = 0;
     TWA_CUDA(c, cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     TWA_CUDA(c, cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
-    dev_free_async(c, d, c->stream);
     TWA_CUDA(c, cudaStreamSynchronize(c->stream));
     o->Sz = h[0];
     o->Sz_se = h[1];
@@ -153,26 +152,17 @@ int reduce_observables(twa_ctx* c, twa_obs* o) {
 }  // namespace twa
 
 namespace {
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-double* g_noalloc_base[NOALLOC_MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device, looked up once per
-// device (the host-side symbol is only a stand-in, not a device address).
+// Device address of the scratch array in the context current on this thread.
+// The host-side symbol is only a stand-in, not a device address, and the device
+// address belongs to one CUDA context: it changes after cudaDeviceReset and
+// differs in a context the caller created itself. So it is looked up on every
+// call; the lookup allocates nothing (the first lookup in a context loads the
+// library's device code into that context).
 int noalloc_base(double** base) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return twa::cuda_check(nullptr, e, "twa_reduce_moments_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
-        return twa::set_error(nullptr, TWA_EUNSUPPORTED, "twa_reduce_moments_noalloc: device index >= 64");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_base[dev]) {
-        double* p = nullptr;
-        e = cudaGetSymbolAddress((void**)&p, twa_noalloc_scratch);
-        if (e != cudaSuccess) return twa::cuda_check(nullptr, e, "twa_reduce_moments_noalloc: cudaGetSymbolAddress");
-        g_noalloc_base[dev] = p;
-    }
-    *base = g_noalloc_base[dev];
+    double* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, twa_noalloc_scratch);
+    if (e != cudaSuccess) return twa::cuda_check(nullptr, e, "twa_reduce_moments_noalloc: cudaGetSymbolAddress");
+    *base = p;
     return TWA_OK;
 }
 }  // namespace

@@ -112,6 +112,32 @@ __global__ void k_min_reduce(const double* v, int64_t n, double* out) {
     if (threadIdx.x == 0) *out = sm[0];
 }
 
+// Squared Frobenius norms of W - R and of W (R = L L^T), one block:
+// out[0] = sum (W - R)^2, out[1] = sum W^2.
+__global__ void k_residual_norms(const double* W, const double* R, int64_t n2, double* out) {
+    __shared__ double sd[256], sw[256];
+    double d = 0.0, ww = 0.0;
+    for (int64_t e = threadIdx.x; e < n2; e += blockDim.x) {
+        const double x = W[e] - R[e];
+        d += x * x;
+        ww += W[e] * W[e];
+    }
+    sd[threadIdx.x] = d;
+    sw[threadIdx.x] = ww;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sd[threadIdx.x] += sd[threadIdx.x + s];
+            sw[threadIdx.x] += sw[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sd[0];
+        out[1] = sw[0];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Lanczos for the extreme eigenvalues of W. y = W v, one warp per row.
 __global__ void k_matvec(const double* W, const double* v, double* y, int64_t N) {
@@ -263,9 +289,11 @@ int setup_pump(twa_ctx* c) {
     k_pump_matrix<<<grid, 256, 0, st>>>(c->W64, N, c->alpha, c->w);
     TWA_CUDA(c, cudaGetLastError());
 
-    double* piv = nullptr;
-    TWA_CUDA(c, dev_malloc_async(c, &piv, sizeof(double) * (N + 8), st));
+    Scratch<double> piv_buf(c, st);
+    TWA_CUDA(c, piv_buf.alloc(sizeof(double) * (N + 8)));
+    double* piv = piv_buf.p;
     c->clipped = 0;
+    c->factor_residual = 0.0;
     if (c->w == 0.0 || c->alpha == 0.0 || isinf(c->alpha)) {
         const int mode = (c->w == 0.0) ? 2 : (c->alpha == 0.0 ? 0 : 1);
         k_special_factor<<<grid, 256, 0, st>>>(c->L64, N, mode, sqrt(c->w));
@@ -295,13 +323,26 @@ int setup_pump(twa_ctx* c) {
         if (fl[FLAG_NOTPSD] > 0) {
             c->clipped = (int64_t)fl[FLAG_NOTPSD];
             if (!c->opts.clip_negative) {
-                dev_free_async(c, piv, st);
                 return set_error(c, TWA_ENOTPSD,
                                  "pump matrix not positive definite: pivot " +
                                      std::to_string((long long)fl[FLAG_NOTPSD_IDX] - 1) + " <= 0 (" +
                                      std::to_string((long long)fl[FLAG_NOTPSD]) + " such pivots)");
             }
             TWA_CUDA(c, cudaMemsetAsync(c->d_flags + FLAG_NOTPSD, 0, 2 * sizeof(unsigned long long), st));
+            // clipping zeroes the column of each non-positive pivot (it is not an
+            // eigenvalue clip): report how far L L^T is from W, ||W - L L^T||_F / ||W||_F
+            Scratch<double> r_buf(c, st);
+            TWA_CUDA(c, r_buf.alloc(sizeof(double) * (N * N + 2)));
+            double* R = r_buf.p;
+            TWA_CUDA(c, cudaMemsetAsync(R, 0, sizeof(double) * N * N, st));
+            gemm_f64(c->L64, N, c->L64, N, R, N, N, N, N, 1.0, 0.0, true, false, st);
+            k_residual_norms<<<1, 256, 0, st>>>(c->W64, R, N * N, R + N * N);
+            double nr[2] = {0.0, 0.0};
+            const cudaError_t e1 = cudaGetLastError();
+            const cudaError_t e2 = cudaMemcpyAsync(nr, R + N * N, sizeof(nr), cudaMemcpyDeviceToHost, st);
+            const cudaError_t e3 = cudaStreamSynchronize(st);
+            TWA_CUDA(c, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3));
+            c->factor_residual = nr[1] > 0.0 ? sqrt(nr[0] / nr[1]) : 0.0;
         }
     }
 
@@ -309,8 +350,9 @@ int setup_pump(twa_ctx* c) {
     // the low end of the spectrum is dense for long-range pumps, so the Krylov
     // space is taken large (the full space for N <= 1024)
     const int kmax = (int)(N < 1024 ? N : 1024);
-    double* lz = nullptr;
-    TWA_CUDA(c, dev_malloc_async(c, &lz, sizeof(double) * (4 * N + 2 * kmax + 8), st));
+    Scratch<double> lz_buf(c, st);
+    TWA_CUDA(c, lz_buf.alloc(sizeof(double) * (4 * N + 2 * kmax + 8)));
+    double* lz = lz_buf.p;
     double *v0 = lz, *v1 = lz + N, *v2 = lz + 2 * N, *y = lz + 3 * N;
     double *al = lz + 4 * N, *be = al + kmax, *ext = be + kmax;
     k_lanczos_start<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(v1, N);
@@ -330,8 +372,6 @@ int setup_pump(twa_ctx* c) {
     TWA_CUDA(c, cudaStreamSynchronize(st));
     c->w_max = e2[0];
     c->w_min = e2[1];
-    dev_free_async(c, lz, st);
-    dev_free_async(c, piv, st);
     TWA_CUDA(c, cudaStreamSynchronize(st));
     return TWA_OK;
 }

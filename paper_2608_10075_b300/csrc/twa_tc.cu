@@ -153,14 +153,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 // when another CTA has already given up and `follow_abort` is set), counting the
 // timeout in flags[FLAG_TIMEOUT].
 __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long* flags,
-                                       bool follow_abort) {
+                                       bool follow_abort, unsigned long long limit_ns = WAIT_NS) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     volatile unsigned long long* vf = flags;
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (follow_abort && vf[FLAG_TIMEOUT] != 0ull) return false;
-        if (gtimer() - t0 > WAIT_NS) {
+        if (gtimer() - t0 > limit_ns) {
             atomicAdd(&flags[FLAG_TIMEOUT], 1ull);
             return false;
         }
@@ -718,6 +718,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
 
 // ---------------------------------------------------------------------------
 // elementwise kernels of the mixed path
+
+// One bounded wait, by the routine every tensor-core kernel uses on its
+// mbarriers, on a barrier that nothing arrives on: it gives up after limit_ns
+// and counts the timeout in flags[FLAG_TIMEOUT], touching nothing else.
+__global__ void k_wait_probe(unsigned long long* flags, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait(&bar, 0u, flags, false, limit_ns);
+    }
+}
 
 __global__ void k_split_matrix(const double* src, int64_t N, int64_t ldk, __nv_bfloat16* hi, __nv_bfloat16* lo,
                                int tf32) {
@@ -1665,9 +1677,15 @@ int tc_set_state(twa_ctx* c, const double* sx, const double* sy, const double* s
     return tc_state_changed(c);
 }
 
-int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
-    if (c->fft) return fft_field(c, s, P, K);
+int tc_field(twa_ctx* c, const double* s, double* P, int64_t K, int which) {
+    if (c->fft && which == 0) return fft_field(c, s, P, K);
     TcState* t = c->tc;
+    // W: the state's images (hi + lo in the split precisions) and the context's
+    // term count. L: the operand rounded once, as the step rounds its noise eta,
+    // against L hi + lo in the split precisions (two products; three in the FP32
+    // mode, whose eta keeps a lo image) -- the step's L.eta arithmetic.
+    const int nterms = which == 1 ? leta_terms(t) : t->terms;
+    const bool b_lo = which == 1 ? nterms == 3 : t->terms == 3;
     const int64_t N = c->N, ldk = t->ldk;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
     float* out = nullptr;
@@ -1683,15 +1701,17 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K) {
         if (with_lo) TWA_CUDA(c, cudaMemsetAsync(lo, 0, ni, c->stream));
         k_split_vectors<<<nblk(K * N, 256), 256, 0, c->stream>>>(s, K, N, ldk, hi, lo, tf32);
         TcMaps fm{};
-        fm.a0 = t->tmWhi;
-        fm.a1 = t->tmWlo;
+        fm.a0 = which == 1 ? t->tmLhi : t->tmWhi;
+        fm.a1 = which == 1 ? t->tmLlo : t->tmWlo;
         int rc;
         if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, t->bn, t->kc))) return rc;
-        if ((rc = make_map(c, &fm.b1, with_lo ? lo : hi, K, N, ldk, t->bn, t->kc))) return rc;
+        if ((rc = make_map(c, &fm.b1, (with_lo && b_lo) ? lo : hi, K, N, ldk, t->bn, t->kc))) return rc;
         TcArgs fa = base_args(c);
         fa.n_vec = K;
         fa.field_out = out;
-        rc = (t->terms == 3) ? launch_cfg<MODE_FIELD, 3>(c, fm, fa) : launch_cfg<MODE_FIELD, 1>(c, fm, fa);
+        rc = nterms == 3   ? launch_cfg<MODE_FIELD, 3>(c, fm, fa)
+             : nterms == 2 ? launch_cfg<MODE_FIELD, 2>(c, fm, fa)
+                           : launch_cfg<MODE_FIELD, 1>(c, fm, fa);
         if (rc) return rc;
         k_widen<<<nblk(K * N, 256), 256, 0, c->stream>>>(out, P, K * N);
         TWA_CUDA(c, cudaGetLastError());
@@ -1807,6 +1827,12 @@ int tc_batch_step(twa_ctx* lead, TcBatch* b, int64_t t) {
 }
 
 // Change the tile configuration of a context (re-encodes its tensor maps).
+int wait_probe(twa_ctx* c, int64_t limit_ns) {
+    k_wait_probe<<<1, 32, 0, c->stream>>>(c->d_flags, (unsigned long long)limit_ns);
+    TWA_CUDA(c, cudaGetLastError());
+    return TWA_OK;
+}
+
 int tc_set_tiles(twa_ctx* c, int bn, int kc) {
     TcState* t = c->tc;
     mix_free(t);   // its descriptors and the captured steps hold the old tensor maps

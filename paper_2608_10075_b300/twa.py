@@ -77,7 +77,7 @@ class Obs(ctypes.Structure):
                                                   "G2num", "G2num_se", "g2", "g2_se")] + \
                [(n, ctypes.c_int64) for n in ("M", "steps", "samples")] + \
                [(n, ctypes.c_double) for n in ("w_max", "w_min", "w_tilde", "stability", "min_pivot")] + \
-               [(n, ctypes.c_int64) for n in ("clipped", "nonfinite")]
+               [(n, ctypes.c_int64) for n in ("clipped", "nonfinite")] + [("factor_residual", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -99,12 +99,13 @@ class GradOut(ctypes.Structure):
 
 
 OBJECTIVE = {"SpSm": 0, "g2": 1}
+MATRIX = {"W": 0, "L": 1}
 
 
 class Point(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("alpha", ctypes.c_double), ("w", ctypes.c_double),
                 ("Gamma", ctypes.c_double), ("dt", ctypes.c_double), ("steps", ctypes.c_int64),
-                ("window_start", ctypes.c_double)]
+                ("window_start", ctypes.c_double), ("means", ctypes.c_void_p)]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -121,12 +122,14 @@ _SIGNATURES = {
     "twa_set_state": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int]),
     "twa_get_moments": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "twa_field": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
+    "twa_contract": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int64]),
     "twa_reduce_moments": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
     "twa_reduce_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Obs)]),
     "twa_grad": (ctypes.c_int, [_P, ctypes.POINTER(GradReq), ctypes.POINTER(GradOut), _P]),
     "twa_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(Opts),
                                      _P, _P]),
     "twa_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "twa_wait_probe": (ctypes.c_int, [_P, ctypes.c_int64]),
     "twa_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "twa_last_error": (ctypes.c_char_p, [_P]),
     "twa_destroy": (None, [_P]),
@@ -267,6 +270,19 @@ class TWA:
         self._check(lib().twa_field(self._h, ps, po, int(s.shape[0])))
         return out
 
+    def contract(self, s, matrix="W", out=None):
+        """P[k] = A s[k] for a CUDA float64 tensor s of shape [K][N], A = W
+        (matrix="W") or the noise factor L (matrix="L"), in the arithmetic of
+        the context's step (twa_contract)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(s)
+        (ps, ds), (po, do) = _ptr(s), _ptr(out)
+        if not (ds and do):
+            raise ValueError("contract() takes CUDA tensors")
+        self._check(lib().twa_contract(self._h, MATRIX[matrix], ps, po, int(s.shape[0])))
+        return out
+
     def grad(self, objective, M, steps, checkpoint=64, want_alpha=True, per_traj=False):
         """Pathwise dJ/dw and dJ/dalpha at fixed noise (twa_grad). With per_traj,
         also the [M][2] per-trajectory samples whose mean is the derivative."""
@@ -280,6 +296,11 @@ class TWA:
         if per_traj:
             d["per_traj"] = buf
         return d
+
+    def wait_probe(self, limit_us):
+        """Enqueue one bounded device wait that runs out (twa_wait_probe); the
+        next synchronising call raises TWA_ETIMEOUT."""
+        self._check(lib().twa_wait_probe(self._h, int(limit_us)))
 
     def profile(self, enable=True):
         self._check(lib().twa_profile(self._h, 1 if enable else 0))
@@ -326,13 +347,19 @@ def reduce_moments(means, N):
     return o.as_dict()
 
 
-def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None, integrator="heun"):
+def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None, integrator="heun",
+              means=False):
     """twa_batch_run: points = list of dicts with N, alpha, w, Gamma, dt, steps,
-    window_start. Returns (list of observables dicts, (BN, K-stage config))."""
+    window_start. Returns (list of observables dicts, (BN, K-stage config));
+    with means=True every dict also holds "means", the point's per-trajectory
+    window means [M][5]."""
+    import numpy as np
     arr = (Point * len(points))()
+    bufs = [np.empty((int(M), 5)) if means else None for _ in points]
     for k, p in enumerate(points):
         arr[k] = Point(int(p["N"]), float(p["alpha"]), float(p["w"]), float(p["Gamma"]), float(p["dt"]),
-                       int(p["steps"]), float(p.get("window_start", 0.0)))
+                       int(p["steps"]), float(p.get("window_start", 0.0)),
+                       ctypes.c_void_p(bufs[k].ctypes.data) if means else None)
     o = Opts()
     lib().twa_opts_default(ctypes.byref(o))
     o.precision = PRECISION[precision]
@@ -347,7 +374,11 @@ def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None
                              ctypes.byref(o), ctypes.cast(out, ctypes.c_void_p), ctypes.cast(tiles, ctypes.c_void_p))
     if rc != TWA_OK:
         raise TWAError(rc, last_error(None))
-    return [x.as_dict() for x in out], (tiles[0], tiles[1])
+    res = [x.as_dict() for x in out]
+    if means:
+        for d, b in zip(res, bufs):
+            d["means"] = b
+    return res, (tiles[0], tiles[1])
 
 
 NOALLOC_MAX_M = 65536

@@ -1,5 +1,10 @@
 """Batched scans (twa_batch_run) through the C ABI.
 
+Against the oracle: every point's per-trajectory window means over its first
+steps follow the oracle run on the same BF16-rounded normals within the bound
+derived in tests/mixed_bounds.py, and after a windowed run each point's
+observables lie within 3 standard errors of the plain FP64 oracle's.
+
 Every point of a batch runs the same kernels, with the same tile arithmetic,
 as when it runs alone: a tile's accumulation order along K does not depend on
 the K-stage width, the per-site results do not depend on the trajectory-tile
@@ -10,7 +15,11 @@ whatever tile configuration the autotuner picks.
 import math
 import os
 
+import numpy as np
 import pytest
+
+from oracle.twa_oracle import TWAOracle
+from tests.mixed_bounds import BF16NoiseOracle, step_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +85,58 @@ def test_batch_rejects_fp64():
     with pytest.raises(twa.TWAError) as e:
         twa.batch_run(POINTS[:1], 8, precision="fp64")
     assert e.value.name == "TWA_EUNSUPPORTED"
+
+
+# uneven points: ragged N (37, 130, 300), the extreme exponents of the scans
+ORACLE_POINTS = [
+    dict(N=300, alpha=0.25, w=60.0, Gamma=1.0, dt=2e-4),
+    dict(N=37, alpha=1.0, w=3.0, Gamma=1.0, dt=1e-3),
+    dict(N=130, alpha=2.0, w=10.0, Gamma=1.0, dt=3e-4),
+    dict(N=200, alpha=0.5, w=100.0, Gamma=1.0, dt=1e-4),
+]
+
+
+def _moment_bound(o, D):
+    """Bound of the window-moment samples (S^z, A, A^2, A S^z, (S^z)^2) of the
+    oracle's current state when every collective sum S^a may be off by D[m]."""
+    Sx, Sy, Sz = o.sx.sum(1), o.sy.sum(1), o.sz.sum(1)
+    A = 0.25 * (Sx * Sx + Sy * Sy)
+    dA = 0.5 * (np.abs(Sx) + np.abs(Sy)) * D + 0.5 * D * D
+    return np.stack([D, dA, 2 * np.abs(A) * dA + dA * dA, np.abs(A) * D + np.abs(Sz) * dA + dA * D,
+                     2 * np.abs(Sz) * D + D * D], axis=1)
+
+
+def test_batch_points_track_the_oracle_per_trajectory():
+    from paper_2608_10075_b300 import twa
+    M, seed, steps = 160, 3, 3
+    pts = [dict(p, steps=steps, window_start=0.0) for p in ORACLE_POINTS]
+    res, _ = twa.batch_run(pts, M, seed=seed, means=True)
+    for p, r in zip(pts, res):
+        o = BF16NoiseOracle(p["N"], p["alpha"], p["w"], p["Gamma"], p["dt"], seed, M)
+        tol = 0.0
+        mbound = np.zeros((M, 5))
+        for _ in range(steps):
+            tol = tol + step_bound(o, o.sx, o.sy, o.sz)
+            o.run(1)
+            # state differences <= 2 x the summed step bounds (tests/mixed_bounds.py),
+            # summed over sites; the kernel forms S^a in FP32 (N 2^-23 sqrt 3 more)
+            D = (2.0 * tol).sum(axis=1) + p["N"] * 2.0 ** -23 * math.sqrt(3.0)
+            mbound += _moment_bound(o, D)
+        mbound /= steps
+        ref = o.window_means()
+        err = np.abs(r["means"] - ref)
+        assert np.all(err <= mbound), (p, float(np.max(err / mbound)))
+        assert r["samples"] == steps and r["nonfinite"] == 0
+
+
+def test_batch_observables_within_3se_of_the_oracle():
+    from paper_2608_10075_b300 import twa
+    M, seed, steps = 256, 21, 400
+    pts = [dict(p, steps=steps, window_start=0.5 * steps * p["dt"]) for p in ORACLE_POINTS]
+    res, _ = twa.batch_run(pts, M, seed=seed)
+    for p, r in zip(pts, res):
+        o = TWAOracle(p["N"], p["alpha"], p["w"], p["Gamma"], p["dt"], seed, M, window_start=p["window_start"])
+        o.run(steps)
+        ob = o.observables()
+        for k in ("Sz", "SpSm", "G2num", "g2"):
+            assert abs(r[k] - ob[k]) <= 3.0 * math.hypot(r[k + "_se"], ob[k + "_se"]), (p, k, r[k], ob[k])

@@ -13,15 +13,20 @@ with TF32 halves: residual and dropped lo*lo term 2^-22 each, so ~3 * 2^-22
 |w s| per product. The tests use these bounds with a factor of two of margin.
 
 Trajectories. The mixed path rounds its normals to BF16 (relative 2^-9), so a
-trajectory only stays close to the oracle's for a few steps; beyond that the
-comparison is statistical: ensemble observables within 3 standard errors.
+trajectory only stays close to the plain oracle's for a few steps; beyond that
+the comparison is statistical: ensemble observables within 3 standard errors.
+The BF16X3 trajectories are checked against the oracle run on the same
+BF16-rounded normals, within the term-by-term bound of tests/mixed_bounds.py
+(~2^-17 of the noise and field sums per step, plus the few normals that sit at
+a BF16 rounding boundary), which a dropped lo image of L exceeds.
 """
 import math
 
 import numpy as np
 import pytest
 
-from oracle.twa_oracle import TWAOracle, pump_matrix
+from oracle.twa_oracle import TWAOracle, noise_factor, pump_matrix
+from tests.mixed_bounds import BF16NoiseOracle, bf16, track
 
 pytestmark = pytest.mark.gpu
 
@@ -99,7 +104,77 @@ def test_initial_state_is_exact(prec):
     assert np.array_equal(gx, o.sx) and np.array_equal(gy, o.sy) and np.array_equal(gz, o.sz)
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-2), ("bf16", 3e-2), ("tf32", 1e-2), ("fp32", 1e-4)])
+def _leta_bound(prec, N, absref):
+    """Bound of |L.eta - kernel| for eta exactly representable in BF16 (so the
+    kernel's noise operand is eta itself): the L representation error of the
+    precision (BF16X3: hi + lo leaves 2^-18 after the FP32 image's 2^-24; one
+    BF16 term 2^-9; TF32 2^-11; the FP32 split 2^-22) plus FP32 accumulation in
+    N/16 instruction steps, with a factor of two of margin."""
+    rep = {"bf16x3": 2.0 ** -18 + 2.0 ** -24, "bf16": 2.0 ** -9, "tf32": 2.0 ** -11,
+           "fp32": 2.0 ** -22 + 2.0 ** -24}[prec]
+    return 2.0 * (rep + (N / 16.0) * 2.0 ** -22) * absref
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32"])
+@pytest.mark.parametrize("N,K", [(16, 8), (300, 600), (129, 257), (1024, 512)])
+def test_noise_factor_contraction_bound(prec, N, K):
+    # the step's L.eta arithmetic alone (twa_contract, matrix L): BF16X3 takes L
+    # hi + lo against the noise rounded once to BF16 (two products)
+    import torch
+    twa = _twa()
+    rng = np.random.default_rng(4)
+    eta = bf16(rng.standard_normal((K, N)))
+    L = noise_factor(N, 1.0, N / 2.0)
+    with twa.TWA(N, 1.0, N / 2.0, 1.0, 1e-4, precision=prec) as g:
+        P = g.contract(torch.tensor(eta, device="cuda"), matrix="L").cpu().numpy()
+    ref = eta @ L.T
+    absref = np.abs(eta) @ np.abs(L).T
+    bound = _leta_bound(prec, N, absref)
+    err = np.abs(P - ref)
+    assert np.all(err <= bound + 1e-30), float(np.max(err / (absref + 1e-300)))
+    if prec == "bf16x3":
+        # the bound resolves the lo image: L hi alone (a dropped lo term) breaks it
+        planted = eta @ bf16(L).T
+        assert np.mean(np.abs(planted - ref) > bound) > 0.1
+
+
+def test_noise_factor_contraction_full_size_sampled():
+    # N = 10^4, 2 x 1024 noise vectors (the benchmark's launch shape), BF16X3,
+    # rows of L recomputed one by one
+    import torch
+    twa = _twa()
+    N, K = 10000, 2048
+    rng = np.random.default_rng(5)
+    eta = bf16(rng.standard_normal((K, N)))
+    with twa.TWA(N, 1.0, 5000.0, 1.0, 2e-5, precision="bf16x3") as g:
+        P = g.contract(torch.tensor(eta, device="cuda"), matrix="L").cpu().numpy()
+    L = noise_factor(N, 1.0, 5000.0)
+    rows = np.array([0, 1, 127, 128, 129, 4999, 5000, 9871, 9998, 9999] + list(rng.choice(N, 54, replace=False)))
+    Lr = L[rows]
+    ref = eta @ Lr.T
+    absref = np.abs(eta) @ np.abs(Lr).T
+    bound = _leta_bound("bf16x3", N, absref)
+    err = np.abs(P[:, rows] - ref)
+    assert np.all(err <= bound), float(np.max(err / absref))
+    planted = eta @ bf16(Lr).T
+    assert np.mean(np.abs(planted - ref) > bound) > 0.1
+
+
+def test_bf16x3_trajectories_track_bf16_noise_oracle():
+    # every entry of three consecutive steps within the derived per-step bound
+    twa = _twa()
+    for N, M in ((300, 200), (128, 128), (45, 3), (130, 257)):
+        alpha, w, G, dt = 1.0, 8.0, 1.0, 2e-3
+        o = BF16NoiseOracle(N, alpha, w, G, dt, 11, M)
+        with twa.TWA(N, alpha, w, G, dt, seed=11, precision="bf16x3") as g:
+            def step():
+                g.run(M, 1)
+                return g.get_state()
+            worst = track(o, step, 3)
+        assert worst <= 1.0
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 3e-2), ("tf32", 1e-2), ("fp32", 1e-4)])
 @pytest.mark.parametrize("N,M", [(300, 200), (128, 128), (45, 3)])
 def test_trajectories_track_oracle_for_a_few_steps(prec, tol, N, M):
     # Here the noise increment per site is sqrt(w dt) eta ~ 0.13 eta; rounding eta
@@ -140,20 +215,23 @@ def test_ensemble_observables_within_3se(prec):
 
 def test_full_size_sampled_trajectories():
     # N = 10^4, alpha = 1, w = N/2, dt = 2e-5, M = 1024 in the launch shape the
-    # benchmark times; three trajectories recomputed one by one by the oracle.
+    # benchmark times; three trajectories recomputed one by one by the oracle on
+    # the same BF16-rounded normals, within the derived per-step bound.
     twa = _twa()
     N, alpha, w, G, dt, M = 10000, 1.0, 5000.0, 1.0, 2e-5, 1024
+    states = []
     with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3") as g:
-        g.run(M, 2)
-        gx, gy, gz = g.get_state()
-    assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 5e-6
+        for _ in range(2):
+            g.run(M, 1)
+            states.append(g.get_state())
+    for gx, gy, gz in states:
+        assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 5e-6
     W = pump_matrix(N, alpha, w)
     L = np.linalg.cholesky(W)
     for m in (0, 517, 1023):
-        o = TWAOracle(N, alpha, w, G, dt, 0, 1, m0=m, W=W, L=L)
-        o.run(2)
-        err = max(np.max(np.abs(gx[m] - o.sx[0])), np.max(np.abs(gy[m] - o.sy[0])), np.max(np.abs(gz[m] - o.sz[0])))
-        assert err < 1e-2, (m, err)
+        o = BF16NoiseOracle(N, alpha, w, G, dt, 0, 1, m0=m, W=W, L=L)
+        it = iter(states)
+        assert track(o, lambda: tuple(a[m:m + 1] for a in next(it)), 2) <= 1.0
 
 
 def test_full_size_sampled_field():

@@ -104,6 +104,23 @@ def test_pump_matrix_limits():
     assert W[0, 0] == 2.0 and W[0, 1] == 1.0 and W[4, 0] == 2.0 / 5.0 and W[1, 3] == 2.0 / 3.0
 
 
+def test_pump_matrix_rounding_breaks_definiteness_near_alpha_zero():
+    # Eq. 2 is positive definite for every alpha > 0 (convex decreasing sequence),
+    # but at alpha = 1e-15 the entries differ from w by a few ulps only, so the
+    # stored FP64 matrix is rank one plus rounding noise of both signs: it has a
+    # negative eigenvalue and no Cholesky factor. This is the case the clip
+    # option of the library is tested on; at alpha = 1e-12 the spread
+    # alpha ln(1 + |i-j|) is far above the rounding and the factor exists.
+    N, w = 200, 5.0
+    W = pump_matrix(N, 1e-15, w)
+    assert np.linalg.eigvalsh(W)[0] < 0.0
+    with pytest.raises(np.linalg.LinAlgError):
+        np.linalg.cholesky(W)
+    W12 = pump_matrix(N, 1e-12, w)
+    assert np.linalg.eigvalsh(W12)[0] > 0.0
+    np.linalg.cholesky(W12)
+
+
 @pytest.mark.parametrize("alpha", [0.0, 0.75, 2.0, math.inf])
 def test_noise_covariance_equals_pump_times_dt(alpha):
     # Sec. S1: <chi_i chi_j> = w_ij delta(t-t'), <xi xi> = Gamma delta(t-t').
