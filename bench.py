@@ -5,7 +5,8 @@
 Workload: N = 10^4 spins, alpha = 1, w = N Gamma / 2, Gamma = 1, dt = 2e-5,
 M = 1024 trajectories per GPU (weak scaling: rank r runs trajectories
 [r M, (r+1) M) of one ensemble), W and L held as BF16 hi+lo images, FP32 state,
-BF16X3 contractions on tcgen05. One step = one stochastic-Heun step of all M
+BF16X2 contractions on tcgen05 (W hi + lo and L hi + lo against the state and
+the noise rounded once to BF16). One step = one stochastic-Heun step of all M
 trajectories: noise, L.eta and W.s (predictor), W.s~ (corrector), moments.
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
@@ -30,7 +31,7 @@ from paper_2608_10075_b300.configs import LARGE_N1E4 as CFG  # noqa: E402
 METRIC = "spin-traj-steps/s at N=1e4 (mixed vs FP64 GPU, observables within 3 SE)"
 UNIT = "spin-traj-steps/s"
 WORKLOAD = ("TWA stochastic Heun, N=10000 alpha=1 w=5000 Gamma=1 dt=2e-5, M=1024 trajectories/GPU, "
-            "BF16X3 (hi+lo W, L) tcgen05 contractions, FP32 state")
+            "BF16X2 tcgen05 contractions (hi+lo W, L against a BF16 operand), FP32 state")
 REF_SAMPLE_M = 16
 
 
@@ -152,13 +153,47 @@ def contraction_flops(N, M, terms_w=3, terms_l=2):
     """Tensor-core FLOPs per launch of each contraction kernel.
 
     predict / correct: W.s over all N^2 entries for 2M columns with `terms_w`
-    products (BF16X3: 3); noise_factor: L.eta over the N(N+1)/2 lower-triangular
-    entries with `terms_l` products (hi and lo of L against the BF16 noise).
+    products (BF16X3: 3, BF16X2: 2); noise_factor: L.eta over the N(N+1)/2
+    lower-triangular entries with `terms_l` products (hi and lo of L against the
+    BF16 noise: 2).
     """
     cols = 2 * M
     wflops = 2.0 * N * N * cols * terms_w
     lflops = 2.0 * (N * (N + 1) / 2.0) * cols * terms_l
     return {"predict": wflops, "correct": wflops, "noise_factor": lflops}
+
+
+def fft_length(N):
+    """Circle length of the Toeplitz route: the smallest even 2^a 3^b 5^c >= max(2, 2N - 2)."""
+    P = max(2, 2 * N - 2)
+    while True:
+        v = P
+        for f in (2, 3, 5):
+            while v % f == 0:
+                v //= f
+        if v == 1 and P % 2 == 0:
+            return P
+        P += 1
+
+
+# FP32 peak of the FFT route's ALU work: 148 SMs x 128 FP32 lanes x 2 FLOP per
+# FMA x 2032 MHz (the maximum SM clock)
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2032e6 / 1e12
+
+
+def fft_roofline(N, M, kernel_ms):
+    """FP32 roofline of the FFT route's dominant kernel (predictor or corrector:
+    one forward and one inverse complex transform of length P per trajectory,
+    5 P log2 P FLOP each)."""
+    import math
+    P = fft_length(N)
+    flops = 2 * 5.0 * P * math.log2(P) * M
+    k = max(("predict", "correct"), key=lambda x: kernel_ms.get(x, 0.0))
+    achieved = flops / (kernel_ms[k] * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "k_fft_%s" % ("pred" if k == "predict" else "corr"), "P": P,
+            "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP/FMA x 2032 MHz",
+            "flops_per_launch": flops, "kernel_ms": kernel_ms[k]}
 
 
 def host_threads():
@@ -226,38 +261,43 @@ def algorithmic_flops(N, M, lib_flops, launches, terms_w, terms_l):
     return 2.0 * N * N * 2 * M * launches + l_exec / terms_l
 
 
-def precision_check(twa, stream, rank, M_sub=128, steps=200):
-    """The metric's qualifier on a subset of the ensemble: BF16X3 and the FP64
-    GPU path on the same trajectories and seeds, `steps` steps, window over the
-    second half; unpaired differences in units of the combined standard error,
-    and the paired per-trajectory difference with its standard error."""
+def precision_check(twa, stream, rank, precisions, M_sub=128, steps=200):
+    """The metric's qualifier on a subset of the ensemble: each mixed precision
+    and the FP64 GPU path on the same trajectories and seeds, `steps` steps,
+    window over the second half; unpaired differences in units of the combined
+    standard error, and the paired per-trajectory difference with its
+    standard error."""
     import math
 
     import numpy as np
     N = CFG["N"]
     t0 = (steps // 2) * CFG["dt"]
     obs, smp = {}, {}
-    for prec in (CFG["precision"], "fp64"):
+    for prec in ("fp64",) + tuple(precisions):
         with twa.TWA(N, CFG["alpha"], CFG["w"], CFG["Gamma"], CFG["dt"], seed=0, precision=prec, stream=stream,
                      traj_offset=rank * CFG["M"], window_start=t0) as g:
             g.run(M_sub, steps)
             obs[prec] = g.observables()
             Sz, A, A2, ASz, Sz2 = g.moments().T
             smp[prec] = {"Sz": Sz, "SpSm": A + 0.5 * Sz, "G2num": A2 + 2 * ASz - Sz / 3 + 0.5 * Sz2 - 4.0 / 3.0 * A}
-    a, b = obs[CFG["precision"]], obs["fp64"]
-    out = {"trajectories": M_sub, "steps": steps, "window_steps": steps - steps // 2, "observables": {}}
-    worst = 0.0
-    for k in ("Sz", "SpSm", "G2num", "g2"):
-        se = math.hypot(a[k + "_se"], b[k + "_se"])
-        r = {"mixed": a[k], "fp64": b[k], "diff_in_se": (a[k] - b[k]) / se}
-        if k in smp["fp64"]:
-            d = smp[CFG["precision"]][k] - smp["fp64"][k]
-            r["paired_diff"] = float(np.mean(d))
-            r["paired_se"] = float(np.std(d, ddof=1) / math.sqrt(M_sub))
-        worst = max(worst, abs(r["diff_in_se"]))
-        out["observables"][k] = r
-    out["max_abs_diff_in_se"] = worst
-    out["within_3se"] = worst <= 3.0
+    out = {"trajectories": M_sub, "steps": steps, "window_steps": steps - steps // 2}
+    b = obs["fp64"]
+    for prec in precisions:
+        a = obs[prec]
+        res = {"observables": {}}
+        worst = 0.0
+        for k in ("Sz", "SpSm", "G2num", "g2"):
+            se = math.hypot(a[k + "_se"], b[k + "_se"])
+            r = {"mixed": a[k], "fp64": b[k], "diff_in_se": (a[k] - b[k]) / se}
+            if k in smp["fp64"]:
+                d = smp[prec][k] - smp["fp64"][k]
+                r["paired_diff"] = float(np.mean(d))
+                r["paired_se"] = float(np.std(d, ddof=1) / math.sqrt(M_sub))
+            worst = max(worst, abs(r["diff_in_se"]))
+            res["observables"][k] = r
+        res["max_abs_diff_in_se"] = worst
+        res["within_3se"] = worst <= 3.0
+        out[prec] = res
     return out
 
 
@@ -311,8 +351,8 @@ def run_ours(args, rank, world, dist):
     ctx.profile(False)
     c3 = clocks.mark()
     step_kernel_ms = sum(v[0] for v in prof.values()) / max(kp, 1)
-    terms_w = {"bf16x3": 3, "fp32": 3}.get(CFG["precision"], 1)
-    terms_l = {"bf16x3": 2, "fp32": 3}.get(CFG["precision"], 1)
+    terms_w = {"bf16x3": 3, "fp32": 3, "bf16x2": 2}.get(CFG["precision"], 1)
+    terms_l = {"bf16x3": 2, "fp32": 3, "bf16x2": 2, "bf16l2": 2}.get(CFG["precision"], 1)
     flops = contraction_flops(N, M, terms_w, terms_l)
     # the library reports the executed FLOPs of each launch it timed: the
     # predictor and corrector launches of step t also carry L.eta tiles of t + 1
@@ -405,12 +445,15 @@ def run_ours(args, rank, world, dist):
     if not args.no_side:
         side["fft_route"] = side_run(CFG["precision"], "fft", min(K, 300), 3)
         side["fft_route"]["speedup_vs_dense"] = side["fft_route"]["value"] / value
+        side["fft_route"]["roofline"] = fft_roofline(N, M, side["fft_route"]["kernel_ms_per_step"])
         # W.s by FFT and the pump noise from the same circulant embedding: no contraction left
         side["fft_route_circulant_noise"] = side_run(CFG["precision"], "fft", min(K, 300), 3, noise="circulant")
         side["fft_route_circulant_noise"]["speedup_vs_dense"] = side["fft_route_circulant_noise"]["value"] / value
+        side["fft_route_circulant_noise"]["roofline"] = fft_roofline(
+            N, M, side["fft_route_circulant_noise"]["kernel_ms_per_step"])
         # the dense route in the other tensor-core precisions (one-term BF16, TF32,
         # and the FP32-accurate TF32 split)
-        for prec in ("bf16", "tf32", "fp32"):
+        for prec in ("bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2"):
             if prec != CFG["precision"]:
                 side["dense_" + prec] = side_run(prec, "dense", min(K, 300), 3)
                 side["dense_" + prec]["speedup_vs_main"] = side["dense_" + prec]["value"] / value
@@ -421,7 +464,8 @@ def run_ours(args, rank, world, dist):
         side["fp64_gpu"]["mixed_speedup"] = value / side["fp64_gpu"]["value"]
     qualifier = None
     if not args.no_precision_check:
-        qualifier = precision_check(twa, stream, rank)
+        others = tuple(p for p in ("bf16x3", "bf16x2", "bf16l2") if p != CFG["precision"])
+        qualifier = precision_check(twa, stream, rank, (CFG["precision"],) + (() if args.no_side else others))
     clocks.stop()
 
     cpu = None

@@ -81,6 +81,16 @@ extern "C" {
                                 accumulation (about 2^-22 relative per product, the
                                 order of an FP32 product), FP32 state. Same coverage
                                 as TWA_PREC_TF32                                      */
+#define TWA_PREC_BF16X2  5   /* W and L held as BF16 hi + lo, their operand (the state,
+                                the noise) rounded once to BF16: two products per entry,
+                                A_hi*v + A_lo*v, FP32 accumulation, FP32 state. W.s is
+                                W.bf16(s) to ~2^-17; L.eta is the BF16X3 arithmetic.
+                                twa_run, twa_field, twa_contract, twa_batch_run;
+                                not twa_grad                                         */
+#define TWA_PREC_BF16L2  6   /* W one BF16 product (W_hi*s_hi), L split as in BF16X2
+                                (L_hi*eta + L_lo*eta): the noise factor, whose rounding
+                                biases single-term BF16, keeps ~16 bits. Same coverage
+                                as TWA_PREC_BF16X2                                    */
 
 typedef struct twa_ctx twa_ctx;   /* opaque, owned by the library */
 
@@ -155,6 +165,17 @@ typedef struct twa_opts {
 
 #define TWA_ROUTE_DENSE 0   /* tensor-core contraction with the dense W          */
 #define TWA_ROUTE_FFT   1   /* circulant-embedding FFT convolution, FP32         */
+#define TWA_ROUTE_RESIDENT 2 /* small systems (N <= TWA_RESIDENT_MAX_N), precision
+                                TWA_PREC_FP32: every twa_run call is one launch in
+                                which each CTA integrates its trajectories for all
+                                steps with the state in shared memory (W and L too
+                                when they fit, else streamed through it from L2);
+                                W.s and L.eta as FP32 FMA chains, FP32 normals (not
+                                rounded to BF16), FP32 state, FP64 moments. Heun
+                                and midpoint; Cholesky noise draw. twa_field and
+                                twa_contract on such a context run the FP32
+                                tensor-core split                                   */
+#define TWA_RESIDENT_MAX_N 512
 
 /* Pump-noise draws. Circulant: on a circle of even length P >= 2N - 2 (the
    smallest 2^a 3^b 5^c), c_d = w / (1 + min(d, P - d))^alpha is the first row
@@ -178,7 +199,8 @@ typedef struct twa_opts {
 #define TWA_PROF_GEMM64    4   /* FP64 path: one SIMT contraction               */
 #define TWA_PROF_ELEM64    5   /* FP64 path: elementwise / reduction kernels    */
 #define TWA_PROF_NOISE_FACTOR 6 /* mixed path: L.eta contraction -> noise part  */
-#define TWA_PROF_KINDS     7
+#define TWA_PROF_RESIDENT  7   /* resident route: one launch of all steps        */
+#define TWA_PROF_KINDS     8
 
 typedef struct twa_obs {
     /* ensemble means over trajectories of the per-trajectory window means, and
@@ -272,6 +294,8 @@ TWA_API int twa_field(twa_ctx* ctx, const double* s, double* P, int64_t K);
  *  - FP64: DFMA (the K range of L stops at the diagonal);
  *  - BF16X3: W hi/lo against an hi/lo split of s (three products), or L hi/lo
  *    against s rounded once to BF16 (two products), FP32 accumulation;
+ *  - BF16X2: W or L hi/lo against s rounded once to BF16 (two products);
+ *  - BF16L2: W one BF16 product; L as in BF16X2;
  *  - BF16: one product of BF16 images; TF32: one product of TF32 images;
  *  - FP32: TF32 hi/lo splits of both operands (three products).
  * On the FFT route TWA_MAT_W runs the FFT convolution, TWA_MAT_L the dense
@@ -342,8 +366,8 @@ typedef struct twa_point {
  *
  * Every point gets its own pump matrix, Cholesky factor and M trajectories (set
  * up concurrently from several host threads, each on its own stream; seed
- * and opts as for twa_init; opts->precision must be TWA_PREC_BF16 or
- * TWA_PREC_BF16X3, opts->window_start is replaced by each point's, and every
+ * and opts as for twa_init; opts->precision must be TWA_PREC_BF16,
+ * TWA_PREC_BF16X3, TWA_PREC_BF16X2 or TWA_PREC_BF16L2, opts->window_start is replaced by each point's, and every
  * point runs the dense route with the Cholesky noise draw). A step of all
  * points still running is the single-context step done for all of them at
  * once: noise of the next step, one persistent launch with every point's W.s +
@@ -355,15 +379,80 @@ typedef struct twa_point {
  * The results equal those of running every point alone with twa_run. A point
  * whose `means` is not NULL also gets its per-trajectory window means there.
  *
+ * With opts->ws_route = TWA_ROUTE_RESIDENT (precision TWA_PREC_FP32, every
+ * N <= TWA_RESIDENT_MAX_N) the whole scan is one launch per CTA shape: each CTA
+ * integrates its trajectories of one point for all of that point's steps with
+ * the state in shared memory (results equal each point run alone on that
+ * route; tiles receives (0, 0)).
+ *
  * Tile shapes: unless TWA_TC_BN / TWA_TC_KC are set in the environment, a
  * built-in autotuner times the compiled configurations on a few steps of the
  * points that run in the stage with the most work (steps x N^2 of the points
  * still running; the state is saved and restored around the trials) and keeps
  * the fastest. tiles: NULL or int[2] receiving the chosen (BN, K-stage config).
- * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (a precision other than BF16 and
- * BF16X3), plus those of twa_init and twa_sync. Synchronises. */
+ * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (a precision other than BF16, BF16X3,
+ * BF16X2 and BF16L2), plus those of twa_init and twa_sync. Synchronises. */
 TWA_API int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,
                           twa_obs* out, int* tiles);
+
+/* request of twa_correlation */
+typedef struct twa_corr_req {
+    int64_t M;              /* trajectories (Philox indices traj_offset + 0 .. M-1),
+                               each integrated as three copies                      */
+    int64_t prep_steps;     /* steps from the discrete-Wigner start to the kick      */
+    int64_t lag_steps;      /* steps after the kick                                  */
+    int64_t lag_stride;     /* C(tau) recorded at tau = k lag_stride dt, k = 0 ..
+                               lag_steps / lag_stride (k = 0: right after the kick)  */
+    double  eps;            /* kick strength in (0, 1): every spin of a copy is
+                               rotated by the angle 2 eps                            */
+    int64_t n_omega;        /* spectrum points, omega_j = -omega_max + j 2 omega_max
+                               / (n_omega - 1), j < n_omega (>= 3)                   */
+    double  omega_max;      /* > 0                                                   */
+} twa_corr_req;
+
+typedef struct twa_corr_out {
+    int64_t M;              /* trajectories                                          */
+    int64_t n_lags;         /* 1 + lag_steps / lag_stride                            */
+    double  dtau;           /* lag_stride dt                                         */
+    double  fwhm, fwhm_se;  /* linewidth: FWHM of S(omega), block-jackknife SE      */
+    double  omega_peak;     /* grid frequency of the maximum of S                    */
+    double  S_peak;         /* that maximum                                          */
+    double  spsm_tau0;      /* Re C(0): the equal-time <S+S-> at the kick            */
+} twa_corr_out;
+
+/* Two-time correlation <S+(tau) S-(0)>, its spectrum and the linewidth (Sec.
+ * S1, closing part; main text, "Observables and method": S(omega) = 2 Re int
+ * dt e^{i omega t} <S+(t) S-(0)>, linewidth = its full width at half maximum).
+ *
+ * Runs its own M trajectories with the context's parameters, seed, options and
+ * precision (the trajectories twa_run would produce; the state of twa_run is
+ * neither read nor changed): prep_steps steps, then every trajectory gets two
+ * more copies with the same noise (same Philox counters), kicked by
+ * eps delta(t) S^x and by eps delta(t) S^y -- every spin rotated about x, resp.
+ * y, by 2 eps, the action of exp(-i eps S^b) on Pauli spins -- and the three
+ * copies run lag_steps more steps. At lag 0 and every lag_stride-th step the
+ * per-trajectory products S^a(t) S^b(t0) and the responses
+ * chi_ab = (S^a of the copy kicked by S^b - S^a) / eps (a, b in {x, y}) are
+ * summed, and
+ *   C(tau) = 1/4 [S^x S^x + S^y S^y + i (S^y S^x - S^x S^y)](tau)
+ *          + i/8 (chi_xx + chi_yy + i chi_yx - i chi_xy)(tau)
+ * (with S^+ = (S^x + i S^y) / 2, sigma^+ = (sigma^x + i sigma^y) / 2; the
+ * commutator part is normalised so that C(0+) = A + <S^z>/2, the equal-time
+ * estimator). S(omega) = 2 Re sum_k c_k e^{i omega tau_k} C(tau_k) dtau with
+ * trapezoid weights c_k; FWHM from the grid maximum and the linear
+ * interpolation of the first half-maximum crossing on each side (NaN if a side
+ * has none). Standard errors by delete-one jackknife over min(32, M) blocks of
+ * trajectories, the whole estimate recomputed per block. FP64 reductions.
+ *
+ * C: NULL or host [n_lags][2] (Re, Im of C(tau)); S: NULL or host [n_omega];
+ * parts: NULL or host [n_lags][8], the ensemble means of S^x(t)S^x(t0),
+ * S^y(t)S^y(t0), S^x(t)S^y(t0), S^y(t)S^x(t0), chi_xx, chi_yx, chi_xy, chi_yy;
+ * C_se: NULL or host [n_lags][2], jackknife SE of Re C and Im C. Synchronises.
+ * Temporarily holds three contexts' buffers (pump matrix and factor included).
+ * Errors: TWA_EINVAL (NULL, bad counts, eps, omega grid), TWA_ENOMEM,
+ * TWA_ECUDA, TWA_ENONFINITE, TWA_ETIMEOUT. */
+TWA_API int twa_correlation(twa_ctx* ctx, const twa_corr_req* req, twa_corr_out* out, double* C, double* S,
+                            double* parts, double* C_se);
 
 /* Ensemble reduction alone: observables and standard errors (the same FP64
  * device reduction twa_observables uses) of M caller-supplied per-trajectory

@@ -141,6 +141,7 @@ void drop_graphs(twa_ctx* c) {
 // Steps either replay the captured step graphs or launch the kernels directly
 // (profiling, very short runs, or TWA_NO_GRAPH set).
 int run_steps(twa_ctx* c, int64_t steps) {
+    if (c->res_W) return twa::res_run(c, steps);   // resident route: all steps in one launch
     int64_t t = c->steps;
     if (c->profiling || steps < 4 || c->graph_failed || getenv("TWA_NO_GRAPH")) return run_eager(c, t, steps);
     int rc;
@@ -206,15 +207,20 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
     if (!(w >= 0.0) || isinf(w)) return set_error(nullptr, TWA_EINVAL, "twa_init: w must be finite and >= 0");
     if (!(Gamma >= 0.0) || isinf(Gamma)) return set_error(nullptr, TWA_EINVAL, "twa_init: Gamma must be finite and >= 0");
     if (!(dt > 0.0) || isinf(dt)) return set_error(nullptr, TWA_EINVAL, "twa_init: dt must be finite and > 0");
-    if (o.precision < TWA_PREC_FP64 || o.precision > TWA_PREC_FP32)
+    if (o.precision < TWA_PREC_FP64 || o.precision > TWA_PREC_BF16L2)
         return set_error(nullptr, TWA_EINVAL, "twa_init: unknown precision");
     if (o.init_state != -1 && o.init_state != 1) return set_error(nullptr, TWA_EINVAL, "twa_init: init_state must be +-1");
     if (!(o.window_start >= 0.0) || isinf(o.window_start))
         return set_error(nullptr, TWA_EINVAL, "twa_init: window_start must be finite and >= 0");
     if (o.traj_offset < 0 || o.traj_offset > MAX_COUNTER)
         return set_error(nullptr, TWA_EINVAL, "twa_init: traj_offset must be in [0, 2^32-1]");
-    if (o.ws_route != TWA_ROUTE_DENSE && o.ws_route != TWA_ROUTE_FFT)
-        return set_error(nullptr, TWA_EINVAL, "twa_init: ws_route must be TWA_ROUTE_DENSE or TWA_ROUTE_FFT");
+    if (o.ws_route != TWA_ROUTE_DENSE && o.ws_route != TWA_ROUTE_FFT && o.ws_route != TWA_ROUTE_RESIDENT)
+        return set_error(nullptr, TWA_EINVAL,
+                         "twa_init: ws_route must be TWA_ROUTE_DENSE, TWA_ROUTE_FFT or TWA_ROUTE_RESIDENT");
+    if (o.ws_route == TWA_ROUTE_RESIDENT && o.precision != TWA_PREC_FP32)
+        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the resident route runs with precision TWA_PREC_FP32");
+    if (o.ws_route == TWA_ROUTE_RESIDENT && N > TWA_RESIDENT_MAX_N)
+        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the resident route holds N <= 512 sites");
     if (o.ws_route == TWA_ROUTE_FFT && o.precision == TWA_PREC_FP64)
         return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the FFT route runs with the tensor-core precisions only");
     if ((o.alloc == nullptr) != (o.free == nullptr))
@@ -273,6 +279,7 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
         twa::NvtxRange r2("twa_init: operand images, FFT plan");
         if (use_tc(c) && (rc = twa::tc_prepare(c))) return fail(rc);
         if (o.ws_route == TWA_ROUTE_FFT && (rc = twa::fft_prepare(c))) return fail(rc);
+        if (o.ws_route == TWA_ROUTE_RESIDENT && (rc = twa::res_prepare(c))) return fail(rc);
     }
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -448,7 +455,8 @@ int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
     if (c->opts.traj_offset + r->M - 1 > MAX_COUNTER)
         return set_error(c, TWA_EINVAL, "twa_grad: traj_offset + M exceeds the 32-bit trajectory counter");
     if (!(c->w > 0.0)) return set_error(c, TWA_EUNSUPPORTED, "twa_grad: needs w > 0");
-    if (c->opts.precision == TWA_PREC_TF32 || c->opts.precision == TWA_PREC_FP32)
+    if (c->opts.precision != TWA_PREC_FP64 && c->opts.precision != TWA_PREC_BF16 &&
+        c->opts.precision != TWA_PREC_BF16X3)
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: runs on the FP64, BF16 and BF16X3 precisions");
     if (c->opts.integrator != TWA_INT_HEUN)
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: differentiates the Heun integrator only");
@@ -547,6 +555,7 @@ void twa_destroy(twa_ctx* c) {
     free_run_buffers(c);
     if (c->tc) twa::tc_free(c);
     twa::fft_free(c);
+    twa::res_free(c);
     void* p[] = {c->W64, c->L64, c->d_t, c->d_count, c->d_flags};
     for (void* q : p) twa::dev_free(c, q);
     delete c;

@@ -225,9 +225,20 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
     twa_opts_default(&o);
     o.precision = TWA_PREC_BF16X3;
     if (opts) o = *opts;
-    if (o.precision != TWA_PREC_BF16 && o.precision != TWA_PREC_BF16X3)
-        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: batches run on the BF16 precision paths");
-    o.ws_route = TWA_ROUTE_DENSE;
+    const bool resident = o.ws_route == TWA_ROUTE_RESIDENT;
+    if (resident) {
+        // every point's whole run in one launch per CTA shape (FP32 SIMT)
+        if (o.precision != TWA_PREC_FP32)
+            return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: the resident route runs in TWA_PREC_FP32");
+        for (int p = 0; p < n; ++p)
+            if (pts[p].N > TWA_RESIDENT_MAX_N)
+                return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: the resident route holds N <= 512");
+    } else {
+        if (o.precision != TWA_PREC_BF16 && o.precision != TWA_PREC_BF16X3 && o.precision != TWA_PREC_BF16X2 &&
+            o.precision != TWA_PREC_BF16L2)
+            return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: batches run on the BF16 precision paths");
+        o.ws_route = TWA_ROUTE_DENSE;
+    }
     o.noise_route = TWA_NOISE_CHOLESKY;
     for (int p = 0; p < n; ++p)
         if (pts[p].steps < 1 || pts[p].steps > 0xFFFFFFFFll)
@@ -295,6 +306,24 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
             }
     }
     twa_ctx* lead = ctx[0];
+    if (resident) {
+        std::vector<int64_t> steps(n);
+        for (int p = 0; p < n; ++p) steps[p] = pts[p].steps;
+        if ((rc = twa::res_run_many(ctx.data(), steps.data(), n, lead, (cudaStream_t)o.stream))) {
+            set_error(nullptr, rc, lead->err);
+            return cleanup(rc);
+        }
+        if (tiles) tiles[0] = tiles[1] = 0;   // no tensor-core tiles on this route
+        for (int p = 0; p < n; ++p) {
+            ctx[p]->steps = pts[p].steps;
+            if ((rc = twa_observables(ctx[p], &out[p])) ||
+                (pts[p].means && (rc = twa_get_moments(ctx[p], pts[p].means, 0)))) {
+                set_error(nullptr, rc, ctx[p]->err);
+                return cleanup(rc);
+            }
+        }
+        return cleanup(TWA_OK);
+    }
     int bn = lead->tc->bn, kc = lead->tc->kc;
     if (!getenv("TWA_TC_BN") && !getenv("TWA_TC_KC")) {
         // tune on the points of the stage with the most work (steps x N^2 of the

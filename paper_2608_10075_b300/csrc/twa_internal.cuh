@@ -36,7 +36,8 @@ constexpr int TC_BK = 64;
 // Buffers of the mixed-precision path (twa_tc.cu, twa_fft.cu).
 struct TcState {
     int64_t M = 0, N = 0, ldk = 0, n_rt = 0;
-    int terms = 3;                               // 1 (BF16, TF32) or 3 (BF16X3, FP32)
+    int terms = 3;                               // products per W entry: 1 (BF16, BF16L2, TF32), 2 (BF16X2), 3 (BF16X3, FP32)
+    int lterms = 2;                              // products per L entry: 1 (BF16, TF32), 2, 3 (FP32)
     int bn = 256, kc = 0;                        // tile width and K-stage configuration
     int num_sms = 148;
     __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
@@ -120,6 +121,10 @@ struct twa_ctx {
     double* xi = nullptr;    // [M][2] collective normals
     double* S = nullptr;     // [M][4] collective sums of the current state
     double* Sp = nullptr;    // [M][4] collective sums of the predictor
+
+    // resident route: FP32 copies of W and L (NULL on the other routes)
+    float* res_W = nullptr;
+    float* res_L = nullptr;
 
     // tensor-core (BF16 / BF16X3) path, and the FFT plan of the Toeplitz route
     twa::TcState* tc = nullptr;
@@ -341,6 +346,13 @@ int fft_predict(twa_ctx* c);                     // W.s by FFT + Heun predictor 
 int fft_correct(twa_ctx* c);                     // W.s~ by FFT + corrector + moments (one step)
 int fft_noise(twa_ctx* c);                       // circulant noise draw -> noise part (one step)
 int fft_field(twa_ctx* c, const double* s, double* P, int64_t K);
+// twa_resident.cu (resident route)
+bool res_config(int64_t N, int* T, bool* resident, size_t* smem);
+int res_prepare(twa_ctx* c);                     // FP32 copies of W and L
+void res_free(twa_ctx* c);
+int res_run(twa_ctx* c, int64_t steps);          // all steps in one launch
+// steps[k] steps of each resident context cs[k] in one launch per CTA shape
+int res_run_many(twa_ctx* const* cs, const int64_t* steps, int n, twa_ctx* lead, cudaStream_t st);
 // twa_adjoint.cu
 int grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_traj);
 // twa_reduce.cu

@@ -94,7 +94,7 @@ struct KCfg<2> {   // 16 TF32 = 64 B rows, SWIZZLE_64B, four stages
 inline int kcfg_bk(int kc) { return kc == 0 ? KCfg<0>::BK : kc == 1 ? KCfg<1>::BK : KCfg<2>::BK; }
 // products per L.eta entry: one term, two (L hi + lo against the single BF16 eta
 // of BF16X3) or three (FP32 mode: eta split into TF32 hi + lo as well)
-inline int leta_terms(const TcState* t) { return t->terms == 3 ? (t->kc == 2 ? 3 : 2) : 1; }
+inline int leta_terms(const TcState* t) { return t->lterms; }
 
 template <int BN, int KC>
 struct Geo {
@@ -281,6 +281,7 @@ struct GroupDesc {   // 64-byte aligned through its tensor maps
     TcMaps maps;
     TcArgs args;
     int mode;               // kernel mode of this problem's tiles (MODE_MIX launches)
+    int nterms;             // tensor-core products per entry of this problem's tiles
 };
 struct Group {
     const GroupDesc* desc;
@@ -340,11 +341,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             ap = &grp.desc[lo].args;
             tl = t - grp.start[lo];
             if (MODE == MODE_MIX) {
-                // W.s tiles take the template's term count, L.eta tiles one term
-                // fewer when their noise operand is a single BF16 value (in the
-                // FP32 mode eta has a lo image too)
+                // each problem's mode and product count from its descriptor: W.s
+                // tiles take the precision's W count (the template's), L.eta tiles
+                // that of L (two products when L is split and the noise operand is
+                // a single BF16 value; three in the FP32 mode, whose eta is split too)
                 md = grp.desc[lo].mode;
-                nt = (md == MODE_LETA) ? (NT == 3 ? (TFM ? 3 : 2) : 1) : NT;
+                nt = grp.desc[lo].nterms;
             }
         }
         const int64_t nct = (ap->n_vec + BN - 1) / BN;
@@ -1125,7 +1127,18 @@ int tc_prepare(twa_ctx* c) {
     t->N = c->N;
     t->ldk = (c->N + 7) / 8 * 8;
     t->n_rt = (c->N + BM - 1) / BM;
-    t->terms = (c->opts.precision == TWA_PREC_BF16X3 || c->opts.precision == TWA_PREC_FP32) ? 3 : 1;
+    // products per entry of W (against the state) and of L (against the noise):
+    // BF16X3 and FP32: three for W (hi*hi + hi*lo + lo*hi); L two (BF16X3: the
+    // noise is one BF16 value) or three (FP32: the noise is split too). BF16X2:
+    // W and L split, their operand one BF16 value: two and two. BF16L2: W one
+    // BF16 product, L split: one and two. BF16, TF32: one and one.
+    switch (c->opts.precision) {
+        case TWA_PREC_BF16X3: t->terms = 3; t->lterms = 2; break;
+        case TWA_PREC_FP32: t->terms = 3; t->lterms = 3; break;
+        case TWA_PREC_BF16X2: t->terms = 2; t->lterms = 2; break;
+        case TWA_PREC_BF16L2: t->terms = 1; t->lterms = 2; break;
+        default: t->terms = 1; t->lterms = 1; break;
+    }
     // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1}.
     // Default measured fastest at N = 10^4, M = 1024: 256-wide tiles, four 32-wide
     // K stages (SWIZZLE_64B). The TF32 and FP32 precisions have one configuration:
@@ -1244,7 +1257,9 @@ int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t 
     TcArgs a = base_args(c);
     a.n_vec = K;
     a.field_out = out;
-    return (t->terms == 3) ? launch_cfg<MODE_FIELD, 3>(c, m, a) : launch_cfg<MODE_FIELD, 1>(c, m, a);
+    return t->terms == 3   ? launch_cfg<MODE_FIELD, 3>(c, m, a)
+           : t->terms == 2 ? launch_cfg<MODE_FIELD, 2>(c, m, a)
+                           : launch_cfg<MODE_FIELD, 1>(c, m, a);
 }
 
 void tc_free(twa_ctx* c) {
@@ -1490,9 +1505,9 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
             ca.oHi = t->Shi; ca.oLo = t->Slo;
             ca.part_in = t->partp; ca.part_out = t->part;
             GroupDesc* g = &d[par * nprob];
-            g[q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo}, pa, MODE_PRED};
-            g[n + q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo}, ca, MODE_CORR};
-            g[2 * n + q] = GroupDesc{TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmElo}, la, MODE_LETA};
+            g[q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo}, pa, MODE_PRED, ntw};
+            g[n + q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo}, ca, MODE_CORR, ntw};
+            g[2 * n + q] = GroupDesc{TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmElo}, la, MODE_LETA, ntl};
         }
     }
     p->host = d;
@@ -1570,7 +1585,7 @@ void tc_steps_done(twa_ctx* c, int64_t t_next) {
 int tc_launch_step(twa_ctx* c, int64_t t) {
     TcState* ts = c->tc;
     const int64_t M = c->M, N = c->N;
-    const bool x3 = ts->terms == 3;
+    const int ntw = ts->terms;
     int rc;
     if (c->fft) {
         // Toeplitz route: W.s by FFT with the Heun update in the same kernel; the
@@ -1614,14 +1629,16 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         const GroupDesc* h = mp->host.data() + 3 * (t & 1);   // predictor, corrector, L.eta
         {
             ProfScope p(c, TWA_PROF_PREDICT, mp->w_flops);
-            rc = x3 ? launch_cfg<MODE_PRED, 3>(c, h[0].maps, h[0].args)
-                    : launch_cfg<MODE_PRED, 1>(c, h[0].maps, h[0].args);
+            rc = ntw == 3   ? launch_cfg<MODE_PRED, 3>(c, h[0].maps, h[0].args)
+                 : ntw == 2 ? launch_cfg<MODE_PRED, 2>(c, h[0].maps, h[0].args)
+                            : launch_cfg<MODE_PRED, 1>(c, h[0].maps, h[0].args);
         }
         if (rc) return rc;
         {
             ProfScope p(c, TWA_PROF_CORRECT, mp->w_flops);
-            rc = x3 ? launch_cfg<MODE_CORR, 3>(c, h[1].maps, h[1].args)
-                    : launch_cfg<MODE_CORR, 1>(c, h[1].maps, h[1].args);
+            rc = ntw == 3   ? launch_cfg<MODE_CORR, 3>(c, h[1].maps, h[1].args)
+                 : ntw == 2 ? launch_cfg<MODE_CORR, 2>(c, h[1].maps, h[1].args)
+                            : launch_cfg<MODE_CORR, 1>(c, h[1].maps, h[1].args);
         }
         if (rc) return rc;
     } else {
@@ -1636,8 +1653,9 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         for (int L = 0; L < 2; ++L) {
             const Group g{dp, mp->start, mp->nprob, mp->list[L], mp->first[L], mp->ctas[L]};
             ProfScope p(c, L == 0 ? TWA_PROF_PREDICT : TWA_PROF_CORRECT, mp->flops[L]);
-            rc = x3 ? launch_cfg<MODE_MIX, 3>(c, none, fa, g, mp->tiles[L])
-                    : launch_cfg<MODE_MIX, 1>(c, none, fa, g, mp->tiles[L]);
+            rc = ntw == 3   ? launch_cfg<MODE_MIX, 3>(c, none, fa, g, mp->tiles[L])
+                 : ntw == 2 ? launch_cfg<MODE_MIX, 2>(c, none, fa, g, mp->tiles[L])
+                            : launch_cfg<MODE_MIX, 1>(c, none, fa, g, mp->tiles[L]);
             if (rc) return rc;
         }
     }
@@ -1685,7 +1703,7 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K, int which) {
     // against L hi + lo in the split precisions (two products; three in the FP32
     // mode, whose eta keeps a lo image) -- the step's L.eta arithmetic.
     const int nterms = which == 1 ? leta_terms(t) : t->terms;
-    const bool b_lo = which == 1 ? nterms == 3 : t->terms == 3;
+    const bool b_lo = nterms == 3;   // the operand's lo image is read by three-product tiles only
     const int64_t N = c->N, ldk = t->ldk;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
     float* out = nullptr;
@@ -1729,7 +1747,7 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K, int which) {
 
 struct TcBatch {
     int n = 0;
-    bool x3 = true;
+    int terms = 3, lterms = 2;   // products per entry of W and of L
     int64_t noise_elems = 0, traj = 0;
     MixPlan* mix = nullptr;   // the mixed launches of all problems
     StepDesc* sd = nullptr;
@@ -1751,13 +1769,15 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
     TcBatch* b = new TcBatch();
     b->owner = lead;
     b->n = n;
-    b->x3 = lead->tc->terms == 3;
+    b->terms = lead->tc->terms;
+    b->lterms = lead->tc->lterms;
     std::vector<StepDesc> sd(n);
     std::vector<int64_t> ns(n + 1, 0), ms(n + 1, 0);
     for (int p = 0; p < n; ++p) {
         twa_ctx* c = ctxs[p];
         TcState* t = c->tc;
-        if (!t || t->terms != lead->tc->terms || t->bn != lead->tc->bn || t->kc != lead->tc->kc || c->M == 0) {
+        if (!t || t->terms != lead->tc->terms || t->lterms != lead->tc->lterms || t->bn != lead->tc->bn ||
+            t->kc != lead->tc->kc || c->M == 0) {
             tc_batch_free(b);
             return set_error(lead, TWA_EINVAL, "batch: contexts differ in precision or tiles, or have no trajectories");
         }
@@ -1800,8 +1820,8 @@ int tc_batch_prime(twa_ctx* lead, TcBatch* b, int64_t t) {
     const GroupDesc* ld = mp->desc + mp->nprob * ((t & 1) ^ 1) + 2 * n;
     const TcMaps none{};
     const Group g{ld, mp->lstart, n};
-    const int rc = b->x3 ? launch_cfg<MODE_LETA, 2>(lead, none, b->flag_args, g, mp->leta_tiles)
-                         : launch_cfg<MODE_LETA, 1>(lead, none, b->flag_args, g, mp->leta_tiles);
+    const int rc = b->lterms == 2 ? launch_cfg<MODE_LETA, 2>(lead, none, b->flag_args, g, mp->leta_tiles)
+                                  : launch_cfg<MODE_LETA, 1>(lead, none, b->flag_args, g, mp->leta_tiles);
     if (rc) return rc;
     TWA_CUDA(lead, cudaGetLastError());
     return TWA_OK;
@@ -1816,8 +1836,9 @@ int tc_batch_step(twa_ctx* lead, TcBatch* b, int64_t t) {
     const GroupDesc* dp = mp->desc + mp->nprob * (t & 1);
     for (int L = 0; L < 2; ++L) {
         const Group g{dp, mp->start, mp->nprob, mp->list[L], mp->first[L], mp->ctas[L]};
-        const int rc = b->x3 ? launch_cfg<MODE_MIX, 3>(lead, none, b->flag_args, g, mp->tiles[L])
-                             : launch_cfg<MODE_MIX, 1>(lead, none, b->flag_args, g, mp->tiles[L]);
+        const int rc = b->terms == 3   ? launch_cfg<MODE_MIX, 3>(lead, none, b->flag_args, g, mp->tiles[L])
+                       : b->terms == 2 ? launch_cfg<MODE_MIX, 2>(lead, none, b->flag_args, g, mp->tiles[L])
+                                       : launch_cfg<MODE_MIX, 1>(lead, none, b->flag_args, g, mp->tiles[L]);
         if (rc) return rc;
     }
     k_close_group<<<nblk(32 * b->traj, 256), 256, 0, lead->stream>>>(b->sd, b->mstart, b->n);

@@ -6,7 +6,7 @@
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
-path and on the mixed paths (BF16, TF32, BF16X3, FP32 from a TF32 split,
+path and on the mixed paths (BF16, TF32, BF16X3, BF16X2, BF16L2, FP32 from a TF32 split,
 BF16X3 with the FFT pump field);
 each observable is reported with its standard error and, per mixed path, the
 paired difference to FP64 (mean over trajectories of the per-trajectory
@@ -74,6 +74,8 @@ def precision_study(args):
         for name, prec, route, noise in (("bf16", "bf16", "dense", "cholesky"),
                                          ("tf32", "tf32", "dense", "cholesky"),
                                          ("bf16x3", "bf16x3", "dense", "cholesky"),
+                                         ("bf16x2", "bf16x2", "dense", "cholesky"),
+                                         ("bf16l2", "bf16l2", "dense", "cholesky"),
                                          ("fp32", "fp32", "dense", "cholesky"),
                                          ("bf16x3_fft", "bf16x3", "fft", "cholesky"),
                                          ("fft_circulant_noise", "bf16x3", "fft", "circulant")):
@@ -161,8 +163,13 @@ def gradient_study(args):
 
 def scan_study(args):
     """The 96-point scan (N in {100, 300, 1000, 3000}, six alpha, four w, M = 512,
-    dt = 0.02 / (N Gamma)) over a shortened horizon T: one batched run against the
-    same points run one after another. Throughput counts N M steps per point."""
+    dt = 0.02 / (N Gamma)) over the horizon T (the workload's is 1 / Gamma).
+    Throughput counts N M steps per point. With --small-route resident the
+    points with N <= 512 run as one resident batch (FP32, each CTA integrating
+    its trajectories for all steps in one launch) on a stream of their own,
+    concurrently with the dense batch of the larger points."""
+    import threading
+
     from .configs import SCAN_POINTS, scan_points
     pts = scan_points()
     for p in pts:
@@ -170,12 +177,39 @@ def scan_study(args):
         p["window_start"] = 0.5 * p["steps"] * p["dt"]
     M = SCAN_POINTS["M"]
     units = sum(p["N"] * M * p["steps"] for p in pts)
+    groups = [("dense", args.precision, "dense", pts)]
+    if args.small_route == "resident":
+        small = [p for p in pts if p["N"] <= twa.RESIDENT_MAX_N]
+        groups = [("dense", args.precision, "dense", [p for p in pts if p["N"] > twa.RESIDENT_MAX_N]),
+                  ("resident", "fp32", "resident", small)]
+    results, times = {}, {}
+
+    def run_group(name, prec, route, gp, stream):
+        t0 = time.perf_counter()
+        results[name] = twa.batch_run(gp, M, seed=0, precision=prec, ws_route=route, stream=stream)
+        times[name] = time.perf_counter() - t0
+
+    streams = [None] * len(groups)
+    if len(groups) > 1:
+        import torch
+        streams = [torch.cuda.Stream() for _ in groups]
     t = time.perf_counter()
-    res, tiles = twa.batch_run(pts, M, seed=0, precision=args.precision)
+    th = [threading.Thread(target=run_group, args=(*g, s)) for g, s in zip(groups, streams)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
     t_batch = time.perf_counter() - t
+    res = []
+    for name, _, _, gp in groups:
+        res += results[name][0]
     line = {"study": "scan", "points": len(pts), "M": M, "T": args.T, "precision": args.precision,
-            "spin_traj_steps": units, "batched_seconds": t_batch, "batched_rate": units / t_batch,
-            "tiles": list(tiles), "nonfinite": sum(r["nonfinite"] for r in res)}
+            "small_route": args.small_route, "spin_traj_steps": units, "batched_seconds": t_batch,
+            "batched_rate": units / t_batch,
+            "groups": {name: {"points": len(gp), "precision": prec, "route": route, "seconds": times[name],
+                              "spin_traj_steps": sum(p["N"] * M * p["steps"] for p in gp),
+                              "tiles": list(results[name][1])} for name, prec, route, gp in groups},
+            "nonfinite": sum(r["nonfinite"] for r in res)}
     if args.sequential:
         t = time.perf_counter()
         for p in pts:
@@ -185,8 +219,9 @@ def scan_study(args):
                 g.sync()
         t_seq = time.perf_counter() - t
         line.update(sequential_seconds=t_seq, sequential_rate=units / t_seq, batch_speedup=t_seq / t_batch)
-    line["sample"] = [{k: res[i][k] for k in ("sigma_z", "SpSm", "g2", "w_tilde")} | {"N": pts[i]["N"],
-                      "alpha": pts[i]["alpha"], "w": pts[i]["w"]} for i in range(0, len(pts), 23)]
+    order = [p for _, _, _, gp in groups for p in gp]
+    line["sample"] = [{k: res[i][k] for k in ("sigma_z", "SpSm", "g2", "w_tilde")} | {"N": order[i]["N"],
+                      "alpha": order[i]["alpha"], "w": order[i]["w"]} for i in range(0, len(order), 23)]
     print(json.dumps(line), flush=True)
 
 
@@ -236,16 +271,17 @@ def phase_study(args, runner=None):
         wts = list(np.linspace(args.wt_min, args.wt_max, args.n_wt))
     cal = [dict(N=N, alpha=a, w=1.0, Gamma=1.0, dt=args.dt_scale / N, steps=1, window_start=0.0)
            for N in Ns for a in alphas]
-    res, _ = runner(cal, 8, seed=0, precision=args.precision)
+    route = getattr(args, "route", "dense")
+    res, _ = runner(cal, 8, seed=0, precision=args.precision, ws_route=route)
     w_max_unit = {(p["N"], p["alpha"]): r["w_max"] for p, r in zip(cal, res)}
     pts = phase_grid(Ns, alphas, wts, args.T, args.window, args.dt_scale, w_max_unit)
     t = time.perf_counter()
     res, tiles = runner([{k: v for k, v in p.items() if k != "wt"} for p in pts], args.M, seed=0,
-                        precision=args.precision)
+                        precision=args.precision, ws_route=route)
     secs = time.perf_counter() - t
     for d in phase_lines(pts, res):
         d.update(M=args.M, T=args.T, window=args.window, dt=args.dt_scale / d["N"], precision=args.precision,
-                 batch_seconds=secs, points_in_batch=len(pts), tiles=list(tiles))
+                 route=route, batch_seconds=secs, points_in_batch=len(pts), tiles=list(tiles))
         print(json.dumps(d), flush=True)
 
 
@@ -256,6 +292,8 @@ def main():
     s.add_argument("--T", type=float, default=0.02, help="horizon in 1/Gamma (the full scan is T = 1)")
     s.add_argument("--precision", default="bf16x3")
     s.add_argument("--sequential", action="store_true", help="also run the points one by one")
+    s.add_argument("--small-route", choices=["dense", "resident"], default="dense",
+                   help="route of the points with N <= 512")
     p = sub.add_parser("precision")
     p.add_argument("--M-ref", type=int, default=512)
     p.add_argument("--M-full", type=int, default=MIXED_N1024["M"])
@@ -273,6 +311,8 @@ def main():
     f.add_argument("--window", type=float, default=5.0, help="averaging window at the end of the run, 1/Gamma")
     f.add_argument("--dt-scale", type=float, default=0.02, help="dt = dt_scale / (Gamma N)")
     f.add_argument("--precision", default="bf16x3")
+    f.add_argument("--route", choices=["dense", "resident"], default="dense",
+                   help="resident: every point's run in one launch (FP32, N <= 512)")
     q = sub.add_parser("gradients")
     q.add_argument("--M", type=int, default=ADJOINT_N1024["M"])
     q.add_argument("--steps", type=int, default=0)

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libtwa.so")
 TWA_OK = 0
 ERRORS = {-1: "TWA_EINVAL", -2: "TWA_ENOTPSD", -3: "TWA_ENOMEM", -4: "TWA_ECUDA", -5: "TWA_ETIMEOUT",
           -6: "TWA_ENONFINITE", -7: "TWA_ESTATE", -8: "TWA_EUNSUPPORTED"}
-PRECISION = {"fp64": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "fp32": 4}
+PRECISION = {"fp64": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "fp32": 4, "bf16x2": 5, "bf16l2": 6}
 
 
 class TWAError(RuntimeError):
@@ -67,7 +67,8 @@ def _allocator(allocator):
             FREE_FN(lambda p, s, u: f(int(p), int(s or 0))))
 
 
-ROUTE = {"dense": 0, "fft": 1}
+ROUTE = {"dense": 0, "fft": 1, "resident": 2}
+RESIDENT_MAX_N = 512
 NOISE = {"cholesky": 0, "circulant": 1}
 INTEGRATOR = {"heun": 0, "midpoint": 1}
 
@@ -107,6 +108,20 @@ class Point(ctypes.Structure):
                 ("Gamma", ctypes.c_double), ("dt", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("window_start", ctypes.c_double), ("means", ctypes.c_void_p)]
 
+class CorrReq(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("prep_steps", ctypes.c_int64), ("lag_steps", ctypes.c_int64),
+                ("lag_stride", ctypes.c_int64), ("eps", ctypes.c_double), ("n_omega", ctypes.c_int64),
+                ("omega_max", ctypes.c_double)]
+
+
+class CorrOut(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("n_lags", ctypes.c_int64)] + \
+               [(n, ctypes.c_double) for n in ("dtau", "fwhm", "fwhm_se", "omega_peak", "S_peak", "spsm_tau0")]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -128,6 +143,7 @@ _SIGNATURES = {
     "twa_grad": (ctypes.c_int, [_P, ctypes.POINTER(GradReq), ctypes.POINTER(GradOut), _P]),
     "twa_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(Opts),
                                      _P, _P]),
+    "twa_correlation": (ctypes.c_int, [_P, ctypes.POINTER(CorrReq), ctypes.POINTER(CorrOut), _P, _P, _P, _P]),
     "twa_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "twa_wait_probe": (ctypes.c_int, [_P, ctypes.c_int64]),
     "twa_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -297,6 +313,30 @@ class TWA:
             d["per_traj"] = buf
         return d
 
+    def correlation(self, M, prep_steps, lag_steps, lag_stride, eps, n_omega, omega_max):
+        """Two-time correlation, spectrum and linewidth (twa_correlation).
+        Returns a dict: the twa_corr_out fields, "C" (complex [n_lags]),
+        "C_se" ([n_lags][2]), "S" ([n_omega]), "omega" ([n_omega]), "parts"
+        ([n_lags][8])."""
+        import numpy as np
+        r = CorrReq(int(M), int(prep_steps), int(lag_steps), int(lag_stride), float(eps), int(n_omega),
+                    float(omega_max))
+        # buffers sized for a valid request; the library rejects the others
+        n_lags = 1 + max(int(lag_steps), 0) // max(int(lag_stride), 1)
+        C = np.empty((n_lags, 2))
+        Cse = np.empty((n_lags, 2))
+        S = np.empty(max(int(n_omega), 1))
+        parts = np.empty((n_lags, 8))
+        o = CorrOut()
+        self._check(lib().twa_correlation(self._h, ctypes.byref(r), ctypes.byref(o), ctypes.c_void_p(C.ctypes.data),
+                                          ctypes.c_void_p(S.ctypes.data), ctypes.c_void_p(parts.ctypes.data),
+                                          ctypes.c_void_p(Cse.ctypes.data)))
+        d = o.as_dict()
+        d.update(C=C[:, 0] + 1j * C[:, 1], C_se=Cse, S=S, parts=parts,
+                 omega=np.array([-omega_max + j * (2.0 * omega_max / (n_omega - 1)) for j in range(n_omega - 1)]
+                                + [omega_max]))
+        return d
+
     def wait_probe(self, limit_us):
         """Enqueue one bounded device wait that runs out (twa_wait_probe); the
         next synchronising call raises TWA_ETIMEOUT."""
@@ -332,7 +372,7 @@ class TWA:
         self.close()
 
 
-PROF_KINDS = ("noise", "predict", "correct", "close", "gemm64", "elem64", "noise_factor")
+PROF_KINDS = ("noise", "predict", "correct", "close", "gemm64", "elem64", "noise_factor", "resident")
 
 
 def reduce_moments(means, N):
@@ -348,7 +388,7 @@ def reduce_moments(means, N):
 
 
 def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None, integrator="heun",
-              means=False):
+              means=False, ws_route="dense"):
     """twa_batch_run: points = list of dicts with N, alpha, w, Gamma, dt, steps,
     window_start. Returns (list of observables dicts, (BN, K-stage config));
     with means=True every dict also holds "means", the point's per-trajectory
@@ -364,6 +404,7 @@ def batch_run(points, M, seed=0, precision="bf16x3", stream=None, allocator=None
     lib().twa_opts_default(ctypes.byref(o))
     o.precision = PRECISION[precision]
     o.integrator = INTEGRATOR[integrator]
+    o.ws_route = ROUTE[ws_route]
     o.stream = _stream_handle(stream)
     alloc = _allocator(allocator)
     if alloc is not None:

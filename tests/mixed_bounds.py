@@ -55,10 +55,16 @@ class BF16NoiseOracle(TWAOracle):
         return xi_x, xi_y, bf16(eta_x), bf16(eta_y)
 
 
-def step_bound(o, sx, sy, sz):
-    """Bound, per trajectory and site, of the difference that one BF16X3 step
-    adds between the kernel and ``BF16NoiseOracle`` o, for the step o is about
-    to take from the state (sx, sy, sz)."""
+# representation error of a W.s product per precision: BF16X3 splits W and s
+# (three products: 3 2^-18); BF16X2 splits W but rounds s once to BF16
+# (2^-9 + 2^-18); BF16L2 rounds both (2 2^-9). L.eta is split in all three.
+W_REP = {"bf16x3": 3 * 2.0 ** -18, "bf16x2": 2.0 ** -9 + 2.0 ** -18, "bf16l2": 2 * 2.0 ** -9 + 2.0 ** -18}
+
+
+def step_bound(o, sx, sy, sz, prec="bf16x3"):
+    """Bound, per trajectory and site, of the difference that one step of the
+    mixed path (`prec`) adds between the kernel and ``BF16NoiseOracle`` o, for
+    the step o is about to take from the state (sx, sy, sz)."""
     N, dt, G = o.N, o.dt, o.Gamma
     xi_x, xi_y, ex, ey = TWAOracle.noise(o, o.t)          # unrounded FP64 normals
     absL, absW = np.abs(o.L), np.abs(o.W)
@@ -72,7 +78,7 @@ def step_bound(o, sx, sy, sz):
     # pump field at the state and at the predictor (|s~| <= |s| (1 + |b|))
     wsum = np.maximum(np.abs(sx) @ absW.T, np.abs(sy) @ absW.T)
     bmax = _field_size(o, sx, sy, sz)
-    dp = 0.5 * dt * (3 * 2.0 ** -18 + 2.0 ** -24 + acc) * wsum * (1.0 + bmax)
+    dp = 0.5 * dt * (W_REP[prec] + 2.0 ** -24 + acc) * wsum * (1.0 + bmax)
     dxi = math.sqrt(G * dt) * 2e-6 * max(np.max(np.abs(xi_x)), np.max(np.abs(xi_y)))
     db = dq + dp + dxi
     return 2.0 * math.sqrt(3.0) * (1.0 + bmax) * math.sqrt(2.0) * db + 8 * 2.0 ** -24 * math.sqrt(3.0)
@@ -85,7 +91,7 @@ def _field_size(o, sx, sy, sz):
     return float(np.max(np.hypot(bx, by)))
 
 
-def track(o_ref, run_gpu, steps):
+def track(o_ref, run_gpu, steps, prec="bf16x3"):
     """Advance the BF16-noise oracle and the kernel step by step; after step k
     check |kernel - oracle| <= 2 x (sum of the step bounds so far) element by
     element (the factor 2 covers the growth of earlier differences over a few
@@ -94,7 +100,7 @@ def track(o_ref, run_gpu, steps):
     tol = 0.0
     worst = 0.0
     for _ in range(steps):
-        tol = tol + step_bound(o_ref, o_ref.sx, o_ref.sy, o_ref.sz)
+        tol = tol + step_bound(o_ref, o_ref.sx, o_ref.sy, o_ref.sz, prec)
         o_ref.run(1)
         gx, gy, gz = run_gpu()
         err = np.maximum(np.maximum(np.abs(gx - o_ref.sx), np.abs(gy - o_ref.sy)), np.abs(gz - o_ref.sz))

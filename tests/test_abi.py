@@ -75,10 +75,10 @@ def test_init_rejects_bad_parameters(args, frag):
 
 def test_init_rejects_bad_options():
     with pytest.raises(twa.TWAError) as e:
-        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=7)
+        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=-1)
     assert e.value.code == -1
     with pytest.raises(twa.TWAError) as e:
-        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=5)          # one past TWA_PREC_FP32
+        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=7)          # one past TWA_PREC_BF16L2
     assert e.value.code == -1 and "precision" in str(e.value)
     with pytest.raises(twa.TWAError) as e:
         twa.TWA(4, 1.0, 1.0, 1.0, 0.1, integrator=2)
@@ -108,7 +108,8 @@ def test_precision_and_integrator_constants_match_the_header():
     val = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (TWA_\w+)\s+(-?\d+)", hdr)}
     assert twa.PRECISION == {"fp64": val["TWA_PREC_FP64"], "bf16": val["TWA_PREC_BF16"],
                              "bf16x3": val["TWA_PREC_BF16X3"], "tf32": val["TWA_PREC_TF32"],
-                             "fp32": val["TWA_PREC_FP32"]}
+                             "fp32": val["TWA_PREC_FP32"], "bf16x2": val["TWA_PREC_BF16X2"],
+                             "bf16l2": val["TWA_PREC_BF16L2"]}
     assert twa.INTEGRATOR == {"heun": val["TWA_INT_HEUN"], "midpoint": val["TWA_INT_MIDPOINT"]}
     import ctypes
     o = twa.Opts()

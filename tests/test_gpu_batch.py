@@ -67,6 +67,20 @@ def test_batch_equals_points_run_alone(tiles):
         assert math.isfinite(r["w_max"]) and r["nonfinite"] == 0
 
 
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16l2"])
+def test_batch_in_the_two_product_precisions_equals_points_run_alone(prec):
+    from paper_2608_10075_b300 import twa
+    M, seed = 64, 5
+    res, _ = twa.batch_run(POINTS, M, seed=seed, precision=prec)
+    for p, r in zip(POINTS, res):
+        with twa.TWA(p["N"], p["alpha"], p["w"], p["Gamma"], p["dt"], seed=seed, precision=prec,
+                     window_start=p["window_start"]) as g:
+            g.run(M, p["steps"])
+            ref = g.observables()
+        for k in ("Sz", "SpSm", "G2num", "g2", "Sz_se", "g2_se"):
+            assert abs(r[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (p, k, r[k], ref[k])
+
+
 def test_batch_with_the_midpoint_integrator_equals_points_run_alone():
     # the midpoint scheme's descriptors (corrector rotating s in place, predictor
     # writing the midpoint images) inside one batched plan

@@ -41,6 +41,10 @@ def _field_check(prec, N, K, alpha, w, seed=2):
     twa = _twa()
     rng = np.random.default_rng(seed)
     s = rng.choice([-1.0, 1.0], size=(K, N)) * rng.uniform(0.2, 1.7, size=(K, N))
+    if prec in ("bf16x2", "bf16l2"):
+        # these precisions round the operand once to BF16: give it exact BF16 values,
+        # so that the check is of the W representation and the accumulation
+        s = bf16(s)
     W = pump_matrix(N, alpha, w)
     with twa.TWA(N, alpha, w, 1.0, 1e-4, precision=prec) as g:
         P = g.field(torch.tensor(s, device="cuda")).cpu().numpy()
@@ -52,6 +56,8 @@ def _field_check(prec, N, K, alpha, w, seed=2):
         bound = 2.0 * (2 * 2.0 ** -11 + N * 2.0 ** -24) * absref
     elif prec == "fp32":
         bound = 2.0 * (3 * 2.0 ** -22 + 2.0 ** -24 + N * 2.0 ** -24) * absref
+    elif prec == "bf16x2":
+        bound = 2.0 * (2.0 ** -18 + 2.0 ** -24 + N * 2.0 ** -24) * absref
     else:
         bound = 2.0 * (2 * 2.0 ** -9 + N * 2.0 ** -24) * absref
     err = np.abs(P - ref)
@@ -59,7 +65,7 @@ def _field_check(prec, N, K, alpha, w, seed=2):
     return float(np.max(err / absref))
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2"])
 @pytest.mark.parametrize("N,K", [(16, 8), (300, 600), (129, 257), (1024, 512)])
 def test_field_contraction_bound(prec, N, K):
     # several 128-site row tiles and 256-row column tiles, with ragged tails
@@ -111,11 +117,12 @@ def _leta_bound(prec, N, absref):
     BF16 term 2^-9; TF32 2^-11; the FP32 split 2^-22) plus FP32 accumulation in
     N/16 instruction steps, with a factor of two of margin."""
     rep = {"bf16x3": 2.0 ** -18 + 2.0 ** -24, "bf16": 2.0 ** -9, "tf32": 2.0 ** -11,
-           "fp32": 2.0 ** -22 + 2.0 ** -24}[prec]
+           "fp32": 2.0 ** -22 + 2.0 ** -24, "bf16x2": 2.0 ** -18 + 2.0 ** -24,
+           "bf16l2": 2.0 ** -18 + 2.0 ** -24}[prec]
     return 2.0 * (rep + (N / 16.0) * 2.0 ** -22) * absref
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2"])
 @pytest.mark.parametrize("N,K", [(16, 8), (300, 600), (129, 257), (1024, 512)])
 def test_noise_factor_contraction_bound(prec, N, K):
     # the step's L.eta arithmetic alone (twa_contract, matrix L): BF16X3 takes L
@@ -132,7 +139,7 @@ def test_noise_factor_contraction_bound(prec, N, K):
     bound = _leta_bound(prec, N, absref)
     err = np.abs(P - ref)
     assert np.all(err <= bound + 1e-30), float(np.max(err / (absref + 1e-300)))
-    if prec == "bf16x3":
+    if prec in ("bf16x3", "bf16x2", "bf16l2"):
         # the bound resolves the lo image: L hi alone (a dropped lo term) breaks it
         planted = eta @ bf16(L).T
         assert np.mean(np.abs(planted - ref) > bound) > 0.1
@@ -160,17 +167,18 @@ def test_noise_factor_contraction_full_size_sampled():
     assert np.mean(np.abs(planted - ref) > bound) > 0.1
 
 
-def test_bf16x3_trajectories_track_bf16_noise_oracle():
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "bf16l2"])
+def test_split_noise_trajectories_track_bf16_noise_oracle(prec):
     # every entry of three consecutive steps within the derived per-step bound
     twa = _twa()
     for N, M in ((300, 200), (128, 128), (45, 3), (130, 257)):
         alpha, w, G, dt = 1.0, 8.0, 1.0, 2e-3
         o = BF16NoiseOracle(N, alpha, w, G, dt, 11, M)
-        with twa.TWA(N, alpha, w, G, dt, seed=11, precision="bf16x3") as g:
+        with twa.TWA(N, alpha, w, G, dt, seed=11, precision=prec) as g:
             def step():
                 g.run(M, 1)
                 return g.get_state()
-            worst = track(o, step, 3)
+            worst = track(o, step, 3, prec)
         assert worst <= 1.0
 
 
@@ -196,7 +204,7 @@ def test_trajectories_track_oracle_for_a_few_steps(prec, tol, N, M):
             assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 5e-6
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2"])
 def test_ensemble_observables_within_3se(prec):
     # N = 256, alpha = 1, w = 32, M = 512, dt = 1e-3, T = 1, window (0.5, 1]
     N, alpha, w, G, dt, M, T, t0 = 256, 1.0, 32.0, 1.0, 1e-3, 512, 1.0, 0.5

@@ -10,7 +10,7 @@ from paper_2608_10075_b300 import studies
 
 
 def _fake_runner(calls):
-    def run(points, M, seed=0, precision="bf16x3"):
+    def run(points, M, seed=0, precision="bf16x3", ws_route="dense"):
         calls.append((points, M))
         res = []
         for p in points:
