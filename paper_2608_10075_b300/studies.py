@@ -3,6 +3,8 @@
     python -m paper_2608_10075_b300.studies precision [--M-ref 512] [--steps S]
     python -m paper_2608_10075_b300.studies gradients [--M 2048] [--steps S]
     python -m paper_2608_10075_b300.studies phase [--Ns 100] [--alphas 0.5 1 2] [--T 15]
+    python -m paper_2608_10075_b300.studies linewidth [--N 500] [--alpha 1] [--wt 0.5]
+    python -m paper_2608_10075_b300.studies scan [--T 1.0] [--small-route resident]
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
@@ -103,7 +105,12 @@ def _observables(N, alpha, w, G, dt, steps, M, t0):
 
 
 def gradient_study(args):
-    c = ADJOINT_N1024
+    c = dict(ADJOINT_N1024)
+    # other sizes (e.g. N = 10^4, w = N Gamma / 4, dt = 2e-5) on request
+    for k in ("N", "w", "dt", "delta"):
+        v = getattr(args, k, None)
+        if v:
+            c[k] = type(c[k])(v)
     N, alpha, w, G, dt = c["N"], c["alpha"], c["w"], c["Gamma"], c["dt"]
     steps = args.steps or int(round(c["T"] / dt))
     t0 = 0.5 * steps * dt            # window: the second half of the run
@@ -165,9 +172,9 @@ def scan_study(args):
     """The 96-point scan (N in {100, 300, 1000, 3000}, six alpha, four w, M = 512,
     dt = 0.02 / (N Gamma)) over the horizon T (the workload's is 1 / Gamma).
     Throughput counts N M steps per point. With --small-route resident the
-    points with N <= 512 run as one resident batch (FP32, each CTA integrating
-    its trajectories for all steps in one launch) on a stream of their own,
-    concurrently with the dense batch of the larger points."""
+    points with N <= --resident-max-n run as one resident batch (FP32, each CTA
+    integrating its trajectories for all steps in one launch) on a stream of
+    their own, concurrently with the dense batch of the larger points."""
     import threading
 
     from .configs import SCAN_POINTS, scan_points
@@ -179,8 +186,9 @@ def scan_study(args):
     units = sum(p["N"] * M * p["steps"] for p in pts)
     groups = [("dense", args.precision, "dense", pts)]
     if args.small_route == "resident":
-        small = [p for p in pts if p["N"] <= twa.RESIDENT_MAX_N]
-        groups = [("dense", args.precision, "dense", [p for p in pts if p["N"] > twa.RESIDENT_MAX_N]),
+        # the resident route is faster only where the dense one is launch-bound
+        small = [p for p in pts if p["N"] <= args.resident_max_n]
+        groups = [("dense", args.precision, "dense", [p for p in pts if p["N"] > args.resident_max_n]),
                   ("resident", "fp32", "resident", small)]
     results, times = {}, {}
 
@@ -285,6 +293,32 @@ def phase_study(args, runner=None):
         print(json.dumps(d), flush=True)
 
 
+def linewidth_study(args):
+    """The linewidth of the main text ("Observables and method") at one phase point:
+    w from the target w~ (one calibration context: w_max is linear in w), a
+    preparation of T_prep, then the two-time correlation over T_meas from the
+    three trajectory copies (twa_correlation), its spectrum and FWHM."""
+    N, a, G = args.N, args.alpha, 1.0
+    dt = args.dt_scale / (G * N)
+    with twa.TWA(N, a, 1.0, G, dt, seed=0, precision=args.precision) as g:
+        g.run(8, 1)
+        wmax1 = g.observables()["w_max"]
+    w = args.wt * G * N / wmax1
+    prep = int(round(args.T_prep / dt))
+    lags = int(round(args.T_meas / dt))
+    stride = max(1, lags // args.n_lags)
+    t = time.perf_counter()
+    with twa.TWA(N, a, w, G, dt, seed=0, precision=args.precision, window_start=prep * dt) as g:
+        r = g.correlation(args.M, prep, lags, stride, args.eps, args.n_omega, args.omega_max)
+    secs = time.perf_counter() - t
+    out = {"study": "linewidth", "N": N, "alpha": a, "w_tilde": args.wt, "w": w, "dt": dt, "M": args.M,
+           "prep_steps": prep, "lag_steps": lags, "lag_stride": stride, "eps": args.eps, "precision": args.precision,
+           "fwhm": r["fwhm"], "fwhm_se": r["fwhm_se"], "omega_peak": r["omega_peak"], "S_peak": r["S_peak"],
+           "spsm_tau0": r["spsm_tau0"], "C_over_C0": [float(abs(c) / abs(r["C"][0])) for c in r["C"][::max(1, len(r["C"]) // 20)]],
+           "seconds": secs}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -293,7 +327,9 @@ def main():
     s.add_argument("--precision", default="bf16x3")
     s.add_argument("--sequential", action="store_true", help="also run the points one by one")
     s.add_argument("--small-route", choices=["dense", "resident"], default="dense",
-                   help="route of the points with N <= 512")
+                   help="route of the small points")
+    s.add_argument("--resident-max-n", type=int, default=128,
+                   help="largest N run on the resident route (<= 512)")
     p = sub.add_parser("precision")
     p.add_argument("--M-ref", type=int, default=512)
     p.add_argument("--M-full", type=int, default=MIXED_N1024["M"])
@@ -313,9 +349,26 @@ def main():
     f.add_argument("--precision", default="bf16x3")
     f.add_argument("--route", choices=["dense", "resident"], default="dense",
                    help="resident: every point's run in one launch (FP32, N <= 512)")
+    lw = sub.add_parser("linewidth")
+    lw.add_argument("--N", type=int, default=500)
+    lw.add_argument("--alpha", type=float, default=1.0)
+    lw.add_argument("--wt", type=float, default=0.5, help="target w~ = w_max / (Gamma N)")
+    lw.add_argument("--M", type=int, default=1024)
+    lw.add_argument("--T-prep", type=float, default=10.0)
+    lw.add_argument("--T-meas", type=float, default=5.0)
+    lw.add_argument("--dt-scale", type=float, default=0.05)
+    lw.add_argument("--n-lags", type=int, default=1000)
+    lw.add_argument("--eps", type=float, default=1e-2)
+    lw.add_argument("--n-omega", type=int, default=801)
+    lw.add_argument("--omega-max", type=float, default=20.0)
+    lw.add_argument("--precision", default="bf16x2")
     q = sub.add_parser("gradients")
     q.add_argument("--M", type=int, default=ADJOINT_N1024["M"])
     q.add_argument("--steps", type=int, default=0)
+    q.add_argument("--N", type=int, default=0, help="sites (default: the adjoint workload's 1024)")
+    q.add_argument("--w", type=float, default=0.0, help="pump prefactor (default N Gamma / 4 of the workload)")
+    q.add_argument("--dt", type=float, default=0.0)
+    q.add_argument("--delta", type=float, default=0.0, help="finite-difference step (default 1e-4)")
     a = ap.parse_args()
     if a.cmd == "precision":
         precision_study(a)
@@ -323,6 +376,8 @@ def main():
         phase_study(a)
     elif a.cmd == "scan":
         scan_study(a)
+    elif a.cmd == "linewidth":
+        linewidth_study(a)
     else:
         gradient_study(a)
 

@@ -4,8 +4,10 @@ central finite differences with common random numbers, through the C ABI.
 The FP64 GPU adjoint and the oracle tangent compute the same pathwise
 derivative of the same discretised trajectories, so they agree per trajectory
 to rounding (1e-8 relative here). The mixed-precision adjoint (FP32 tape,
-BF16X3 contractions) differs by its arithmetic only; over the short horizons
-tested it stays within 1e-2 of the FP64 result.
+BF16X3 contractions) differs by its arithmetic only: over the short horizons
+tested it stays within 1e-2 of the FP64 result, and the paired per-trajectory
+difference of the two (the precision error of the estimate) is checked to be a
+small fraction of the gradient's standard error.
 """
 import numpy as np
 import pytest
@@ -94,6 +96,24 @@ def test_mixed_adjoint_close_to_fp64(objective):
     for k in ("dJ_dw", "dJ_dalpha"):
         a, b = out["fp64"][k], out["bf16x3"][k]
         assert abs(a - b) <= 1e-2 * abs(a) + 3 * out["fp64"][k + "_se"] * 1e-2, (k, a, b)
+
+
+@pytest.mark.parametrize("objective", ["SpSm", "g2"])
+def test_mixed_adjoint_error_is_far_below_the_sampling_error(objective):
+    # per-trajectory gradient samples of the BF16X3 and FP64 adjoints on the same
+    # trajectories: their paired difference (the precision error) must be a small
+    # fraction of the standard error the gradient is quoted with
+    import math
+    twa = _twa()
+    N, alpha, w, G, dt, M, steps, t0 = 256, 1.0, 32.0, 1.0, 1e-3, 128, 40, 0.02
+    out = {}
+    for prec in ("fp64", "bf16x3"):
+        with twa.TWA(N, alpha, w, G, dt, seed=1, precision=prec, window_start=t0) as g:
+            out[prec] = g.grad(objective, M, steps, checkpoint=16, per_traj=True)
+    for col, k in ((0, "dJ_dw"), (1, "dJ_dalpha")):
+        d = out["bf16x3"]["per_traj"][:, col] - out["fp64"]["per_traj"][:, col]
+        paired, paired_se = abs(float(d.mean())), float(d.std(ddof=1) / math.sqrt(M))
+        assert paired + 3.0 * paired_se <= 0.2 * out["fp64"][k + "_se"], (k, paired, paired_se, out["fp64"][k + "_se"])
 
 
 def test_autograd_function_wraps_the_adjoint():
