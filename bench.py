@@ -404,7 +404,7 @@ def run_ours(args, rank, world, dist):
 
     # ---- sustained: a seconds-long block of steps under the power limit ----
     sustained = None
-    if not args.no_side:
+    if not args.no_sustained:
         ks = args.sustained_steps
         c4 = clocks.mark()
         a0 = torch.cuda.Event(enable_timing=True)
@@ -518,7 +518,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-side", action="store_true", help="skip the FFT-route, FP64-GPU and sustained legs")
+    ap.add_argument("--no-side", action="store_true", help="skip the FFT-route, other-precision and FP64-GPU legs")
+    ap.add_argument("--no-sustained", action="store_true", help="skip the seconds-long sustained leg")
     ap.add_argument("--no-precision-check", action="store_true",
                     help="skip the mixed-vs-FP64 comparison on a 128-trajectory subset")
     ap.add_argument("--sustained-steps", type=int, default=2500,

@@ -128,7 +128,11 @@ int time_batch(std::vector<twa_ctx*>& ctx, int steps, float* ms) {
 // Pick the fastest compiled tile configuration for this batch. Every context is
 // put back to its snapshot before returning, also when a trial fails.
 int autotune(std::vector<twa_ctx*>& ctx, int* bn, int* kc) {
-    const int cand[][2] = {{256, 1}, {192, 1}, {256, 0}, {128, 1}};
+    // the six-stage one-operand ring (KC = 3) is a candidate for the precisions
+    // with at most two products per entry
+    const bool one_b = ctx[0]->tc->terms <= 2 && ctx[0]->tc->lterms <= 2;
+    std::vector<std::pair<int, int>> cand = {{256, 1}, {192, 1}, {256, 0}, {128, 1}};
+    if (one_b) cand.push_back({256, 3});
     std::vector<Snapshot> snap(ctx.size());
     const int bn0 = *bn, kc0 = *kc;
     auto put_back = [&](int rc) {
@@ -145,7 +149,7 @@ int autotune(std::vector<twa_ctx*>& ctx, int* bn, int* kc) {
     }
     float best = INFINITY;
     for (auto& cd : cand) {
-        int rc = set_tiles_all(ctx, cd[0], cd[1]);
+        int rc = set_tiles_all(ctx, cd.first, cd.second);
         float ms = 0.f;
         if (!rc) rc = time_batch(ctx, 5, &ms);
         if (rc) {
@@ -155,8 +159,8 @@ int autotune(std::vector<twa_ctx*>& ctx, int* bn, int* kc) {
         }
         if (ms < best) {
             best = ms;
-            *bn = cd[0];
-            *kc = cd[1];
+            *bn = cd.first;
+            *kc = cd.second;
         }
     }
     const int rc = put_back(TWA_OK);

@@ -68,30 +68,40 @@ enum Mode { MODE_FIELD = 0, MODE_LETA = 1, MODE_PRED = 2, MODE_CORR = 3, MODE_MI
 // K-stage configurations: K tile width (elements), element size, swizzle and ring
 // depth. KC = 2 is the TF32 precision mode: FP32 containers holding TF32 values,
 // kind::tf32 MMAs (K = 8 per instruction, the same 32 bytes of a row as 16 BF16).
+// KC = 3 is KC = 1 for the precisions whose operand has no lo image (at most two
+// products per entry): a stage holds A hi, A lo and one B image, 32 KB instead of
+// 48 KB, so the ring is six stages deep in the same shared memory.
 template <int KC>
 struct KCfg;
 template <>
 struct KCfg<0> {   // 64 BF16 = 128 B rows, SWIZZLE_128B, two stages
     static constexpr int BK = 64, STAGES = 2, ESZ = 2;
-    static constexpr bool TF32 = false;
+    static constexpr bool TF32 = false, ONE_B = false;
     static constexpr uint64_t LAYOUT = 2;   // descriptor layout code of SWIZZLE_128B
     static constexpr uint32_t SBO = 1024;   // 8 rows x 128 B
 };
 template <>
 struct KCfg<1> {   // 32 BF16 = 64 B rows, SWIZZLE_64B, four stages
     static constexpr int BK = 32, STAGES = 4, ESZ = 2;
-    static constexpr bool TF32 = false;
+    static constexpr bool TF32 = false, ONE_B = false;
     static constexpr uint64_t LAYOUT = 4;   // SWIZZLE_64B
     static constexpr uint32_t SBO = 512;    // 8 rows x 64 B
 };
 template <>
 struct KCfg<2> {   // 16 TF32 = 64 B rows, SWIZZLE_64B, four stages
     static constexpr int BK = 16, STAGES = 4, ESZ = 4;
-    static constexpr bool TF32 = true;
+    static constexpr bool TF32 = true, ONE_B = false;
     static constexpr uint64_t LAYOUT = 4;
     static constexpr uint32_t SBO = 512;
 };
-inline int kcfg_bk(int kc) { return kc == 0 ? KCfg<0>::BK : kc == 1 ? KCfg<1>::BK : KCfg<2>::BK; }
+template <>
+struct KCfg<3> {   // 32 BF16 = 64 B rows, SWIZZLE_64B, six stages of A hi, A lo, B
+    static constexpr int BK = 32, STAGES = 6, ESZ = 2;
+    static constexpr bool TF32 = false, ONE_B = true;
+    static constexpr uint64_t LAYOUT = 4;
+    static constexpr uint32_t SBO = 512;
+};
+inline int kcfg_bk(int kc) { return kc == 0 ? KCfg<0>::BK : kc == 2 ? KCfg<2>::BK : KCfg<1>::BK; }
 // products per L.eta entry: one term, two (L hi + lo against the single BF16 eta
 // of BF16X3) or three (FP32 mode: eta split into TF32 hi + lo as well)
 inline int leta_terms(const TcState* t) { return t->lterms; }
@@ -102,7 +112,7 @@ struct Geo {
     static constexpr int A_BYTES = BM * BK * KCfg<KC>::ESZ;
     static constexpr int B_BYTES = BN * BK * KCfg<KC>::ESZ;
     static constexpr int MMAS = BK * KCfg<KC>::ESZ / 32;   // MMAs per stage: 32 bytes of K each
-    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + (KCfg<KC>::ONE_B ? 1 : 2) * B_BYTES;
     static constexpr int TILES = STAGES * STAGE_BYTES;
     static constexpr int NTRAJ = BN / 2;
     static constexpr int EXTRA = (2 * STAGES + 4) * 8 + 16 + NTRAJ * 2 * 4 * 2 + 4 * NTRAJ * 3 * 4;
@@ -404,8 +414,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 int64_t rt, ct;
                 int md, nt;
                 resolve(t, mp, ap, rt, ct, md, nt);
-                // operands of this tile: W/L hi (+ lo), B hi (+ lo)
-                const int na = (nt >= 2) ? 2 : 1, nb = (nt == 3) ? 2 : 1;
+                // operands of this tile: W/L hi (+ lo), B hi (+ lo; never in a
+                // one-B configuration, which the host uses for at most two products)
+                const int na = (nt >= 2) ? 2 : 1, nb = (nt == 3 && !KCfg<KC>::ONE_B) ? 2 : 1;
                 const uint32_t tx = na * G_::A_BYTES + nb * G_::B_BYTES;
                 if (grp.count && mp != prev) {
                     // descriptors written to global memory before the launch: make them
@@ -479,7 +490,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                         const uint32_t ko = kk * 32;   // 16 BF16 or 8 TF32 = 32 B along the swizzled row
                         mma_issue<TFM>(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b0 + ko), G_::IDESC,
                                  (kt > 0 || kk > 0) ? 1u : 0u);
-                        if (nt == 3) {
+                        if (nt == 3 && !KCfg<KC>::ONE_B) {
                             mma_issue<TFM>(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b1 + ko), G_::IDESC, 1u);
                             mma_issue<TFM>(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
                         }
@@ -1057,6 +1068,8 @@ int launch_cfg(twa_ctx* c, const TcMaps& maps, const TcArgs& a, const Group& grp
     TWA_TC_CASE(128, 0)
     TWA_TC_CASE(128, 1)
     TWA_TC_CASE(256, 2)
+    TWA_TC_CASE(256, 3)
+    TWA_TC_CASE(128, 3)
 #undef TWA_TC_CASE
     return set_error(c, TWA_EUNSUPPORTED, "tensor-core tile configuration not compiled");
 }
@@ -1139,20 +1152,27 @@ int tc_prepare(twa_ctx* c) {
         case TWA_PREC_BF16L2: t->terms = 1; t->lterms = 2; break;
         default: t->terms = 1; t->lterms = 1; break;
     }
-    // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1}.
-    // Default measured fastest at N = 10^4, M = 1024: 256-wide tiles, four 32-wide
-    // K stages (SWIZZLE_64B). The TF32 and FP32 precisions have one configuration:
-    // 256-wide tiles, four 16-wide FP32 K stages (KC = 2).
+    // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1, 3}
+    // (3: at most two products per entry, BN 128 or 256).
+    // Defaults measured fastest at N = 10^4, M = 1024: 256-wide tiles with 32-wide K
+    // stages (SWIZZLE_64B), six stages of one operand image for the precisions with
+    // at most two products (same-box A/B, BF16X2: 2-3.5 % faster per step at a
+    // 6 % lower power-capped clock than four stages), four stages otherwise. The
+    // TF32 and FP32 precisions have one configuration: 256-wide tiles, four 16-wide
+    // FP32 K stages (KC = 2).
     const bool tf32 = c->opts.precision == TWA_PREC_TF32 || c->opts.precision == TWA_PREC_FP32;
     if (tf32 && (getenv("TWA_TC_BN") || getenv("TWA_TC_KC")))
         return set_error(c, TWA_EINVAL, "TWA_TC_BN / TWA_TC_KC do not apply to the TF32 and FP32 precisions");
     t->bn = tf32 ? 256 : env_int("TWA_TC_BN", 256);
-    t->kc = tf32 ? 2 : env_int("TWA_TC_KC", 1);
+    t->kc = tf32 ? 2 : env_int("TWA_TC_KC", (t->terms <= 2 && t->lterms <= 2) ? 3 : 1);
     // TWA_SEPARATE_LETA=1: dense step as separate noise, L.eta, predictor and
     // corrector launches instead of the two mixed launches (same results)
     t->separate_leta = env_int("TWA_SEPARATE_LETA", 0) != 0;
-    if (!tf32 && (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1)))
-        return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0 or 1");
+    if (!tf32 && (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1 || t->kc == 3)))
+        return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0, 1 or 3");
+    if (t->kc == 3 && t->bn == 192 && !getenv("TWA_TC_KC")) t->kc = 1;   // no six-stage 192-wide build
+    if (t->kc == 3 && (t->terms > 2 || t->lterms > 2 || t->bn == 192))
+        return set_error(c, TWA_EINVAL, "TWA_TC_KC = 3 holds one operand image: at most two products, BN 128 or 256");
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
         t->num_sms = sms;
@@ -1847,13 +1867,13 @@ int tc_batch_step(twa_ctx* lead, TcBatch* b, int64_t t) {
     return TWA_OK;
 }
 
-// Change the tile configuration of a context (re-encodes its tensor maps).
 int wait_probe(twa_ctx* c, int64_t limit_ns) {
     k_wait_probe<<<1, 32, 0, c->stream>>>(c->d_flags, (unsigned long long)limit_ns);
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }
 
+// Change the tile configuration of a context (re-encodes its tensor maps).
 int tc_set_tiles(twa_ctx* c, int bn, int kc) {
     TcState* t = c->tc;
     mix_free(t);   // its descriptors and the captured steps hold the old tensor maps

@@ -58,7 +58,7 @@ def test_batch_equals_points_run_alone(tiles):
     if tiles:
         assert cfg == (int(tiles[0]), int(tiles[1]))
     else:
-        assert cfg in ((256, 1), (192, 1), (256, 0), (128, 1))
+        assert cfg in ((256, 1), (192, 1), (256, 0), (128, 1))   # BF16X3: no six-stage candidate
     for p, r in zip(POINTS, res):
         ref = _alone(p, M, seed)
         assert r["steps"] == p["steps"] and r["samples"] == ref["samples"]

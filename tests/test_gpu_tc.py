@@ -301,3 +301,25 @@ def test_tf32_modes_reject_what_they_do_not_cover(prec, monkeypatch):
     with pytest.raises(twa.TWAError) as e:
         twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision=prec)
     assert e.value.name == "TWA_EINVAL"
+
+
+def test_six_stage_ring_gives_the_same_bits(monkeypatch):
+    # TWA_TC_KC = 3 (six stages of A hi, A lo and one operand image) issues the same
+    # MMAs in the same K order as the four-stage ring: identical states and sums
+    twa = _twa()
+    N, M = 300, 200
+    out = {}
+    for kc in ("1", "3"):
+        monkeypatch.setenv("TWA_TC_KC", kc)
+        for prec in ("bf16x2", "bf16l2", "bf16"):
+            with twa.TWA(N, 1.0, 8.0, 1.0, 2e-3, seed=3, precision=prec, window_start=0.004) as g:
+                g.run(M, 6)
+                out[kc, prec] = (g.get_state(), g.moments())
+    for prec in ("bf16x2", "bf16l2", "bf16"):
+        for a, b in zip(out["1", prec][0], out["3", prec][0]):
+            assert np.array_equal(a, b), prec
+        assert np.array_equal(out["1", prec][1], out["3", prec][1]), prec
+    monkeypatch.setenv("TWA_TC_KC", "3")
+    with pytest.raises(twa.TWAError) as e:
+        twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="bf16x3")
+    assert e.value.name == "TWA_EINVAL"
