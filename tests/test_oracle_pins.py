@@ -239,6 +239,50 @@ def test_twa_close_to_exact_at_weak_pump():
     assert ob["Sz"] > -0.5 * N
 
 
+@pytest.mark.parametrize("alpha", [0.5, 2.0])
+def test_direct_steady_state_equals_time_evolution(alpha):
+    # the reduced direct solve (popcount sector, real symmetric unknowns) against
+    # the long-time limit of the full dense superoperator, a method with neither
+    # reduction; and the sparse superoperator equals the dense one term for term
+    N, w = 4, 0.7
+    W = pump_matrix(N, alpha, w)
+    assert np.array_equal(lb.liouvillian_sparse(N, W, 1.0).toarray(), lb.liouvillian(N, W, 1.0))
+    a = lb.steady_state_unique(N, W, 1.0)
+    b = lb.steady_state(N, W, 1.0, T=400.0)
+    assert np.max(np.abs(a - b)) < 1e-10
+    with pytest.raises(ValueError):
+        lb.steady_state_unique(N, pump_matrix(N, 0.0, w), 1.0)   # collective pump: not unique
+
+
+def test_direct_steady_state_n8_is_a_stationary_density_matrix():
+    N = 8
+    W = pump_matrix(N, 1.0, 0.5)
+    rho = lb.steady_state_unique(N, W, 1.0)
+    L = lb.liouvillian_sparse(N, W, 1.0)
+    res = L @ rho.reshape(-1, order="F")
+    assert np.max(np.abs(res)) < 1e-12 * abs(L).max()
+    assert abs(np.trace(rho) - 1.0) < 1e-12
+    assert np.linalg.eigvalsh(rho).min() > -1e-12
+    ex = lb.expectations(rho, N)
+    # between the empty state (S^z = -N) and the normalised pump's weak-pump regime
+    assert -N < ex["Sz"] < 0.0 and ex["SpSm"] > 0.0
+
+
+def test_twa_close_to_exact_at_weak_pump_n8():
+    # N = 8 (the largest brute-force case): TWA against the exact steady state in
+    # the weak-pump regime; observed TWA errors 2.3 % (S^z), 0.6 % (<S+S->), 2.7 %
+    # (g2) with 2048 trajectories, so the tolerances leave a margin, not a
+    # standard-error bound
+    N, alpha, w = 8, 1.0, 0.5
+    ex = lb.expectations(lb.steady_state_unique(N, pump_matrix(N, alpha, w), 1.0), N)
+    o = TWAOracle(N, alpha, w, 1.0, 0.01, 23, 1024, init_sz=-1.0, window_start=20.0)
+    o.run(6000)
+    ob = o.observables()
+    assert abs(ob["Sz"] - ex["Sz"]) < 0.06 * abs(ex["Sz"]) + 3 * ob["Sz_se"]
+    assert abs(ob["SpSm"] - ex["SpSm"]) < 0.03 * abs(ex["SpSm"]) + 3 * ob["SpSm_se"]
+    assert abs(ob["g2"] - ex["g2"]) < 0.05 * abs(ex["g2"]) + 3 * ob["g2_se"]
+
+
 def test_special_cases():
     # No decay and no pump: the state never moves.
     o = TWAOracle(5, 1.0, 0.0, 0.0, 0.01, 2, 16, init_sz=-1.0)
