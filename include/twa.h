@@ -390,8 +390,12 @@ typedef struct twa_point {
  * points that run in the stage with the most work (steps x N^2 of the points
  * still running; the state is saved and restored around the trials) and keeps
  * the fastest. tiles: NULL or int[2] receiving the chosen (BN, K-stage config:
- * 0 = two 64-wide stages, 1 = four 32-wide stages, 3 = six 32-wide stages with
- * one operand image, for the precisions with at most two products per entry).
+ * 0 = 64-wide stages of four operand images, 1 = 32-wide stages of four
+ * images, 3 = 32-wide stages of one operand image and 4 = 64-wide stages of
+ * one operand image, the last two for the precisions with at most two products
+ * per entry). With 256-wide tiles the BF16 precisions run on CTA pairs (two
+ * CTAs of a cluster share each 256-row tile; TWA_TC_PAIR=0 turns this off);
+ * every configuration gives the same results bit for bit.
  * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (a precision other than BF16, BF16X3,
  * BF16X2 and BF16L2), plus those of twa_init and twa_sync. Synchronises. */
 TWA_API int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,

@@ -128,11 +128,15 @@ int time_batch(std::vector<twa_ctx*>& ctx, int steps, float* ms) {
 // Pick the fastest compiled tile configuration for this batch. Every context is
 // put back to its snapshot before returning, also when a trial fails.
 int autotune(std::vector<twa_ctx*>& ctx, int* bn, int* kc) {
-    // the six-stage one-operand ring (KC = 3) is a candidate for the precisions
-    // with at most two products per entry
+    // the one-operand rings (KC = 3, 4) are candidates for the precisions with at
+    // most two products per entry
     const bool one_b = ctx[0]->tc->terms <= 2 && ctx[0]->tc->lterms <= 2;
     std::vector<std::pair<int, int>> cand = {{256, 1}, {192, 1}, {256, 0}, {128, 1}};
-    if (one_b) cand.push_back({256, 3});
+    if (ctx[0]->tc->pair) cand = {{256, 0}, {256, 1}};   // the configurations compiled for CTA pairs (default)
+    if (one_b) {
+        cand.push_back({256, 3});
+        cand.push_back({256, 4});
+    }
     std::vector<Snapshot> snap(ctx.size());
     const int bn0 = *bn, kc0 = *kc;
     auto put_back = [&](int rc) {

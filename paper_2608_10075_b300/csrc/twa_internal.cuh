@@ -39,7 +39,9 @@ struct TcState {
     int terms = 3;                               // products per W entry: 1 (BF16, BF16L2, TF32), 2 (BF16X2), 3 (BF16X3, FP32)
     int lterms = 2;                              // products per L entry: 1 (BF16, TF32), 2, 3 (FP32)
     int bn = 256, kc = 0;                        // tile width and K-stage configuration
+    int pair = 0;                                // CTA pairs: 256-row tiles on clusters of two (cta_group::2)
     int num_sms = 148;
+    int clusters = 0;                            // resident clusters of two of the pair kernel
     __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
     float *X = nullptr, *Y = nullptr, *Z = nullptr;       // state [M][N]
     float *Xp = nullptr, *Yp = nullptr, *Zp = nullptr;    // predictor

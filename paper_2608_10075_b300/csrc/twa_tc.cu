@@ -101,16 +101,50 @@ struct KCfg<3> {   // 32 BF16 = 64 B rows, SWIZZLE_64B, six stages of A hi, A lo
     static constexpr uint64_t LAYOUT = 4;
     static constexpr uint32_t SBO = 512;
 };
-inline int kcfg_bk(int kc) { return kc == 0 ? KCfg<0>::BK : kc == 2 ? KCfg<2>::BK : KCfg<1>::BK; }
+template <>
+struct KCfg<4> {   // 64 BF16 = 128 B rows, SWIZZLE_128B, three stages of A hi, A lo, B
+    static constexpr int BK = 64, STAGES = 3, ESZ = 2;
+    static constexpr bool TF32 = false, ONE_B = true;
+    static constexpr uint64_t LAYOUT = 2;
+    static constexpr uint32_t SBO = 1024;
+};
+// Pair-CTA configurations: the two CTAs of a cluster share one 256-row MMA
+// (tcgen05.mma.cta_group::2). Each holds the A rows of its own 128-row tile and
+// half of the B rows, so a B image takes half the bytes of a stage and the ring
+// is deeper in the same shared memory: A hi, A lo, B hi, B lo halves in six
+// stages (KC = 1), A hi, A lo and one B half in eight (KC = 3).
+template <int KC, bool PAIR>
+struct RingDepth {
+    static constexpr int value = KCfg<KC>::STAGES;
+};
+template <>
+struct RingDepth<1, true> {
+    static constexpr int value = 6;
+};
+template <>
+struct RingDepth<3, true> {
+    static constexpr int value = 8;
+};
+template <>
+struct RingDepth<4, true> {   // 3 x 16 KB
+    static constexpr int value = 4;
+};
+template <>
+struct RingDepth<0, true> {   // 4 x 16 KB
+    static constexpr int value = 3;
+};
+inline int kcfg_bk(int kc) { return (kc == 0 || kc == 4) ? 64 : kc == 2 ? KCfg<2>::BK : KCfg<1>::BK; }
 // products per L.eta entry: one term, two (L hi + lo against the single BF16 eta
 // of BF16X3) or three (FP32 mode: eta split into TF32 hi + lo as well)
 inline int leta_terms(const TcState* t) { return t->lterms; }
 
-template <int BN, int KC>
+template <int BN, int KC, bool PAIR = false>
 struct Geo {
-    static constexpr int BK = KCfg<KC>::BK, STAGES = KCfg<KC>::STAGES;
+    static constexpr int BK = KCfg<KC>::BK, STAGES = RingDepth<KC, PAIR>::value;
+    static constexpr int BROWS = PAIR ? BN / 2 : BN;   // B rows one CTA holds
+    static constexpr int MROWS = PAIR ? 2 * BM : BM;   // M of the MMA
     static constexpr int A_BYTES = BM * BK * KCfg<KC>::ESZ;
-    static constexpr int B_BYTES = BN * BK * KCfg<KC>::ESZ;
+    static constexpr int B_BYTES = BROWS * BK * KCfg<KC>::ESZ;
     static constexpr int MMAS = BK * KCfg<KC>::ESZ / 32;   // MMAs per stage: 32 bytes of K each
     static constexpr int STAGE_BYTES = 2 * A_BYTES + (KCfg<KC>::ONE_B ? 1 : 2) * B_BYTES;
     static constexpr int TILES = STAGES * STAGE_BYTES;
@@ -120,10 +154,10 @@ struct Geo {
     static constexpr uint32_t NCOLS = (2 * BN <= 256) ? 256 : 512;
     // instruction descriptor: D = F32 (bits 4-5 = 1), A and B format at bits 7-9 and
     // 10-12 (kind::f16: BF16 = 1; kind::tf32: TF32 = 2), both K-major, N >> 3 at
-    // bits 17-22, M >> 4 at bits 24-28.
+    // bits 17-22, M >> 4 at bits 24-28 (M = 256 for a CTA pair).
     static constexpr uint32_t FMT = KCfg<KC>::TF32 ? 2u : 1u;
     static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                      ((uint32_t)(BM >> 4) << 24);
+                                      ((uint32_t)(MROWS >> 4) << 24);
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -147,28 +181,42 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// CL: acquire at cluster scope, for a barrier that threads of the peer CTA
+// arrive on remotely
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
+    if constexpr (CL) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+    }
     return ok != 0;
 }
 
 // Wait for the phase with the given parity; gives up after WAIT_NS (or at once
 // when another CTA has already given up and `follow_abort` is set), counting the
 // timeout in flags[FLAG_TIMEOUT].
+template <bool CL = false>
 __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long* flags,
                                        bool follow_abort, unsigned long long limit_ns = WAIT_NS) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try<CL>(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     volatile unsigned long long* vf = flags;
     while (true) {
-        if (mbar_try(bar, parity)) return true;
+        if (mbar_try<CL>(bar, parity)) return true;
         if (follow_abort && vf[FLAG_TIMEOUT] != 0ull) return false;
         if (gtimer() - t0 > limit_ns) {
             atomicAdd(&flags[FLAG_TIMEOUT], 1ull);
@@ -182,6 +230,61 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
             smem_u32(dst)),
         "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// ---- CTA pairs (clusters of two) ----
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the variable at p in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+    return a;
+}
+
+// every thread of both CTAs; orders shared-memory accesses across the pair
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion is counted on a
+// barrier of either CTA of the pair (the leader's: its MMA reads both halves)
+__device__ __forceinline__ void tma_load_pair(void* dst, const CUtensorMap* map, uint32_t cluster_bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(cluster_bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// 256-row MMA of the pair, issued by the leader: A rows 0-127 and B rows 0..N/2-1
+// from the leader's shared memory, the rest from the peer's at the same offsets;
+// D rows 0-127 into the leader's TMEM, 128-255 into the peer's
+__device__ __forceinline__ void mma_issue_pair(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtm),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// arrive on the barrier at this offset in both CTAs once the pair's MMAs issued
+// so far are complete
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
         : "memory");
 }
 
@@ -304,10 +407,15 @@ struct Group {
     int ctas = 0;   // grid of a scheduled launch
 };
 
-template <int MODE, int NT, int BN, int KC>
+// PAIR: launched in clusters of two CTAs that share each 256-row tile (row tiles
+// 2r and 2r + 1 of row unit r): both stream their own A rows and half of the B
+// rows, the leader (rank 0) issues the cta_group::2 MMAs, and each runs the
+// epilogue of its own 128 rows from its own TMEM.
+template <int MODE, int NT, int BN, int KC, bool PAIR = false>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMaps maps, const TcArgs args,
                                                    const Group grp) {
-    using G_ = Geo<BN, KC>;
+    using G_ = Geo<BN, KC, PAIR>;
+    static_assert(!(PAIR && KCfg<KC>::TF32), "CTA pairs run the BF16 configurations");
     constexpr int BK = G_::BK, STAGES = G_::STAGES, NTRAJ = G_::NTRAJ;
     constexpr bool TFM = KCfg<KC>::TF32;   // TF32 mode: kind::tf32 MMAs, FP32-container images
     extern __shared__ uint8_t smem_raw[];
@@ -322,13 +430,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
     float* red = sS + 2 * NTRAJ * 2;             // [4][NTRAJ][3]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // scheduling unit: the CTA, or the cluster of a pair (both CTAs walk its list)
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const int64_t unit = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+    const int64_t units = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
+    // row tiles are handed out in row units: one 128-row tile, or two for a pair
+    auto row_units = [](int64_t n_rt) -> int64_t { return PAIR ? (n_rt + 1) >> 1 : n_rt; };
     // flat tile list: one problem, or the problems of the group one after another
-    const int64_t ntiles = grp.count ? grp.start[grp.count] : args.n_rt * ((args.n_vec + BN - 1) / BN);
-    // this CTA's tiles: the k-th is tile_of(k), k < n_mine
-    const int64_t n_mine = grp.sched ? (int64_t)(grp.sched_start[blockIdx.x + 1] - grp.sched_start[blockIdx.x])
-                                     : ((int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+    const int64_t ntiles = grp.count ? grp.start[grp.count] : row_units(args.n_rt) * ((args.n_vec + BN - 1) / BN);
+    // this unit's tiles: the k-th is tile_of(k), k < n_mine
+    const int64_t n_mine = grp.sched ? (int64_t)(grp.sched_start[unit + 1] - grp.sched_start[unit])
+                                     : (unit < ntiles ? (ntiles - 1 - unit) / units + 1 : 0);
     auto tile_of = [&](int64_t k) -> int64_t {
-        return grp.sched ? (int64_t)grp.sched[grp.sched_start[blockIdx.x] + k] : (int64_t)blockIdx.x + k * gridDim.x;
+        return grp.sched ? (int64_t)grp.sched[grp.sched_start[unit] + k] : unit + k * units;
     };
     // problem of flat tile t, the tile's (row tile, trajectory tile) within it, and
     // its mode and term count (the template's, except in MODE_MIX launches)
@@ -362,9 +476,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
         const int64_t nct = (ap->n_vec + BN - 1) / BN;
         rt = tl / nct;
         ct = tl - rt * nct;
-        // L.eta: row tile r needs 2r + 2 K stages (triangular L); hand out the
+        // L.eta: row unit r needs (r + 1) M-rows of K (triangular L); hand out the
         // longest tiles first so the persistent CTAs finish together
-        if (md == MODE_LETA) rt = ap->n_rt - 1 - rt;
+        if (md == MODE_LETA) rt = row_units(ap->n_rt) - 1 - rt;
     };
 
     if (threadIdx.x == 0) {
@@ -374,24 +488,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], EPI_WARPS);
+            // a pair's accumulator is free once the epilogues of both CTAs drained it
+            mbar_init(&tempty[b], PAIR ? 2 * EPI_WARPS : EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(G_::NCOLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        // a pair allocates collectively: the same columns in both CTAs' TMEM
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(G_::NCOLS));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(G_::NCOLS));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync();   // both CTAs' barriers initialised before any cross-CTA arrival
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
     auto k_tiles = [&](const TcArgs* ap, int64_t rt, int md) -> int {
         const int nk = (int)((ap->N + BK - 1) / BK);
         if (md != MODE_LETA) return nk;
-        const int k1 = (int)((rt * BM + BM + BK - 1) / BK);   // L is lower triangular
+        const int k1 = (int)(((rt + 1) * G_::MROWS + BK - 1) / BK);   // L is lower triangular (rt: row unit)
         return k1 < nk ? k1 : nk;
     };
 
@@ -426,20 +551,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ms[k]) : "memory");
                     prev = mp;
                 }
-                const int y_a = (int)(rt * BM), y_b = (int)(ct * BN);
+                // a pair's CTA: its own row tile of the unit, its half of the B rows
+                const int y_a = (int)((PAIR ? 2 * rt + rank : rt) * BM);
+                const int y_b = (int)(ct * BN + (PAIR ? rank * (BN / 2) : 0));
                 const int nkt = k_tiles(ap, rt, md);
                 for (int kt = 0; kt < nkt; ++kt) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u, args.flags, true)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&full[stage], tx);
                     uint8_t* st = tiles + stage * G_::STAGE_BYTES;
                     const int kx = kt * BK;
-                    tma_load(st, &mp->a0, &full[stage], kx, y_a);
-                    if (na == 2) tma_load(st + G_::A_BYTES, &mp->a1, &full[stage], kx, y_a);
-                    tma_load(st + 2 * G_::A_BYTES, &mp->b0, &full[stage], kx, y_b);
-                    if (nb == 2) tma_load(st + 2 * G_::A_BYTES + G_::B_BYTES, &mp->b1, &full[stage], kx, y_b);
+                    if constexpr (PAIR) {
+                        // both CTAs' copies complete on the leader's barrier, which
+                        // expects the bytes of the two
+                        if (rank == 0) mbar_expect_tx(&full[stage], 2 * tx);
+                        const uint32_t fb = cluster_addr(&full[stage], 0);
+                        tma_load_pair(st, &mp->a0, fb, kx, y_a);
+                        if (na == 2) tma_load_pair(st + G_::A_BYTES, &mp->a1, fb, kx, y_a);
+                        tma_load_pair(st + 2 * G_::A_BYTES, &mp->b0, fb, kx, y_b);
+                        if (nb == 2) tma_load_pair(st + 2 * G_::A_BYTES + G_::B_BYTES, &mp->b1, fb, kx, y_b);
+                    } else {
+                        mbar_expect_tx(&full[stage], tx);
+                        tma_load(st, &mp->a0, &full[stage], kx, y_a);
+                        if (na == 2) tma_load(st + G_::A_BYTES, &mp->a1, &full[stage], kx, y_a);
+                        tma_load(st + 2 * G_::A_BYTES, &mp->b0, &full[stage], kx, y_b);
+                        if (nb == 2) tma_load(st + 2 * G_::A_BYTES + G_::B_BYTES, &mp->b1, &full[stage], kx, y_b);
+                    }
                     issued[stage] = true;
                     last_ph[stage] = (int)ph;
                     if (++stage == STAGES) {
@@ -450,13 +588,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             }
             if (!ok) {
                 // let copies already in flight land before the CTA can exit
-                for (int s = 0; s < STAGES; ++s)
-                    if (issued[s]) mbar_wait(&full[s], (uint32_t)last_ph[s], args.flags, false);
+                if (PAIR && rank == 1) {
+                    // they complete on the leader's barriers, which this CTA cannot
+                    // wait on: give them a bounded time (a copy takes microseconds)
+                    const uint64_t t0 = gtimer();
+                    while (gtimer() - t0 < 200000ull) {
+                    }
+                } else {
+                    for (int s = 0; s < STAGES; ++s)
+                        if (issued[s]) mbar_wait(&full[s], (uint32_t)last_ph[s], args.flags, false);
+                }
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
+        // ---------------- MMA issuer (a pair's leader only) ----------------
+        // one MMA: this CTA's (cta_group::1), or the pair's 256-row one
+        auto issue = [&](uint32_t dcol, uint64_t ad, uint64_t bd, uint32_t acc) {
+            if constexpr (PAIR) mma_issue_pair(dcol, ad, bd, G_::IDESC, acc);
+            else mma_issue<TFM>(dcol, ad, bd, G_::IDESC, acc);
+        };
+        auto commit = [&](uint64_t* bar) {
+            if constexpr (PAIR) mma_commit_pair(bar);   // both CTAs' barriers
+            else mma_commit(bar);
+        };
+        if (lane == 0 && (!PAIR || rank == 0)) {
             uint32_t stage = 0, ph = 0;
             bool ok = true;
             int it = 0, last_b = -1;
@@ -465,7 +620,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 const int64_t t = tile_of(k);
                 const int b = it & 1;
                 const uint32_t use = (uint32_t)(it >> 1);
-                if (!mbar_wait(&tempty[b], (use & 1u) ^ 1u, args.flags, true)) {
+                if (!mbar_wait<PAIR>(&tempty[b], (use & 1u) ^ 1u, args.flags, true)) {
                     ok = false;
                     break;
                 }
@@ -488,21 +643,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
 #pragma unroll
                     for (int kk = 0; kk < G_::MMAS; ++kk) {
                         const uint32_t ko = kk * 32;   // 16 BF16 or 8 TF32 = 32 B along the swizzled row
-                        mma_issue<TFM>(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b0 + ko), G_::IDESC,
-                                 (kt > 0 || kk > 0) ? 1u : 0u);
+                        issue(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b0 + ko), (kt > 0 || kk > 0) ? 1u : 0u);
                         if (nt == 3 && !KCfg<KC>::ONE_B) {
-                            mma_issue<TFM>(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b1 + ko), G_::IDESC, 1u);
-                            mma_issue<TFM>(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
+                            issue(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b1 + ko), 1u);
+                            issue(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), 1u);
                         }
-                        if (nt == 2) mma_issue<TFM>(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), G_::IDESC, 1u);
+                        if (nt == 2) issue(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), 1u);
                     }
-                    mma_commit(&empty[stage]);
+                    commit(&empty[stage]);
                     if (++stage == STAGES) {
                         stage = 0;
                         ph ^= 1u;
                     }
                 }
-                mma_commit(&tfull[b]);   // this tile's accumulator is complete (or drained, after an abort)
+                commit(&tfull[b]);   // this tile's accumulator is complete (or drained, after an abort)
                 last_b = b;
                 last_par = use & 1u;
             }
@@ -524,6 +678,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             int64_t rt, ct;
             int md, nt;
             resolve(t, mp_, ap_, rt, ct, md, nt);
+            if constexpr (PAIR) rt = 2 * rt + rank;   // this CTA's row tile of the unit
             const TcArgs& args = *ap_;        // this tile's problem (shadows the launch argument)
             const int64_t M = args.M;
             // every rounding of the epilogue is spelled out (fmaf, __fmul_rn,
@@ -698,7 +853,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             // accumulator b may be overwritten by the next tile's MMAs
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (lane == 0) {
+                if (PAIR && rank == 1) mbar_arrive_cluster(cluster_addr(&tempty[b], 0));   // the leader's
+                else mbar_arrive(&tempty[b]);
+            }
             if (md == MODE_CORR) {
                 const unsigned tot = __reduce_add_sync(0xffffffffu, nonfinite);
                 if (lane == 0 && tot) atomicAdd(&args.flags[FLAG_NONFINITE], (unsigned long long)tot);
@@ -708,7 +866,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 epi_sync();   // every epilogue thread, live or not
                 for (int j = et; j < NTRAJ; j += EPI_THREADS) {
                     const int64_t m = m0 + j;
-                    if (!live || m >= M) continue;
+                    // (a pair's second row tile may lie past the last one)
+                    if (!live || m >= M || rt >= args.n_rt) continue;
                     float4 o;
                     o.x = red[(0 * NTRAJ + j) * 3] + red[(1 * NTRAJ + j) * 3] + red[(2 * NTRAJ + j) * 3] +
                           red[(3 * NTRAJ + j) * 3];
@@ -723,9 +882,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
         }
     }
     __syncthreads();
+    // no CTA of a pair leaves while the other may still reach its shared memory
+    if constexpr (PAIR) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G_::NCOLS));
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G_::NCOLS));
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G_::NCOLS));
     }
 }
 
@@ -1033,24 +1197,82 @@ int make_map(twa_ctx* c, CUtensorMap* map, const void* base, int64_t rows, int64
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                     const_cast<void*>(base), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, kc == 0 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    (kc == 0 || kc == 4) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(c, TWA_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return TWA_OK;
 }
 
-template <int MODE, int NT, int BN, int KC>
+template <int MODE, int NT, int BN, int KC, bool PAIR>
 int launch_one(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_tiles, const Group& grp) {
-    auto kern = k_tc<MODE, NT, BN, KC>;
+    auto kern = k_tc<MODE, NT, BN, KC, PAIR>;
+    constexpr int smem = Geo<BN, KC, PAIR>::SMEM;
     static std::atomic<bool> attr{false};   // contexts may be set up from several host threads
     if (!attr.load()) {
-        TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<BN, KC>::SMEM));
+        TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr.store(true);
     }
-    const int64_t g = grp.sched ? grp.ctas : (n_tiles < c->tc->num_sms ? n_tiles : c->tc->num_sms);
-    kern<<<(unsigned)g, NTHREADS, Geo<BN, KC>::SMEM, c->stream>>>(maps, a, grp);
+    if constexpr (!PAIR) {
+        const int64_t g = grp.sched ? grp.ctas : (n_tiles < c->tc->num_sms ? n_tiles : c->tc->num_sms);
+        kern<<<(unsigned)g, NTHREADS, smem, c->stream>>>(maps, a, grp);
+    } else {
+        // clusters of two CTAs; a schedule's units are clusters
+        const int64_t units = grp.sched ? grp.ctas : (n_tiles < c->tc->clusters ? n_tiles : c->tc->clusters);
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(2 * units), 1, 1);
+        cfg.blockDim = dim3(NTHREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        TWA_CUDA(c, cudaLaunchKernelEx(&cfg, kern, maps, a, grp));
+    }
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
+}
+
+// Clusters of two CTAs of the pair kernel that can be resident at once (the
+// persistent grid of a pair launch): 0 if the device cannot place one.
+template <int NT, int KC>
+int pair_clusters_of(twa_ctx* c) {
+    auto kern = k_tc<MODE_MIX, NT, 256, KC, true>;
+    constexpr int smem = Geo<256, KC, true>::SMEM;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * (c->tc->num_sms / 2)), 1, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int pair_clusters(twa_ctx* c) {
+    const TcState* t = c->tc;
+    if (t->kc == 3) return t->terms == 2 ? pair_clusters_of<2, 3>(c) : pair_clusters_of<1, 3>(c);
+    if (t->kc == 4) return t->terms == 2 ? pair_clusters_of<2, 4>(c) : pair_clusters_of<1, 4>(c);
+    if (t->kc == 0)
+        return t->terms == 3 ? pair_clusters_of<3, 0>(c) : t->terms == 2 ? pair_clusters_of<2, 0>(c)
+                                                                          : pair_clusters_of<1, 0>(c);
+    return t->terms == 3 ? pair_clusters_of<3, 1>(c) : t->terms == 2 ? pair_clusters_of<2, 1>(c)
+                                                                      : pair_clusters_of<1, 1>(c);
 }
 
 // One problem (grp.count = 0) or a group of problems in one persistent launch.
@@ -1058,9 +1280,18 @@ template <int MODE, int NT>
 int launch_cfg(twa_ctx* c, const TcMaps& maps, const TcArgs& a, const Group& grp = Group{nullptr, nullptr, 0},
                int64_t group_tiles = 0) {
     const int bn = c->tc->bn, kc = c->tc->kc;
-    const int64_t n_tiles = grp.count ? group_tiles : a.n_rt * ((a.n_vec + bn - 1) / bn);
+    const bool pair = c->tc->pair != 0;
+    const int64_t n_ru = pair ? (a.n_rt + 1) / 2 : a.n_rt;   // row units
+    const int64_t n_tiles = grp.count ? group_tiles : n_ru * ((a.n_vec + bn - 1) / bn);
+    if (pair) {
+        if (bn == 256 && kc == 1) return launch_one<MODE, NT, 256, 1, true>(c, maps, a, n_tiles, grp);
+        if (bn == 256 && kc == 3) return launch_one<MODE, NT, 256, 3, true>(c, maps, a, n_tiles, grp);
+        if (bn == 256 && kc == 4) return launch_one<MODE, NT, 256, 4, true>(c, maps, a, n_tiles, grp);
+        if (bn == 256 && kc == 0) return launch_one<MODE, NT, 256, 0, true>(c, maps, a, n_tiles, grp);
+        return set_error(c, TWA_EUNSUPPORTED, "CTA pairs: tile configuration not compiled");
+    }
 #define TWA_TC_CASE(BN_, KC_) \
-    if (bn == BN_ && kc == KC_) return launch_one<MODE, NT, BN_, KC_>(c, maps, a, n_tiles, grp);
+    if (bn == BN_ && kc == KC_) return launch_one<MODE, NT, BN_, KC_, false>(c, maps, a, n_tiles, grp);
     TWA_TC_CASE(256, 0)
     TWA_TC_CASE(256, 1)
     TWA_TC_CASE(192, 0)
@@ -1070,6 +1301,7 @@ int launch_cfg(twa_ctx* c, const TcMaps& maps, const TcArgs& a, const Group& grp
     TWA_TC_CASE(256, 2)
     TWA_TC_CASE(256, 3)
     TWA_TC_CASE(128, 3)
+    TWA_TC_CASE(256, 4)
 #undef TWA_TC_CASE
     return set_error(c, TWA_EUNSUPPORTED, "tensor-core tile configuration not compiled");
 }
@@ -1107,18 +1339,52 @@ int env_int(const char* name, int dflt) {
     return v ? atoi(v) : dflt;
 }
 
+bool pair_capable(const TcState* t) { return t->bn == 256 && t->kc != 2; }
+
+// CTA pairs need a compiled pair configuration and room for at least one
+// cluster of two; records how many clusters a persistent pair launch uses.
+// Unless TWA_TC_PAIR forces them, a configuration without pairs runs on single
+// CTAs instead.
+int pair_check(twa_ctx* c) {
+    TcState* t = c->tc;
+    const bool forced = getenv("TWA_TC_PAIR") != nullptr;
+    if (!t->pair) return TWA_OK;
+    if (!pair_capable(t)) {
+        if (!forced) {
+            t->pair = 0;
+            return TWA_OK;
+        }
+        return set_error(c, TWA_EINVAL,
+                         "TWA_TC_PAIR runs 256-wide tiles with 32-wide K stages (TWA_TC_KC 1 or 3) in the BF16 precisions");
+    }
+    const int n = pair_clusters(c);
+    if (n < 1) {
+        if (!forced) {
+            t->pair = 0;
+            return TWA_OK;
+        }
+        return set_error(c, TWA_EUNSUPPORTED, "no cluster of two CTAs of the pair kernel fits on this device");
+    }
+    t->clusters = n;
+    return TWA_OK;
+}
+
+// B rows one CTA loads per tile: all BN, or half of them in a CTA pair
+int b_box(const TcState* t) { return t->pair ? t->bn / 2 : t->bn; }
+
 int make_state_maps(twa_ctx* c) {
     TcState* t = c->tc;
     int rc;
     const int64_t R = 2 * c->M;
+    const int bb = b_box(t);
     // where no lo image is kept (TF32; eta outside the FP32 mode) the lo map
     // aliases the hi image: it is never read (one term)
-    if ((rc = make_map(c, &t->tmShi, t->Shi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmSlo, t->Slo ? t->Slo : t->Shi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmPhi, t->Phi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmPlo, t->Plo ? t->Plo : t->Phi, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmE, t->E, R, c->N, t->ldk, t->bn, t->kc))) return rc;
-    if ((rc = make_map(c, &t->tmElo, t->Elo ? t->Elo : t->E, R, c->N, t->ldk, t->bn, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmShi, t->Shi, R, c->N, t->ldk, bb, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmSlo, t->Slo ? t->Slo : t->Shi, R, c->N, t->ldk, bb, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmPhi, t->Phi, R, c->N, t->ldk, bb, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmPlo, t->Plo ? t->Plo : t->Phi, R, c->N, t->ldk, bb, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmE, t->E, R, c->N, t->ldk, bb, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmElo, t->Elo ? t->Elo : t->E, R, c->N, t->ldk, bb, t->kc))) return rc;
     return TWA_OK;
 }
 
@@ -1152,30 +1418,44 @@ int tc_prepare(twa_ctx* c) {
         case TWA_PREC_BF16L2: t->terms = 1; t->lterms = 2; break;
         default: t->terms = 1; t->lterms = 1; break;
     }
-    // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1, 3}
-    // (3: at most two products per entry, BN 128 or 256).
-    // Defaults measured fastest at N = 10^4, M = 1024: 256-wide tiles with 32-wide K
-    // stages (SWIZZLE_64B), six stages of one operand image for the precisions with
-    // at most two products (same-box A/B, BF16X2: 2-3.5 % faster per step at a
-    // 6 % lower power-capped clock than four stages), four stages otherwise. The
-    // TF32 and FP32 precisions have one configuration: 256-wide tiles, four 16-wide
-    // FP32 K stages (KC = 2).
+    // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1, 3, 4}
+    // (3: at most two products per entry, BN 128 or 256; 4: the same with 64-wide
+    // K stages and 128-byte swizzle, BN 256).
+    // Defaults measured fastest at N = 10^4, M = 1024 (same-box A/B, all bit-identical):
+    // 256-wide tiles on CTA pairs with 64-wide K stages and 128-byte swizzle -- one
+    // operand image per stage for the precisions with at most two products (KC = 4;
+    // BF16X2: 1.63 ms/step against 1.83 for single CTAs with six 32-wide stages),
+    // four images otherwise (KC = 0; BF16X3: 2.15 against 2.45 ms). On single CTAs
+    // the 32-wide four-image stage is faster for BF16X3 (KC = 1). The TF32 and FP32
+    // precisions have one configuration: 256-wide tiles, four 16-wide FP32 K stages
+    // (KC = 2).
     const bool tf32 = c->opts.precision == TWA_PREC_TF32 || c->opts.precision == TWA_PREC_FP32;
     if (tf32 && (getenv("TWA_TC_BN") || getenv("TWA_TC_KC")))
         return set_error(c, TWA_EINVAL, "TWA_TC_BN / TWA_TC_KC do not apply to the TF32 and FP32 precisions");
     t->bn = tf32 ? 256 : env_int("TWA_TC_BN", 256);
-    t->kc = tf32 ? 2 : env_int("TWA_TC_KC", (t->terms <= 2 && t->lterms <= 2) ? 3 : 1);
+    const bool one_b = t->terms <= 2 && t->lterms <= 2;
+    const int kc_default = one_b ? (t->bn == 256 ? 4 : t->bn == 128 ? 3 : 1) : (t->bn == 256 ? 0 : 1);
+    t->kc = tf32 ? 2 : env_int("TWA_TC_KC", kc_default);
     // TWA_SEPARATE_LETA=1: dense step as separate noise, L.eta, predictor and
     // corrector launches instead of the two mixed launches (same results)
     t->separate_leta = env_int("TWA_SEPARATE_LETA", 0) != 0;
-    if (!tf32 && (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1 || t->kc == 3)))
-        return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0, 1 or 3");
-    if (t->kc == 3 && t->bn == 192 && !getenv("TWA_TC_KC")) t->kc = 1;   // no six-stage 192-wide build
+    if (!tf32 &&
+        (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1 || t->kc == 3 || t->kc == 4)))
+        return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0, 1, 3 or 4");
     if (t->kc == 3 && (t->terms > 2 || t->lterms > 2 || t->bn == 192))
         return set_error(c, TWA_EINVAL, "TWA_TC_KC = 3 holds one operand image: at most two products, BN 128 or 256");
+    if (t->kc == 4 && (t->terms > 2 || t->lterms > 2 || t->bn != 256))
+        return set_error(c, TWA_EINVAL, "TWA_TC_KC = 4 holds one operand image: at most two products, BN 256");
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
         t->num_sms = sms;
+    // CTA pairs (256-row tiles on clusters of two, tcgen05 cta_group::2) wherever a
+    // pair configuration is compiled: the BF16 precisions with 256-wide tiles and
+    // 32-wide K stages (same-box A/B at N = 10^4, BF16X2: 3 % faster per step, same
+    // bits). TWA_TC_PAIR=0 / 1 forces them off / on.
+    t->pair = env_int("TWA_TC_PAIR", pair_capable(t) ? 1 : 0) != 0;
+    if (int rc = pair_check(c)) return rc;
+    if (!t->pair && !getenv("TWA_TC_KC") && t->kc == 0) t->kc = 1;   // the single-CTA default
     const size_t nb = (size_t)(tf32 ? 4 : 2) * c->N * t->ldk;
     __nv_bfloat16** m4[] = {&t->Whi, &t->Lhi, &t->Wlo, &t->Llo};
     for (int k = 0; k < (tf32 && t->terms == 1 ? 2 : 4); ++k)
@@ -1262,8 +1542,8 @@ int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t 
             return set_error(c, TWA_ENOMEM, "device vector images");
         TWA_CUDA(c, cudaMemsetAsync(t->Vhi, 0, ni, c->stream));
         TWA_CUDA(c, cudaMemsetAsync(t->Vlo, 0, ni, c->stream));
-        if ((rc = make_map(c, &t->tmVhi, t->Vhi, K, c->N, t->ldk, t->bn, t->kc))) return rc;
-        if ((rc = make_map(c, &t->tmVlo, t->Vlo, K, c->N, t->ldk, t->bn, t->kc))) return rc;
+        if ((rc = make_map(c, &t->tmVhi, t->Vhi, K, c->N, t->ldk, b_box(t), t->kc))) return rc;
+        if ((rc = make_map(c, &t->tmVlo, t->Vlo, K, c->N, t->ldk, b_box(t), t->kc))) return rc;
         t->vec_rows = K;
     }
     k_split_vectors_f32<<<nblk(K * c->N, 256), 256, 0, c->stream>>>(in, K, c->N, t->ldk, t->Vhi, t->Vlo);
@@ -1400,6 +1680,11 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
     const TcState* t0 = cs[0]->tc;
     const int bn = t0->bn, bk = kcfg_bk(t0->kc);
     const int ntw = t0->terms, ntl = leta_terms(t0);
+    // tiles are (row unit, column tile) pairs; a row unit is one 128-row tile, or
+    // two on a CTA pair, and the scheduling units are CTAs or clusters of two
+    const bool pair = t0->pair != 0;
+    const int64_t bmu = pair ? 2 * BM : BM;
+    auto units_of = [&](int64_t n_rt) { return pair ? (n_rt + 1) / 2 : n_rt; };
     const int nprob = 3 * n;
     p->nprob = nprob;
     // flat tile ranges: [W.s + predictor of 0..n-1][W.s~ + corrector][L.eta]
@@ -1408,7 +1693,7 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
         const TcState* t = cs[q]->tc;
         nct[q] = (2 * cs[q]->M + bn - 1) / bn;
         nk[q] = (cs[q]->N + bk - 1) / bk;
-        const int64_t T = t->n_rt * nct[q];
+        const int64_t T = units_of(t->n_rt) * nct[q];
         st[q + 1] = T;
         st[n + q + 1] = T;
         st[2 * n + q + 1] = T;
@@ -1426,8 +1711,8 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
     std::vector<std::pair<int64_t, int32_t>> pjobs, cjobs, ljobs;
     std::vector<double> fl(st[nprob]);
     for (int q = 0; q < n; ++q) {
-        const int64_t N = cs[q]->N, M = cs[q]->M, n_rt = cs[q]->tc->n_rt;
-        auto rows_of = [&](int64_t rt) { return std::min<int64_t>(BM, N - rt * BM); };
+        const int64_t N = cs[q]->N, M = cs[q]->M, n_ru = units_of(cs[q]->tc->n_rt);
+        auto rows_of = [&](int64_t ru) { return std::min<int64_t>(bmu, N - ru * bmu); };
         auto cols_of = [&](int64_t ct) { return (double)std::min<int64_t>(bn, 2 * M - ct * bn); };
         for (int64_t x = 0; x < st[q + 1] - st[q]; ++x) {
             const int64_t rt = x / nct[q], ct = x - rt * nct[q];
@@ -1435,10 +1720,10 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
             pjobs.push_back({nk[q] * ntw, (int32_t)(st[q] + x)});
             cjobs.push_back({nk[q] * ntw, (int32_t)(st[n + q] + x)});
             fl[st[q] + x] = fl[st[n + q] + x] = f;
-            // the kernel hands out L.eta row tiles longest first
-            const int64_t lrt = n_rt - 1 - rt;
-            const int64_t k1 = std::min<int64_t>((lrt * BM + BM + bk - 1) / bk, nk[q]);
-            const double r0 = (double)(lrt * BM), r1 = r0 + rows_of(lrt);
+            // the kernel hands out L.eta row units longest first
+            const int64_t lrt = n_ru - 1 - rt;
+            const int64_t k1 = std::min<int64_t>((lrt * bmu + bmu + bk - 1) / bk, nk[q]);
+            const double r0 = (double)(lrt * bmu), r1 = r0 + rows_of(lrt);
             ljobs.push_back({k1 * ntl, (int32_t)(st[2 * n + q] + x)});
             fl[st[2 * n + q] + x] = 2.0 * ((r1 * (r1 + 1) - r0 * (r0 + 1)) / 2.0) * cols_of(ct) * ntl;   // triangle
         }
@@ -1448,7 +1733,7 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
                          return a.first > b.first;
                      });
     // the predictor's launch takes the kl longest L.eta tiles, the corrector's the rest
-    const int sms = t0->num_sms;
+    const int sms = pair ? t0->clusters : t0->num_sms;
     auto ctas_for = [&](int64_t k) { return (int)std::min<int64_t>(k, sms); };
     const int64_t Tl = (int64_t)ljobs.size();
     auto span_of = [&](int64_t kl) {
@@ -1742,8 +2027,8 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K, int which) {
         fm.a0 = which == 1 ? t->tmLhi : t->tmWhi;
         fm.a1 = which == 1 ? t->tmLlo : t->tmWlo;
         int rc;
-        if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, t->bn, t->kc))) return rc;
-        if ((rc = make_map(c, &fm.b1, (with_lo && b_lo) ? lo : hi, K, N, ldk, t->bn, t->kc))) return rc;
+        if ((rc = make_map(c, &fm.b0, hi, K, N, ldk, b_box(t), t->kc))) return rc;
+        if ((rc = make_map(c, &fm.b1, (with_lo && b_lo) ? lo : hi, K, N, ldk, b_box(t), t->kc))) return rc;
         TcArgs fa = base_args(c);
         fa.n_vec = K;
         fa.field_out = out;
@@ -1797,7 +2082,7 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
         twa_ctx* c = ctxs[p];
         TcState* t = c->tc;
         if (!t || t->terms != lead->tc->terms || t->lterms != lead->tc->lterms || t->bn != lead->tc->bn ||
-            t->kc != lead->tc->kc || c->M == 0) {
+            t->kc != lead->tc->kc || t->pair != lead->tc->pair || c->M == 0) {
             tc_batch_free(b);
             return set_error(lead, TWA_EINVAL, "batch: contexts differ in precision or tiles, or have no trajectories");
         }
@@ -1883,7 +2168,10 @@ int tc_set_tiles(twa_ctx* c, int bn, int kc) {
     }
     t->bn = bn;
     t->kc = kc;
-    int rc = make_matrix_maps(c);
+    t->pair = env_int("TWA_TC_PAIR", pair_capable(t) ? 1 : 0) != 0;
+    int rc = pair_check(c);
+    if (rc) return rc;
+    rc = make_matrix_maps(c);
     if (rc) return rc;
     return c->M ? make_state_maps(c) : TWA_OK;
 }

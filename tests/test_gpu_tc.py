@@ -303,23 +303,56 @@ def test_tf32_modes_reject_what_they_do_not_cover(prec, monkeypatch):
     assert e.value.name == "TWA_EINVAL"
 
 
-def test_six_stage_ring_gives_the_same_bits(monkeypatch):
-    # TWA_TC_KC = 3 (six stages of A hi, A lo and one operand image) issues the same
-    # MMAs in the same K order as the four-stage ring: identical states and sums
+TILE_CONFIGS = {
+    # (TWA_TC_PAIR, TWA_TC_KC): single CTAs and CTA pairs, 32- and 64-wide K stages,
+    # four operand images or one per stage
+    "one_image": [("0", "1"), ("0", "3"), ("0", "4"), ("1", "1"), ("1", "3"), ("1", "4"), ("1", "0")],
+    "four_images": [("0", "1"), ("0", "0"), ("1", "1"), ("1", "0")],
+}
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16l2", "bf16", "bf16x3"])
+@pytest.mark.parametrize("N,M", [(300, 200), (1024, 128)])
+def test_every_tile_configuration_gives_the_same_bits(monkeypatch, prec, N, M):
+    # every K-stage configuration, on single CTAs or on CTA pairs (256-row
+    # tcgen05.mma.cta_group::2 tiles split over two CTAs), issues the same MMAs in
+    # the same K order into each accumulator row: identical states, window sums and
+    # contractions. N = 300 has an odd number of 128-row tiles (a pair's second
+    # tile lies past the last row) and M = 200 a ragged trajectory tile.
+    import torch
     twa = _twa()
-    N, M = 300, 200
+    rng = np.random.default_rng(1)
+    s = torch.tensor(rng.standard_normal((5, N)), dtype=torch.float64, device="cuda")
     out = {}
-    for kc in ("1", "3"):
+    cfgs = TILE_CONFIGS["four_images" if prec == "bf16x3" else "one_image"]
+    for pair, kc in cfgs:
+        monkeypatch.setenv("TWA_TC_PAIR", pair)
         monkeypatch.setenv("TWA_TC_KC", kc)
-        for prec in ("bf16x2", "bf16l2", "bf16"):
-            with twa.TWA(N, 1.0, 8.0, 1.0, 2e-3, seed=3, precision=prec, window_start=0.004) as g:
-                g.run(M, 6)
-                out[kc, prec] = (g.get_state(), g.moments())
-    for prec in ("bf16x2", "bf16l2", "bf16"):
-        for a, b in zip(out["1", prec][0], out["3", prec][0]):
-            assert np.array_equal(a, b), prec
-        assert np.array_equal(out["1", prec][1], out["3", prec][1]), prec
-    monkeypatch.setenv("TWA_TC_KC", "3")
+        with twa.TWA(N, 1.0, 8.0, 1.0, 2e-3, seed=3, precision=prec, window_start=0.004) as g:
+            g.run(M, 6)
+            out[pair, kc] = (g.get_state(), g.moments(), g.field(s).cpu().numpy(), g.contract(s, "L").cpu().numpy())
+    ref = out[cfgs[0]]
+    for cfg in cfgs[1:]:
+        got = out[cfg]
+        for a, b in zip(ref[0], got[0]):
+            assert np.array_equal(a, b), cfg
+        for k in (1, 2, 3):
+            assert np.array_equal(ref[k], got[k]), (cfg, k)
+
+
+def test_tile_configuration_rejections(monkeypatch):
+    twa = _twa()
+    for kc in ("3", "4"):   # one operand image per stage: at most two products
+        monkeypatch.setenv("TWA_TC_KC", kc)
+        with pytest.raises(twa.TWAError) as e:
+            twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="bf16x3")
+        assert e.value.name == "TWA_EINVAL"
+    monkeypatch.delenv("TWA_TC_KC")
+    monkeypatch.setenv("TWA_TC_PAIR", "1")   # no pair configuration for the FP32 K stages
     with pytest.raises(twa.TWAError) as e:
-        twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="bf16x3")
+        twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="tf32")
+    assert e.value.name == "TWA_EINVAL"
+    monkeypatch.setenv("TWA_TC_BN", "192")   # nor for 192-wide tiles
+    with pytest.raises(twa.TWAError) as e:
+        twa.TWA(64, 1.0, 8.0, 1.0, 1e-3, precision="bf16x2")
     assert e.value.name == "TWA_EINVAL"
