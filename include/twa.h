@@ -85,8 +85,8 @@ extern "C" {
                                 the noise) rounded once to BF16: two products per entry,
                                 A_hi*v + A_lo*v, FP32 accumulation, FP32 state. W.s is
                                 W.bf16(s) to ~2^-17; L.eta is the BF16X3 arithmetic.
-                                twa_run, twa_field, twa_contract, twa_batch_run;
-                                not twa_grad                                         */
+                                twa_run, twa_field, twa_contract, twa_batch_run,
+                                twa_grad                                             */
 #define TWA_PREC_BF16L2  6   /* W one BF16 product (W_hi*s_hi), L split as in BF16X2
                                 (L_hi*eta + L_lo*eta): the noise factor, whose rounding
                                 biases single-term BF16, keeps ~16 bits. Same coverage
@@ -222,6 +222,12 @@ typedef struct twa_obs {
     int64_t nonfinite;          /* spin components found non-finite             */
     double factor_residual;     /* ||W - L L^T||_F / ||W||_F when clip_negative
                                    zeroed columns (else 0, not computed)        */
+    int64_t fft_length;         /* FFT route: circle length P of the embedding
+                                   (the smallest 2^a 3^b 5^c >= 2N - 2 that is even
+                                   when one CTA holds the transform, i.e. P <= 28000,
+                                   else a multiple of 4 fft_ctas); 0 otherwise  */
+    int64_t fft_ctas;           /* FFT route: CTAs per trajectory (1; 2, 4 or 8
+                                   as a thread-block cluster); 0 otherwise      */
 } twa_obs;
 
 /* Fill *opts with the defaults listed above. Returns TWA_EINVAL if opts is NULL. */
@@ -334,8 +340,9 @@ typedef struct twa_grad_out {
  * state every `checkpoint` steps, then the reverse sweep: each block is
  * recomputed from its checkpoint and the cotangent is pulled back through the
  * renormalisation, the Heun corrector and the predictor, with W.beta
- * contractions on the precision path of the context (FP64 SIMT or BF16X3
- * tensor cores with an FP32 tape). Parameter derivatives use dW/dw = W/w,
+ * contractions on the precision path of the context (FP64 SIMT, or the BF16,
+ * BF16X3, BF16X2 or BF16L2 tensor-core arithmetic of the forward step with an
+ * FP32 tape). Parameter derivatives use dW/dw = W/w,
  * dL/dw = L/(2w), dW/dalpha = -ln(1+|i-j|) W and the Cholesky derivative
  * dL = L Phi(L^-1 dW L^-T). The objective is linearised at the forward run's
  * ensemble means (g2 through the quotient rule).

@@ -22,7 +22,9 @@ draw chi = L eta (``twa_oracle``) is one, this module is another:
 * Random stream: (a_k, b_k) are the Box-Muller pair of the Philox4x32-10 call
   at counter (trajectory m, step t, frequency k, stream 2); the collective noise
   xi keeps its counter (m, t, N, stream 0).
-* Length: P is the smallest even 2^a 3^b 5^c with P >= max(2, 2N - 2).
+* Length: P is the smallest even 2^a 3^b 5^c with P >= max(2, 2N - 2), or a
+  given even P >= 2N - 2 (any such circle gives a valid embedding; the library
+  takes a multiple of 4 C when C CTAs share one transform and reports P).
 
 A library FFT (numpy.fft) serves as the transform; the tests pin it against the
 sums above written out term by term.
@@ -87,9 +89,13 @@ class TWAOracleCirculant(TWAOracle):
     """``TWAOracle`` with the pump noise drawn through the circulant embedding
     instead of the Cholesky factor (same law, different per-trajectory values)."""
 
-    def __init__(self, N, alpha, w, Gamma, dt, seed, M, **kw):
+    def __init__(self, N, alpha, w, Gamma, dt, seed, M, P=None, **kw):
+        # this draw needs no factor of W: skip the base class's Cholesky
+        kw.setdefault("L", np.zeros((0, 0)))
         super().__init__(N, alpha, w, Gamma, dt, seed, M, **kw)
-        self.P = embedding_length(self.N)
+        self.P = embedding_length(self.N) if P is None else int(P)
+        if self.P % 2 or self.P < max(2, 2 * self.N - 2):
+            raise ValueError("the circle length must be even and >= 2N - 2")
         self.lam = embedding_spectrum(embedded_sequence(self.N, self.alpha, self.w, self.P))
 
     def noise_increments(self, t):

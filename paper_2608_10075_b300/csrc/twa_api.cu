@@ -337,6 +337,8 @@ int twa_observables(twa_ctx* c, twa_obs* out) {
     out->min_pivot = c->min_pivot;
     out->clipped = c->clipped;
     out->factor_residual = c->factor_residual;
+    out->fft_length = c->fft ? c->fft->P : 0;
+    out->fft_ctas = c->fft ? c->fft->C : 0;
     unsigned long long fl[twa::FLAG_COUNT];
     TWA_CUDA(c, cudaMemcpy(fl, c->d_flags, sizeof(fl), cudaMemcpyDeviceToHost));
     out->nonfinite = (int64_t)fl[twa::FLAG_NONFINITE];
@@ -455,9 +457,8 @@ int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
     if (c->opts.traj_offset + r->M - 1 > MAX_COUNTER)
         return set_error(c, TWA_EINVAL, "twa_grad: traj_offset + M exceeds the 32-bit trajectory counter");
     if (!(c->w > 0.0)) return set_error(c, TWA_EUNSUPPORTED, "twa_grad: needs w > 0");
-    if (c->opts.precision != TWA_PREC_FP64 && c->opts.precision != TWA_PREC_BF16 &&
-        c->opts.precision != TWA_PREC_BF16X3)
-        return set_error(c, TWA_EUNSUPPORTED, "twa_grad: runs on the FP64, BF16 and BF16X3 precisions");
+    if (c->opts.precision == TWA_PREC_TF32 || c->opts.precision == TWA_PREC_FP32)
+        return set_error(c, TWA_EUNSUPPORTED, "twa_grad: runs on the FP64 and BF16 precisions (BF16, BF16X3, BF16X2, BF16L2)");
     if (c->opts.integrator != TWA_INT_HEUN)
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: differentiates the Heun integrator only");
     if (c->opts.noise_route != TWA_NOISE_CHOLESKY)

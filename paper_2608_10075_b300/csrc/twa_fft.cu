@@ -19,7 +19,19 @@
 // natural order: no permutation pass. The Heun predictor / corrector of the
 // trajectory then run in the same kernel, with the collective sums S^a reduced
 // in the block.
+//
+// Longer transforms (P > 28000, N > 14001) spread one trajectory over a cluster
+// of C = 2, 4 or 8 CTAs on as many SMs: position p lives in the shared memory of
+// CTA p mod C at offset p / C. A butterfly of stride m touches positions
+// congruent mod C when C divides m, so with the radices ordered 5s, 3s, 2s, 4s
+// (the strides of all stages but the last are then multiples of 4 C or more)
+// every stage is local to one CTA except the middle one (stride 1), which reads
+// and writes the other CTAs' shared memory (distributed shared memory,
+// ld/st.shared::cluster) between two cluster barriers.
 #include <math.h>
+#include <stdlib.h>
+
+#include <type_traits>
 
 #include "twa_internal.cuh"
 
@@ -27,18 +39,27 @@ namespace twa {
 namespace {
 
 constexpr int FT = 1024;                 // threads per CTA
-constexpr int64_t FFT_MAX_P = 28000;     // P complex FP32 values in shared memory (219 KB)
-constexpr int TW_LO = 128;               // two-level twiddles: w^n = hi[n / 128] lo[n % 128]
-constexpr int64_t TW_HI_MAX = (FFT_MAX_P + TW_LO - 1) / TW_LO;
-// lo entry k is stored at k + k / 16: the strided lookups n = j * step of the
-// middle stages (step a multiple of 16 or 32) then fall on distinct banks
-constexpr int TW_LO_PADDED = TW_LO + TW_LO / 16;
+constexpr int64_t FFT_MAX_PLOC = 28000;  // complex FP32 values of one CTA's share of the transform (219 KB)
+constexpr int FFT_MAX_C = 8;             // CTAs per trajectory (portable cluster size)
+// two-level twiddles: w^n = hi[n / LO] lo[n % LO]; LO = 128 for one CTA (hi table
+// <= 219 entries at P <= 28000), 256 for clusters (P <= 120000 at N <= 60000)
+template <int C>
+struct TwCfg {
+    static constexpr int LOG = C == 1 ? 7 : 8;
+    static constexpr int LO = 1 << LOG;
+    // lo entry k is stored at k + k / 16: the strided lookups n = j * step of the
+    // middle stages (step a multiple of 16 or 32) then fall on distinct banks
+    static constexpr int PADDED = LO + LO / 16;
+};
 __host__ __device__ constexpr int lo_slot(int k) { return k + (k >> 4); }
+template <int C>
+__host__ __device__ constexpr int log2c() { return C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3; }
 
 struct FftArgs {
     int64_t N, M, P;
     int nst;
     int radix[40];
+    unsigned local_mask;                 // bit s: stage s (stride m_s) stays inside one CTA of the cluster
     const float* lam;
     const float2* tw;
     float G, dt;
@@ -66,6 +87,51 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// ---------------------------------------------------------------------------
+// cluster helpers: rank, barrier, distributed shared memory
+template <int C>
+__device__ __forceinline__ int cl_rank() {
+    if constexpr (C == 1) return 0;
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// barrier between two stages: the cluster's when either reads or writes another
+// CTA's shared memory, the block's otherwise
+template <int C>
+__device__ __forceinline__ void stage_sync(bool cluster) {
+    if constexpr (C > 1) {
+        if (cluster) {
+            cl_sync();
+            return;
+        }
+    }
+    __syncthreads();
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t cl_map(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float2 cl_ld(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cl_st(uint32_t a, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ float cl_ldf(uint32_t a) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
 
 // Radix-R DFT in registers: y_k = sum_q a_q exp(-+ 2 pi i q k / R) (INV: +).
 template <int R, bool INV>
@@ -114,11 +180,14 @@ __device__ __forceinline__ void dft(float2* a) {
 }
 
 // Twiddles w^n = exp(-2 pi i n / P) from two small shared-memory tables:
-// w^n = hi[n / 128] * lo[n % 128] (one complex product, FP32 accurate).
+// w^n = hi[n / LO] * lo[n % LO] (one complex product, FP32 accurate).
+template <int C>
 struct Tw {
     const float2* hi;
     const float2* lo;
-    __device__ __forceinline__ float2 operator[](int n) const { return cmul(hi[n >> 7], lo[lo_slot(n & (TW_LO - 1))]); }
+    __device__ __forceinline__ float2 operator[](int n) const {
+        return cmul(hi[n >> TwCfg<C>::LOG], lo[lo_slot(n & (TwCfg<C>::LO - 1))]);
+    }
 };
 
 // One stage over butterflies of radix R and stride m (span L = m R): DIF applies
@@ -128,14 +197,19 @@ struct Tw {
 // The butterfly's R inputs come from `ld(position)` and its outputs go to
 // `st(position, value)`: shared memory inside the transform, global memory in
 // the first and last stages, which thereby replace separate load/store passes.
-template <int R, bool INV, typename LD, typename ST>
-__device__ __forceinline__ void stage_io(int P, int m, const Tw tw, LD& ld, ST& st) {
-    const int L = m * R, step = P / L, nb = P / R;   // P <= FFT_MAX_P: 32-bit indices
-    // butterfly u = b m + j; advancing u by FT advances (b, j) by (db, dj), with
+// CTA `rank` of a cluster of C runs the butterflies u = rank (mod C): when C
+// divides m, all R positions of such a butterfly are = rank (mod C), i.e. in its
+// own shared memory.
+template <int R, bool INV, int C, typename LD, typename ST>
+__device__ __forceinline__ void stage_io(int P, int m, const Tw<C> tw, LD& ld, ST& st, int rank) {
+    const int L = m * R, step = P / L, nb = P / R;   // P <= 120000: 32-bit indices
+    constexpr int U = FT * C;
+    // butterfly u = b m + j; advancing u by U advances (b, j) by (db, dj), with
     // one carry: no integer division inside the loop
-    const int db = FT / m, dj = FT - db * m;
-    int b = (int)threadIdx.x / m, j = (int)threadIdx.x - b * m;
-    for (int u = threadIdx.x; u < nb; u += FT) {
+    const int db = U / m, dj = U - db * m;
+    const int u0 = rank + C * (int)threadIdx.x;
+    int b = u0 / m, j = u0 - b * m;
+    for (int u = u0; u < nb; u += U) {
         const int jc = j, base = b * L + j;
         b += db;
         j += dj;
@@ -164,22 +238,22 @@ __device__ __forceinline__ void stage_io(int P, int m, const Tw tw, LD& ld, ST& 
     }
 }
 
-template <bool INV, typename LD, typename ST>
-__device__ __forceinline__ void stage_any(int r, int P, int m, const Tw tw, LD& ld, ST& st) {
+template <bool INV, int C, typename LD, typename ST>
+__device__ __forceinline__ void stage_any(int r, int P, int m, const Tw<C> tw, LD& ld, ST& st, int rank) {
     switch (r) {
-        case 4: stage_io<4, INV>(P, m, tw, ld, st); break;
-        case 2: stage_io<2, INV>(P, m, tw, ld, st); break;
-        case 3: stage_io<3, INV>(P, m, tw, ld, st); break;
-        default: stage_io<5, INV>(P, m, tw, ld, st); break;
+        case 4: stage_io<4, INV, C>(P, m, tw, ld, st, rank); break;
+        case 2: stage_io<2, INV, C>(P, m, tw, ld, st, rank); break;
+        case 3: stage_io<3, INV, C>(P, m, tw, ld, st, rank); break;
+        default: stage_io<5, INV, C>(P, m, tw, ld, st, rank); break;
     }
 }
 
 // Last forward stage, product with the spectrum and first inverse stage in one
 // pass: all three work on the same groups of R neighbouring positions (stride
 // m = 1, twiddles 1), so each group stays in registers.
-template <int R, typename LD, typename ST>
-__device__ __forceinline__ void middle_io(int P, const float* __restrict__ lam, LD& ld, ST& st) {
-    for (int u = threadIdx.x; u < P / R; u += FT) {
+template <int R, int C, typename LD, typename ST>
+__device__ __forceinline__ void middle_io(int P, const float* __restrict__ lam, LD& ld, ST& st, int rank) {
+    for (int u = rank + C * (int)threadIdx.x; u < P / R; u += FT * C) {
         const int base = u * R;
         float2 a[R];
 #pragma unroll
@@ -196,32 +270,60 @@ __device__ __forceinline__ void middle_io(int P, const float* __restrict__ lam, 
     }
 }
 
-template <typename LD, typename ST>
-__device__ __forceinline__ void middle_any(int r, int P, const float* lam, LD& ld, ST& st) {
+template <int C, typename LD, typename ST>
+__device__ __forceinline__ void middle_any(int r, int P, const float* lam, LD& ld, ST& st, int rank) {
     switch (r) {
-        case 4: middle_io<4>(P, lam, ld, st); break;
-        case 2: middle_io<2>(P, lam, ld, st); break;
-        case 3: middle_io<3>(P, lam, ld, st); break;
-        default: middle_io<5>(P, lam, ld, st); break;
+        case 4: middle_io<4, C>(P, lam, ld, st, rank); break;
+        case 2: middle_io<2, C>(P, lam, ld, st, rank); break;
+        case 3: middle_io<3, C>(P, lam, ld, st, rank); break;
+        default: middle_io<5, C>(P, lam, ld, st, rank); break;
     }
 }
 
+// Position p of the transform: this CTA's shared memory (offset p / C; the
+// caller guarantees p = rank mod C) ...
+template <int C>
 struct SmemLd {
     const float2* buf;
-    __device__ __forceinline__ float2 operator()(int p) const { return buf[p]; }
+    __device__ __forceinline__ float2 operator()(int p) const { return buf[p >> log2c<C>()]; }
 };
+template <int C>
 struct SmemSt {
     float2* buf;
-    __device__ __forceinline__ void operator()(int p, float2 v) const { buf[p] = v; }
+    __device__ __forceinline__ void operator()(int p, float2 v) const { buf[p >> log2c<C>()] = v; }
+};
+// ... or the shared memory of CTA p mod C of the cluster
+template <int C>
+struct ClLd {
+    uint32_t base;   // shared-window address of the transform in this CTA
+    __device__ __forceinline__ float2 operator()(int p) const {
+        return cl_ld(cl_map(base + 8u * (uint32_t)(p >> log2c<C>()), (uint32_t)(p & (C - 1))));
+    }
+};
+template <int C>
+struct ClSt {
+    uint32_t base;
+    __device__ __forceinline__ void operator()(int p, float2 v) const {
+        cl_st(cl_map(base + 8u * (uint32_t)(p >> log2c<C>()), (uint32_t)(p & (C - 1))), v);
+    }
 };
 
-// Twiddle tables into shared memory right after the P values of buf.
-__device__ Tw load_twiddles(float2* buf, const FftArgs& a) {
-    float2* thi = buf + a.P;
-    float2* tlo = thi + TW_HI_MAX;
-    for (int64_t k = threadIdx.x; k * TW_LO < a.P; k += FT) thi[k] = a.tw[k * TW_LO];
-    for (int j = threadIdx.x; j < TW_LO; j += FT) tlo[lo_slot(j)] = (j < a.P) ? a.tw[j] : make_float2(1.f, 0.f);
-    return Tw{thi, tlo};
+// shared memory of one FFT CTA: its share of the transform and the two twiddle tables
+__host__ __device__ inline int64_t tw_hi_entries(int64_t P, int C) {
+    const int lo = C == 1 ? TwCfg<1>::LO : TwCfg<2>::LO;
+    return (P + lo - 1) / lo;
+}
+__host__ __device__ inline int64_t tw_lo_entries(int C) { return C == 1 ? TwCfg<1>::PADDED : TwCfg<2>::PADDED; }
+
+// Twiddle tables into shared memory right after this CTA's P / C values of buf.
+template <int C>
+__device__ Tw<C> load_twiddles(float2* buf, const FftArgs& a) {
+    float2* thi = buf + a.P / C;
+    float2* tlo = thi + tw_hi_entries(a.P, C);
+    constexpr int LO = TwCfg<C>::LO;
+    for (int64_t k = threadIdx.x; k * LO < a.P; k += FT) thi[k] = a.tw[k * LO];
+    for (int j = threadIdx.x; j < LO; j += FT) tlo[lo_slot(j)] = (j < a.P) ? a.tw[j] : make_float2(1.f, 0.f);
+    return Tw<C>{thi, tlo};
 }
 
 // Sum of v over the block (all threads receive it). `scratch` holds 32 floats.
@@ -236,45 +338,82 @@ __device__ float block_sum(float v, float* scratch) {
     return t;
 }
 
+// Sums of v[k] over the trajectory's CTAs (all threads of all of them receive
+// them): block sums, then the C partial sums added in rank order, so every CTA
+// holds the same bits. xch: K floats of shared memory.
+template <int C, int K>
+__device__ void traj_sums(float (&v)[K], float* scratch, float* xch) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = block_sum(v[k], scratch);
+    if constexpr (C > 1) {
+        if (threadIdx.x == 0)
+            for (int k = 0; k < K; ++k) xch[k] = v[k];
+        cl_sync();
+        const uint32_t xa = smem_addr(xch);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float t = 0.f;
+            for (int r = 0; r < C; ++r) t += cl_ldf(cl_map(xa + 4u * (uint32_t)k, (uint32_t)r));
+            v[k] = t;
+        }
+        cl_sync();   // every CTA has read the partial sums before any of them moves on
+    }
+}
+
+__device__ __forceinline__ bool stage_local(const FftArgs& a, int s) { return (a.local_mask >> s) & 1u; }
+
 // P * (C v) for the circulant C with spectrum lam (digit-reversed order), v read
 // by `in(position)` (zero beyond the vector) and the result handed to
 // `out(position, value)`; `after_first` runs after the first stage (all threads,
-// may synchronise), `before_last` before the last one. buf holds the transform
-// and, after it, the twiddle tables.
-template <typename IN, typename OUT, typename F1, typename F2>
-__device__ __forceinline__ void circulant_io(float2* buf, const FftArgs& a, IN& in, OUT& out, F1 after_first,
-                                             F2 before_last) {
-    const Tw tw = load_twiddles(buf, a);
-    SmemLd sld{buf};
-    SmemSt sst{buf};
+// may synchronise), `before_last` before the last one. buf holds this CTA's share
+// of the transform and, after it, the twiddle tables.
+template <int C, typename IN, typename OUT, typename F1, typename F2>
+__device__ __forceinline__ void circulant_io(float2* buf, const FftArgs& a, int rank, IN& in, OUT& out,
+                                             F1 after_first, F2 before_last) {
+    const Tw<C> tw = load_twiddles<C>(buf, a);
+    SmemLd<C> sld{buf};
+    SmemSt<C> sst{buf};
+    ClLd<C> cld{smem_addr(buf)};
+    ClSt<C> cst{smem_addr(buf)};
     const int P = (int)a.P, nst = a.nst;
     __syncthreads();
-    if (nst == 1) {
+    if (nst == 1) {   // P <= 5: one CTA
         after_first();
         before_last();
-        middle_any(a.radix[0], P, a.lam, in, out);
+        middle_any<C>(a.radix[0], P, a.lam, in, out, rank);
         return;
     }
     int m = P;
     for (int s = 0; s + 1 < nst; ++s) {
         m /= a.radix[s];
-        if (s == 0) stage_any<false>(a.radix[s], P, m, tw, in, sst);
-        else stage_any<false>(a.radix[s], P, m, tw, sld, sst);
-        __syncthreads();
+        const bool loc = stage_local(a, s);
+        if (s == 0) {
+            if (loc) stage_any<false, C>(a.radix[s], P, m, tw, in, sst, rank);
+            else stage_any<false, C>(a.radix[s], P, m, tw, in, cst, rank);
+        } else {
+            if (loc) stage_any<false, C>(a.radix[s], P, m, tw, sld, sst, rank);
+            else stage_any<false, C>(a.radix[s], P, m, tw, cld, cst, rank);
+        }
+        stage_sync<C>(!(loc && stage_local(a, s + 1)));
         if (s == 0) after_first();
     }
-    middle_any(a.radix[nst - 1], P, a.lam, sld, sst);
-    __syncthreads();
+    // the middle pass (stride 1): local only for one CTA
+    if constexpr (C == 1) middle_any<C>(a.radix[nst - 1], P, a.lam, sld, sst, rank);
+    else middle_any<C>(a.radix[nst - 1], P, a.lam, cld, cst, rank);
+    stage_sync<C>(true);
     m = a.radix[nst - 1];
     for (int s = nst - 2; s >= 0; --s) {
+        const bool loc = stage_local(a, s);
         if (s == 0) {
             before_last();
-            stage_any<true>(a.radix[s], P, m, tw, sld, out);
+            if (loc) stage_any<true, C>(a.radix[s], P, m, tw, sld, out, rank);
+            else stage_any<true, C>(a.radix[s], P, m, tw, cld, out, rank);
         } else {
-            stage_any<true>(a.radix[s], P, m, tw, sld, sst);
+            if (loc) stage_any<true, C>(a.radix[s], P, m, tw, sld, sst, rank);
+            else stage_any<true, C>(a.radix[s], P, m, tw, cld, cst, rank);
         }
         m *= a.radix[s];
-        __syncthreads();
+        stage_sync<C>(!(loc && (s == 0 || stage_local(a, s - 1))));
     }
 }
 
@@ -370,10 +509,13 @@ struct CorrOut {
     }
 };
 
+template <int C>
 __global__ void __launch_bounds__(FT, 1) k_fft_pred(const __grid_constant__ FftArgs a) {
     extern __shared__ float2 buf[];
     __shared__ float scratch[32];
-    const int64_t off = (int64_t)blockIdx.x * a.N;
+    __shared__ float xch[4];
+    const int rank = cl_rank<C>();
+    const int64_t off = (int64_t)(blockIdx.x / C) * a.N;
     StateIn in{a.X + off, a.Y + off, (int)a.N};
     PredOut out{&a, off};
     out.inv = 1.0f / (float)a.P;
@@ -381,17 +523,22 @@ __global__ void __launch_bounds__(FT, 1) k_fft_pred(const __grid_constant__ FftA
     auto first = [&]() {
         if (a.nst == 1)
             for (int p = threadIdx.x; p < a.N; p += FT) in(p);   // sums only (tiny P)
-        out.Sx = block_sum(in.sx, scratch);
-        out.Sy = block_sum(in.sy, scratch);
+        float v[2] = {in.sx, in.sy};
+        traj_sums<C>(v, scratch, xch);
+        out.Sx = v[0];
+        out.Sy = v[1];
         in.sx = in.sy = 0.f;
     };
-    circulant_io(buf, a, in, out, first, [] {});
+    circulant_io<C>(buf, a, rank, in, out, first, [] {});
 }
 
+template <int C>
 __global__ void __launch_bounds__(FT, 1) k_fft_corr(const __grid_constant__ FftArgs a) {
     extern __shared__ float2 buf[];
     __shared__ float scratch[32];
-    const int64_t m = blockIdx.x, off = m * a.N;
+    __shared__ float xch[4];
+    const int rank = cl_rank<C>();
+    const int64_t m = blockIdx.x / C, off = m * a.N;
     const int64_t t1 = *a.d_t + 1;
     StateIn in{a.X + off, a.Y + off, (int)a.N};
     CorrOut out{&a, off};
@@ -400,15 +547,19 @@ __global__ void __launch_bounds__(FT, 1) k_fft_corr(const __grid_constant__ FftA
     auto first = [&]() {
         if (a.nst == 1)
             for (int p = threadIdx.x; p < a.N; p += FT) in(p);
-        out.Sx = block_sum(in.sx, scratch);
-        out.Sy = block_sum(in.sy, scratch);
+        float v[2] = {in.sx, in.sy};
+        traj_sums<C>(v, scratch, xch);
+        out.Sx = v[0];
+        out.Sy = v[1];
         in.sx = in.sy = 0.f;
     };
-    circulant_io(buf, a, in, out, first, [] {});
-    const float Sx = block_sum(out.sx, scratch), Sy = block_sum(out.sy, scratch), Sz = block_sum(out.sz, scratch);
+    circulant_io<C>(buf, a, rank, in, out, first, [] {});
+    float v[3] = {out.sx, out.sy, out.sz};
+    traj_sums<C>(v, scratch, xch);
+    const float Sx = v[0], Sy = v[1], Sz = v[2];
     const unsigned nb = __reduce_add_sync(0xffffffffu, out.bad);
     if ((threadIdx.x & 31) == 0 && nb) atomicAdd(&a.flags[FLAG_NONFINITE], (unsigned long long)nb);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && rank == 0) {
         if (window_sample(t1, a.n_window, a.n_stride)) {
             // window moments S^z, A, A^2, A S^z, (S^z)^2 with A = ((S^x)^2 + (S^y)^2) / 4
             const double dx = Sx, dy = Sy, dz = Sz;
@@ -422,7 +573,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_corr(const __grid_constant__ FftA
         }
         __threadfence();
         const unsigned long long done = atomicAdd(&a.flags[FLAG_DONE], 1ull);
-        if (done == gridDim.x - 1) {   // last trajectory of the step: advance the counter
+        if (done == gridDim.x / C - 1) {   // last trajectory of the step: advance the counter
             a.flags[FLAG_DONE] = 0ull;
             if (window_sample(t1, a.n_window, a.n_stride)) *a.d_count += 1;
             __threadfence();
@@ -461,30 +612,43 @@ struct NoiseOut {
     }
 };
 
+template <int C>
 __global__ void __launch_bounds__(FT, 1) k_fft_noise(const __grid_constant__ FftArgs a, const float* nscale,
                                                      const int32_t* nfreq, uint64_t seed, int64_t m0, float sgdt,
                                                      float sdt, float* Bnx, float* Bny) {
     extern __shared__ float2 buf[];
-    const int64_t m = blockIdx.x, off = m * a.N;
+    const int rank = cl_rank<C>();
+    const int64_t m = blockIdx.x / C, off = m * a.N;
     const uint32_t t = (uint32_t)(*a.d_t), mg = (uint32_t)(m0 + m);
-    const Tw tw = load_twiddles(buf, a);
+    const Tw<C> tw = load_twiddles<C>(buf, a);
     float xi_x, xi_y;
     normal2_f32(seed, mg, t, (uint32_t)a.N, xi_x, xi_y);
     NoiseIn in{nscale, nfreq, seed, mg, t};
     NoiseOut out{Bnx + off, Bny + off, (int)a.N, __fmul_rn(sgdt, xi_x), __fmul_rn(sgdt, xi_y), sdt};
-    SmemLd sld{buf};
-    SmemSt sst{buf};
+    SmemLd<C> sld{buf};
+    SmemSt<C> sst{buf};
+    ClLd<C> cld{smem_addr(buf)};
+    ClSt<C> cst{smem_addr(buf)};
     const int P = (int)a.P, nst = a.nst;
-    __syncthreads();
+    // every CTA of the cluster is running before the first stage writes into them
+    stage_sync<C>(true);
     // unnormalised inverse transform, digit-reversed input -> natural order
     int mm = 1;
     for (int s = nst - 1; s >= 0; --s) {
-        if (s == nst - 1 && s == 0) stage_any<true>(a.radix[s], P, mm, tw, in, out);
-        else if (s == nst - 1) stage_any<true>(a.radix[s], P, mm, tw, in, sst);
-        else if (s == 0) stage_any<true>(a.radix[s], P, mm, tw, sld, out);
-        else stage_any<true>(a.radix[s], P, mm, tw, sld, sst);
+        const bool loc = stage_local(a, s);
+        if (s == nst - 1 && s == 0) stage_any<true, C>(a.radix[s], P, mm, tw, in, out, rank);
+        else if (s == nst - 1) {
+            if (loc) stage_any<true, C>(a.radix[s], P, mm, tw, in, sst, rank);
+            else stage_any<true, C>(a.radix[s], P, mm, tw, in, cst, rank);
+        } else if (s == 0) {
+            if (loc) stage_any<true, C>(a.radix[s], P, mm, tw, sld, out, rank);
+            else stage_any<true, C>(a.radix[s], P, mm, tw, cld, out, rank);
+        } else {
+            if (loc) stage_any<true, C>(a.radix[s], P, mm, tw, sld, sst, rank);
+            else stage_any<true, C>(a.radix[s], P, mm, tw, cld, cst, rank);
+        }
         mm *= a.radix[s];
-        __syncthreads();
+        stage_sync<C>(!(loc && (s == 0 || stage_local(a, s - 1))));
     }
 }
 
@@ -508,13 +672,15 @@ struct FieldOut {
     }
 };
 
+template <int C>
 __global__ void __launch_bounds__(FT, 1) k_fft_field(const __grid_constant__ FftArgs a) {
     extern __shared__ float2 buf[];
-    const int64_t k0 = 2 * (int64_t)blockIdx.x, k1 = k0 + 1;
+    const int rank = cl_rank<C>();
+    const int64_t k0 = 2 * (int64_t)(blockIdx.x / C), k1 = k0 + 1;
     const bool two = k1 < a.K;
     FieldIn in{a.field_in + k0 * a.N, two ? a.field_in + k1 * a.N : nullptr, (int)a.N};
     FieldOut out{a.field_out + k0 * a.N, two ? a.field_out + k1 * a.N : nullptr, (int)a.N, 1.0 / (double)a.P};
-    circulant_io(buf, a, in, out, [] {}, [] {});
+    circulant_io<C>(buf, a, rank, in, out, [] {}, [] {});
 }
 
 // exp(-2 pi i n / P), accurate to FP32 rounding (FP64 sincospi).
@@ -585,6 +751,7 @@ FftArgs base_args(twa_ctx* c) {
     a.P = f->P;
     a.nst = f->nst;
     for (int s = 0; s < f->nst; ++s) a.radix[s] = f->radix[s];
+    a.local_mask = f->local_mask;
     a.lam = f->lam;
     a.tw = f->tw;
     a.G = (float)c->Gamma;
@@ -595,32 +762,127 @@ FftArgs base_args(twa_ctx* c) {
     return a;
 }
 
-// shared memory of one FFT CTA: the transform and the two twiddle tables
-size_t smem_bytes(int64_t P) { return sizeof(float2) * (size_t)(P + TW_HI_MAX + TW_LO_PADDED); }
+// shared memory of one FFT CTA: its share of the transform and the two twiddle tables
+size_t smem_bytes(int64_t P, int C) {
+    return sizeof(float2) * (size_t)(P / C + tw_hi_entries(P, C) + tw_lo_entries(C));
+}
 
-int set_smem(twa_ctx* c, const void* kern) {
-    TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_bytes(c->fft->P)));
+// Call f with the cluster size as a compile-time constant.
+template <typename F>
+int with_c(int C, F f) {
+    switch (C) {
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        default: return f(std::integral_constant<int, 8>{});
+    }
+}
+
+// One CTA per unit (trajectory, vector pair), or one cluster of C CTAs per unit.
+template <typename... KArgs, typename... Args>
+int fft_launch(twa_ctx* c, void (*kern)(KArgs...), int64_t units, Args... args) {
+    const int C = c->fft->C;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(units * C));
+    cfg.blockDim = dim3(FT);
+    cfg.dynamicSmemBytes = smem_bytes(c->fft->P, C);
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = C > 1 ? 1 : 0;
+    TWA_CUDA(c, cudaLaunchKernelEx(&cfg, kern, args...));
     return TWA_OK;
+}
+
+template <int C>
+int set_smem(twa_ctx* c) {
+    const void* ks[] = {(const void*)k_fft_pred<C>, (const void*)k_fft_corr<C>, (const void*)k_fft_field<C>,
+                        (const void*)k_fft_noise<C>};
+    const int bytes = (int)smem_bytes(c->fft->P, C);
+    for (const void* k : ks) TWA_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    if (C > 1) {   // the cluster must fit: C SMs of one GPC, each holding one such CTA
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3(FT);
+        cfg.dynamicSmemBytes = (size_t)bytes;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        TWA_CUDA(c, cudaOccupancyMaxActiveClusters(&n, (const void*)k_fft_corr<C>, &cfg));
+        if (n < 1) return set_error(c, TWA_EUNSUPPORTED, "FFT route: no cluster of " + std::to_string(C) + " CTAs fits");
+    }
+    return TWA_OK;
+}
+
+int env_int(const char* name, int dflt) {
+    const char* v = getenv(name);
+    return v ? atoi(v) : dflt;
 }
 
 }  // namespace
 
 int fft_prepare(twa_ctx* c) {
-    int64_t P = 2 * c->N - 2 > 2 ? 2 * c->N - 2 : 2;
-    while (P % 2 || !smooth(P)) ++P;
-    if (P > FFT_MAX_P)
-        return set_error(c, TWA_EUNSUPPORTED, "FFT route: transform length " + std::to_string((long long)P) +
-                                                  " does not fit in shared memory (2N - 2 <= 28000 needed)");
+    const int64_t need = 2 * c->N - 2 > 2 ? 2 * c->N - 2 : 2;
+    int max_smem = 0;
+    TWA_CUDA(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    // the transform in one CTA while it fits its shared memory, else in the
+    // smallest cluster that holds it; TWA_FFT_CLUSTER = 1, 2, 4 or 8 forces the size
+    const int forced = env_int("TWA_FFT_CLUSTER", 0);
+    if (forced && forced != 1 && forced != 2 && forced != 4 && forced != 8)
+        return set_error(c, TWA_EINVAL, "TWA_FFT_CLUSTER must be 1, 2, 4 or 8");
+    int C = 0;
+    int64_t P = 0;
+    for (int cc = 1; cc <= FFT_MAX_C; cc *= 2) {
+        if (forced && cc != forced) continue;
+        // smallest 2^a 3^b 5^c >= need that is even (one CTA) or a multiple of 4 C
+        // (a cluster: every stage's butterfly count then divides among its CTAs)
+        const int64_t q = cc == 1 ? 2 : 4 * cc;
+        int64_t p = need;
+        while (p % q || !smooth(p)) ++p;
+        if (p / cc <= FFT_MAX_PLOC && smem_bytes(p, cc) <= (size_t)max_smem) {
+            C = cc;
+            P = p;
+            break;
+        }
+    }
+    if (!C)
+        return set_error(c, TWA_EUNSUPPORTED, "FFT route: the transform for N = " + std::to_string((long long)c->N) +
+                                                  " does not fit the shared memory of a cluster of " +
+                                                  std::to_string(forced ? forced : FFT_MAX_C) + " CTAs");
     FftPlan* f = new FftPlan();
     c->fft = f;
     f->P = P;
+    f->C = C;
     int64_t v = P;
     f->nst = 0;
-    while (v % 4 == 0) { f->radix[f->nst++] = 4; v /= 4; }
-    while (v % 2 == 0) { f->radix[f->nst++] = 2; v /= 2; }
-    while (v % 3 == 0) { f->radix[f->nst++] = 3; v /= 3; }
-    while (v % 5 == 0) { f->radix[f->nst++] = 5; v /= 5; }
+    if (C == 1) {   // radices 4, (2), 3, 5
+        while (v % 4 == 0) { f->radix[f->nst++] = 4; v /= 4; }
+        while (v % 2 == 0) { f->radix[f->nst++] = 2; v /= 2; }
+        while (v % 3 == 0) { f->radix[f->nst++] = 3; v /= 3; }
+        while (v % 5 == 0) { f->radix[f->nst++] = 5; v /= 5; }
+    } else {        // radices 5, 3, (2), 4: the powers of two last, so the strides stay multiples of C
+        while (v % 5 == 0) { f->radix[f->nst++] = 5; v /= 5; }
+        while (v % 3 == 0) { f->radix[f->nst++] = 3; v /= 3; }
+        int two = 0;   // v = 2^two now
+        for (int64_t t = v; t > 1; t /= 2) ++two;
+        if (two % 2) { f->radix[f->nst++] = 2; v /= 2; }
+        while (v % 4 == 0) { f->radix[f->nst++] = 4; v /= 4; }
+    }
+    // stage s has stride m_s = P / (r_0 ... r_s); it stays inside one CTA when C divides m_s
+    f->local_mask = 0;
+    for (int64_t s = 0, m = P; s < f->nst; ++s) {
+        m /= f->radix[s];
+        if (m % C == 0) f->local_mask |= 1u << s;
+    }
     Scratch<double> cseq_buf(c, c->stream);
     if (dev_malloc(c, &f->lam, sizeof(float) * P) != cudaSuccess ||
         dev_malloc(c, &f->tw, sizeof(float2) * P) != cudaSuccess ||
@@ -637,11 +899,7 @@ int fft_prepare(twa_ctx* c) {
     k_fft_sequence<<<(unsigned)((P / 2 + 256) / 256), 256, 0, c->stream>>>(cseq, P, c->alpha, c->w);
     k_fft_lambda<<<g, 256, 0, c->stream>>>(f->lam, f->nscale, f->nfreq, cseq, P, rp);
     TWA_CUDA(c, cudaGetLastError());
-    int rc;
-    if ((rc = set_smem(c, (const void*)k_fft_pred)) || (rc = set_smem(c, (const void*)k_fft_corr)) ||
-        (rc = set_smem(c, (const void*)k_fft_field)) || (rc = set_smem(c, (const void*)k_fft_noise)))
-        return rc;
-    return TWA_OK;
+    return with_c(C, [&](auto cc) { return set_smem<decltype(cc)::value>(c); });
 }
 
 void fft_free(twa_ctx* c) {
@@ -658,9 +916,7 @@ int fft_predict(twa_ctx* c) {
     a.X = t->X; a.Y = t->Y; a.Z = t->Z;
     a.Bnx = t->Bx; a.Bny = t->By;
     a.oX = t->Xp; a.oY = t->Yp; a.oZ = t->Zp;
-    k_fft_pred<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(a);
-    TWA_CUDA(c, cudaGetLastError());
-    return TWA_OK;
+    return with_c(c->fft->C, [&](auto cc) { return fft_launch(c, k_fft_pred<decltype(cc)::value>, c->M, a); });
 }
 
 int fft_correct(twa_ctx* c) {
@@ -675,20 +931,22 @@ int fft_correct(twa_ctx* c) {
     a.d_count = c->d_count;
     a.n_window = c->n_window;
     a.n_stride = c->n_stride;
-    k_fft_corr<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(a);
-    TWA_CUDA(c, cudaGetLastError());
-    return TWA_OK;
+    return with_c(c->fft->C, [&](auto cc) { return fft_launch(c, k_fft_corr<decltype(cc)::value>, c->M, a); });
 }
 
 int fft_noise(twa_ctx* c) {
     TcState* t = c->tc;
     FftArgs a = base_args(c);
     a.d_t = c->d_t;
-    k_fft_noise<<<(unsigned)c->M, FT, smem_bytes(c->fft->P), c->stream>>>(
-        a, c->fft->nscale, c->fft->nfreq, c->seed, c->opts.traj_offset, (float)sqrt(c->Gamma * c->dt),
-        (float)sqrt(c->dt), t->Bx, t->By);
-    TWA_CUDA(c, cudaGetLastError());
-    return TWA_OK;
+    const float* ns = c->fft->nscale;
+    const int32_t* nf = c->fft->nfreq;
+    const uint64_t seed = c->seed;
+    const int64_t m0 = c->opts.traj_offset;
+    const float sgdt = (float)sqrt(c->Gamma * c->dt), sdt = (float)sqrt(c->dt);
+    float *bx = t->Bx, *by = t->By;
+    return with_c(c->fft->C, [&](auto cc) {
+        return fft_launch(c, k_fft_noise<decltype(cc)::value>, c->M, a, ns, nf, seed, m0, sgdt, sdt, bx, by);
+    });
 }
 
 int fft_field(twa_ctx* c, const double* s, double* P, int64_t K) {
@@ -696,9 +954,7 @@ int fft_field(twa_ctx* c, const double* s, double* P, int64_t K) {
     a.field_in = s;
     a.field_out = P;
     a.K = K;
-    k_fft_field<<<(unsigned)((K + 1) / 2), FT, smem_bytes(c->fft->P), c->stream>>>(a);
-    TWA_CUDA(c, cudaGetLastError());
-    return TWA_OK;
+    return with_c(c->fft->C, [&](auto cc) { return fft_launch(c, k_fft_field<decltype(cc)::value>, (K + 1) / 2, a); });
 }
 
 }  // namespace twa

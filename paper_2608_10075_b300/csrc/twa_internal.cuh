@@ -42,7 +42,10 @@ struct TcState {
     int pair = 0;                                // CTA pairs: 256-row tiles on clusters of two (cta_group::2)
     int num_sms = 148;
     int clusters = 0;                            // resident clusters of two of the pair kernel
+    // images of W / w and L / sqrt(w) (w > 0; of W and L when w = 0): a change of
+    // w leaves them bit for bit unchanged and enters only through the factors below
     __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Lhi = nullptr, *Llo = nullptr;   // [N][ldk]
+    double wsc = 1.0, lsc = 1.0;   // W = wsc * (image of W), L = lsc * (image of L)
     float *X = nullptr, *Y = nullptr, *Z = nullptr;       // state [M][N]
     float *Xp = nullptr, *Yp = nullptr, *Zp = nullptr;    // predictor
     float *Bx = nullptr, *By = nullptr;                   // noise part of the field increment
@@ -72,7 +75,10 @@ struct TcState {
 
 // Circulant-embedding FFT plan of the Toeplitz pump matrix (twa_fft.cu).
 struct FftPlan {
-    int64_t P = 0;               // transform length: smallest even 2^a 3^b 5^c >= max(2, 2N - 2)
+    int64_t P = 0;               // transform length: smallest 2^a 3^b 5^c >= max(2, 2N - 2), even (one CTA)
+                                 // or a multiple of 4 C (a cluster of C CTAs per trajectory)
+    int C = 1;                   // CTAs per trajectory: 1, or 2, 4, 8 for P > 28000 (thread-block cluster)
+    unsigned local_mask = 0;     // bit s: the stage of stride P / (r_0 ... r_s) stays inside one CTA
     int nst = 0;                 // number of stages
     int radix[40] = {0};         // radix of each stage (DIF order)
     float* lam = nullptr;        // spectrum of the embedding, in the DIF output order

@@ -371,7 +371,8 @@ struct TcMaps {
 
 struct TcArgs {
     int64_t N, M, ldk, n_rt, n_vec;   // n_vec: B rows (2M, or K vectors in the field mode)
-    float G, dt, sgdt, sdt;
+    float hdtG, hdtw, sgdt, sdt;      // dt G / 2, dt w / 2 (w: scale of the W image), sqrt(G dt), sqrt(w dt)
+    float fsc;                        // FIELD: factor applied to the accumulator (the image's scale)
     int renorm;
     int integ;                        // TWA_INT_HEUN or TWA_INT_MIDPOINT
     const float *X, *Y, *Z;           // PRED: s; CORR: s~ (midpoint scheme: s)
@@ -681,9 +682,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
             if constexpr (PAIR) rt = 2 * rt + rank;   // this CTA's row tile of the unit
             const TcArgs& args = *ap_;        // this tile's problem (shadows the launch argument)
             const int64_t M = args.M;
+            const float hdtG = args.hdtG, hdtw = args.hdtw, sdt = args.sdt, sgdt = args.sgdt, fsc = args.fsc;
             // every rounding of the epilogue is spelled out (fmaf, __fmul_rn,
             // __fadd_rn), so that all kernel variants give the same bits
-            const float Gm = args.G, hdt = 0.5f * args.dt;
             const int64_t i0 = rt * BM, n0 = ct * BN, m0 = n0 >> 1;
             const int64_t i = i0 + 32 * q + lane;        // site of this thread
             const bool site_ok = i < args.N;
@@ -732,19 +733,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
                                 const int64_t n = n0 + 16 * c + j;
-                                if (n < args.n_vec) args.field_out[n * args.N + i] = pv[j];
+                                if (n < args.n_vec) args.field_out[n * args.N + i] = __fmul_rn(fsc, pv[j]);
                             }
                         }
                     } else if constexpr (EM == MODE_LETA) {
-                        // noise part of the field increment: sqrt(G dt) xi^a - sqrt(dt) (L eta^a)_i
+                        // noise part of the field increment: sqrt(G dt) xi^a - sqrt(dt) (L eta^a)_i,
+                        // sqrt(dt) L = sqrt(w dt) times the accumulated image of L / sqrt(w)
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj) {
                             const int jl = 8 * c + jj;
                             const int64_t m = m0 + jl;
                             if (!site_ok || m >= M) continue;
                             const int64_t e = m * args.N + i;
-                            args.oBnx[e] = fmaf(-args.sdt, pv[2 * jj], __fmul_rn(args.sgdt, sS[2 * jl]));
-                            args.oBny[e] = fmaf(-args.sdt, pv[2 * jj + 1], __fmul_rn(args.sgdt, sS[2 * jl + 1]));
+                            args.oBnx[e] = fmaf(-sdt, pv[2 * jj], __fmul_rn(sgdt, sS[2 * jl]));
+                            args.oBny[e] = fmaf(-sdt, pv[2 * jj + 1], __fmul_rn(sgdt, sS[2 * jl + 1]));
                         }
                     } else {
                         float rx[8], ry[8], rz[8];
@@ -756,9 +758,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                             if (!site_ok || m >= M) continue;
                             const int64_t e = m * args.N + i;
                             const float x = args.X[e], y = args.Y[e], z = args.Z[e];
-                            // B^a = 1/2 (G S^a - P^a) dt + noise part
-                            const float Bxv = fmaf(fmaf(Gm, sS[2 * jl], -pv[2 * jj]), hdt, args.Bnx[e]);
-                            const float Byv = fmaf(fmaf(Gm, sS[2 * jl + 1], -pv[2 * jj + 1]), hdt, args.Bny[e]);
+                            // B^a = 1/2 (G S^a - P^a) dt + noise part, P = w times the
+                            // accumulated product of the image of W / w
+                            const float Bxv = fmaf(-hdtw, pv[2 * jj], fmaf(hdtG, sS[2 * jl], args.Bnx[e]));
+                            const float Byv = fmaf(-hdtw, pv[2 * jj + 1], fmaf(hdtG, sS[2 * jl + 1], args.Bny[e]));
                             const int64_t r0 = (2 * m) * args.ldk + i;
                             if constexpr (EM == MODE_PRED) {
                                 float xp, yp, zp;
@@ -908,12 +911,13 @@ __global__ void k_wait_probe(unsigned long long* flags, unsigned long long limit
     }
 }
 
+// Images of inv * src (inv: the reciprocal of the scale the epilogue applies).
 __global__ void k_split_matrix(const double* src, int64_t N, int64_t ldk, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                               int tf32) {
+                               int tf32, double inv) {
     const int64_t n2 = N * ldk;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / ldk, k = e - r * ldk;
-        const float v = (k < N) ? (float)src[r * N + k] : 0.f;
+        const float v = (k < N) ? (float)(inv * src[r * N + k]) : 0.f;
         if (tf32) {   // TF32 images in FP32 containers: hi, and lo where it exists
             const float h = to_tf32(v);
             reinterpret_cast<float*>(hi)[e] = h;
@@ -1324,10 +1328,11 @@ TcArgs base_args(twa_ctx* c) {
     a.ldk = t->ldk;
     a.n_rt = t->n_rt;
     a.n_vec = 2 * t->M;
-    a.G = (float)c->Gamma;
-    a.dt = (float)c->dt;
+    a.hdtG = (float)(0.5 * c->dt * c->Gamma);
+    a.hdtw = (float)(0.5 * c->dt * t->wsc);
     a.sgdt = (float)sqrt(c->Gamma * c->dt);
-    a.sdt = (float)sqrt(c->dt);
+    a.sdt = (float)(sqrt(c->dt) * t->lsc);
+    a.fsc = 1.0f;
     a.renorm = c->opts.renormalize;
     a.integ = c->opts.integrator;
     a.flags = c->d_flags;
@@ -1461,8 +1466,13 @@ int tc_prepare(twa_ctx* c) {
     for (int k = 0; k < (tf32 && t->terms == 1 ? 2 : 4); ++k)
         if (dev_malloc(c, m4[k], nb) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device operand images");
     const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
-    k_split_matrix<<<g, 256, 0, c->stream>>>(c->W64, c->N, t->ldk, t->Whi, t->Wlo, tf32);
-    k_split_matrix<<<g, 256, 0, c->stream>>>(c->L64, c->N, t->ldk, t->Lhi, t->Llo, tf32);
+    // W = w W1 and L = sqrt(w) L1 with W1, L1 independent of w: the images hold W1
+    // and L1 and the epilogues apply w and sqrt(w), so runs at w (1 +- delta) differ
+    // only in those two FP32 factors (finite differences in w see no image rounding)
+    t->wsc = c->w > 0.0 ? c->w : 1.0;
+    t->lsc = c->w > 0.0 ? sqrt(c->w) : 1.0;
+    k_split_matrix<<<g, 256, 0, c->stream>>>(c->W64, c->N, t->ldk, t->Whi, t->Wlo, tf32, 1.0 / t->wsc);
+    k_split_matrix<<<g, 256, 0, c->stream>>>(c->L64, c->N, t->ldk, t->Lhi, t->Llo, tf32, 1.0 / t->lsc);
     TWA_CUDA(c, cudaGetLastError());
     return make_matrix_maps(c);
 }
@@ -1522,7 +1532,7 @@ int tc_set_extra_matrix(twa_ctx* c, int slot, const double* A64) {
             return set_error(c, TWA_ENOMEM, "device extra matrix images");
     }
     const unsigned g = nblk(c->N * t->ldk, 256) > 8192 ? 8192 : nblk(c->N * t->ldk, 256);
-    k_split_matrix<<<g, 256, 0, c->stream>>>(A64, c->N, t->ldk, t->Xhi[slot], t->Xlo[slot], 0);
+    k_split_matrix<<<g, 256, 0, c->stream>>>(A64, c->N, t->ldk, t->Xhi[slot], t->Xlo[slot], 0, 1.0);
     TWA_CUDA(c, cudaGetLastError());
     int rc;
     if ((rc = make_map(c, &t->tmXhi[slot], t->Xhi[slot], c->N, c->N, t->ldk, BM, t->kc))) return rc;
@@ -1557,9 +1567,12 @@ int tc_contract_f32(twa_ctx* c, int which, const float* in, float* out, int64_t 
     TcArgs a = base_args(c);
     a.n_vec = K;
     a.field_out = out;
-    return t->terms == 3   ? launch_cfg<MODE_FIELD, 3>(c, m, a)
-           : t->terms == 2 ? launch_cfg<MODE_FIELD, 2>(c, m, a)
-                           : launch_cfg<MODE_FIELD, 1>(c, m, a);
+    a.fsc = which == 0 ? (float)t->wsc : which == 1 ? (float)t->lsc : 1.0f;   // extra matrices: unscaled images
+    // L and dL/dalpha against the noise: the step's L.eta product count
+    const int nterms = (which == 1 || which == 3) ? leta_terms(t) : t->terms;
+    return nterms == 3   ? launch_cfg<MODE_FIELD, 3>(c, m, a)
+           : nterms == 2 ? launch_cfg<MODE_FIELD, 2>(c, m, a)
+                         : launch_cfg<MODE_FIELD, 1>(c, m, a);
 }
 
 void tc_free(twa_ctx* c) {
@@ -2032,6 +2045,7 @@ int tc_field(twa_ctx* c, const double* s, double* P, int64_t K, int which) {
         TcArgs fa = base_args(c);
         fa.n_vec = K;
         fa.field_out = out;
+        fa.fsc = (float)(which == 1 ? t->lsc : t->wsc);
         rc = nterms == 3   ? launch_cfg<MODE_FIELD, 3>(c, fm, fa)
              : nterms == 2 ? launch_cfg<MODE_FIELD, 2>(c, fm, fa)
                            : launch_cfg<MODE_FIELD, 1>(c, fm, fa);

@@ -98,8 +98,8 @@ def precision_study(args):
         print(json.dumps(line), flush=True)
 
 
-def _observables(N, alpha, w, G, dt, steps, M, t0):
-    with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3", window_start=t0) as g:
+def _observables(N, alpha, w, G, dt, steps, M, t0, precision="bf16x3"):
+    with twa.TWA(N, alpha, w, G, dt, seed=0, precision=precision, window_start=t0) as g:
         g.run(M, steps)
         return g.observables()
 
@@ -115,11 +115,12 @@ def gradient_study(args):
     steps = args.steps or int(round(c["T"] / dt))
     t0 = 0.5 * steps * dt            # window: the second half of the run
     M, d = args.M, c["delta"]
+    prec = getattr(args, "precision", "bf16x3")
     out = {"study": "gradients", "N": N, "alpha": alpha, "w": w, "dt": dt, "steps": steps, "M": M,
-           "checkpoint": c["checkpoint"], "delta": d}
+           "checkpoint": c["checkpoint"], "delta": d, "precision": prec}
     for obj in ("SpSm", "g2"):
         t = time.perf_counter()
-        with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3", window_start=t0) as g:
+        with twa.TWA(N, alpha, w, G, dt, seed=0, precision=prec, window_start=t0) as g:
             r = g.grad(obj, M, steps, checkpoint=c["checkpoint"], want_alpha=True)
         out["adjoint_" + obj] = {**r, "seconds": time.perf_counter() - t}
     fd = {}
@@ -129,16 +130,16 @@ def gradient_study(args):
         for s in (+1, -1):
             aa = alpha + s * d if key == "alpha" else alpha
             ww = w * (1 + s * d) if key == "w" else w
-            vals.append(_observables(N, aa, ww, G, dt, steps, M, t0))
+            vals.append(_observables(N, aa, ww, G, dt, steps, M, t0, prec))
         for obj in ("SpSm", "g2"):
             fd["d%s_d%s" % (obj, key)] = (vals[0][obj] - vals[1][obj]) / (2 * h)
     out["crn_fd"] = fd
     out["crn_fd_seconds"] = time.perf_counter() - t
     # The same differences through twa_grad's own forward run (the run the adjoint
-    # differentiates), from the forward means it returns. The BF16 hi/lo images of
-    # W and L represent w_ij to ~2^-17 relative, so a parameter step delta moves the
-    # represented matrix by delta plus rounding of that size: differences need
-    # delta >> 2^-17 (1e-3 leaves ~2^-17 / 2e-3 = 0.4 % of rounding in the quotient).
+    # differentiates), from the forward means it returns. The tensor-core images
+    # hold W / w and L / sqrt(w), so a step in w changes only two FP32 factors; a
+    # step in alpha changes the images, whose BF16 hi/lo pairs represent w_ij to
+    # ~2^-17 relative (rounding of that size enters the alpha quotient).
     for dd in (d, 10 * d):
         fdt = {}
         for key, h in (("w", w * dd), ("alpha", dd)):
@@ -146,7 +147,7 @@ def gradient_study(args):
             for s in (+1, -1):
                 aa = alpha + s * dd if key == "alpha" else alpha
                 ww = w * (1 + s * dd) if key == "w" else w
-                with twa.TWA(N, aa, ww, G, dt, seed=0, precision="bf16x3", window_start=t0) as g:
+                with twa.TWA(N, aa, ww, G, dt, seed=0, precision=prec, window_start=t0) as g:
                     mu = g.grad("SpSm", M, steps, checkpoint=c["checkpoint"], want_alpha=False)["mu"]
                 Sz, A, A2, ASz, Sz2 = mu
                 spsm = A + 0.5 * Sz
@@ -369,6 +370,7 @@ def main():
     q.add_argument("--w", type=float, default=0.0, help="pump prefactor (default N Gamma / 4 of the workload)")
     q.add_argument("--dt", type=float, default=0.0)
     q.add_argument("--delta", type=float, default=0.0, help="finite-difference step (default 1e-4)")
+    q.add_argument("--precision", default="bf16x3", help="precision of the adjoint and of the differences")
     a = ap.parse_args()
     if a.cmd == "precision":
         precision_study(a)

@@ -78,7 +78,8 @@ class Obs(ctypes.Structure):
                                                   "G2num", "G2num_se", "g2", "g2_se")] + \
                [(n, ctypes.c_int64) for n in ("M", "steps", "samples")] + \
                [(n, ctypes.c_double) for n in ("w_max", "w_min", "w_tilde", "stability", "min_pivot")] + \
-               [(n, ctypes.c_int64) for n in ("clipped", "nonfinite")] + [("factor_residual", ctypes.c_double)]
+               [(n, ctypes.c_int64) for n in ("clipped", "nonfinite")] + [("factor_residual", ctypes.c_double)] + \
+               [(n, ctypes.c_int64) for n in ("fft_length", "fft_ctas")]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

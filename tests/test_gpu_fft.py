@@ -99,11 +99,139 @@ def test_fft_route_full_size_runs():
         assert err < 1e-3, (m, err)
 
 
-def test_fft_route_rejects_what_it_cannot_do():
+def test_fft_route_rejects_what_it_cannot_do(monkeypatch):
     twa = _twa()
     with pytest.raises(twa.TWAError) as e:
-        twa.TWA(20000, 1.0, 1.0, 1.0, 1e-4, precision="bf16x3", ws_route="fft")
+        twa.TWA(64, 1.0, 1.0, 1.0, 1e-4, precision="fp64", ws_route="fft")
     assert e.value.name == "TWA_EUNSUPPORTED"
+    monkeypatch.setenv("TWA_FFT_CLUSTER", "3")
+    with pytest.raises(twa.TWAError) as e:
+        twa.TWA(64, 1.0, 1.0, 1.0, 1e-4, precision="bf16x3", ws_route="fft")
+    assert e.value.name == "TWA_EINVAL"
+
+
+# ---------------------------------------------------------------------------
+# transforms longer than one CTA's shared memory (P > 28000, N > 14001): one
+# thread-block cluster of 2, 4 or 8 CTAs per trajectory, the transform spread
+# over their shared memories
+
+def _toeplitz_reference(s, alpha, w):
+    """sum_j w / (1 + |i - j|)^alpha s_j for each row of s, in FP64 by a
+    zero-padded numpy FFT (exact linear convolution up to FP64 rounding)."""
+    K, N = s.shape
+    d = np.arange(-(N - 1), N, dtype=np.float64)
+    k = w / np.power(np.abs(d) + 1.0, alpha)
+    n = 1 << int(math.ceil(math.log2(3 * N)))
+    S = np.fft.rfft(s, n=n, axis=1)
+    Kf = np.fft.rfft(k, n=n)
+    full = np.fft.irfft(S * Kf[None, :], n=n, axis=1)
+    return full[:, N - 1:2 * N - 1]
+
+
+def _circle(g, M=2):
+    """(P, CTAs per trajectory) the context reports after a one-step run."""
+    g.run(M, 1)
+    ob = g.observables()
+    return ob["fft_length"], ob["fft_ctas"]
+
+
+def test_toeplitz_reference_is_the_dense_product():
+    rng = np.random.default_rng(1)
+    s = rng.normal(size=(3, 301))
+    W = pump_matrix(301, 0.7, 5.0)
+    assert np.allclose(_toeplitz_reference(s, 0.7, 5.0), s @ W.T, rtol=0, atol=1e-11 * np.abs(s @ W.T).max())
+
+
+@pytest.mark.parametrize("N,alpha,ctas", [(14002, 1.0, 2), (20000, 0.5, 2), (30001, 1.0, 4), (56002, 2.0, 8)])
+def test_cluster_fft_field_matches_definition(N, alpha, ctas):
+    import torch
+    twa = _twa()
+    K = 3
+    rng = np.random.default_rng(N)
+    s = rng.normal(size=(K, N))
+    with twa.TWA(N, alpha, N / 2.0, 1.0, 1e-6, precision="bf16x3", ws_route="fft") as g:
+        P = g.field(torch.tensor(s, device="cuda")).cpu().numpy()
+        plen, c = _circle(g)
+    assert c == ctas and plen % (4 * ctas) == 0 and plen >= 2 * N - 2 and plen // ctas <= 28000
+    ref = _toeplitz_reference(s, alpha, N / 2.0)
+    assert np.linalg.norm(P - ref) <= 2e-6 * np.linalg.norm(ref)
+    assert np.max(np.abs(P - ref)) <= 5e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("ctas", [2, 4, 8])
+@pytest.mark.parametrize("N", [3, 37, 1000, 10000])
+def test_forced_cluster_fft_field_matches_definition(monkeypatch, N, ctas):
+    # the cluster form on transforms that would fit one CTA: the stages whose
+    # stride C does not divide run through the other CTAs' shared memory
+    import torch
+    monkeypatch.setenv("TWA_FFT_CLUSTER", str(ctas))
+    twa = _twa()
+    K, alpha = 5, 1.3
+    rng = np.random.default_rng(N + ctas)
+    s = rng.normal(size=(K, N))
+    with twa.TWA(N, alpha, N / 2.0, 1.0, 1e-6, precision="bf16x3", ws_route="fft") as g:
+        P = g.field(torch.tensor(s, device="cuda")).cpu().numpy()
+        plen, c = _circle(g)
+    assert c == ctas and plen % (4 * ctas) == 0
+    ref = _toeplitz_reference(s, alpha, N / 2.0)
+    assert np.linalg.norm(P - ref) <= 2e-6 * np.linalg.norm(ref)
+    assert np.max(np.abs(P - ref)) <= 5e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("integrator", ["heun", "midpoint"])
+def test_cluster_fft_route_tracks_one_cta(monkeypatch, integrator):
+    # N = 300 on clusters of 2, 4, 8 against one CTA per trajectory: both draw
+    # the same noise (dense L.eta), so trajectories differ by the transform's
+    # FP32 rounding only; moments and observables come out the same
+    twa = _twa()
+    N, M, alpha, w, dt, steps = 300, 40, 1.0, 20.0, 1e-3, 6
+    out = {}
+    for ctas in (1, 2, 4, 8):
+        monkeypatch.setenv("TWA_FFT_CLUSTER", str(ctas))
+        with twa.TWA(N, alpha, w, 1.0, dt, seed=3, precision="bf16x3", ws_route="fft", integrator=integrator) as g:
+            g.run(M, steps)
+            out[ctas] = (g.get_state(), g.observables())
+    for ctas in (2, 4, 8):
+        err = max(np.max(np.abs(a - b)) for a, b in zip(out[1][0], out[ctas][0]))
+        assert err < 2e-5, (ctas, err)
+        assert out[ctas][1]["fft_ctas"] == ctas
+        for k in ("Sz", "SpSm", "g2"):
+            assert abs(out[ctas][1][k] - out[1][1][k]) <= 1e-4 * abs(out[1][1][k]), (ctas, k)
+
+
+def test_cluster_fft_route_tracks_dense_route_at_n20000():
+    twa = _twa()
+    N, alpha, w, G, dt, M, steps = 20000, 1.0, 10000.0, 1.0, 1e-5, 8, 3
+    st = {}
+    for route in ("fft", "dense"):
+        with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3", ws_route=route) as g:
+            g.run(M, steps)
+            st[route] = g.get_state()
+            if route == "fft":
+                assert g.observables()["fft_ctas"] == 2
+    x, y, z = st["fft"]
+    assert np.max(np.abs(x * x + y * y + z * z - 3.0)) < 5e-6
+    err = max(np.max(np.abs(a - b)) for a, b in zip(st["fft"], st["dense"]))
+    assert err < 1e-3, err
+
+
+def test_cluster_circulant_route_tracks_its_oracle():
+    # N = 15000 (P = 30000 on clusters of two): every step FFT-only; trajectories
+    # 0 and 5 against the oracle on the circle length the library reports
+    from oracle.circulant import TWAOracleCirculant
+    twa = _twa()
+    N, alpha, w, G, dt, M, steps = 15000, 1.0, 7500.0, 1.0, 2e-5, 6, 2
+    with twa.TWA(N, alpha, w, G, dt, seed=0, precision="bf16x3", ws_route="fft", noise_route="circulant") as g:
+        g.run(M, steps)
+        x, y, z = g.get_state()
+        ob = g.observables()
+    assert ob["fft_ctas"] == 2 and ob["fft_length"] % 8 == 0
+    assert np.max(np.abs(x * x + y * y + z * z - 3.0)) < 5e-6
+    for m in (0, 5):
+        o = TWAOracleCirculant(N, alpha, w, G, dt, 0, 1, m0=m, P=ob["fft_length"])
+        o.run(steps)
+        err = max(np.max(np.abs(a[m] - b[0])) for a, b in zip((x, y, z), (o.sx, o.sy, o.sz)))
+        assert err < 5e-5, (m, err)
 
 
 # ---------------------------------------------------------------------------

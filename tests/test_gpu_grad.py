@@ -3,8 +3,8 @@ central finite differences with common random numbers, through the C ABI.
 
 The FP64 GPU adjoint and the oracle tangent compute the same pathwise
 derivative of the same discretised trajectories, so they agree per trajectory
-to rounding (1e-8 relative here). The mixed-precision adjoint (FP32 tape,
-BF16X3 contractions) differs by its arithmetic only: over the short horizons
+to rounding (1e-8 relative here). The mixed-precision adjoints (FP32 tape,
+BF16X3 or BF16X2 contractions) differ by their arithmetic only: over the short horizons
 tested it stays within 1e-2 of the FP64 result, and the paired per-trajectory
 difference of the two (the precision error of the estimate) is checked to be a
 small fraction of the gradient's standard error.
@@ -85,35 +85,87 @@ def test_fp64_adjoint_matches_crn_finite_difference_on_gpu():
     assert abs(r["dJ_dalpha"] - fd_a) <= 1e-5 * abs(fd_a)
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
 @pytest.mark.parametrize("objective", ["SpSm", "g2"])
-def test_mixed_adjoint_close_to_fp64(objective):
+def test_mixed_adjoint_close_to_fp64(objective, prec):
     twa = _twa()
     N, alpha, w, G, dt, M, steps, t0 = 256, 1.0, 32.0, 1.0, 1e-3, 128, 40, 0.02
     out = {}
-    for prec in ("fp64", "bf16x3"):
-        with twa.TWA(N, alpha, w, G, dt, seed=1, precision=prec, window_start=t0) as g:
-            out[prec] = g.grad(objective, M, steps, checkpoint=16)
+    for p in ("fp64", prec):
+        with twa.TWA(N, alpha, w, G, dt, seed=1, precision=p, window_start=t0) as g:
+            out[p] = g.grad(objective, M, steps, checkpoint=16)
     for k in ("dJ_dw", "dJ_dalpha"):
-        a, b = out["fp64"][k], out["bf16x3"][k]
+        a, b = out["fp64"][k], out[prec][k]
         assert abs(a - b) <= 1e-2 * abs(a) + 3 * out["fp64"][k + "_se"] * 1e-2, (k, a, b)
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
 @pytest.mark.parametrize("objective", ["SpSm", "g2"])
-def test_mixed_adjoint_error_is_far_below_the_sampling_error(objective):
-    # per-trajectory gradient samples of the BF16X3 and FP64 adjoints on the same
+def test_mixed_adjoint_error_is_far_below_the_sampling_error(objective, prec):
+    # per-trajectory gradient samples of the mixed and FP64 adjoints on the same
     # trajectories: their paired difference (the precision error) must be a small
     # fraction of the standard error the gradient is quoted with
     import math
     twa = _twa()
     N, alpha, w, G, dt, M, steps, t0 = 256, 1.0, 32.0, 1.0, 1e-3, 128, 40, 0.02
     out = {}
-    for prec in ("fp64", "bf16x3"):
-        with twa.TWA(N, alpha, w, G, dt, seed=1, precision=prec, window_start=t0) as g:
-            out[prec] = g.grad(objective, M, steps, checkpoint=16, per_traj=True)
+    for p in ("fp64", prec):
+        with twa.TWA(N, alpha, w, G, dt, seed=1, precision=p, window_start=t0) as g:
+            out[p] = g.grad(objective, M, steps, checkpoint=16, per_traj=True)
     for col, k in ((0, "dJ_dw"), (1, "dJ_dalpha")):
-        d = out["bf16x3"]["per_traj"][:, col] - out["fp64"]["per_traj"][:, col]
+        d = out[prec]["per_traj"][:, col] - out["fp64"]["per_traj"][:, col]
         paired, paired_se = abs(float(d.mean())), float(d.std(ddof=1) / math.sqrt(M))
         assert paired + 3.0 * paired_se <= 0.2 * out["fp64"][k + "_se"], (k, paired, paired_se, out["fp64"][k + "_se"])
+
+
+def test_mixed_adjoint_matches_finite_differences_at_delta_1e4():
+    # central differences with common random numbers at the relative step
+    # delta = 1e-4 in w, through the same BF16X3 forward run the adjoint
+    # differentiates: the tensor-core images hold W / w and L / sqrt(w), so the
+    # runs at w (1 +- delta) differ only in the FP32 factors w and sqrt(w) of the
+    # epilogue, not by a rounding of their images of size 2^-17 / (2 delta) ~ 4 %.
+    # (BF16X2 and BF16 round the state itself to BF16 for W.s: their forward map
+    # is piecewise constant on the scale 2^-9, which a step of 1e-4 does not
+    # resolve; their adjoints are checked against the FP64 adjoint above.)
+    prec = "bf16x3"
+    twa = _twa()
+    N, alpha, w, G, dt, M, steps, t0, d = 256, 1.0, 32.0, 1.0, 1e-3, 128, 60, 0.03, 1e-4
+    kw = dict(seed=5, precision=prec, window_start=t0)
+    with twa.TWA(N, alpha, w, G, dt, **kw) as g:
+        r = g.grad("SpSm", M, steps, checkpoint=16, want_alpha=False)
+    J = []
+    for s in (+1, -1):
+        with twa.TWA(N, alpha, w * (1 + s * d), G, dt, **kw) as g:
+            J.append(g.grad("SpSm", M, steps, checkpoint=16, want_alpha=False)["J"])
+    fd = (J[0] - J[1]) / (2 * w * d)
+    assert abs(r["dJ_dw"] - fd) <= 1e-2 * abs(fd), (r["dJ_dw"], fd)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "fp32", "tf32"])
+def test_tensor_core_images_do_not_depend_on_w(prec):
+    # W.s and L.eta of the step at w and at 2w: the images are those of W / w
+    # and L / sqrt(w), so the FP32 results scale exactly (2 is exact, and so is
+    # sqrt(2) w.r.t. the same rounding of the accumulated product times the
+    # factor: compare against the unit-w product times the factor)
+    import torch
+    twa = _twa()
+    N, alpha, K = 300, 0.8, 6
+    g_ = torch.Generator().manual_seed(3)
+    s = torch.randn(K, N, generator=g_, dtype=torch.float64).cuda()
+    out = {}
+    for w in (4.0, 8.0, 4.0 * (1 + 1e-4)):
+        with twa.TWA(N, alpha, w, 1.0, 1e-3, precision=prec) as g:
+            out[w] = (g.contract(s, "W").cpu().numpy(), g.contract(s, "L").cpu().numpy())
+    W4, L4 = out[4.0]
+    W8, L8 = out[8.0]
+    assert np.array_equal(W8, 2.0 * W4)
+    # L: sqrt(8) / sqrt(4) = sqrt(2) is not exact in FP32; the accumulators agree,
+    # so the results differ by the rounding of the two products only
+    np.testing.assert_allclose(L8, np.sqrt(2.0) * L4, rtol=3e-7, atol=0)
+    w1 = 4.0 * (1 + 1e-4)
+    W1, L1 = out[w1]
+    np.testing.assert_allclose(W1, W4 * (w1 / 4.0), rtol=3e-7, atol=0)
+    np.testing.assert_allclose(L1, L4 * np.sqrt(w1 / 4.0), rtol=3e-7, atol=0)
 
 
 def test_autograd_function_wraps_the_adjoint():

@@ -61,10 +61,10 @@ def test_spectrum_is_nonnegative(N, alpha):
     assert lam.min() >= -1e-12 * lam.max()
 
 
-def _explicit_map(N, alpha, w):
+def _explicit_map(N, alpha, w, P=None):
     """Real N x 2P matrices Ax, Ay with chi^x = Ax [a; b], chi^y = Ay [a; b],
     from Y_j = sum_k sqrt(lam_k / P) (a_k + i b_k) (cos + i sin)(2 pi j k / P)."""
-    P = embedding_length(N)
+    P = embedding_length(N) if P is None else P
     c = embedded_sequence(N, alpha, w, P)
     lam = [sum(c[d] * math.cos(2.0 * math.pi * k * d / P) for d in range(P)) for k in range(P)]
     Ax = np.zeros((N, 2 * P))
@@ -87,6 +87,30 @@ def test_draw_has_covariance_W(N, alpha, w):
     assert np.allclose(Ax @ Ax.T, W, rtol=0, atol=tol)
     assert np.allclose(Ay @ Ay.T, W, rtol=0, atol=tol)
     assert np.allclose(Ax @ Ay.T, 0.0, rtol=0, atol=tol)   # independent components
+
+
+@pytest.mark.parametrize("N,alpha,w,P", [(5, 1.0, 3.0, 16), (7, 0.5, 1.0, 32), (9, 2.0, 4.0, 24), (6, 0.0, 2.0, 40),
+                                         (4, math.inf, 1.0, 8)])
+def test_any_longer_even_circle_has_covariance_W(N, alpha, w, P):
+    # the cluster form of the library takes P a multiple of 4 C, not always the
+    # smallest even smooth bound: the embedding on any even P >= 2N - 2 is exact
+    assert P % 2 == 0 and P > embedding_length(N)
+    Ax, Ay = _explicit_map(N, alpha, w, P)
+    W = pump_matrix(N, alpha, w)
+    tol = 1e-12 * w * Ax.shape[1]
+    assert np.allclose(Ax @ Ax.T, W, rtol=0, atol=tol)
+    assert np.allclose(Ay @ Ay.T, W, rtol=0, atol=tol)
+    assert np.allclose(Ax @ Ay.T, 0.0, rtol=0, atol=tol)
+    o = TWAOracleCirculant(N, alpha, w, 1.0, 1e-3, 3, 2, P=P)
+    assert o.P == P and o.L.size == 0
+    cx, cy = circulant_chi(3, np.array([0, 1]), 4, N, o.lam)
+    a, b = philox_normals(3, np.uint64(1), np.uint64(4), np.arange(P, dtype=np.uint64), 2)
+    v = np.concatenate([a, b])
+    extra = 1e-6 if alpha == 0.0 else 0.0
+    assert np.allclose(cx[1], Ax @ v, rtol=0, atol=1e-12 * (1 + np.abs(Ax @ v).max()) + extra)
+    assert np.allclose(cy[1], Ay @ v, rtol=0, atol=1e-12 * (1 + np.abs(Ay @ v).max()) + extra)
+    with pytest.raises(ValueError):
+        TWAOracleCirculant(N, alpha, w, 1.0, 1e-3, 3, 2, P=2 * N - 4)
 
 
 @pytest.mark.parametrize("N,alpha,w", [(5, 1.0, 3.0), (8, 0.0, 2.0), (11, 1.7, 0.5), (2, math.inf, 1.0)])
