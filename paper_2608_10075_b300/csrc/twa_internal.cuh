@@ -51,9 +51,20 @@ struct TcState {
     float *Bx = nullptr, *By = nullptr;                   // noise part of the field increment
     __nv_bfloat16 *Shi = nullptr, *Slo = nullptr;         // images of s   [2M][ldk]
     __nv_bfloat16 *Phi = nullptr, *Plo = nullptr;         // images of s~  [2M][ldk]
+    // noise images: eta of step s in E (s even) or E1 (s odd) on the dense route,
+    // so that the draw of step t + 2 can run while the launches of step t read
+    // step t + 1's; the FFT route uses E alone
     __nv_bfloat16* E = nullptr;                           // eta           [2M][ldk]
     __nv_bfloat16* Elo = nullptr;                         // lo image of eta (FP32 mode only)
-    float* XI = nullptr;                                  // [M][2]
+    float* XI = nullptr;                                  // [M][2] collective normals
+    __nv_bfloat16 *E1 = nullptr, *Elo1 = nullptr;         // the odd-step buffers
+    float* XI1 = nullptr;
+    CUtensorMap tmE1, tmElo1;
+    // the noise draw of step t + 2 on a second stream beside step t's launches
+    // (TWA_NOISE_OVERLAP = 0: on the context's stream, before them)
+    bool overlap_noise = true;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float* part = nullptr;                                // [n_rt][M][4] sums of s
     float* partp = nullptr;                               // [n_rt][M][4] sums of s~
     CUtensorMap tmWhi, tmWlo, tmLhi, tmLlo, tmShi, tmSlo, tmPhi, tmPlo, tmE, tmElo;

@@ -993,13 +993,21 @@ __global__ void k_part_tc(const float* X, const float* Y, const float* Z, float*
 // Noise of step t = *d_t + toff: eta (FP32 Box-Muller, rounded to BF16, or to TF32
 // in an FP32 container, with a TF32 lo image Elo in the FP32 mode) into the
 // B-operand image rows 2m / 2m+1, and the collective pair xi (site index N) into XI.
-__global__ void k_noise_tc(__nv_bfloat16* E, __nv_bfloat16* Elo, float* XI, int64_t M, int64_t N, int64_t ldk,
-                           uint64_t seed, const int64_t* d_t, int64_t toff, int64_t m0, int tf32) {
+// Noise of step s = *d_t + toff (pump normals as the B-operand image, collective
+// normals into XI) into the buffers of s's parity: (E0, Elo0, XI0) for even s,
+// (E1, Elo1, XI1) for odd s (the same pointers twice where one buffer serves).
+__global__ void k_noise_tc(__nv_bfloat16* E0, __nv_bfloat16* Elo0, float* XI0, __nv_bfloat16* E1,
+                           __nv_bfloat16* Elo1, float* XI1, int64_t M, int64_t N, int64_t ldk, uint64_t seed,
+                           const int64_t* d_t, int64_t toff, int64_t m0, int tf32) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t NP = N + 1;
     if (e >= M * NP) return;
     const int64_t m = e / NP, i = e - m * NP;
-    const uint32_t t = (uint32_t)(*d_t + toff);
+    const int64_t s = *d_t + toff;
+    const uint32_t t = (uint32_t)s;
+    __nv_bfloat16* E = (s & 1) ? E1 : E0;
+    __nv_bfloat16* Elo = (s & 1) ? Elo1 : Elo0;
+    float* XI = (s & 1) ? XI1 : XI0;
     float gx, gy;
     normal2_f32(seed, (uint32_t)(m0 + m), t, (uint32_t)i, gx, gy);
     if (i < N) {
@@ -1071,8 +1079,8 @@ __global__ void k_close_tc(const float* part, int64_t M, int64_t n_rt, double* m
 // grouped per-step kernels of a batch of problems
 
 struct StepDesc {
-    __nv_bfloat16* E;
-    float* XI;
+    __nv_bfloat16 *E, *E1;   // noise images of even / odd steps
+    float *XI, *XI1;
     const float* part;
     double* mom;
     int64_t* d_t;
@@ -1091,7 +1099,8 @@ __device__ __forceinline__ int find_problem(const int64_t* start, int n, int64_t
     return lo;
 }
 
-// Noise of every problem's step *d_t + toff (start = prefix of M (N + 1)).
+// Noise of every problem's step *d_t + toff (start = prefix of M (N + 1)), into
+// the buffers of that step's parity.
 __global__ void k_noise_group(const StepDesc* sd, const int64_t* start, int n, int64_t toff) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= start[n]) return;
@@ -1100,13 +1109,16 @@ __global__ void k_noise_group(const StepDesc* sd, const int64_t* start, int n, i
     const int64_t el = e - start[p], NP = d.N + 1;
     const int64_t m = el / NP, i = el - m * NP;
     float gx, gy;
-    normal2_f32(d.seed, (uint32_t)(d.m0 + m), (uint32_t)(*d.d_t + toff), (uint32_t)i, gx, gy);
+    const int64_t st = *d.d_t + toff;
+    normal2_f32(d.seed, (uint32_t)(d.m0 + m), (uint32_t)st, (uint32_t)i, gx, gy);
+    __nv_bfloat16* E = (st & 1) ? d.E1 : d.E;
+    float* XI = (st & 1) ? d.XI1 : d.XI;
     if (i < d.N) {
-        d.E[(2 * m) * d.ldk + i] = __float2bfloat16_rn(gx);
-        d.E[(2 * m + 1) * d.ldk + i] = __float2bfloat16_rn(gy);
+        E[(2 * m) * d.ldk + i] = __float2bfloat16_rn(gx);
+        E[(2 * m + 1) * d.ldk + i] = __float2bfloat16_rn(gy);
     } else {
-        d.XI[2 * m] = gx;
-        d.XI[2 * m + 1] = gy;
+        XI[2 * m] = gx;
+        XI[2 * m + 1] = gy;
     }
 }
 
@@ -1217,26 +1229,37 @@ int launch_one(twa_ctx* c, const TcMaps& maps, const TcArgs& a, int64_t n_tiles,
         TWA_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr.store(true);
     }
+    // the highest launch priority: when the noise draw of a later step runs beside
+    // this launch, the block scheduler places this kernel's CTAs first
+    static int prio = 1;
+    if (prio > 0) {
+        int lo = 0, hi = 0;
+        TWA_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        prio = hi;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
     if constexpr (!PAIR) {
         const int64_t g = grp.sched ? grp.ctas : (n_tiles < c->tc->num_sms ? n_tiles : c->tc->num_sms);
-        kern<<<(unsigned)g, NTHREADS, smem, c->stream>>>(maps, a, grp);
+        cfg.gridDim = dim3((unsigned)g, 1, 1);
+        cfg.numAttrs = 1;
     } else {
         // clusters of two CTAs; a schedule's units are clusters
         const int64_t units = grp.sched ? grp.ctas : (n_tiles < c->tc->clusters ? n_tiles : c->tc->clusters);
-        cudaLaunchConfig_t cfg{};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeClusterDimension;
+        at[1].val.clusterDim.x = 2;
+        at[1].val.clusterDim.y = 1;
+        at[1].val.clusterDim.z = 1;
         cfg.gridDim = dim3((unsigned)(2 * units), 1, 1);
-        cfg.blockDim = dim3(NTHREADS, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = c->stream;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        TWA_CUDA(c, cudaLaunchKernelEx(&cfg, kern, maps, a, grp));
+        cfg.numAttrs = 2;
     }
+    TWA_CUDA(c, cudaLaunchKernelEx(&cfg, kern, maps, a, grp));
     TWA_CUDA(c, cudaGetLastError());
     return TWA_OK;
 }
@@ -1390,6 +1413,8 @@ int make_state_maps(twa_ctx* c) {
     if ((rc = make_map(c, &t->tmPlo, t->Plo ? t->Plo : t->Phi, R, c->N, t->ldk, bb, t->kc))) return rc;
     if ((rc = make_map(c, &t->tmE, t->E, R, c->N, t->ldk, bb, t->kc))) return rc;
     if ((rc = make_map(c, &t->tmElo, t->Elo ? t->Elo : t->E, R, c->N, t->ldk, bb, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmE1, t->E1, R, c->N, t->ldk, bb, t->kc))) return rc;
+    if ((rc = make_map(c, &t->tmElo1, t->Elo1 ? t->Elo1 : t->E1, R, c->N, t->ldk, bb, t->kc))) return rc;
     return TWA_OK;
 }
 
@@ -1444,6 +1469,7 @@ int tc_prepare(twa_ctx* c) {
     // TWA_SEPARATE_LETA=1: dense step as separate noise, L.eta, predictor and
     // corrector launches instead of the two mixed launches (same results)
     t->separate_leta = env_int("TWA_SEPARATE_LETA", 0) != 0;
+    t->overlap_noise = env_int("TWA_NOISE_OVERLAP", 1) != 0;
     if (!tf32 &&
         (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1 || t->kc == 3 || t->kc == 4)))
         return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0, 1, 3 or 4");
@@ -1494,7 +1520,15 @@ int tc_alloc(twa_ctx* c) {
         if (dev_malloc(c, b[k], ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device images");
         TWA_CUDA(c, cudaMemsetAsync(*b[k], 0, ni, c->stream));
     }
+    // the odd-step noise buffers (dense route; the FFT route draws into E only)
+    if (dev_malloc(c, &t->E1, ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device images");
+    TWA_CUDA(c, cudaMemsetAsync(t->E1, 0, ni, c->stream));
+    if (t->Elo) {
+        if (dev_malloc(c, &t->Elo1, ni) != cudaSuccess) return set_error(c, TWA_ENOMEM, "device images");
+        TWA_CUDA(c, cudaMemsetAsync(t->Elo1, 0, ni, c->stream));
+    }
     if (dev_malloc(c, &t->XI, sizeof(float) * 2 * c->M) != cudaSuccess ||
+        dev_malloc(c, &t->XI1, sizeof(float) * 2 * c->M) != cudaSuccess ||
         dev_malloc(c, &t->part, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess ||
         dev_malloc(c, &t->partp, sizeof(float) * 4 * c->M * t->n_rt) != cudaSuccess)
         return set_error(c, TWA_ENOMEM, "device sums");
@@ -1510,12 +1544,12 @@ void tc_free_run(twa_ctx* c) {
     if (!t) return;
     mix_free(t);
     float** f[] = {&t->X, &t->Y, &t->Z, &t->Xp, &t->Yp, &t->Zp, &t->Bx, &t->By, &t->Bx1,
-                   &t->By1, &t->XI, &t->part, &t->partp};
+                   &t->By1, &t->XI, &t->XI1, &t->part, &t->partp};
     for (auto p : f) {
         dev_free(c, *p);
         *p = nullptr;
     }
-    __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E, &t->Elo};
+    __nv_bfloat16** b[] = {&t->Shi, &t->Slo, &t->Phi, &t->Plo, &t->E, &t->Elo, &t->E1, &t->Elo1};
     for (auto p : b) {
         dev_free(c, *p);
         *p = nullptr;
@@ -1579,6 +1613,12 @@ void tc_free(twa_ctx* c) {
     TcState* t = c->tc;
     if (!t) return;
     tc_free_run(c);
+    if (t->side) {
+        cudaStreamSynchronize(t->side);
+        cudaStreamDestroy(t->side);
+    }
+    if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+    if (t->ev_join) cudaEventDestroy(t->ev_join);
     void* extra[] = {t->Xhi[0], t->Xhi[1], t->Xlo[0], t->Xlo[1], t->Vhi, t->Vlo};
     for (void* p : extra) dev_free(c, p);
     void* all[] = {t->Whi, t->Wlo, t->Lhi, t->Llo};
@@ -1806,7 +1846,7 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
             float* ny = par ? t->By : t->By1;
             TcArgs la = base_args(c), pa = base_args(c), ca = base_args(c);
             la.flags = pa.flags = ca.flags = ec->d_flags;
-            la.XI = t->XI;
+            la.XI = par ? t->XI : t->XI1;       // collective normals of step t + 1
             la.oBnx = nx;
             la.oBny = ny;
             pa.X = t->X; pa.Y = t->Y; pa.Z = t->Z;
@@ -1825,7 +1865,9 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
             GroupDesc* g = &d[par * nprob];
             g[q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmShi, t->tmSlo}, pa, MODE_PRED, ntw};
             g[n + q] = GroupDesc{TcMaps{t->tmWhi, t->tmWlo, t->tmPhi, t->tmPlo}, ca, MODE_CORR, ntw};
-            g[2 * n + q] = GroupDesc{TcMaps{t->tmLhi, t->tmLlo, t->tmE, t->tmElo}, la, MODE_LETA, ntl};
+            // L.eta of step t + 1: its noise images are E (t + 1 even) or E1 (odd)
+            g[2 * n + q] = GroupDesc{TcMaps{t->tmLhi, t->tmLlo, par ? t->tmE : t->tmE1, par ? t->tmElo : t->tmElo1},
+                                     la, MODE_LETA, ntl};
         }
     }
     p->host = d;
@@ -1863,32 +1905,52 @@ int mix_build(twa_ctx* c) {
 static bool tc_mixed_step(const twa_ctx* c) { return c->tc && !c->fft; }
 
 namespace {
+// The second stream (lowest priority) and the fork / join events of the noise draw.
+int side_stream(twa_ctx* c) {
+    TcState* ts = c->tc;
+    if (ts->side) return TWA_OK;
+    int lo = 0, hi = 0;
+    TWA_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    TWA_CUDA(c, cudaStreamCreateWithPriority(&ts->side, cudaStreamNonBlocking, lo));
+    TWA_CUDA(c, cudaEventCreateWithFlags(&ts->ev_fork, cudaEventDisableTiming));
+    TWA_CUDA(c, cudaEventCreateWithFlags(&ts->ev_join, cudaEventDisableTiming));
+    return TWA_OK;
+}
+
 // Noise of step t (= *d_t) and its noise part, by a standalone L.eta launch,
 // into the buffer of the step's parity.
 int noise_part_alone(twa_ctx* c, int64_t t) {
     TcState* ts = c->tc;
     {
         ProfScope p(c, TWA_PROF_NOISE);
-        k_noise_tc<<<nblk(c->M * (c->N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->Elo, ts->XI, c->M, c->N, ts->ldk, c->seed,
-                                                                        c->d_t, 0, c->opts.traj_offset, ts->kc == 2);
+        k_noise_tc<<<nblk(c->M * (c->N + 1), 256), 256, 0, c->stream>>>(
+            ts->E, ts->Elo, ts->XI, ts->E1, ts->Elo1, ts->XI1, c->M, c->N, ts->ldk, c->seed, c->d_t, 0,
+            c->opts.traj_offset, ts->kc == 2);
     }
+    const bool odd = t & 1;
     TcArgs la = base_args(c);
-    la.XI = ts->XI;
-    la.oBnx = (t & 1) ? ts->Bx1 : ts->Bx;
-    la.oBny = (t & 1) ? ts->By1 : ts->By;
-    const TcMaps lm{ts->tmLhi, ts->tmLlo, ts->tmE, ts->tmElo};
+    la.XI = odd ? ts->XI1 : ts->XI;
+    la.oBnx = odd ? ts->Bx1 : ts->Bx;
+    la.oBny = odd ? ts->By1 : ts->By;
+    const TcMaps lm{ts->tmLhi, ts->tmLlo, odd ? ts->tmE1 : ts->tmE, odd ? ts->tmElo1 : ts->tmElo};
     ProfScope p(c, TWA_PROF_NOISE_FACTOR, ts->mix->leta_flops);
     return launch_leta(c, lm, la);
 }
 }  // namespace
 
-// Noise part of step t into its buffer, unless already there.
+// Noise part of step t into its buffer and the noise of step t + 1 into its
+// images, unless already there (after step t - 1 both are).
 int tc_prime(twa_ctx* c, int64_t t) {
     TcState* ts = c->tc;
     if (!tc_mixed_step(c) || ts->separate_leta || ts->bn_ready == t) return TWA_OK;
     int rc;
     if (!ts->mix && (rc = mix_build(c))) return rc;
     if ((rc = noise_part_alone(c, t))) return rc;
+    // and the noise of step t + 1, which step t's L.eta tiles read
+    k_noise_tc<<<nblk(c->M * (c->N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->Elo, ts->XI, ts->E1, ts->Elo1, ts->XI1,
+                                                                    c->M, c->N, ts->ldk, c->seed, c->d_t, 1,
+                                                                    c->opts.traj_offset, ts->kc == 2);
+    TWA_CUDA(c, cudaGetLastError());
     ts->bn_ready = t;
     return TWA_OK;
 }
@@ -1914,9 +1976,9 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         } else {
             {
                 ProfScope p(c, TWA_PROF_NOISE);
-                k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->Elo, ts->XI, M, N, ts->ldk, c->seed,
-                                                                         c->d_t, 0, c->opts.traj_offset,
-                                                                         ts->kc == 2);
+                k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->Elo, ts->XI, ts->E, ts->Elo,
+                                                                         ts->XI, M, N, ts->ldk, c->seed, c->d_t, 0,
+                                                                         c->opts.traj_offset, ts->kc == 2);
             }
             TcArgs la = base_args(c);
             la.XI = ts->XI;
@@ -1960,11 +2022,23 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         }
         if (rc) return rc;
     } else {
-        {
-            ProfScope p(c, TWA_PROF_NOISE);   // noise of step t + 1 (L.eta tiles below)
-            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, c->stream>>>(ts->E, ts->Elo, ts->XI, M, N, ts->ldk, c->seed, c->d_t,
-                                                                     1, c->opts.traj_offset, ts->kc == 2);
+        // the noise of step t + 2 (read by the L.eta tiles of step t + 1) into the
+        // buffers of t's parity, which step t's launches do not read: on a second
+        // stream beside them (joined before the closing kernel advances the step
+        // counter the draw reads), or before them on this stream when profiling
+        const bool side = ts->overlap_noise && !c->profiling;
+        if (side) {
+            if ((rc = side_stream(c))) return rc;
+            TWA_CUDA(c, cudaEventRecord(ts->ev_fork, c->stream));
+            TWA_CUDA(c, cudaStreamWaitEvent(ts->side, ts->ev_fork, 0));
         }
+        {
+            ProfScope p(c, TWA_PROF_NOISE);
+            k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, side ? ts->side : c->stream>>>(
+                ts->E, ts->Elo, ts->XI, ts->E1, ts->Elo1, ts->XI1, M, N, ts->ldk, c->seed, c->d_t, 2,
+                c->opts.traj_offset, ts->kc == 2);
+        }
+        if (side) TWA_CUDA(c, cudaEventRecord(ts->ev_join, ts->side));
         const TcMaps none{};
         const TcArgs fa = base_args(c);   // flags of the launch
         const GroupDesc* dp = mp->desc + mp->nprob * (t & 1);
@@ -1976,6 +2050,7 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
                             : launch_cfg<MODE_MIX, 1>(c, none, fa, g, mp->tiles[L]);
             if (rc) return rc;
         }
+        if (side) TWA_CUDA(c, cudaStreamWaitEvent(c->stream, ts->ev_join, 0));
     }
     {
         ProfScope p(c, TWA_PROF_CLOSE);
@@ -2101,8 +2176,8 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
             return set_error(lead, TWA_EINVAL, "batch: contexts differ in precision or tiles, or have no trajectories");
         }
         t->bn_ready = -1;   // the batch writes the noise-part buffers of its contexts
-        sd[p] = StepDesc{t->E, t->XI, t->part, c->mom, c->d_t, c->d_count, c->M, c->N, t->ldk, t->n_rt,
-                         c->n_window, c->n_stride, c->opts.traj_offset, c->seed};
+        sd[p] = StepDesc{t->E, t->E1, t->XI, t->XI1, t->part, c->mom, c->d_t, c->d_count, c->M, c->N, t->ldk,
+                         t->n_rt, c->n_window, c->n_stride, c->opts.traj_offset, c->seed};
         ns[p + 1] = ns[p] + c->M * (c->N + 1);
         ms[p + 1] = ms[p] + c->M;
     }
@@ -2130,7 +2205,8 @@ int tc_batch_build(twa_ctx* const* ctxs, int n, twa_ctx* lead, TcBatch** out) {
 }
 
 // Noise of step t and its noise part for every problem (one grouped L.eta
-// launch), into the buffers of t's parity: the first step of a batch.
+// launch), into the buffers of t's parity, and the noise of step t + 1: the
+// first step of a batch.
 int tc_batch_prime(twa_ctx* lead, TcBatch* b, int64_t t) {
     MixPlan* mp = b->mix;
     const int n = b->n;
@@ -2142,24 +2218,38 @@ int tc_batch_prime(twa_ctx* lead, TcBatch* b, int64_t t) {
     const int rc = b->lterms == 2 ? launch_cfg<MODE_LETA, 2>(lead, none, b->flag_args, g, mp->leta_tiles)
                                   : launch_cfg<MODE_LETA, 1>(lead, none, b->flag_args, g, mp->leta_tiles);
     if (rc) return rc;
+    // the noise of step t + 1, read by the L.eta tiles of step t
+    k_noise_group<<<nblk(b->noise_elems, 256), 256, 0, lead->stream>>>(b->sd, b->nstart, n, 1);
     TWA_CUDA(lead, cudaGetLastError());
     return TWA_OK;
 }
 
-// Step t of every problem (its noise part already in place): noise of step t + 1,
-// the two mixed launches, window moments, counters.
+// Step t of every problem (its noise part and the noise of step t + 1 already in
+// place): noise of step t + 2, the two mixed launches, window moments, counters.
 int tc_batch_step(twa_ctx* lead, TcBatch* b, int64_t t) {
     MixPlan* mp = b->mix;
     const TcMaps none{};
-    k_noise_group<<<nblk(b->noise_elems, 256), 256, 0, lead->stream>>>(b->sd, b->nstart, b->n, 1);
+    // as in the single-context step: the draw of step t + 2 on the lead's second
+    // stream beside the two launches, joined before the counters advance
+    int rc = TWA_OK;
+    TcState* lt = lead->tc;
+    const bool side = lt->overlap_noise;
+    if (side) {
+        if ((rc = side_stream(lead))) return rc;
+        TWA_CUDA(lead, cudaEventRecord(lt->ev_fork, lead->stream));
+        TWA_CUDA(lead, cudaStreamWaitEvent(lt->side, lt->ev_fork, 0));
+    }
+    k_noise_group<<<nblk(b->noise_elems, 256), 256, 0, side ? lt->side : lead->stream>>>(b->sd, b->nstart, b->n, 2);
+    if (side) TWA_CUDA(lead, cudaEventRecord(lt->ev_join, lt->side));
     const GroupDesc* dp = mp->desc + mp->nprob * (t & 1);
     for (int L = 0; L < 2; ++L) {
         const Group g{dp, mp->start, mp->nprob, mp->list[L], mp->first[L], mp->ctas[L]};
-        const int rc = b->terms == 3   ? launch_cfg<MODE_MIX, 3>(lead, none, b->flag_args, g, mp->tiles[L])
-                       : b->terms == 2 ? launch_cfg<MODE_MIX, 2>(lead, none, b->flag_args, g, mp->tiles[L])
-                                       : launch_cfg<MODE_MIX, 1>(lead, none, b->flag_args, g, mp->tiles[L]);
+        rc = b->terms == 3   ? launch_cfg<MODE_MIX, 3>(lead, none, b->flag_args, g, mp->tiles[L])
+             : b->terms == 2 ? launch_cfg<MODE_MIX, 2>(lead, none, b->flag_args, g, mp->tiles[L])
+                             : launch_cfg<MODE_MIX, 1>(lead, none, b->flag_args, g, mp->tiles[L]);
         if (rc) return rc;
     }
+    if (side) TWA_CUDA(lead, cudaStreamWaitEvent(lead->stream, lt->ev_join, 0));
     k_close_group<<<nblk(32 * b->traj, 256), 256, 0, lead->stream>>>(b->sd, b->mstart, b->n);
     k_advance_group<<<nblk(b->n, 128), 128, 0, lead->stream>>>(b->sd, b->n);
     TWA_CUDA(lead, cudaGetLastError());

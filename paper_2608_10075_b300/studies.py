@@ -5,6 +5,7 @@
     python -m paper_2608_10075_b300.studies phase [--Ns 100] [--alphas 0.5 1 2] [--T 15]
     python -m paper_2608_10075_b300.studies linewidth [--N 500] [--alpha 1] [--wt 0.5]
     python -m paper_2608_10075_b300.studies scan [--T 1.0] [--small-route resident]
+    python -m paper_2608_10075_b300.studies routes [--Ns 10000 20000 30000 60000] [--M 1024]
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
@@ -28,6 +29,12 @@ gradients: N = 1024, alpha = 1, w = N Gamma / 4, dt = 1e-4, T = 2, window
 (1, 2], checkpoints every 64 steps. twa_grad (BF16X3) gives d<S+S->/dw,
 d<S+S->/dalpha and dg2/dalpha; central differences with common random numbers
 (the same seed, delta = 1e-4) of the mixed forward run check them.
+
+routes: the dense route and the Toeplitz/FFT route (Cholesky and circulant
+noise draws) at N beyond the benchmark's 10^4, alpha = 1, w = N Gamma / 2,
+dt = 2e-5, M trajectories: time per step (CUDA events around twa_run after a
+warm-up) and spin-trajectory-steps per second, with the FFT route's circle
+length and CTAs per trajectory (one CTA up to P = 28000, else a cluster).
 
 Each study prints one JSON line per case.
 """
@@ -320,6 +327,32 @@ def linewidth_study(args):
     print(json.dumps(out), flush=True)
 
 
+def routes_study(args):
+    import torch
+    for N in args.Ns:
+        w, dt = N / 2.0, 2e-5
+        for route, noise in (("dense", "cholesky"), ("fft", "cholesky"), ("fft", "circulant")):
+            t = time.perf_counter()
+            with twa.TWA(N, 1.0, w, 1.0, dt, seed=0, precision=args.precision, ws_route=route,
+                         noise_route=noise) as g:
+                setup = time.perf_counter() - t
+                g.run(args.M, args.warmup)
+                g.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.run(args.M, args.steps)
+                e1.record()
+                g.sync()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                ob = g.observables()
+            print(json.dumps({"study": "routes", "N": N, "route": route, "noise": noise, "M": args.M,
+                              "precision": args.precision, "ms_per_step": ms,
+                              "spin_traj_steps_per_s": N * args.M / (ms * 1e-3), "setup_s": setup,
+                              "fft_length": ob["fft_length"], "fft_ctas": ob["fft_ctas"],
+                              "sigma_z": ob["sigma_z"], "nonfinite": ob["nonfinite"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -371,8 +404,16 @@ def main():
     q.add_argument("--dt", type=float, default=0.0)
     q.add_argument("--delta", type=float, default=0.0, help="finite-difference step (default 1e-4)")
     q.add_argument("--precision", default="bf16x3", help="precision of the adjoint and of the differences")
+    r = sub.add_parser("routes")
+    r.add_argument("--Ns", type=int, nargs="+", default=[10000, 20000, 30000, 60000])
+    r.add_argument("--M", type=int, default=1024)
+    r.add_argument("--steps", type=int, default=20)
+    r.add_argument("--warmup", type=int, default=3)
+    r.add_argument("--precision", default="bf16x2")
     a = ap.parse_args()
-    if a.cmd == "precision":
+    if a.cmd == "routes":
+        routes_study(a)
+    elif a.cmd == "precision":
         precision_study(a)
     elif a.cmd == "phase":
         phase_study(a)

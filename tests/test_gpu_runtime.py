@@ -52,6 +52,31 @@ def test_graph_replay_is_bit_exact(prec):
         assert np.array_equal(u, v)
 
 
+@pytest.mark.parametrize("graph", [True, False])
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3", "fp32"])
+def test_noise_draw_beside_the_launches_gives_the_same_bits(monkeypatch, prec, graph):
+    # the noise of step t + 2 drawn on a second stream while step t's launches
+    # run (default) versus on the context's stream before them; with a
+    # continuation and a set_state in between (the noise is primed again)
+    from paper_2608_10075_b300 import twa
+    out = {}
+    for overlap in ("1", "0"):
+        monkeypatch.setenv("TWA_NOISE_OVERLAP", overlap)
+        if not graph:
+            monkeypatch.setenv("TWA_NO_GRAPH", "1")
+        with twa.TWA(260, 1.0, 20.0, 1.0, 1e-3, seed=9, precision=prec, window_start=0.004) as g:
+            g.run(70, 7)
+            g.run(70, 6)
+            x, y, z = g.get_state()
+            g.set_state(x, y, z)
+            g.run(70, 5)
+            out[overlap] = (g.get_state(), g.observables())
+    for u, v in zip(out["1"][0], out["0"][0]):
+        assert np.array_equal(u, v)
+    for k in ("Sz", "SpSm", "G2num", "g2"):
+        assert out["1"][1][k] == out["0"][1][k]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_trajectory_shards_reproduce_one_run(prec):
     # trajectories [40, 70) run alone with traj_offset 40 equal rows 40..69 of the full run
