@@ -124,7 +124,11 @@ typedef struct twa_opts {
                                offsets and reproduce the unsharded run exactly     */
     int    ws_route;        /* pump field sum_j w_ij s_j: TWA_ROUTE_DENSE (default,
                                any W) or TWA_ROUTE_FFT (uses that Eq. 2 is Toeplitz;
-                               tensor-core precisions only, 2N - 2 <= 28000)       */
+                               tensor-core precisions only; one CTA per trajectory
+                               while 2N - 2 <= 28000, else a thread-block cluster
+                               of 2, 4 or 8 CTAs holding the transform in their
+                               shared memories; TWA_FFT_CLUSTER = 1, 2, 4 or 8 in
+                               the environment forces the cluster size)            */
     int    noise_route;     /* draw of the pump noise chi (covariance w_ij dt, Sec. S1):
                                TWA_NOISE_CHOLESKY (default: chi = L eta) or
                                TWA_NOISE_CIRCULANT (FFT of the circulant embedding;
@@ -164,7 +168,8 @@ typedef struct twa_opts {
 #define TWA_INT_MIDPOINT 1
 
 #define TWA_ROUTE_DENSE 0   /* tensor-core contraction with the dense W          */
-#define TWA_ROUTE_FFT   1   /* circulant-embedding FFT convolution, FP32         */
+#define TWA_ROUTE_FFT   1   /* circulant-embedding FFT convolution, FP32 (any N
+                                up to the library's limit of 60000)            */
 #define TWA_ROUTE_RESIDENT 2 /* small systems (N <= TWA_RESIDENT_MAX_N), precision
                                 TWA_PREC_FP32: every twa_run call is one launch in
                                 which each CTA integrates its trajectories for all
@@ -238,7 +243,9 @@ TWA_API int twa_opts_default(twa_opts* opts);
  * Builds W in FP64 on the device and factors it (L L^T = W, lower triangular;
  * alpha = 0: the exact rank-one factor L[:,0] = sqrt(w); alpha = +INF: sqrt(w) I),
  * and computes the spectrum diagnostics. For the BF16 modes it also stores the
- * BF16 hi/lo images of W and L. On success *out owns all device memory.
+ * BF16 hi/lo images of W / w and L / sqrt(w) (of W and L when w = 0; the
+ * step multiplies by w and sqrt(w) in FP32, so contexts that differ only in w
+ * hold the same images). On success *out owns all device memory.
  * Errors: TWA_EINVAL (bad numbers, N < 1, NULL out), TWA_ENOTPSD (a pivot
  * <= 0 without clip_negative), TWA_ENOMEM, TWA_ECUDA. */
 TWA_API int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma,
