@@ -60,6 +60,8 @@ struct FftArgs {
     int nst;
     int radix[40];
     unsigned local_mask;                 // bit s: stage s (stride m_s) stays inside one CTA of the cluster
+    int wl;                              // one CTA: stages s >= wl run warp by warp (nst: none)
+    int Lw;                              // span of stage wl's blocks: each warp owns whole blocks
     const float* lam;
     const float2* tw;
     float G, dt;
@@ -280,6 +282,99 @@ __device__ __forceinline__ void middle_any(int r, int P, const float* lam, LD& l
     }
 }
 
+// The same stage with the butterflies of whole blocks of span Lw (a block of
+// stage wl: it holds entire blocks of every later stage) given to one warp each:
+// warp w takes blocks w, w + 32, ...; within a block, butterfly t = b' m + j
+// (sub-block b' of span L = m R, offset j) goes to lane t mod 32. Consecutive
+// warp-local stages then touch only the warp's own positions and need a warp
+// barrier instead of a block barrier. Same butterflies, same arithmetic.
+template <int R, bool INV, typename LD, typename ST>
+__device__ __forceinline__ void stage_warp(int P, int m, int Lw, const Tw<1> tw, LD& ld, ST& st) {
+    const int L = m * R, step = P / L, per = Lw / R, ntop = P / Lw;
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int db = 32 / m, dj = 32 - db * m;
+    for (int B = warp; B < ntop; B += FT / 32) {
+        const int top = B * Lw;
+        int b = lane / m, j = lane - b * m;
+        for (int t = lane; t < per; t += 32) {
+            const int jc = j, base = top + b * L + j;
+            b += db;
+            j += dj;
+            if (j >= m) {
+                j -= m;
+                ++b;
+            }
+            float2 a[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) a[q] = ld(base + q * m);
+            float2 w[R];
+            w[1] = tw[jc * step];
+#pragma unroll
+            for (int k = 2; k < R; ++k) w[k] = cmul(w[k - 1], w[1]);
+            if (!INV) {
+                dft<R, false>(a);
+#pragma unroll
+                for (int k = 1; k < R; ++k) a[k] = cmul(a[k], w[k]);
+            } else {
+#pragma unroll
+                for (int k = 1; k < R; ++k) a[k] = cmulc(a[k], w[k]);
+                dft<R, true>(a);
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) st(base + q * m, a[q]);
+        }
+    }
+}
+
+template <bool INV, typename LD, typename ST>
+__device__ __forceinline__ void stage_warp_any(int r, int P, int m, int Lw, const Tw<1> tw, LD& ld, ST& st) {
+    switch (r) {
+        case 4: stage_warp<4, INV>(P, m, Lw, tw, ld, st); break;
+        case 2: stage_warp<2, INV>(P, m, Lw, tw, ld, st); break;
+        case 3: stage_warp<3, INV>(P, m, Lw, tw, ld, st); break;
+        default: stage_warp<5, INV>(P, m, Lw, tw, ld, st); break;
+    }
+}
+
+template <int R, typename LD, typename ST>
+__device__ __forceinline__ void middle_warp(int P, int Lw, const float* __restrict__ lam, LD& ld, ST& st) {
+    const int per = Lw / R, ntop = P / Lw;
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    for (int B = warp; B < ntop; B += FT / 32) {
+        for (int t = lane; t < per; t += 32) {
+            const int base = B * Lw + t * R;
+            float2 a[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) a[q] = ld(base + q);
+            dft<R, false>(a);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const float l = __ldg(&lam[base + q]);
+                a[q] = make_float2(a[q].x * l, a[q].y * l);
+            }
+            dft<R, true>(a);
+#pragma unroll
+            for (int q = 0; q < R; ++q) st(base + q, a[q]);
+        }
+    }
+}
+
+template <typename LD, typename ST>
+__device__ __forceinline__ void middle_warp_any(int r, int P, int Lw, const float* lam, LD& ld, ST& st) {
+    switch (r) {
+        case 4: middle_warp<4>(P, Lw, lam, ld, st); break;
+        case 2: middle_warp<2>(P, Lw, lam, ld, st); break;
+        case 3: middle_warp<3>(P, Lw, lam, ld, st); break;
+        default: middle_warp<5>(P, Lw, lam, ld, st); break;
+    }
+}
+
+// barrier after a stage: the warp's when it and the next stage are both warp-local
+__device__ __forceinline__ void warp_or_block_sync(bool warp_only) {
+    if (warp_only) __syncwarp();
+    else __syncthreads();
+}
+
 // Position p of the transform: this CTA's shared memory (offset p / C; the
 // caller guarantees p = rank mod C) ...
 template <int C>
@@ -384,6 +479,35 @@ __device__ __forceinline__ void circulant_io(float2* buf, const FftArgs& a, int 
         return;
     }
     int m = P;
+    if constexpr (C == 1) {
+        // one CTA: stages from wl on (the middle pass included) run warp by warp
+        const int wl = a.wl, Lw = a.Lw;
+        for (int s = 0; s + 1 < nst; ++s) {
+            m /= a.radix[s];
+            if (s == 0) stage_any<false, C>(a.radix[s], P, m, tw, in, sst, rank);
+            else if (s >= wl) stage_warp_any<false>(a.radix[s], P, m, Lw, tw, sld, sst);
+            else stage_any<false, C>(a.radix[s], P, m, tw, sld, sst, rank);
+            warp_or_block_sync(s >= wl);
+            if (s == 0) after_first();
+        }
+        if (nst - 1 >= wl) middle_warp_any(a.radix[nst - 1], P, Lw, a.lam, sld, sst);
+        else middle_any<C>(a.radix[nst - 1], P, a.lam, sld, sst, rank);
+        warp_or_block_sync(nst - 2 >= wl);
+        m = a.radix[nst - 1];
+        for (int s = nst - 2; s >= 0; --s) {
+            if (s == 0) {
+                before_last();
+                stage_any<true, C>(a.radix[s], P, m, tw, sld, out, rank);
+            } else if (s >= wl) {
+                stage_warp_any<true>(a.radix[s], P, m, Lw, tw, sld, sst);
+            } else {
+                stage_any<true, C>(a.radix[s], P, m, tw, sld, sst, rank);
+            }
+            m *= a.radix[s];
+            warp_or_block_sync(s - 1 >= wl);
+        }
+        return;
+    }
     for (int s = 0; s + 1 < nst; ++s) {
         m /= a.radix[s];
         const bool loc = stage_local(a, s);
@@ -398,8 +522,7 @@ __device__ __forceinline__ void circulant_io(float2* buf, const FftArgs& a, int 
         if (s == 0) after_first();
     }
     // the middle pass (stride 1): local only for one CTA
-    if constexpr (C == 1) middle_any<C>(a.radix[nst - 1], P, a.lam, sld, sst, rank);
-    else middle_any<C>(a.radix[nst - 1], P, a.lam, cld, cst, rank);
+    middle_any<C>(a.radix[nst - 1], P, a.lam, cld, cst, rank);
     stage_sync<C>(true);
     m = a.radix[nst - 1];
     for (int s = nst - 2; s >= 0; --s) {
@@ -634,6 +757,21 @@ __global__ void __launch_bounds__(FT, 1) k_fft_noise(const __grid_constant__ Fft
     stage_sync<C>(true);
     // unnormalised inverse transform, digit-reversed input -> natural order
     int mm = 1;
+    if constexpr (C == 1) {
+        // stages from wl on run warp by warp (the first stage reads global memory)
+        const int wl = a.wl, Lw = a.Lw;
+        for (int s = nst - 1; s >= 0; --s) {
+            if (s == nst - 1 && s == 0) stage_any<true, C>(a.radix[s], P, mm, tw, in, out, rank);
+            else if (s == 0) stage_any<true, C>(a.radix[s], P, mm, tw, sld, out, rank);
+            else if (s >= wl && s == nst - 1) stage_warp_any<true>(a.radix[s], P, mm, Lw, tw, in, sst);
+            else if (s >= wl) stage_warp_any<true>(a.radix[s], P, mm, Lw, tw, sld, sst);
+            else if (s == nst - 1) stage_any<true, C>(a.radix[s], P, mm, tw, in, sst, rank);
+            else stage_any<true, C>(a.radix[s], P, mm, tw, sld, sst, rank);
+            mm *= a.radix[s];
+            warp_or_block_sync(s - 1 >= wl);
+        }
+        return;
+    }
     for (int s = nst - 1; s >= 0; --s) {
         const bool loc = stage_local(a, s);
         if (s == nst - 1 && s == 0) stage_any<true, C>(a.radix[s], P, mm, tw, in, out, rank);
@@ -752,6 +890,8 @@ FftArgs base_args(twa_ctx* c) {
     a.nst = f->nst;
     for (int s = 0; s < f->nst; ++s) a.radix[s] = f->radix[s];
     a.local_mask = f->local_mask;
+    a.wl = f->wl;
+    a.Lw = (int)f->Lw;
     a.lam = f->lam;
     a.tw = f->tw;
     a.G = (float)c->Gamma;
@@ -876,6 +1016,23 @@ int fft_prepare(twa_ctx* c) {
         for (int64_t t = v; t > 1; t /= 2) ++two;
         if (two % 2) { f->radix[f->nst++] = 2; v /= 2; }
         while (v % 4 == 0) { f->radix[f->nst++] = 4; v /= 4; }
+    }
+    // one CTA: the first stage s >= 1 with at least 32 blocks (span P / (r_0 ... r_{s-1}))
+    // that 32 warps share evenly enough (the busiest warp at most 1.25x the mean)
+    // runs, with every later stage, warp by warp (TWA_FFT_WARP = 0: no such stage)
+    f->wl = f->nst;
+    f->Lw = 0;
+    if (C == 1 && env_int("TWA_FFT_WARP", 1) != 0) {
+        int64_t L = P;
+        for (int s = 0; s < f->nst; ++s) {
+            const int64_t ntop = P / L;
+            if (s >= 1 && ntop >= 32 && (ntop + 31) / 32 * 32 * 4 <= ntop * 5) {
+                f->wl = s;
+                f->Lw = L;
+                break;
+            }
+            L /= f->radix[s];
+        }
     }
     // stage s has stride m_s = P / (r_0 ... r_s); it stays inside one CTA when C divides m_s
     f->local_mask = 0;

@@ -90,6 +90,8 @@ struct FftPlan {
                                  // or a multiple of 4 C (a cluster of C CTAs per trajectory)
     int C = 1;                   // CTAs per trajectory: 1, or 2, 4, 8 for P > 28000 (thread-block cluster)
     unsigned local_mask = 0;     // bit s: the stage of stride P / (r_0 ... r_s) stays inside one CTA
+    int wl = 0;                  // one CTA: stages s >= wl run warp by warp (nst: none)
+    int64_t Lw = 0;              // block span of stage wl (each warp owns whole blocks)
     int nst = 0;                 // number of stages
     int radix[40] = {0};         // radix of each stage (DIF order)
     float* lam = nullptr;        // spectrum of the embedding, in the DIF output order

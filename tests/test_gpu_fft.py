@@ -110,6 +110,28 @@ def test_fft_route_rejects_what_it_cannot_do(monkeypatch):
     assert e.value.name == "TWA_EINVAL"
 
 
+@pytest.mark.parametrize("noise", ["cholesky", "circulant"])
+@pytest.mark.parametrize("N", [300, 1000, 4999, 10000])
+def test_warp_local_stages_give_the_same_bits(monkeypatch, N, noise):
+    # the later stages of the one-CTA transform run warp by warp (each warp owns
+    # whole sub-transforms): the same butterflies as the block-wide mapping
+    import torch
+    twa = _twa()
+    rng = np.random.default_rng(N)
+    s = torch.tensor(rng.normal(size=(3, N)), device="cuda")
+    out = {}
+    for warp in ("1", "0"):
+        monkeypatch.setenv("TWA_FFT_WARP", warp)
+        with twa.TWA(N, 1.0, N / 2.0, 1.0, 2e-5, seed=2, precision="bf16x2", ws_route="fft",
+                     noise_route=noise) as g:
+            f = g.field(s).cpu().numpy()
+            g.run(16, 4)
+            out[warp] = (f, g.get_state())
+    assert np.array_equal(out["1"][0], out["0"][0])
+    for u, v in zip(out["1"][1], out["0"][1]):
+        assert np.array_equal(u, v)
+
+
 # ---------------------------------------------------------------------------
 # transforms longer than one CTA's shared memory (P > 28000, N > 14001): one
 # thread-block cluster of 2, 4 or 8 CTAs per trajectory, the transform spread
