@@ -386,24 +386,35 @@ def run_ours(args, rank, world, dist):
                    "noise_factor": "k_tc<LETA> (L.eta)"}[dominant]
 
     # ---- end to end through the C ABI with host buffers ----
-    xs = [torch.empty((M, N), dtype=torch.float64, pin_memory=True) for _ in range(3)]
-    ctx.get_state(out=tuple(x.numpy() for x in xs))
+    # the state arrives from pinned host memory as FP32 (twa_set_state_f32: the
+    # mixed-precision state as it is), every step's moments and the observables
+    # go back; the same with FP64 host buffers (twa_set_state) beside it
     mom_bytes = 5 * 8 * M
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ctx.set_state(*(x.numpy() for x in xs))          # host -> device, pinned
-    ctx.run(M, K)
-    ctx.moments()                                     # device -> host
-    obs = ctx.observables()
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = N * M * world * K / t_e2e
-    h2d = 3 * 8 * M * N
+
+    def end_to_end(dtype):
+        xs = [torch.empty((M, N), dtype=dtype, pin_memory=True) for _ in range(3)]
+        host = tuple(x.numpy() for x in xs)
+        if dtype == torch.float32:
+            ctx.get_state_f32(out=host)
+        else:
+            ctx.get_state(out=host)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_state(*host)                              # host -> device, pinned
+        ctx.run(M, K)
+        ctx.moments()                                     # device -> host
+        ob = ctx.observables()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return N * M * world * K / t, 3 * xs[0].element_size() * M * N, ob
+
+    e2e64, h2d64, _ = end_to_end(torch.float64)
+    e2e, h2d, obs = end_to_end(torch.float32)
     d2h = mom_bytes + 160
 
     # ---- sustained: a seconds-long block of steps under the power limit ----
@@ -505,7 +516,9 @@ def run_ours(args, rank, world, dist):
                          "profile_pass_clocks": clocks.stats(c2, c3)},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
-                    "note": "set_state from pinned host FP64 buffers, K steps, moments and observables to host"},
+                    "note": "set_state_f32 from pinned host FP32 buffers (the mixed-precision state), K steps, "
+                            "moments and observables to host",
+                    "fp64_host_state": {"value": e2e64, "h2d_bytes_per_step": h2d64 / K}},
             "gpu_launches": 4 * K,   # per step: noise, predictor launch, corrector launch, close
             "clocks": clocks.stats(c0, c1),
             "sustained": sustained,

@@ -280,6 +280,15 @@ TWA_API int twa_get_state(twa_ctx* ctx, double* sx, double* sy, double* sz, int 
 TWA_API int twa_set_state(twa_ctx* ctx, int64_t M, const double* sx, const double* sy,
                   const double* sz, int on_device);
 
+/* The same two calls for FP32 buffers of M*N floats each, layout [M][N]: the
+ * state of the tensor-core precisions is FP32, so these copy it as it is (no
+ * conversion; half the bytes of the FP64 calls). twa_get_state_f32
+ * synchronises; twa_set_state_f32 synchronises for host buffers. Errors: as
+ * the FP64 calls, and TWA_EUNSUPPORTED on a TWA_PREC_FP64 context (FP64 spins). */
+TWA_API int twa_get_state_f32(twa_ctx* ctx, float* sx, float* sy, float* sz, int on_device);
+TWA_API int twa_set_state_f32(twa_ctx* ctx, int64_t M, const float* sx, const float* sy,
+                      const float* sz, int on_device);
+
 /* Copy the per-trajectory window means, M*5 doubles [M][5] in the order
  * S^z, A, A^2, A S^z, (S^z)^2 (symmetric-ordered classical moments, Sec. S1
  * item 5), to a host (on_device = 0) or device buffer. Synchronises.

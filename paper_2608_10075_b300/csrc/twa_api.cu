@@ -410,6 +410,38 @@ int twa_set_state(twa_ctx* c, int64_t M, const double* sx, const double* sy, con
     return TWA_OK;
 }
 
+int twa_get_state_f32(twa_ctx* c, float* sx, float* sy, float* sz, int on_device) {
+    if (!c || !sx || !sy || !sz) return set_error(c, TWA_EINVAL, "twa_get_state_f32: NULL argument");
+    if (c->M == 0) return set_error(c, TWA_ESTATE, "twa_get_state_f32: no trajectories yet");
+    if (!use_tc(c)) return set_error(c, TWA_EUNSUPPORTED, "twa_get_state_f32: the FP64 path keeps FP64 spins");
+    const size_t bytes = sizeof(float) * (size_t)c->M * c->N;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    twa::TcState* t = c->tc;
+    TWA_CUDA(c, cudaMemcpyAsync(sx, t->X, bytes, k, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(sy, t->Y, bytes, k, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(sz, t->Z, bytes, k, c->stream));
+    return check_device_flags(c);
+}
+
+int twa_set_state_f32(twa_ctx* c, int64_t M, const float* sx, const float* sy, const float* sz, int on_device) {
+    if (!c || !sx || !sy || !sz) return set_error(c, TWA_EINVAL, "twa_set_state_f32: NULL argument");
+    if (M < 1 || M > (int64_t)1 << 30) return set_error(c, TWA_EINVAL, "twa_set_state_f32: M must be in [1, 2^30]");
+    if (c->M != 0 && M != c->M) return set_error(c, TWA_EINVAL, "twa_set_state_f32: M differs from the fixed M");
+    if (!use_tc(c)) return set_error(c, TWA_EUNSUPPORTED, "twa_set_state_f32: the FP64 path keeps FP64 spins");
+    int rc;
+    if (c->M == 0 && (rc = fix_M(c, M))) return rc;
+    // straight into the FP32 state the mixed-precision step works on
+    const size_t bytes = sizeof(float) * (size_t)M * c->N;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    twa::TcState* t = c->tc;
+    TWA_CUDA(c, cudaMemcpyAsync(t->X, sx, bytes, k, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(t->Y, sy, bytes, k, c->stream));
+    TWA_CUDA(c, cudaMemcpyAsync(t->Z, sz, bytes, k, c->stream));
+    if ((rc = twa::tc_state_changed(c))) return rc;
+    if (!on_device) TWA_CUDA(c, cudaStreamSynchronize(c->stream));
+    return TWA_OK;
+}
+
 int twa_get_moments(twa_ctx* c, double* out, int on_device) {
     if (!c || !out) return set_error(c, TWA_EINVAL, "twa_get_moments: NULL argument");
     if (c->M == 0) return set_error(c, TWA_ESTATE, "twa_get_moments: no trajectories yet");

@@ -136,6 +136,8 @@ _SIGNATURES = {
     "twa_observables": (ctypes.c_int, [_P, ctypes.POINTER(Obs)]),
     "twa_get_state": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "twa_set_state": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int]),
+    "twa_get_state_f32": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "twa_set_state_f32": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int]),
     "twa_get_moments": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "twa_field": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
     "twa_contract": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int64]),
@@ -172,15 +174,18 @@ def last_error(ctx=None):
     return lib().twa_last_error(ctx).decode()
 
 
-def _ptr(x):
-    """Device or host address of a torch tensor / numpy array (contiguous float64)."""
+def _ptr(x, dtype="float64"):
+    """Device or host address of a torch tensor / numpy array (contiguous, of
+    element type `dtype`)."""
     if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if str(x.dtype) != "torch." + dtype:
+            raise ValueError("expected a %s tensor" % dtype)
         return ctypes.c_void_p(x.data_ptr()), bool(x.is_cuda)
     import numpy as np
-    if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"] and x.dtype == np.float64):
-        raise ValueError("expected a C-contiguous float64 numpy array or a torch tensor")
+    if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"] and x.dtype == np.dtype(dtype)):
+        raise ValueError("expected a C-contiguous %s numpy array or a torch tensor" % dtype)
     return ctypes.c_void_p(x.ctypes.data), False
 
 
@@ -264,10 +269,29 @@ class TWA:
         return out
 
     def set_state(self, sx, sy, sz):
-        (px, dx), (py, _), (pz, _) = (_ptr(a) for a in (sx, sy, sz))
+        """Replace the spins from three [M][N] arrays (numpy or torch, host or
+        CUDA): float64 through twa_set_state, float32 through twa_set_state_f32."""
+        f32 = str(sx.dtype).endswith("float32")
+        (px, dx), (py, _), (pz, _) = (_ptr(a, "float32" if f32 else "float64") for a in (sx, sy, sz))
         M = int(sx.shape[0])
-        self._check(lib().twa_set_state(self._h, M, px, py, pz, 1 if dx else 0))
+        fn = lib().twa_set_state_f32 if f32 else lib().twa_set_state
+        self._check(fn(self._h, M, px, py, pz, 1 if dx else 0))
         self.M = M
+
+    def get_state_f32(self, out=None, device=None):
+        """Spins as three [M][N] float32 arrays (twa_get_state_f32; tensor-core
+        precisions): torch CUDA tensors when `device` is given, numpy otherwise."""
+        M, N = self.M, self.N
+        if out is None:
+            if device is not None:
+                import torch
+                out = tuple(torch.empty((M, N), dtype=torch.float32, device=device) for _ in range(3))
+            else:
+                import numpy as np
+                out = tuple(np.empty((M, N), dtype=np.float32) for _ in range(3))
+        (px, dx), (py, _), (pz, _) = (_ptr(a, "float32") for a in out)
+        self._check(lib().twa_get_state_f32(self._h, px, py, pz, 1 if dx else 0))
+        return out
 
     def moments(self):
         """Per-trajectory window means [M][5]: S^z, A, A^2, A S^z, (S^z)^2."""

@@ -220,3 +220,40 @@ def test_caller_allocator_in_gradients_and_batches():
             assert x[k] == y[k]
     assert log["alloc"] == log["free"] and log["bad_free"] == 0 and not live
     assert torch.cuda.memory_allocated() == base
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "fp32"])
+def test_fp32_state_calls_match_the_fp64_ones(prec):
+    # twa_get_state_f32 / twa_set_state_f32 move the FP32 state as it is: the
+    # FP64 calls see the same values widened, and a run continued from either
+    # gives the same bits (host and device buffers)
+    import torch
+    from paper_2608_10075_b300 import twa
+    kw = dict(seed=6, precision=prec, window_start=0.002)
+    with twa.TWA(150, 1.0, 20.0, 1.0, 1e-3, **kw) as g:
+        g.run(40, 5)
+        a = g.get_state_f32()
+        b = g.get_state()
+        for u, v in zip(a, b):
+            assert u.dtype == np.float32 and np.array_equal(u.astype(np.float64), v)
+        ad = g.get_state_f32(device="cuda")
+        for u, v in zip(a, ad):
+            assert np.array_equal(u, v.cpu().numpy())
+    runs = []
+    for state in (a, b, ad):
+        with twa.TWA(150, 1.0, 20.0, 1.0, 1e-3, **kw) as g:
+            g.set_state(*state)
+            g.run(40, 6)
+            runs.append((g.get_state(), g.observables()))
+    for r in runs[1:]:
+        for u, v in zip(runs[0][0], r[0]):
+            assert np.array_equal(u, v)
+        assert r[1]["SpSm"] == runs[0][1]["SpSm"]
+    with twa.TWA(20, 1.0, 2.0, 1.0, 1e-3, precision="fp64") as g:
+        g.run(4, 1)
+        with pytest.raises(twa.TWAError) as e:
+            g.get_state_f32()
+        assert e.value.name == "TWA_EUNSUPPORTED"
+        with pytest.raises(twa.TWAError) as e:
+            g.set_state(*(np.zeros((4, 20), dtype=np.float32) for _ in range(3)))
+        assert e.value.name == "TWA_EUNSUPPORTED"
