@@ -62,6 +62,9 @@ struct FftArgs {
     unsigned local_mask;                 // bit s: stage s (stride m_s) stays inside one CTA of the cluster
     int wl;                              // one CTA: stages s >= wl run warp by warp (nst: none)
     int Lw;                              // span of stage wl's blocks: each warp owns whole blocks
+    const float2* dtw;                   // one CTA: direct twiddle tables of the stages that have one
+    int dtw_off[40];                     // offset of stage s's table in dtw (-1: two-level lookup)
+    int dtw_total;                       // entries of all direct tables
     const float* lam;
     const float2* tw;
     float G, dt;
@@ -203,7 +206,8 @@ struct Tw {
 // divides m, all R positions of such a butterfly are = rank (mod C), i.e. in its
 // own shared memory.
 template <int R, bool INV, int C, typename LD, typename ST>
-__device__ __forceinline__ void stage_io(int P, int m, const Tw<C> tw, LD& ld, ST& st, int rank) {
+__device__ __forceinline__ void stage_io(int P, int m, const Tw<C> tw, LD& ld, ST& st, int rank,
+                                         const float2* ds) {
     const int L = m * R, step = P / L, nb = P / R;   // P <= 120000: 32-bit indices
     constexpr int U = FT * C;
     // butterfly u = b m + j; advancing u by U advances (b, j) by (db, dj), with
@@ -223,7 +227,8 @@ __device__ __forceinline__ void stage_io(int P, int m, const Tw<C> tw, LD& ld, S
 #pragma unroll
         for (int q = 0; q < R; ++q) a[q] = ld(base + q * m);
         float2 w[R];
-        w[1] = tw[jc * step];
+        // w_L^j: this stage's direct table (one load), or the two-level lookup
+        w[1] = ds ? ds[jc] : tw[jc * step];
 #pragma unroll
         for (int k = 2; k < R; ++k) w[k] = cmul(w[k - 1], w[1]);
         if (!INV) {
@@ -241,12 +246,13 @@ __device__ __forceinline__ void stage_io(int P, int m, const Tw<C> tw, LD& ld, S
 }
 
 template <bool INV, int C, typename LD, typename ST>
-__device__ __forceinline__ void stage_any(int r, int P, int m, const Tw<C> tw, LD& ld, ST& st, int rank) {
+__device__ __forceinline__ void stage_any(int r, int P, int m, const Tw<C> tw, LD& ld, ST& st, int rank,
+                                          const float2* ds = nullptr) {
     switch (r) {
-        case 4: stage_io<4, INV, C>(P, m, tw, ld, st, rank); break;
-        case 2: stage_io<2, INV, C>(P, m, tw, ld, st, rank); break;
-        case 3: stage_io<3, INV, C>(P, m, tw, ld, st, rank); break;
-        default: stage_io<5, INV, C>(P, m, tw, ld, st, rank); break;
+        case 4: stage_io<4, INV, C>(P, m, tw, ld, st, rank, ds); break;
+        case 2: stage_io<2, INV, C>(P, m, tw, ld, st, rank, ds); break;
+        case 3: stage_io<3, INV, C>(P, m, tw, ld, st, rank, ds); break;
+        default: stage_io<5, INV, C>(P, m, tw, ld, st, rank, ds); break;
     }
 }
 
@@ -289,7 +295,7 @@ __device__ __forceinline__ void middle_any(int r, int P, const float* lam, LD& l
 // warp-local stages then touch only the warp's own positions and need a warp
 // barrier instead of a block barrier. Same butterflies, same arithmetic.
 template <int R, bool INV, typename LD, typename ST>
-__device__ __forceinline__ void stage_warp(int P, int m, int Lw, const Tw<1> tw, LD& ld, ST& st) {
+__device__ __forceinline__ void stage_warp(int P, int m, int Lw, const Tw<1> tw, LD& ld, ST& st, const float2* ds) {
     const int L = m * R, step = P / L, per = Lw / R, ntop = P / Lw;
     const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     const int db = 32 / m, dj = 32 - db * m;
@@ -308,7 +314,7 @@ __device__ __forceinline__ void stage_warp(int P, int m, int Lw, const Tw<1> tw,
 #pragma unroll
             for (int q = 0; q < R; ++q) a[q] = ld(base + q * m);
             float2 w[R];
-            w[1] = tw[jc * step];
+            w[1] = ds ? ds[jc] : tw[jc * step];
 #pragma unroll
             for (int k = 2; k < R; ++k) w[k] = cmul(w[k - 1], w[1]);
             if (!INV) {
@@ -327,12 +333,13 @@ __device__ __forceinline__ void stage_warp(int P, int m, int Lw, const Tw<1> tw,
 }
 
 template <bool INV, typename LD, typename ST>
-__device__ __forceinline__ void stage_warp_any(int r, int P, int m, int Lw, const Tw<1> tw, LD& ld, ST& st) {
+__device__ __forceinline__ void stage_warp_any(int r, int P, int m, int Lw, const Tw<1> tw, LD& ld, ST& st,
+                                               const float2* ds) {
     switch (r) {
-        case 4: stage_warp<4, INV>(P, m, Lw, tw, ld, st); break;
-        case 2: stage_warp<2, INV>(P, m, Lw, tw, ld, st); break;
-        case 3: stage_warp<3, INV>(P, m, Lw, tw, ld, st); break;
-        default: stage_warp<5, INV>(P, m, Lw, tw, ld, st); break;
+        case 4: stage_warp<4, INV>(P, m, Lw, tw, ld, st, ds); break;
+        case 2: stage_warp<2, INV>(P, m, Lw, tw, ld, st, ds); break;
+        case 3: stage_warp<3, INV>(P, m, Lw, tw, ld, st, ds); break;
+        default: stage_warp<5, INV>(P, m, Lw, tw, ld, st, ds); break;
     }
 }
 
@@ -418,7 +425,16 @@ __device__ Tw<C> load_twiddles(float2* buf, const FftArgs& a) {
     constexpr int LO = TwCfg<C>::LO;
     for (int64_t k = threadIdx.x; k * LO < a.P; k += FT) thi[k] = a.tw[k * LO];
     for (int j = threadIdx.x; j < LO; j += FT) tlo[lo_slot(j)] = (j < a.P) ? a.tw[j] : make_float2(1.f, 0.f);
+    if constexpr (C == 1) {   // the stages' direct tables, after the two-level ones
+        float2* td = tlo + tw_lo_entries(C);
+        for (int j = threadIdx.x; j < a.dtw_total; j += FT) td[j] = a.dtw[j];
+    }
     return Tw<C>{thi, tlo};
+}
+
+// this CTA's shared-memory copy of stage s's direct twiddle table, or NULL
+__device__ __forceinline__ const float2* stage_table(const float2* buf, const FftArgs& a, int s) {
+    return a.dtw_off[s] < 0 ? nullptr : buf + a.P + tw_hi_entries(a.P, 1) + tw_lo_entries(1) + a.dtw_off[s];
 }
 
 // Sum of v over the block (all threads receive it). `scratch` holds 32 floats.
@@ -484,9 +500,10 @@ __device__ __forceinline__ void circulant_io(float2* buf, const FftArgs& a, int 
         const int wl = a.wl, Lw = a.Lw;
         for (int s = 0; s + 1 < nst; ++s) {
             m /= a.radix[s];
-            if (s == 0) stage_any<false, C>(a.radix[s], P, m, tw, in, sst, rank);
-            else if (s >= wl) stage_warp_any<false>(a.radix[s], P, m, Lw, tw, sld, sst);
-            else stage_any<false, C>(a.radix[s], P, m, tw, sld, sst, rank);
+            const float2* ds = stage_table(buf, a, s);
+            if (s == 0) stage_any<false, C>(a.radix[s], P, m, tw, in, sst, rank, ds);
+            else if (s >= wl) stage_warp_any<false>(a.radix[s], P, m, Lw, tw, sld, sst, ds);
+            else stage_any<false, C>(a.radix[s], P, m, tw, sld, sst, rank, ds);
             warp_or_block_sync(s >= wl);
             if (s == 0) after_first();
         }
@@ -495,13 +512,14 @@ __device__ __forceinline__ void circulant_io(float2* buf, const FftArgs& a, int 
         warp_or_block_sync(nst - 2 >= wl);
         m = a.radix[nst - 1];
         for (int s = nst - 2; s >= 0; --s) {
+            const float2* ds = stage_table(buf, a, s);
             if (s == 0) {
                 before_last();
-                stage_any<true, C>(a.radix[s], P, m, tw, sld, out, rank);
+                stage_any<true, C>(a.radix[s], P, m, tw, sld, out, rank, ds);
             } else if (s >= wl) {
-                stage_warp_any<true>(a.radix[s], P, m, Lw, tw, sld, sst);
+                stage_warp_any<true>(a.radix[s], P, m, Lw, tw, sld, sst, ds);
             } else {
-                stage_any<true, C>(a.radix[s], P, m, tw, sld, sst, rank);
+                stage_any<true, C>(a.radix[s], P, m, tw, sld, sst, rank, ds);
             }
             m *= a.radix[s];
             warp_or_block_sync(s - 1 >= wl);
@@ -761,12 +779,13 @@ __global__ void __launch_bounds__(FT, 1) k_fft_noise(const __grid_constant__ Fft
         // stages from wl on run warp by warp (the first stage reads global memory)
         const int wl = a.wl, Lw = a.Lw;
         for (int s = nst - 1; s >= 0; --s) {
-            if (s == nst - 1 && s == 0) stage_any<true, C>(a.radix[s], P, mm, tw, in, out, rank);
-            else if (s == 0) stage_any<true, C>(a.radix[s], P, mm, tw, sld, out, rank);
-            else if (s >= wl && s == nst - 1) stage_warp_any<true>(a.radix[s], P, mm, Lw, tw, in, sst);
-            else if (s >= wl) stage_warp_any<true>(a.radix[s], P, mm, Lw, tw, sld, sst);
-            else if (s == nst - 1) stage_any<true, C>(a.radix[s], P, mm, tw, in, sst, rank);
-            else stage_any<true, C>(a.radix[s], P, mm, tw, sld, sst, rank);
+            const float2* ds = stage_table(buf, a, s);
+            if (s == nst - 1 && s == 0) stage_any<true, C>(a.radix[s], P, mm, tw, in, out, rank, ds);
+            else if (s == 0) stage_any<true, C>(a.radix[s], P, mm, tw, sld, out, rank, ds);
+            else if (s >= wl && s == nst - 1) stage_warp_any<true>(a.radix[s], P, mm, Lw, tw, in, sst, ds);
+            else if (s >= wl) stage_warp_any<true>(a.radix[s], P, mm, Lw, tw, sld, sst, ds);
+            else if (s == nst - 1) stage_any<true, C>(a.radix[s], P, mm, tw, in, sst, rank, ds);
+            else stage_any<true, C>(a.radix[s], P, mm, tw, sld, sst, rank, ds);
             mm *= a.radix[s];
             warp_or_block_sync(s - 1 >= wl);
         }
@@ -892,6 +911,9 @@ FftArgs base_args(twa_ctx* c) {
     a.local_mask = f->local_mask;
     a.wl = f->wl;
     a.Lw = (int)f->Lw;
+    a.dtw = f->dtw;
+    a.dtw_total = (int)f->dtw_total;
+    for (int k = 0; k < 40; ++k) a.dtw_off[k] = f->dtw_off[k];
     a.lam = f->lam;
     a.tw = f->tw;
     a.G = (float)c->Gamma;
@@ -905,6 +927,18 @@ FftArgs base_args(twa_ctx* c) {
 // shared memory of one FFT CTA: its share of the transform and the two twiddle tables
 size_t smem_bytes(int64_t P, int C) {
     return sizeof(float2) * (size_t)(P / C + tw_hi_entries(P, C) + tw_lo_entries(C));
+}
+// ... and the direct tables of the plan's stages
+size_t plan_smem(const FftPlan* f) { return smem_bytes(f->P, f->C) + sizeof(float2) * (size_t)f->dtw_total; }
+
+// dtw[off_s + j] = w^(j P / L_s) = exp(-2 pi i j / L_s), from the full table tw
+__global__ void k_fft_stage_tables(float2* dtw, const float2* tw, const int64_t* off, const int64_t* step,
+                                   const int64_t* len, int nst) {
+    for (int s = 0; s < nst; ++s) {
+        if (off[s] < 0) continue;
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < len[s]; j += (int64_t)gridDim.x * blockDim.x)
+            dtw[off[s] + j] = tw[j * step[s]];
+    }
 }
 
 // Call f with the cluster size as a compile-time constant.
@@ -925,7 +959,7 @@ int fft_launch(twa_ctx* c, void (*kern)(KArgs...), int64_t units, Args... args) 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(units * C));
     cfg.blockDim = dim3(FT);
-    cfg.dynamicSmemBytes = smem_bytes(c->fft->P, C);
+    cfg.dynamicSmemBytes = plan_smem(c->fft);
     cfg.stream = c->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -942,7 +976,7 @@ template <int C>
 int set_smem(twa_ctx* c) {
     const void* ks[] = {(const void*)k_fft_pred<C>, (const void*)k_fft_corr<C>, (const void*)k_fft_field<C>,
                         (const void*)k_fft_noise<C>};
-    const int bytes = (int)smem_bytes(c->fft->P, C);
+    const int bytes = (int)plan_smem(c->fft);
     for (const void* k : ks) TWA_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     if (C > 1) {   // the cluster must fit: C SMs of one GPC, each holding one such CTA
         cudaLaunchConfig_t cfg = {};
@@ -1056,12 +1090,49 @@ int fft_prepare(twa_ctx* c) {
     k_fft_sequence<<<(unsigned)((P / 2 + 256) / 256), 256, 0, c->stream>>>(cseq, P, c->alpha, c->w);
     k_fft_lambda<<<g, 256, 0, c->stream>>>(f->lam, f->nscale, f->nfreq, cseq, P, rp);
     TWA_CUDA(c, cudaGetLastError());
+    // one CTA: direct twiddle tables for the stages, smallest first, while they fit
+    // the shared memory beside the transform (TWA_FFT_DIRECT_TW = 0: none)
+    for (int s = 0; s < 40; ++s) f->dtw_off[s] = -1;
+    f->dtw_total = 0;
+    if (C == 1 && f->nst > 1 && env_int("TWA_FFT_DIRECT_TW", 1) != 0) {
+        std::vector<int64_t> off(f->nst, -1), step(f->nst, 0), len(f->nst, 0);
+        std::vector<int64_t> ms(f->nst);
+        for (int64_t s = 0, m = P; s < f->nst; ++s) ms[s] = (m /= f->radix[s]);
+        // (1 KB kept back for the kernels' static shared memory)
+        const int64_t room = ((int64_t)max_smem - 1024 - (int64_t)smem_bytes(P, 1)) / (int64_t)sizeof(float2);
+        for (int s = f->nst - 2; s >= 0; --s) {   // the middle stage (stride 1) has no twiddles
+            if (f->dtw_total + ms[s] > room) break;
+            off[s] = f->dtw_total;
+            len[s] = ms[s];
+            step[s] = P / (ms[s] * f->radix[s]);
+            f->dtw_off[s] = (int)f->dtw_total;
+            f->dtw_total += ms[s];
+        }
+        if (f->dtw_total > 0) {
+            Scratch<int64_t> meta(c, c->stream);
+            if (dev_malloc(c, &f->dtw, sizeof(float2) * f->dtw_total) != cudaSuccess ||
+                meta.alloc(sizeof(int64_t) * 3 * f->nst) != cudaSuccess)
+                return set_error(c, TWA_ENOMEM, "device allocation of the FFT plan");
+            std::vector<int64_t> h(3 * f->nst);
+            for (int s = 0; s < f->nst; ++s) {
+                h[s] = off[s];
+                h[f->nst + s] = step[s];
+                h[2 * f->nst + s] = len[s];
+            }
+            TWA_CUDA(c, cudaMemcpyAsync(meta.p, h.data(), sizeof(int64_t) * h.size(), cudaMemcpyHostToDevice,
+                                        c->stream));
+            k_fft_stage_tables<<<64, 256, 0, c->stream>>>(f->dtw, f->tw, meta.p, meta.p + f->nst,
+                                                          meta.p + 2 * f->nst, f->nst);
+            TWA_CUDA(c, cudaGetLastError());
+            TWA_CUDA(c, cudaStreamSynchronize(c->stream));   // h and meta live until here
+        }
+    }
     return with_c(C, [&](auto cc) { return set_smem<decltype(cc)::value>(c); });
 }
 
 void fft_free(twa_ctx* c) {
     if (!c->fft) return;
-    void* p[] = {c->fft->lam, c->fft->tw, c->fft->nscale, c->fft->nfreq};
+    void* p[] = {c->fft->lam, c->fft->tw, c->fft->nscale, c->fft->nfreq, c->fft->dtw};
     for (void* q : p) dev_free(c, q);
     delete c->fft;
     c->fft = nullptr;

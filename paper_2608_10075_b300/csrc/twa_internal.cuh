@@ -92,6 +92,11 @@ struct FftPlan {
     unsigned local_mask = 0;     // bit s: the stage of stride P / (r_0 ... r_s) stays inside one CTA
     int wl = 0;                  // one CTA: stages s >= wl run warp by warp (nst: none)
     int64_t Lw = 0;              // block span of stage wl (each warp owns whole blocks)
+    // one CTA: direct twiddle tables w_L^j, j < m_s, of the stages whose tables fit
+    // the shared memory left beside the transform (dtw_off[s] = -1: two-level lookup)
+    float2* dtw = nullptr;
+    int dtw_off[40];
+    int64_t dtw_total = 0;
     int nst = 0;                 // number of stages
     int radix[40] = {0};         // radix of each stage (DIF order)
     float* lam = nullptr;        // spectrum of the embedding, in the DIF output order
