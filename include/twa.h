@@ -179,8 +179,16 @@ typedef struct twa_opts {
                                 rounded to BF16), FP32 state, FP64 moments. Heun
                                 and midpoint; Cholesky noise draw. twa_field and
                                 twa_contract on such a context run the FP32
-                                tensor-core split                                   */
+                                tensor-core split. With precision TWA_PREC_BF16X2
+                                and N <= TWA_RESIDENT_TC_MAX_N the same route runs
+                                on the tensor cores: each CTA holds the BF16 hi + lo
+                                images of W and L and the BF16 images of its 32
+                                trajectories' state, predictor and noise in shared
+                                memory, the two FP32 accumulators in TMEM and the
+                                FP32 state in registers for all steps; the BF16X2
+                                arithmetic of the dense route                       */
 #define TWA_RESIDENT_MAX_N 512
+#define TWA_RESIDENT_TC_MAX_N 128
 
 /* Pump-noise draws. Circulant: on a circle of even length P >= 2N - 2 (the
    smallest 2^a 3^b 5^c), c_d = w / (1 + min(d, P - d))^alpha is the first row

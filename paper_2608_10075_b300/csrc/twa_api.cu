@@ -141,7 +141,7 @@ void drop_graphs(twa_ctx* c) {
 // Steps either replay the captured step graphs or launch the kernels directly
 // (profiling, very short runs, or TWA_NO_GRAPH set).
 int run_steps(twa_ctx* c, int64_t steps) {
-    if (c->res_W) return twa::res_run(c, steps);   // resident route: all steps in one launch
+    if (c->res_W || c->res_tc) return twa::res_run(c, steps);   // resident route: all steps in one launch
     int64_t t = c->steps;
     if (c->profiling || steps < 4 || c->graph_failed || getenv("TWA_NO_GRAPH")) return run_eager(c, t, steps);
     int rc;
@@ -217,10 +217,14 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
     if (o.ws_route != TWA_ROUTE_DENSE && o.ws_route != TWA_ROUTE_FFT && o.ws_route != TWA_ROUTE_RESIDENT)
         return set_error(nullptr, TWA_EINVAL,
                          "twa_init: ws_route must be TWA_ROUTE_DENSE, TWA_ROUTE_FFT or TWA_ROUTE_RESIDENT");
-    if (o.ws_route == TWA_ROUTE_RESIDENT && o.precision != TWA_PREC_FP32)
-        return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the resident route runs with precision TWA_PREC_FP32");
+    if (o.ws_route == TWA_ROUTE_RESIDENT && o.precision != TWA_PREC_FP32 && o.precision != TWA_PREC_BF16X2)
+        return set_error(nullptr, TWA_EUNSUPPORTED,
+                         "twa_init: the resident route runs with precision TWA_PREC_FP32 or TWA_PREC_BF16X2");
     if (o.ws_route == TWA_ROUTE_RESIDENT && N > TWA_RESIDENT_MAX_N)
         return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the resident route holds N <= 512 sites");
+    if (o.ws_route == TWA_ROUTE_RESIDENT && o.precision == TWA_PREC_BF16X2 && N > TWA_RESIDENT_TC_MAX_N)
+        return set_error(nullptr, TWA_EUNSUPPORTED,
+                         "twa_init: the tensor-core resident route (TWA_PREC_BF16X2) holds N <= 128 sites");
     if (o.ws_route == TWA_ROUTE_FFT && o.precision == TWA_PREC_FP64)
         return set_error(nullptr, TWA_EUNSUPPORTED, "twa_init: the FFT route runs with the tensor-core precisions only");
     if ((o.alloc == nullptr) != (o.free == nullptr))

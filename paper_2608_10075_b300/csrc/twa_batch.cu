@@ -235,12 +235,15 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
     if (opts) o = *opts;
     const bool resident = o.ws_route == TWA_ROUTE_RESIDENT;
     if (resident) {
-        // every point's whole run in one launch per CTA shape (FP32 SIMT)
-        if (o.precision != TWA_PREC_FP32)
-            return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: the resident route runs in TWA_PREC_FP32");
+        // every point's whole run in one launch per CTA shape (FP32 SIMT), or in
+        // one launch on the tensor cores (BF16X2, N <= 128)
+        if (o.precision != TWA_PREC_FP32 && o.precision != TWA_PREC_BF16X2)
+            return set_error(nullptr, TWA_EUNSUPPORTED,
+                             "twa_batch_run: the resident route runs in TWA_PREC_FP32 or TWA_PREC_BF16X2");
+        const int64_t nmax = o.precision == TWA_PREC_BF16X2 ? TWA_RESIDENT_TC_MAX_N : TWA_RESIDENT_MAX_N;
         for (int p = 0; p < n; ++p)
-            if (pts[p].N > TWA_RESIDENT_MAX_N)
-                return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: the resident route holds N <= 512");
+            if (pts[p].N > nmax)
+                return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: N too large for the resident route");
     } else {
         if (o.precision != TWA_PREC_BF16 && o.precision != TWA_PREC_BF16X3 && o.precision != TWA_PREC_BF16X2 &&
             o.precision != TWA_PREC_BF16L2)

@@ -148,9 +148,11 @@ struct twa_ctx {
     double* S = nullptr;     // [M][4] collective sums of the current state
     double* Sp = nullptr;    // [M][4] collective sums of the predictor
 
-    // resident route: FP32 copies of W and L (NULL on the other routes)
+    // resident route: FP32 copies of W and L (NULL on the other routes), or the
+    // tensor-core form (BF16X2, N <= TWA_RESIDENT_TC_MAX_N) on the images of tc
     float* res_W = nullptr;
     float* res_L = nullptr;
+    bool res_tc = false;
 
     // tensor-core (BF16 / BF16X3) path, and the FFT plan of the Toeplitz route
     twa::TcState* tc = nullptr;
@@ -379,6 +381,9 @@ void res_free(twa_ctx* c);
 int res_run(twa_ctx* c, int64_t steps);          // all steps in one launch
 // steps[k] steps of each resident context cs[k] in one launch per CTA shape
 int res_run_many(twa_ctx* const* cs, const int64_t* steps, int n, twa_ctx* lead, cudaStream_t st);
+// twa_restc.cu (resident route on the tensor cores)
+bool restc_capable(const twa_ctx* c);            // BF16X2 and N <= TWA_RESIDENT_TC_MAX_N
+int restc_run_many(twa_ctx* const* cs, const int64_t* steps, int n, twa_ctx* lead, cudaStream_t st);
 // twa_adjoint.cu
 int grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_traj);
 // twa_reduce.cu

@@ -349,6 +349,13 @@ bool res_config(int64_t N, int* T, bool* resident, size_t* smem) {
 }
 
 int res_prepare(twa_ctx* c) {
+    if (c->opts.precision == TWA_PREC_BF16X2) {   // the tensor-core form works on the images of tc
+        if (!restc_capable(c))
+            return set_error(c, TWA_EUNSUPPORTED, "the tensor-core resident route holds N <= " +
+                                                      std::to_string(TWA_RESIDENT_TC_MAX_N) + " sites");
+        c->res_tc = true;
+        return TWA_OK;
+    }
     int T;
     bool r;
     size_t b;
@@ -435,6 +442,18 @@ int launch_shape(twa_ctx* lead, int T, bool r, const ResProblem* d_probs, const 
 // fixed), in one launch per CTA shape, on `st`; step counters and sample counts
 // advanced. A context with steps[k] = 0 is skipped.
 int res_run_many(twa_ctx* const* cs, const int64_t* steps, int n, twa_ctx* lead, cudaStream_t st) {
+    // the tensor-core contexts in one launch of their own, the FP32 ones below
+    std::vector<int64_t> tc_steps(n, 0), simt_steps(n, 0);
+    bool any_tc = false;
+    for (int k = 0; k < n; ++k) {
+        (cs[k]->res_tc ? tc_steps : simt_steps)[k] = steps[k];
+        any_tc = any_tc || (cs[k]->res_tc && steps[k] > 0);
+    }
+    if (any_tc) {
+        const int rc = restc_run_many(cs, tc_steps.data(), n, lead, st);
+        if (rc) return rc;
+    }
+    steps = simt_steps.data();
     struct Item {
         int k, T, ctas;
         bool r;

@@ -6,6 +6,7 @@
     python -m paper_2608_10075_b300.studies linewidth [--N 500] [--alpha 1] [--wt 0.5]
     python -m paper_2608_10075_b300.studies scan [--T 1.0] [--small-route resident]
     python -m paper_2608_10075_b300.studies routes [--Ns 10000 20000 30000 60000] [--M 1024]
+    python -m paper_2608_10075_b300.studies resident [--Ns 16 64 100 128] [--M 1024] [--steps 2000]
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
@@ -35,6 +36,11 @@ noise draws) at N beyond the benchmark's 10^4, alpha = 1, w = N Gamma / 2,
 dt = 2e-5, M trajectories: time per step (CUDA events around twa_run after a
 warm-up) and spin-trajectory-steps per second, with the FFT route's circle
 length and CTAs per trajectory (one CTA up to P = 28000, else a cluster).
+
+resident: the small-N routes side by side -- the resident route on the tensor
+cores (BF16X2, N <= 128), the resident route in FP32 SIMT, the dense route
+(BF16X2) -- at alpha = 1, w = N Gamma / 2, dt = 0.05 / (Gamma N): time per step
+of one call of `steps` steps (CUDA events) after a warm-up call.
 
 Each study prints one JSON line per case.
 """
@@ -180,9 +186,10 @@ def scan_study(args):
     """The 96-point scan (N in {100, 300, 1000, 3000}, six alpha, four w, M = 512,
     dt = 0.02 / (N Gamma)) over the horizon T (the workload's is 1 / Gamma).
     Throughput counts N M steps per point. With --small-route resident the
-    points with N <= --resident-max-n run as one resident batch (FP32, each CTA
-    integrating its trajectories for all steps in one launch) on a stream of
-    their own, concurrently with the dense batch of the larger points."""
+    points with N <= --resident-max-n run as one resident batch (each CTA
+    integrating its trajectories for all steps in one launch; on the tensor cores
+    in the scan's precision when that is BF16X2 and N <= 128, else FP32) on a
+    stream of their own, concurrently with the dense batch of the larger points."""
     import threading
 
     from .configs import SCAN_POINTS, scan_points
@@ -196,8 +203,9 @@ def scan_study(args):
     if args.small_route == "resident":
         # the resident route is faster only where the dense one is launch-bound
         small = [p for p in pts if p["N"] <= args.resident_max_n]
+        res_prec = args.precision if args.precision == "bf16x2" and args.resident_max_n <= 128 else "fp32"
         groups = [("dense", args.precision, "dense", [p for p in pts if p["N"] > args.resident_max_n]),
-                  ("resident", "fp32", "resident", small)]
+                  ("resident", res_prec, "resident", small)]
     results, times = {}, {}
 
     def run_group(name, prec, route, gp, stream):
@@ -353,6 +361,28 @@ def routes_study(args):
                               "sigma_z": ob["sigma_z"], "nonfinite": ob["nonfinite"]}), flush=True)
 
 
+def resident_study(args):
+    import torch
+    for N in args.Ns:
+        for route, prec in (("resident", "bf16x2"), ("resident", "fp32"), ("dense", "bf16x2")):
+            if route == "resident" and prec == "bf16x2" and N > 128:
+                continue
+            with twa.TWA(N, 1.0, N / 2.0, 1.0, 0.05 / N, seed=0, precision=prec, ws_route=route,
+                         window_start=0.0) as g:
+                g.run(args.M, 10)
+                g.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.run(args.M, args.steps)
+                e1.record()
+                g.sync()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+            print(json.dumps({"study": "resident", "N": N, "route": route, "precision": prec, "M": args.M,
+                              "steps": args.steps, "us_per_step": 1e3 * ms / args.steps,
+                              "spin_traj_steps_per_s": N * args.M * args.steps / (ms * 1e-3)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -382,7 +412,7 @@ def main():
     f.add_argument("--dt-scale", type=float, default=0.02, help="dt = dt_scale / (Gamma N)")
     f.add_argument("--precision", default="bf16x3")
     f.add_argument("--route", choices=["dense", "resident"], default="dense",
-                   help="resident: every point's run in one launch (FP32, N <= 512)")
+                   help="resident: every point's run in one launch (FP32 for N <= 512, BF16X2 for N <= 128)")
     lw = sub.add_parser("linewidth")
     lw.add_argument("--N", type=int, default=500)
     lw.add_argument("--alpha", type=float, default=1.0)
@@ -410,9 +440,15 @@ def main():
     r.add_argument("--steps", type=int, default=20)
     r.add_argument("--warmup", type=int, default=3)
     r.add_argument("--precision", default="bf16x2")
+    rs = sub.add_parser("resident")
+    rs.add_argument("--Ns", type=int, nargs="+", default=[16, 64, 100, 128])
+    rs.add_argument("--M", type=int, default=1024)
+    rs.add_argument("--steps", type=int, default=2000)
     a = ap.parse_args()
     if a.cmd == "routes":
         routes_study(a)
+    elif a.cmd == "resident":
+        resident_study(a)
     elif a.cmd == "precision":
         precision_study(a)
     elif a.cmd == "phase":
