@@ -31,7 +31,8 @@ from paper_2608_10075_b300.configs import LARGE_N1E4 as CFG  # noqa: E402
 METRIC = "spin-traj-steps/s at N=1e4 (mixed vs FP64 GPU, observables within 3 SE)"
 UNIT = "spin-traj-steps/s"
 WORKLOAD = ("TWA stochastic Heun, N=10000 alpha=1 w=5000 Gamma=1 dt=2e-5, M=1024 trajectories/GPU, "
-            "BF16X2 tcgen05 contractions (hi+lo W, L against a BF16 operand), FP32 state")
+            "BF16B tcgen05 contractions (W and L one BF16 product, hi+lo within 64 columns of the diagonal, "
+            "against a BF16 operand), FP32 state")
 REF_SAMPLE_M = 16
 
 
@@ -149,20 +150,6 @@ class ClockSampler:
                 "interval_ms": self.interval}
 
 
-def contraction_flops(N, M, terms_w=3, terms_l=2):
-    """Tensor-core FLOPs per launch of each contraction kernel.
-
-    predict / correct: W.s over all N^2 entries for 2M columns with `terms_w`
-    products (BF16X3: 3, BF16X2: 2); noise_factor: L.eta over the N(N+1)/2
-    lower-triangular entries with `terms_l` products (hi and lo of L against the
-    BF16 noise: 2).
-    """
-    cols = 2 * M
-    wflops = 2.0 * N * N * cols * terms_w
-    lflops = 2.0 * (N * (N + 1) / 2.0) * cols * terms_l
-    return {"predict": wflops, "correct": wflops, "noise_factor": lflops}
-
-
 def fft_length(N):
     """Circle length of the Toeplitz route: the smallest even 2^a 3^b 5^c >= max(2, 2N - 2)."""
     P = max(2, 2 * N - 2)
@@ -248,17 +235,6 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
-
-
-def algorithmic_flops(N, M, lib_flops, launches, terms_w, terms_l):
-    """Algorithmic contraction FLOPs of the predictor or corrector launches:
-    one W.s (2 N^2 per column, 2M columns) each plus their share of the L.eta
-    tiles of the next step, counted once (no split-precision multiplier). The
-    library reports executed products (terms_w per W entry, terms_l per L
-    entry); the L.eta share is what remains after the W part."""
-    w_exec = 2.0 * N * N * 2 * M * terms_w * launches
-    l_exec = lib_flops - w_exec
-    return 2.0 * N * N * 2 * M * launches + l_exec / terms_l
 
 
 def precision_check(twa, stream, rank, precisions, M_sub=128, steps=200):
@@ -351,15 +327,17 @@ def run_ours(args, rank, world, dist):
     ctx.profile(False)
     c3 = clocks.mark()
     step_kernel_ms = sum(v[0] for v in prof.values()) / max(kp, 1)
-    terms_w = {"bf16x3": 3, "fp32": 3, "bf16x2": 2}.get(CFG["precision"], 1)
-    terms_l = {"bf16x3": 2, "fp32": 3, "bf16x2": 2, "bf16l2": 2}.get(CFG["precision"], 1)
-    flops = contraction_flops(N, M, terms_w, terms_l)
-    # the library reports the executed FLOPs of each launch it timed: the
-    # predictor and corrector launches of step t also carry L.eta tiles of t + 1
-    lib_flops = sum(prof[k][2] for k in flops)
-    in_mixed = prof["predict"][2] + prof["correct"][2] - kp * (flops["predict"] + flops["correct"])
-    assert min(abs(in_mixed), abs(in_mixed - kp * flops["noise_factor"])) <= 1e-6 * lib_flops, in_mixed
-    assert abs(prof["noise_factor"][2] - prof["noise_factor"][1] * flops["noise_factor"]) <= 1e-6 * lib_flops
+    # per launch class the library reports the tensor-core FLOPs it issued
+    # (products per entry of the precision, the two-product band included) and
+    # the algorithmic FLOPs of the contractions (2 N^2 per column for a W.s, 2
+    # per nonzero of L for an L.eta, counted once); the predictor and corrector
+    # launches of step t also carry the L.eta tiles of t + 1
+    flops = {"predict": 2.0 * N * N * 2 * M, "correct": 2.0 * N * N * 2 * M,
+             "noise_factor": 2.0 * (N * (N + 1) / 2.0) * 2 * M}
+    alg_total = sum(prof[k][3] for k in flops)
+    in_mixed = prof["predict"][3] + prof["correct"][3] - kp * (flops["predict"] + flops["correct"])
+    assert min(abs(in_mixed), abs(in_mixed - kp * flops["noise_factor"])) <= 1e-6 * alg_total, in_mixed
+    assert abs(prof["noise_factor"][3] - prof["noise_factor"][1] * flops["noise_factor"]) <= 1e-6 * alg_total
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     dominant = max((k for k in flops if prof[k][1]), key=lambda k: prof[k][0])
@@ -376,7 +354,7 @@ def run_ours(args, rank, world, dist):
     launches_per_step = prof[dominant][1] / kp
     d_ms = (ms / K) * share / launches_per_step
     d_exec = prof[dominant][2] / n_dom
-    d_algo = algorithmic_flops(N, M, prof[dominant][2], n_dom, terms_w, terms_l) / n_dom
+    d_algo = prof[dominant][3] / n_dom
     achieved = d_algo / (d_ms * 1e-3) / 1e12
     executed_tflops = d_exec / (d_ms * 1e-3) / 1e12
     step_algo = (2 * 2.0 * N * N * 2 * M + 2.0 * N * (N + 1) / 2.0 * 2 * M)   # W.s twice + L.eta once
@@ -468,7 +446,7 @@ def run_ours(args, rank, world, dist):
             N, M, side["fft_route_circulant_noise"]["kernel_ms_per_step"])
         # the dense route in the other tensor-core precisions (one-term BF16, TF32,
         # and the FP32-accurate TF32 split)
-        for prec in ("bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2"):
+        for prec in ("bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2", "bf16b"):
             if prec != CFG["precision"]:
                 side["dense_" + prec] = side_run(prec, "dense", min(K, 300), 3)
                 side["dense_" + prec]["speedup_vs_main"] = side["dense_" + prec]["value"] / value
@@ -479,7 +457,7 @@ def run_ours(args, rank, world, dist):
         side["fp64_gpu"]["mixed_speedup"] = value / side["fp64_gpu"]["value"]
     qualifier = None
     if not args.no_precision_check:
-        others = tuple(p for p in ("bf16x3", "bf16x2", "bf16l2") if p != CFG["precision"])
+        others = tuple(p for p in ("bf16x3", "bf16x2", "bf16l2", "bf16b") if p != CFG["precision"])
         qualifier = precision_check(twa, stream, rank, (CFG["precision"],) + (() if args.no_side else others))
     clocks.stop()
 

@@ -87,10 +87,20 @@ extern "C" {
                                 W.bf16(s) to ~2^-17; L.eta is the BF16X3 arithmetic.
                                 twa_run, twa_field, twa_contract, twa_batch_run,
                                 twa_grad                                             */
-#define TWA_PREC_BF16L2  6   /* W one BF16 product (W_hi*s_hi), L split as in BF16X2
-                                (L_hi*eta + L_lo*eta): the noise factor, whose rounding
-                                biases single-term BF16, keeps ~16 bits. Same coverage
-                                as TWA_PREC_BF16X2                                    */
+#define TWA_PREC_BF16L2  6   /* W one BF16 product (W_hi*s_hi) except within 64 columns
+                                of the diagonal, where it takes W_lo*s_hi too (the
+                                band: all W entries with j in [u - 64, u + 320) for
+                                the 256 rows i in [u, u + 256), u a multiple of 256);
+                                L split as in BF16X2 (L_hi*eta + L_lo*eta). The
+                                largest entries of the Toeplitz W, whose one-term
+                                rounding errors repeat on every row and bias the
+                                steady state, keep ~16 bits. Same coverage as
+                                TWA_PREC_BF16X2                                       */
+#define TWA_PREC_BF16B   7   /* W and L each one BF16 product (A_hi*v) off the band of
+                                TWA_PREC_BF16L2 and two (A_hi*v + A_lo*v) on it, their
+                                operand rounded once to BF16, FP32 accumulation, FP32
+                                state: ~1.03 products per entry of W and of L. Same
+                                coverage as TWA_PREC_BF16X2                           */
 
 typedef struct twa_ctx twa_ctx;   /* opaque, owned by the library */
 
@@ -325,7 +335,9 @@ TWA_API int twa_field(twa_ctx* ctx, const double* s, double* P, int64_t K);
  *  - BF16X3: W hi/lo against an hi/lo split of s (three products), or L hi/lo
  *    against s rounded once to BF16 (two products), FP32 accumulation;
  *  - BF16X2: W or L hi/lo against s rounded once to BF16 (two products);
- *  - BF16L2: W one BF16 product; L as in BF16X2;
+ *  - BF16L2: W one BF16 product, two within 64 columns of the diagonal; L as
+ *    in BF16X2;
+ *  - BF16B: W and L one BF16 product, two within 64 columns of the diagonal;
  *  - BF16: one product of BF16 images; TF32: one product of TF32 images;
  *  - FP32: TF32 hi/lo splits of both operands (three products).
  * On the FFT route TWA_MAT_W runs the FFT convolution, TWA_MAT_L the dense
@@ -365,7 +377,7 @@ typedef struct twa_grad_out {
  * recomputed from its checkpoint and the cotangent is pulled back through the
  * renormalisation, the Heun corrector and the predictor, with W.beta
  * contractions on the precision path of the context (FP64 SIMT, or the BF16,
- * BF16X3, BF16X2 or BF16L2 tensor-core arithmetic of the forward step with an
+ * BF16X3, BF16X2, BF16L2 or BF16B tensor-core arithmetic of the forward step with an
  * FP32 tape). Parameter derivatives use dW/dw = W/w,
  * dL/dw = L/(2w), dW/dalpha = -ln(1+|i-j|) W and the Cholesky derivative
  * dL = L Phi(L^-1 dW L^-T). The objective is linearised at the forward run's
@@ -398,7 +410,7 @@ typedef struct twa_point {
  * Every point gets its own pump matrix, Cholesky factor and M trajectories (set
  * up concurrently from several host threads, each on its own stream; seed
  * and opts as for twa_init; opts->precision must be TWA_PREC_BF16,
- * TWA_PREC_BF16X3, TWA_PREC_BF16X2 or TWA_PREC_BF16L2, opts->window_start is replaced by each point's, and every
+ * TWA_PREC_BF16X3, TWA_PREC_BF16X2, TWA_PREC_BF16L2 or TWA_PREC_BF16B, opts->window_start is replaced by each point's, and every
  * point runs the dense route with the Cholesky noise draw). A step of all
  * points still running is the single-context step done for all of them at
  * once: noise of the next step, one persistent launch with every point's W.s +
@@ -428,7 +440,7 @@ typedef struct twa_point {
  * CTAs of a cluster share each 256-row tile; TWA_TC_PAIR=0 turns this off);
  * every configuration gives the same results bit for bit.
  * Errors: TWA_EINVAL, TWA_EUNSUPPORTED (a precision other than BF16, BF16X3,
- * BF16X2 and BF16L2), plus those of twa_init and twa_sync. Synchronises. */
+ * BF16X2, BF16L2 and BF16B), plus those of twa_init and twa_sync. Synchronises. */
 TWA_API int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t seed, const twa_opts* opts,
                           twa_obs* out, int* tiles);
 
@@ -546,14 +558,17 @@ TWA_API int twa_wait_probe(twa_ctx* ctx, int64_t limit_us);
  * adds no synchronisation. Errors: TWA_EINVAL. */
 TWA_API int twa_profile(twa_ctx* ctx, int enable);
 
-/* Synchronise, then return per kernel class (TWA_PROF_*) the summed event time
- * in ms, the number of launches and the summed algorithmic tensor-core FLOPs
- * of the dense mixed-precision contractions (2 x multiply-adds of the defined
- * product over its nonzero entries -- all of W, the lower triangle of L --
- * times the tensor-core products per entry; 0 for other classes) since profiling
- * started, and clear the record. Each array holds TWA_PROF_KINDS entries and
- * may be NULL. */
-TWA_API int twa_profile_read(twa_ctx* ctx, double* ms, int64_t* launches, double* flops);
+/* Synchronise, then return per kernel class (TWA_PROF_*), summed over the
+ * launches since profiling started, the event time in ms, the number of
+ * launches, and for the dense mixed-precision contractions (0 for other
+ * classes) two FLOP counts: `flops`, the tensor-core FLOPs issued -- 2 x the
+ * multiply-adds over all of W and the lower triangle of L times the products
+ * per entry, plus the second product over the K stages of the two-product band
+ * (TWA_PREC_BF16L2, TWA_PREC_BF16B) -- and `alg_flops`, the algorithmic count:
+ * 2 x the multiply-adds of the defined products over their nonzero entries,
+ * counted once whatever the precision. Then clear the record. Each array holds
+ * TWA_PROF_KINDS entries and may be NULL. */
+TWA_API int twa_profile_read(twa_ctx* ctx, double* ms, int64_t* launches, double* flops, double* alg_flops);
 
 /* One-line description of the last error on ctx (or of the last failed
  * twa_init when ctx is NULL). Never NULL. */

@@ -12,10 +12,11 @@ SMALL_CHAIN = dict(name="N16-fp64", N=16, alpha=1.0, w=8.0, Gamma=1.0, M=1024, d
 MIXED_N1024 = dict(name="N1024-mixed", N=1024, alphas=(0.5, 1.0, 2.0), w=512.0, Gamma=1.0, M=4096, dt=1e-4, T=2.0,
                    window=1.0, precision="bf16x3")
 
-# W and L held as BF16 hi + lo images, FP32 state; the contractions take the
-# state and the noise rounded once to BF16 (precision "bf16x2")
-LARGE_N1E4 = dict(name="N10000-bf16x2", N=10000, alpha=1.0, w=5000.0, Gamma=1.0, M=1024, dt=2e-5, T=0.5,
-                  window=0.2, precision="bf16x2")
+# W and L as BF16 images, one product per entry except hi + lo within 64
+# columns of the diagonal; FP32 state; the contractions take the state and the
+# noise rounded once to BF16 (precision "bf16b")
+LARGE_N1E4 = dict(name="N10000-bf16b", N=10000, alpha=1.0, w=5000.0, Gamma=1.0, M=1024, dt=2e-5, T=0.5,
+                  window=0.2, precision="bf16b")
 
 SCAN_POINTS = dict(name="scan96", Ns=(100, 300, 1000, 3000), alphas=(0.25, 0.5, 0.75, 1.0, 1.5, 2.0),
                    n_w=4, M=512, Gamma=1.0, T=1.0)

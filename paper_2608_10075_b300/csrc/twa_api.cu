@@ -207,7 +207,7 @@ int twa_init(twa_ctx** out, int64_t N, double alpha, double w, double Gamma, dou
     if (!(w >= 0.0) || isinf(w)) return set_error(nullptr, TWA_EINVAL, "twa_init: w must be finite and >= 0");
     if (!(Gamma >= 0.0) || isinf(Gamma)) return set_error(nullptr, TWA_EINVAL, "twa_init: Gamma must be finite and >= 0");
     if (!(dt > 0.0) || isinf(dt)) return set_error(nullptr, TWA_EINVAL, "twa_init: dt must be finite and > 0");
-    if (o.precision < TWA_PREC_FP64 || o.precision > TWA_PREC_BF16L2)
+    if (o.precision < TWA_PREC_FP64 || o.precision > TWA_PREC_BF16B)
         return set_error(nullptr, TWA_EINVAL, "twa_init: unknown precision");
     if (o.init_state != -1 && o.init_state != 1) return set_error(nullptr, TWA_EINVAL, "twa_init: init_state must be +-1");
     if (!(o.window_start >= 0.0) || isinf(o.window_start))
@@ -494,7 +494,7 @@ int twa_grad(twa_ctx* c, const twa_grad_req* r, twa_grad_out* out, double* per_t
         return set_error(c, TWA_EINVAL, "twa_grad: traj_offset + M exceeds the 32-bit trajectory counter");
     if (!(c->w > 0.0)) return set_error(c, TWA_EUNSUPPORTED, "twa_grad: needs w > 0");
     if (c->opts.precision == TWA_PREC_TF32 || c->opts.precision == TWA_PREC_FP32)
-        return set_error(c, TWA_EUNSUPPORTED, "twa_grad: runs on the FP64 and BF16 precisions (BF16, BF16X3, BF16X2, BF16L2)");
+        return set_error(c, TWA_EUNSUPPORTED, "twa_grad: runs on the FP64 and BF16 precisions (BF16, BF16X3, BF16X2, BF16L2, BF16B)");
     if (c->opts.integrator != TWA_INT_HEUN)
         return set_error(c, TWA_EUNSUPPORTED, "twa_grad: differentiates the Heun integrator only");
     if (c->opts.noise_route != TWA_NOISE_CHOLESKY)
@@ -548,10 +548,10 @@ int twa_profile(twa_ctx* c, int enable) {
     return TWA_OK;
 }
 
-int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches, double* flops) {
+int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches, double* flops, double* alg_flops) {
     if (!c) return set_error(nullptr, TWA_EINVAL, "twa_profile_read: ctx is NULL");
     TWA_CUDA(c, cudaStreamSynchronize(c->stream));
-    double t[TWA_PROF_KINDS] = {0}, f[TWA_PROF_KINDS] = {0};
+    double t[TWA_PROF_KINDS] = {0}, f[TWA_PROF_KINDS] = {0}, fa[TWA_PROF_KINDS] = {0};
     int64_t n[TWA_PROF_KINDS] = {0};
     int rc = TWA_OK;
     for (auto& r : c->prof) {
@@ -561,6 +561,7 @@ int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches, double* flops) {
             t[r.kind] += e;
             n[r.kind] += 1;
             f[r.kind] += r.flops;
+            fa[r.kind] += r.alg;
         }
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -570,6 +571,7 @@ int twa_profile_read(twa_ctx* c, double* ms, int64_t* launches, double* flops) {
         if (ms) ms[k] = t[k];
         if (launches) launches[k] = n[k];
         if (flops) flops[k] = f[k];
+        if (alg_flops) alg_flops[k] = fa[k];
     }
     if (rc) return set_error(c, rc, "twa_profile_read: cudaEventElapsedTime failed");
     return TWA_OK;

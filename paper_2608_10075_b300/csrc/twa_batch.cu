@@ -246,7 +246,7 @@ extern "C" int twa_batch_run(const twa_point* pts, int n, int64_t M, uint64_t se
                 return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: N too large for the resident route");
     } else {
         if (o.precision != TWA_PREC_BF16 && o.precision != TWA_PREC_BF16X3 && o.precision != TWA_PREC_BF16X2 &&
-            o.precision != TWA_PREC_BF16L2)
+            o.precision != TWA_PREC_BF16L2 && o.precision != TWA_PREC_BF16B)
             return set_error(nullptr, TWA_EUNSUPPORTED, "twa_batch_run: batches run on the BF16 precision paths");
         o.ws_route = TWA_ROUTE_DENSE;
     }

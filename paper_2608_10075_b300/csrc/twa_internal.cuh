@@ -36,8 +36,10 @@ constexpr int TC_BK = 64;
 // Buffers of the mixed-precision path (twa_tc.cu, twa_fft.cu).
 struct TcState {
     int64_t M = 0, N = 0, ldk = 0, n_rt = 0;
-    int terms = 3;                               // products per W entry: 1 (BF16, BF16L2, TF32), 2 (BF16X2), 3 (BF16X3, FP32)
-    int lterms = 2;                              // products per L entry: 1 (BF16, TF32), 2, 3 (FP32)
+    int terms = 3;                               // products per W entry: 1 (BF16, BF16L2, BF16B, TF32), 2 (BF16X2), 3 (BF16X3, FP32)
+    int lterms = 2;                              // products per L entry: 1 (BF16, BF16B, TF32), 2, 3 (FP32)
+    int band = 0;                                // BF16L2, BF16B: 64-column blocks on each side of a 256-row
+                                                 // unit whose one-product entries take the lo product too
     int bn = 256, kc = 0;                        // tile width and K-stage configuration
     int pair = 0;                                // CTA pairs: 256-row tiles on clusters of two (cta_group::2)
     int num_sms = 148;
@@ -167,7 +169,8 @@ struct twa_ctx {
     struct ProfRec {
         int kind;
         cudaEvent_t a, b;
-        double flops;   // algorithmic tensor-core FLOPs of the launch (0: none)
+        double flops;   // tensor-core FLOPs the launch issues (0: none)
+        double alg;     // algorithmic FLOPs of its contractions (counted once)
     };
     bool profiling = false;
     std::vector<ProfRec> prof;
@@ -187,16 +190,16 @@ struct NvtxRange {
 struct ProfScope {
     twa_ctx* c;
     int kind;
-    double flops;
+    double flops, alg;
     cudaEvent_t a = nullptr, b = nullptr;
-    ProfScope(twa_ctx* ctx, int k, double fl = 0.0) : c(ctx), kind(k), flops(fl) {
+    ProfScope(twa_ctx* ctx, int k, double fl = 0.0, double al = 0.0) : c(ctx), kind(k), flops(fl), alg(al) {
         if (c->profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
             cudaEventRecord(a, c->stream);
     }
     ~ProfScope() {
         if (c->profiling && a && b) {
             cudaEventRecord(b, c->stream);
-            c->prof.push_back({kind, a, b, flops});
+            c->prof.push_back({kind, a, b, flops, alg});
         }
     }
 };

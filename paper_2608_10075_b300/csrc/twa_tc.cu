@@ -375,6 +375,7 @@ struct TcArgs {
     float fsc;                        // FIELD: factor applied to the accumulator (the image's scale)
     int renorm;
     int integ;                        // TWA_INT_HEUN or TWA_INT_MIDPOINT
+    int band;                         // one-product W tiles: see two_product_stages
     const float *X, *Y, *Z;           // PRED: s; CORR: s~ (midpoint scheme: s)
     const float *X0, *Y0, *Z0;        // CORR: s, the state before the step
     const float *Bnx, *Bny;           // PRED, CORR: noise part of the field increment
@@ -407,6 +408,20 @@ struct Group {
     const int32_t* sched_start = nullptr;
     int ctas = 0;   // grid of a scheduled launch
 };
+
+// K stages [kb0, kb1) of a tile of row unit rt (MROWS rows) that take two
+// products although the tile's product count is one (W in BF16L2, W and L in
+// BF16B): the entries
+// with j in [u - 64 band, u + 256 + 64 band), u = the 256-row-aligned start of
+// the tile's rows, i.e. every entry within 64 band columns of the diagonal (and
+// the same set of entries on single CTAs and on CTA pairs, whatever the K-stage
+// width bk, a divisor of 64). Off this band W is one BF16 product.
+__host__ __device__ __forceinline__ void two_product_stages(int64_t rt, int mrows, int bk, int band, int& kb0,
+                                                            int& kb1) {
+    const int64_t u = rt * mrows / 256 * 256;
+    kb0 = (int)((u - 64 * (int64_t)band) / bk);
+    kb1 = (int)((u + 256 + 64 * (int64_t)band) / bk);
+}
 
 // PAIR: launched in clusters of two CTAs that share each 256-row tile (row tiles
 // 2r and 2r + 1 of row unit r): both stream their own A rows and half of the B
@@ -541,9 +556,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 int md, nt;
                 resolve(t, mp, ap, rt, ct, md, nt);
                 // operands of this tile: W/L hi (+ lo), B hi (+ lo; never in a
-                // one-B configuration, which the host uses for at most two products)
-                const int na = (nt >= 2) ? 2 : 1, nb = (nt == 3 && !KCfg<KC>::ONE_B) ? 2 : 1;
-                const uint32_t tx = na * G_::A_BYTES + nb * G_::B_BYTES;
+                // one-B configuration, which the host uses for at most two products);
+                // a one-product W tile takes the lo image on its band stages
+                const int nb = (nt == 3 && !KCfg<KC>::ONE_B) ? 2 : 1;
+                int kb0 = 0, kb1 = 0;
+                if (nt == 1 && ap->band > 0) two_product_stages(rt, G_::MROWS, BK, ap->band, kb0, kb1);
                 if (grp.count && mp != prev) {
                     // descriptors written to global memory before the launch: make them
                     // visible to the tensor-map proxy before the first copy through them
@@ -561,6 +578,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                         ok = false;
                         break;
                     }
+                    const int na = (nt >= 2 || (kt >= kb0 && kt < kb1)) ? 2 : 1;
+                    const uint32_t tx = na * G_::A_BYTES + nb * G_::B_BYTES;
                     uint8_t* st = tiles + stage * G_::STAGE_BYTES;
                     const int kx = kt * BK;
                     if constexpr (PAIR) {
@@ -633,12 +652,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                 int md, nt;
                 resolve(t, mp, ap, rt, ct, md, nt);
                 const int nkt = k_tiles(ap, rt, md);
+                int kb0 = 0, kb1 = 0;
+                if (nt == 1 && ap->band > 0) two_product_stages(rt, G_::MROWS, BK, ap->band, kb0, kb1);
                 for (int kt = 0; kt < nkt; ++kt) {
                     if (!mbar_wait(&full[stage], ph, args.flags, true)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
+                    const bool lo_a = nt == 2 || (kt >= kb0 && kt < kb1);   // A lo against B hi
                     const uint32_t a0 = smem_u32(tiles + stage * G_::STAGE_BYTES);
                     const uint32_t a1 = a0 + G_::A_BYTES, b0 = a0 + 2 * G_::A_BYTES, b1 = b0 + G_::B_BYTES;
 #pragma unroll
@@ -649,7 +671,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                             issue(dcol, sdesc<KC>(a0 + ko), sdesc<KC>(b1 + ko), 1u);
                             issue(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), 1u);
                         }
-                        if (nt == 2) issue(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), 1u);
+                        if (lo_a) issue(dcol, sdesc<KC>(a1 + ko), sdesc<KC>(b0 + ko), 1u);
                     }
                     commit(&empty[stage]);
                     if (++stage == STAGES) {
@@ -1358,6 +1380,7 @@ TcArgs base_args(twa_ctx* c) {
     a.fsc = 1.0f;
     a.renorm = c->opts.renormalize;
     a.integ = c->opts.integrator;
+    a.band = t->band;
     a.flags = c->d_flags;
     return a;
 }
@@ -1440,14 +1463,25 @@ int tc_prepare(twa_ctx* c) {
     // BF16X3 and FP32: three for W (hi*hi + hi*lo + lo*hi); L two (BF16X3: the
     // noise is one BF16 value) or three (FP32: the noise is split too). BF16X2:
     // W and L split, their operand one BF16 value: two and two. BF16L2: W one
-    // BF16 product, L split: one and two. BF16, TF32: one and one.
+    // BF16 product, L split: one and two. BF16B: one and one. BF16, TF32: one
+    // and one. BF16L2 and BF16B take two products near the diagonal (band).
     switch (c->opts.precision) {
         case TWA_PREC_BF16X3: t->terms = 3; t->lterms = 2; break;
         case TWA_PREC_FP32: t->terms = 3; t->lterms = 3; break;
         case TWA_PREC_BF16X2: t->terms = 2; t->lterms = 2; break;
         case TWA_PREC_BF16L2: t->terms = 1; t->lterms = 2; break;
+        case TWA_PREC_BF16B: t->terms = 1; t->lterms = 1; break;
         default: t->terms = 1; t->lterms = 1; break;
     }
+    // BF16L2 (W) and BF16B (W and L): hi + lo within 64 columns of the diagonal
+    // (TWA_TC_BAND blocks of 64 on each side of each 256-row unit; 0 = one
+    // product everywhere), hi alone beyond: the largest entries, whose rounding
+    // errors would add up to the same one-signed error on every row of the
+    // Toeplitz W (and of its Cholesky factor, whose rows converge to one
+    // sequence), keep ~16 bits, at ~3 % more products than one per entry
+    const bool banded = c->opts.precision == TWA_PREC_BF16L2 || c->opts.precision == TWA_PREC_BF16B;
+    t->band = banded ? env_int("TWA_TC_BAND", 1) : 0;
+    if (t->band < 0 || t->band > 64) return set_error(c, TWA_EINVAL, "TWA_TC_BAND must be in 0 .. 64");
     // tile configuration: TWA_TC_BN in {128, 192, 256}, TWA_TC_KC in {0, 1, 3, 4}
     // (3: at most two products per entry, BN 128 or 256; 4: the same with 64-wide
     // K stages and 128-byte swizzle, BN 256).
@@ -1666,8 +1700,10 @@ struct MixPlan {
     int32_t* first[2] = {nullptr, nullptr};   // per launch: [ctas + 1] offsets into list
     int ctas[2] = {0, 0};
     int64_t tiles[2] = {0, 0};
-    double flops[2] = {0.0, 0.0};             // algorithmic tensor-core FLOPs per launch
-    double leta_flops = 0.0, w_flops = 0.0;   // of all L.eta tiles / all W.s tiles of one stage
+    double flops[2] = {0.0, 0.0};             // tensor-core FLOPs issued per launch
+    double alg[2] = {0.0, 0.0};               // algorithmic FLOPs per launch (counted once)
+    double leta_flops = 0.0, w_flops = 0.0;   // issued: all L.eta tiles / all W.s tiles of one stage
+    double leta_alg = 0.0, w_alg = 0.0;       // algorithmic: the same
     int64_t leta_tiles = 0;                   // tiles of the L.eta block
     std::vector<GroupDesc> host;              // host copy of desc
     twa_ctx* owner = nullptr;                 // whose allocator the tables came from
@@ -1760,25 +1796,49 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
             return set_error(ec, TWA_ENOMEM, "device noise part");
     }
 
-    // tile costs in K stages x products; algorithmic FLOPs per tile
+    // tile costs in K stages x products; FLOPs issued and algorithmic per tile
     std::vector<std::pair<int64_t, int32_t>> pjobs, cjobs, ljobs;
-    std::vector<double> fl(st[nprob]);
+    std::vector<double> fl(st[nprob]), fa(st[nprob]);
     for (int q = 0; q < n; ++q) {
         const int64_t N = cs[q]->N, M = cs[q]->M, n_ru = units_of(cs[q]->tc->n_rt);
         auto rows_of = [&](int64_t ru) { return std::min<int64_t>(bmu, N - ru * bmu); };
         auto cols_of = [&](int64_t ct) { return (double)std::min<int64_t>(bn, 2 * M - ct * bn); };
+        const int band = cs[q]->tc->band;
         for (int64_t x = 0; x < st[q + 1] - st[q]; ++x) {
             const int64_t rt = x / nct[q], ct = x - rt * nct[q];
-            const double f = 2.0 * rows_of(rt) * (double)N * cols_of(ct) * ntw;
-            pjobs.push_back({nk[q] * ntw, (int32_t)(st[q] + x)});
-            cjobs.push_back({nk[q] * ntw, (int32_t)(st[n + q] + x)});
+            // one-product W: its two-product band adds stages and K columns
+            int64_t kx = 0, cx = 0;
+            if (ntw == 1 && band > 0) {
+                int kb0, kb1;
+                two_product_stages(rt, (int)bmu, bk, band, kb0, kb1);
+                const int64_t a = std::max<int64_t>(kb0, 0), b = std::min<int64_t>(kb1, nk[q]);
+                if (b > a) {
+                    kx = b - a;
+                    cx = std::min<int64_t>(b * bk, N) - a * bk;
+                }
+            }
+            const double f = 2.0 * rows_of(rt) * (double)(N * ntw + cx) * cols_of(ct);
+            pjobs.push_back({nk[q] * ntw + kx, (int32_t)(st[q] + x)});
+            cjobs.push_back({nk[q] * ntw + kx, (int32_t)(st[n + q] + x)});
             fl[st[q] + x] = fl[st[n + q] + x] = f;
+            fa[st[q] + x] = fa[st[n + q] + x] = 2.0 * rows_of(rt) * (double)N * cols_of(ct);
             // the kernel hands out L.eta row units longest first
             const int64_t lrt = n_ru - 1 - rt;
             const int64_t k1 = std::min<int64_t>((lrt * bmu + bmu + bk - 1) / bk, nk[q]);
             const double r0 = (double)(lrt * bmu), r1 = r0 + rows_of(lrt);
-            ljobs.push_back({k1 * ntl, (int32_t)(st[2 * n + q] + x)});
-            fl[st[2 * n + q] + x] = 2.0 * ((r1 * (r1 + 1) - r0 * (r0 + 1)) / 2.0) * cols_of(ct) * ntl;   // triangle
+            int64_t lkx = 0, lcx = 0;
+            if (ntl == 1 && band > 0) {
+                int kb0, kb1;
+                two_product_stages(lrt, (int)bmu, bk, band, kb0, kb1);
+                const int64_t a = std::max<int64_t>(kb0, 0), b = std::min<int64_t>(kb1, k1);
+                if (b > a) {
+                    lkx = b - a;
+                    lcx = std::min<int64_t>(b * bk, N) - a * bk;
+                }
+            }
+            ljobs.push_back({k1 * ntl + lkx, (int32_t)(st[2 * n + q] + x)});
+            fa[st[2 * n + q] + x] = 2.0 * ((r1 * (r1 + 1) - r0 * (r0 + 1)) / 2.0) * cols_of(ct);   // triangle
+            fl[st[2 * n + q] + x] = fa[st[2 * n + q] + x] * ntl + 2.0 * rows_of(lrt) * (double)lcx * cols_of(ct);
         }
     }
     std::stable_sort(ljobs.begin(), ljobs.end(),
@@ -1824,12 +1884,19 @@ int mix_plan_build(twa_ctx* const* cs, int n, twa_ctx* ec, MixPlan* p) {
             std::sort(lists[L].begin() + firsts[L][c], lists[L].begin() + firsts[L][c + 1]);
         for (int32_t x : lists[L]) {
             p->flops[L] += fl[x];
+            p->alg[L] += fa[x];
             ++seen[x];
         }
     }
-    for (int64_t x = st[2 * n]; x < st[nprob]; ++x) p->leta_flops += fl[x];
+    for (int64_t x = st[2 * n]; x < st[nprob]; ++x) {
+        p->leta_flops += fl[x];
+        p->leta_alg += fa[x];
+    }
     p->leta_tiles = st[nprob] - st[2 * n];
-    for (int64_t x = 0; x < st[n]; ++x) p->w_flops += fl[x];
+    for (int64_t x = 0; x < st[n]; ++x) {
+        p->w_flops += fl[x];
+        p->w_alg += fa[x];
+    }
     // every tile in exactly one launch
     for (int64_t x = 0; x < st[nprob]; ++x)
         if (seen[x] != 1) return set_error(ec, TWA_EUNSUPPORTED, "dense step: internal error in the tile schedule");
@@ -1933,7 +2000,7 @@ int noise_part_alone(twa_ctx* c, int64_t t) {
     la.oBnx = odd ? ts->Bx1 : ts->Bx;
     la.oBny = odd ? ts->By1 : ts->By;
     const TcMaps lm{ts->tmLhi, ts->tmLlo, odd ? ts->tmE1 : ts->tmE, odd ? ts->tmElo1 : ts->tmElo};
-    ProfScope p(c, TWA_PROF_NOISE_FACTOR, ts->mix->leta_flops);
+    ProfScope p(c, TWA_PROF_NOISE_FACTOR, ts->mix->leta_flops, ts->mix->leta_alg);
     return launch_leta(c, lm, la);
 }
 }  // namespace
@@ -2008,14 +2075,14 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         if ((rc = noise_part_alone(c, t))) return rc;
         const GroupDesc* h = mp->host.data() + 3 * (t & 1);   // predictor, corrector, L.eta
         {
-            ProfScope p(c, TWA_PROF_PREDICT, mp->w_flops);
+            ProfScope p(c, TWA_PROF_PREDICT, mp->w_flops, mp->w_alg);
             rc = ntw == 3   ? launch_cfg<MODE_PRED, 3>(c, h[0].maps, h[0].args)
                  : ntw == 2 ? launch_cfg<MODE_PRED, 2>(c, h[0].maps, h[0].args)
                             : launch_cfg<MODE_PRED, 1>(c, h[0].maps, h[0].args);
         }
         if (rc) return rc;
         {
-            ProfScope p(c, TWA_PROF_CORRECT, mp->w_flops);
+            ProfScope p(c, TWA_PROF_CORRECT, mp->w_flops, mp->w_alg);
             rc = ntw == 3   ? launch_cfg<MODE_CORR, 3>(c, h[1].maps, h[1].args)
                  : ntw == 2 ? launch_cfg<MODE_CORR, 2>(c, h[1].maps, h[1].args)
                             : launch_cfg<MODE_CORR, 1>(c, h[1].maps, h[1].args);
@@ -2044,7 +2111,7 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         const GroupDesc* dp = mp->desc + mp->nprob * (t & 1);
         for (int L = 0; L < 2; ++L) {
             const Group g{dp, mp->start, mp->nprob, mp->list[L], mp->first[L], mp->ctas[L]};
-            ProfScope p(c, L == 0 ? TWA_PROF_PREDICT : TWA_PROF_CORRECT, mp->flops[L]);
+            ProfScope p(c, L == 0 ? TWA_PROF_PREDICT : TWA_PROF_CORRECT, mp->flops[L], mp->alg[L]);
             rc = ntw == 3   ? launch_cfg<MODE_MIX, 3>(c, none, fa, g, mp->tiles[L])
                  : ntw == 2 ? launch_cfg<MODE_MIX, 2>(c, none, fa, g, mp->tiles[L])
                             : launch_cfg<MODE_MIX, 1>(c, none, fa, g, mp->tiles[L]);

@@ -10,7 +10,7 @@
 
 precision: N = 1024, alpha in {0.5, 1, 2}, w = N Gamma / 2, dt = 1e-4, T = 2,
 window (1, 2]. The same trajectories (same seed and counters) run on the FP64
-path and on the mixed paths (BF16, TF32, BF16X3, BF16X2, BF16L2, FP32 from a TF32 split,
+path and on the mixed paths (BF16, TF32, BF16X3, BF16X2, BF16L2, BF16B, FP32 from a TF32 split,
 BF16X3 with the FFT pump field);
 each observable is reported with its standard error and, per mixed path, the
 paired difference to FP64 (mean over trajectories of the per-trajectory
@@ -86,14 +86,16 @@ def precision_study(args):
                 "fp64": {k: [ref_obs[k], ref_obs[k + "_se"]] for k in KEYS}, "fp64_seconds": ref_t}
         # the circulant draw has the same noise law but other per-trajectory values,
         # so only its unpaired difference (diff_over_se) measures its error
-        for name, prec, route, noise in (("bf16", "bf16", "dense", "cholesky"),
+        for name, prec, route, noise in [x for x in (("bf16", "bf16", "dense", "cholesky"),
                                          ("tf32", "tf32", "dense", "cholesky"),
                                          ("bf16x3", "bf16x3", "dense", "cholesky"),
                                          ("bf16x2", "bf16x2", "dense", "cholesky"),
                                          ("bf16l2", "bf16l2", "dense", "cholesky"),
+                                         ("bf16b", "bf16b", "dense", "cholesky"),
                                          ("fp32", "fp32", "dense", "cholesky"),
                                          ("bf16x3_fft", "bf16x3", "fft", "cholesky"),
-                                         ("fft_circulant_noise", "bf16x3", "fft", "circulant")):
+                                         ("fft_circulant_noise", "bf16x3", "fft", "circulant"))
+                                         if not args.only or x[0] in args.only]:
             obs, means, secs = _run(N, alpha, w, G, dt, steps, args.M_ref, t0, prec, route, noise)
             s = _linear_samples(means)
             paired = {}
@@ -399,6 +401,8 @@ def main():
     p.add_argument("--M-full", type=int, default=MIXED_N1024["M"])
     p.add_argument("--steps", type=int, default=0)
     p.add_argument("--alphas", type=float, nargs="*", default=None, help="a subset of the study's exponents")
+    p.add_argument("--only", nargs="*", default=None,
+                   help="a subset of the mixed cases (bf16 tf32 bf16x3 bf16x2 bf16l2 bf16b fp32 bf16x3_fft fft_circulant_noise)")
     f = sub.add_parser("phase")
     f.add_argument("--Ns", type=int, nargs="+", default=[100])
     f.add_argument("--alphas", type=float, nargs="+", default=[0.5, 1.0, 2.0])

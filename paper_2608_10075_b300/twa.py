@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libtwa.so")
 TWA_OK = 0
 ERRORS = {-1: "TWA_EINVAL", -2: "TWA_ENOTPSD", -3: "TWA_ENOMEM", -4: "TWA_ECUDA", -5: "TWA_ETIMEOUT",
           -6: "TWA_ENONFINITE", -7: "TWA_ESTATE", -8: "TWA_EUNSUPPORTED"}
-PRECISION = {"fp64": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "fp32": 4, "bf16x2": 5, "bf16l2": 6}
+PRECISION = {"fp64": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "fp32": 4, "bf16x2": 5, "bf16l2": 6, "bf16b": 7}
 
 
 class TWAError(RuntimeError):
@@ -149,7 +149,7 @@ _SIGNATURES = {
     "twa_correlation": (ctypes.c_int, [_P, ctypes.POINTER(CorrReq), ctypes.POINTER(CorrOut), _P, _P, _P, _P]),
     "twa_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "twa_wait_probe": (ctypes.c_int, [_P, ctypes.c_int64]),
-    "twa_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
+    "twa_profile_read": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "twa_last_error": (ctypes.c_char_p, [_P]),
     "twa_destroy": (None, [_P]),
 }
@@ -371,13 +371,14 @@ class TWA:
         self._check(lib().twa_profile(self._h, 1 if enable else 0))
 
     def profile_read(self):
-        """{kind: (total ms, launches, algorithmic tensor FLOPs)} of the kernels
-        timed since profile()."""
+        """{kind: (total ms, launches, tensor-core FLOPs issued, algorithmic
+        FLOPs)} of the kernels timed since profile()."""
         ms = (ctypes.c_double * len(PROF_KINDS))()
         n = (ctypes.c_int64 * len(PROF_KINDS))()
         fl = (ctypes.c_double * len(PROF_KINDS))()
-        self._check(lib().twa_profile_read(self._h, ms, n, fl))
-        return {k: (ms[i], n[i], fl[i]) for i, k in enumerate(PROF_KINDS)}
+        fa = (ctypes.c_double * len(PROF_KINDS))()
+        self._check(lib().twa_profile_read(self._h, ms, n, fl, fa))
+        return {k: (ms[i], n[i], fl[i], fa[i]) for i, k in enumerate(PROF_KINDS)}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -57,8 +57,12 @@ class BF16NoiseOracle(TWAOracle):
 
 # representation error of a W.s product per precision: BF16X3 splits W and s
 # (three products: 3 2^-18); BF16X2 splits W but rounds s once to BF16
-# (2^-9 + 2^-18); BF16L2 rounds both (2 2^-9). L.eta is split in all three.
-W_REP = {"bf16x3": 3 * 2.0 ** -18, "bf16x2": 2.0 ** -9 + 2.0 ** -18, "bf16l2": 2 * 2.0 ** -9 + 2.0 ** -18}
+# (2^-9 + 2^-18); BF16L2 and BF16B round both off their two-product band
+# (2 2^-9). L.eta is split (2^-17 after eta's own rounding, which the reference
+# shares) except in BF16B, whose L is one BF16 product off the band (2^-9).
+W_REP = {"bf16x3": 3 * 2.0 ** -18, "bf16x2": 2.0 ** -9 + 2.0 ** -18, "bf16l2": 2 * 2.0 ** -9 + 2.0 ** -18,
+         "bf16b": 2 * 2.0 ** -9 + 2.0 ** -18}
+L_REP = {"bf16b": 2.0 ** -9}
 
 
 def step_bound(o, sx, sy, sz, prec="bf16x3"):
@@ -71,7 +75,7 @@ def step_bound(o, sx, sy, sz, prec="bf16x3"):
     acc = (N / 16.0) * 2.0 ** -22                          # FP32 accumulation
     sd = math.sqrt(dt)
     lsum = np.maximum(np.abs(ex) @ absL.T, np.abs(ey) @ absL.T)
-    dq = sd * (2.0 ** -17 + 2.0 ** -24 + acc + 2e-6) * lsum
+    dq = sd * (L_REP.get(prec, 2.0 ** -17) + 2.0 ** -24 + acc + 2e-6) * lsum
     flip_x = np.abs(ex) * near_bf16_boundary(ex)
     flip_y = np.abs(ey) * near_bf16_boundary(ey)
     dq += sd * 2.0 ** -8 * np.maximum(flip_x @ absL.T, flip_y @ absL.T)

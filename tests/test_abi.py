@@ -78,7 +78,7 @@ def test_init_rejects_bad_options():
         twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=-1)
     assert e.value.code == -1
     with pytest.raises(twa.TWAError) as e:
-        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=7)          # one past TWA_PREC_BF16L2
+        twa.TWA(4, 1.0, 1.0, 1.0, 0.1, precision=8)          # one past TWA_PREC_BF16B
     assert e.value.code == -1 and "precision" in str(e.value)
     with pytest.raises(twa.TWAError) as e:
         twa.TWA(4, 1.0, 1.0, 1.0, 0.1, integrator=2)
@@ -109,7 +109,7 @@ def test_precision_and_integrator_constants_match_the_header():
     assert twa.PRECISION == {"fp64": val["TWA_PREC_FP64"], "bf16": val["TWA_PREC_BF16"],
                              "bf16x3": val["TWA_PREC_BF16X3"], "tf32": val["TWA_PREC_TF32"],
                              "fp32": val["TWA_PREC_FP32"], "bf16x2": val["TWA_PREC_BF16X2"],
-                             "bf16l2": val["TWA_PREC_BF16L2"]}
+                             "bf16l2": val["TWA_PREC_BF16L2"], "bf16b": val["TWA_PREC_BF16B"]}
     assert twa.INTEGRATOR == {"heun": val["TWA_INT_HEUN"], "midpoint": val["TWA_INT_MIDPOINT"]}
     import ctypes
     o = twa.Opts()

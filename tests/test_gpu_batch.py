@@ -67,12 +67,15 @@ def test_batch_equals_points_run_alone(tiles):
         assert math.isfinite(r["w_max"]) and r["nonfinite"] == 0
 
 
-@pytest.mark.parametrize("prec", ["bf16x2", "bf16l2"])
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16l2", "bf16b"])
 def test_batch_in_the_two_product_precisions_equals_points_run_alone(prec):
     from paper_2608_10075_b300 import twa
     M, seed = 64, 5
-    res, _ = twa.batch_run(POINTS, M, seed=seed, precision=prec)
-    for p, r in zip(POINTS, res):
+    # N = 700: rows whose W (and, in BF16B, L) lie mostly off the two-product band
+    pts = POINTS + ([dict(N=700, alpha=1.0, w=350.0, Gamma=1.0, dt=1e-4, steps=20, window_start=0.001)]
+                    if prec != "bf16x2" else [])
+    res, _ = twa.batch_run(pts, M, seed=seed, precision=prec)
+    for p, r in zip(pts, res):
         with twa.TWA(p["N"], p["alpha"], p["w"], p["Gamma"], p["dt"], seed=seed, precision=prec,
                      window_start=p["window_start"]) as g:
             g.run(M, p["steps"])

@@ -37,7 +37,7 @@ def _run(prec, M=128, steps=400):
     return _RUNS[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "bf16b"])
 def test_mixed_matches_fp64_gpu_at_n1e4(prec):
     M = 128
     obs, smp = {}, {}

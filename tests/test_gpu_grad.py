@@ -85,7 +85,7 @@ def test_fp64_adjoint_matches_crn_finite_difference_on_gpu():
     assert abs(r["dJ_dalpha"] - fd_a) <= 1e-5 * abs(fd_a)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "bf16b"])
 @pytest.mark.parametrize("objective", ["SpSm", "g2"])
 def test_mixed_adjoint_close_to_fp64(objective, prec):
     twa = _twa()

@@ -108,6 +108,33 @@ def test_profile_counts_launches():
     total = p["predict"][2] + p["correct"][2]
     assert abs(total - 4 * (2 * w + l_tri)) <= 1e-9 * total
     assert p["predict"][2] >= 4 * w and p["correct"][2] >= 4 * w
+    # and the algorithmic count: the same products counted once
+    alg = p["predict"][3] + p["correct"][3]
+    assert abs(alg - 4 * (2 * w / 3 + l_tri / 2)) <= 1e-9 * alg
+
+
+def test_profile_counts_the_two_product_band():
+    # BF16B at N = 1000 (four 256-row units): every W entry one product, plus a
+    # second over the K columns [u - 64, u + 320) of each unit's rows; L the
+    # same over its lower triangle, the band's stages counted in full
+    from paper_2608_10075_b300 import twa
+    N, M = 1000, 64
+    with twa.TWA(N, 1.0, 20.0, 1.0, 1e-3, precision="bf16b") as g:
+        g.run(M, 1)
+        g.profile(True)
+        g.run(M, 2)
+        p = g.profile_read()
+        g.profile(False)
+    cols = 2 * M
+    w_alg = 2.0 * N * N * cols
+    l_alg = 2.0 * (N * (N + 1) / 2) * cols
+    band_w = sum(min(256, N - u) * (min(u + 320, N) - max(u - 64, 0)) for u in range(0, N, 256))
+    band_l = sum(min(256, N - u) * (min(u + 256, N) - max(u - 64, 0)) for u in range(0, N, 256))
+    alg = p["predict"][3] + p["correct"][3]
+    issued = p["predict"][2] + p["correct"][2]
+    assert abs(alg - 2 * (2 * w_alg + l_alg)) <= 1e-9 * alg
+    want = 2 * (2 * (w_alg + 2.0 * band_w * cols) + l_alg + 2.0 * band_l * cols)
+    assert abs(issued - want) <= 1e-9 * issued, (issued, want)
 
 
 def test_profile_standalone_noise_factor_after_set_state():

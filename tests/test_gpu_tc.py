@@ -41,7 +41,7 @@ def _field_check(prec, N, K, alpha, w, seed=2):
     twa = _twa()
     rng = np.random.default_rng(seed)
     s = rng.choice([-1.0, 1.0], size=(K, N)) * rng.uniform(0.2, 1.7, size=(K, N))
-    if prec in ("bf16x2", "bf16l2"):
+    if prec in ("bf16x2", "bf16l2", "bf16b"):
         # these precisions round the operand once to BF16: give it exact BF16 values,
         # so that the check is of the W representation and the accumulation
         s = bf16(s)
@@ -65,7 +65,7 @@ def _field_check(prec, N, K, alpha, w, seed=2):
     return float(np.max(err / absref))
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2", "bf16b"])
 @pytest.mark.parametrize("N,K", [(16, 8), (300, 600), (129, 257), (1024, 512)])
 def test_field_contraction_bound(prec, N, K):
     # several 128-site row tiles and 256-row column tiles, with ragged tails
@@ -118,11 +118,11 @@ def _leta_bound(prec, N, absref):
     N/16 instruction steps, with a factor of two of margin."""
     rep = {"bf16x3": 2.0 ** -18 + 2.0 ** -24, "bf16": 2.0 ** -9, "tf32": 2.0 ** -11,
            "fp32": 2.0 ** -22 + 2.0 ** -24, "bf16x2": 2.0 ** -18 + 2.0 ** -24,
-           "bf16l2": 2.0 ** -18 + 2.0 ** -24}[prec]
+           "bf16l2": 2.0 ** -18 + 2.0 ** -24, "bf16b": 2.0 ** -9}[prec]
     return 2.0 * (rep + (N / 16.0) * 2.0 ** -22) * absref
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2", "bf16b"])
 @pytest.mark.parametrize("N,K", [(16, 8), (300, 600), (129, 257), (1024, 512)])
 def test_noise_factor_contraction_bound(prec, N, K):
     # the step's L.eta arithmetic alone (twa_contract, matrix L): BF16X3 takes L
@@ -143,6 +143,43 @@ def test_noise_factor_contraction_bound(prec, N, K):
         # the bound resolves the lo image: L hi alone (a dropped lo term) breaks it
         planted = eta @ bf16(L).T
         assert np.mean(np.abs(planted - ref) > bound) > 0.1
+
+
+@pytest.mark.parametrize("prec,matrix", [("bf16l2", "W"), ("bf16b", "W"), ("bf16b", "L"), ("bf16l2", "L")])
+def test_two_products_exactly_on_the_band(prec, matrix):
+    # unit vectors as operands (exact in BF16): the contraction returns the
+    # columns of W (or L) as the kernel represents them. For rows i in [u, u + 256)
+    # (u a multiple of 256) the entries with j in [u - 64, u + 320) -- every entry
+    # within 64 of the diagonal -- take hi + lo (~2^-16 relative); every other
+    # entry is one BF16 product: the scale times bf16(entry / scale). BF16L2's L
+    # is split everywhere.
+    import torch
+    twa = _twa()
+    N, alpha, w = 1024, 1.0, 512.0
+    A = pump_matrix(N, alpha, w) if matrix == "W" else noise_factor(N, alpha, w)
+    scale = w if matrix == "W" else math.sqrt(w)
+    with twa.TWA(N, alpha, w, 1.0, 1e-4, precision=prec) as g:
+        eye = torch.eye(N, dtype=torch.float64, device="cuda")
+        P = (g.field(eye) if matrix == "W" else g.contract(eye, matrix="L")).cpu().numpy()
+    got = P.T                                   # got[i, j]: entry (i, j) as represented
+    i = np.arange(N)[:, None]
+    j = np.arange(N)[None, :]
+    u = (i // 256) * 256
+    band = (j >= u - 64) & (j < u + 320)
+    if prec == "bf16l2" and matrix == "L":
+        band = np.ones_like(band)
+    nz = A != 0.0
+    rel = np.abs(got - A) / np.where(nz, np.abs(A), 1.0)
+    assert np.all(rel[band & nz] <= 2.0 ** -15), float(np.max(rel[band & nz]))
+    assert np.all(got[~nz] == 0.0)
+    if not np.any(~band & nz):
+        return
+    one = scale * bf16(A / scale)               # one product: the BF16 image, rescaled
+    off = ~band & nz
+    assert np.all(np.abs(got[off] - one[off]) <= 2.0 ** -22 * np.abs(one[off])), \
+        float(np.max(np.abs(got[off] - one[off]) / np.abs(one[off])))
+    assert np.max(rel[off]) > 2.0 ** -12      # and the one-term rounding is really there
+    assert np.all(np.abs(i - j)[off] > 64)
 
 
 def test_noise_factor_contraction_full_size_sampled():
@@ -167,11 +204,12 @@ def test_noise_factor_contraction_full_size_sampled():
     assert np.mean(np.abs(planted - ref) > bound) > 0.1
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "bf16l2"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "bf16l2", "bf16b"])
 def test_split_noise_trajectories_track_bf16_noise_oracle(prec):
-    # every entry of three consecutive steps within the derived per-step bound
+    # every entry of three consecutive steps within the derived per-step bound;
+    # N = 1000 puts most of W and L off the two-product band of BF16L2 and BF16B
     twa = _twa()
-    for N, M in ((300, 200), (128, 128), (45, 3), (130, 257)):
+    for N, M in ((300, 200), (128, 128), (45, 3), (130, 257), (1000, 40)):
         alpha, w, G, dt = 1.0, 8.0, 1.0, 2e-3
         o = BF16NoiseOracle(N, alpha, w, G, dt, 11, M)
         with twa.TWA(N, alpha, w, G, dt, seed=11, precision=prec) as g:
@@ -204,7 +242,7 @@ def test_trajectories_track_oracle_for_a_few_steps(prec, tol, N, M):
             assert np.max(np.abs(gx ** 2 + gy ** 2 + gz ** 2 - 3.0)) < 5e-6
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32", "fp32", "bf16x2", "bf16l2", "bf16b"])
 def test_ensemble_observables_within_3se(prec):
     # N = 256, alpha = 1, w = 32, M = 512, dt = 1e-3, T = 1, window (0.5, 1]
     N, alpha, w, G, dt, M, T, t0 = 256, 1.0, 32.0, 1.0, 1e-3, 512, 1.0, 0.5
@@ -311,7 +349,7 @@ TILE_CONFIGS = {
 }
 
 
-@pytest.mark.parametrize("prec", ["bf16x2", "bf16l2", "bf16", "bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16l2", "bf16b", "bf16", "bf16x3"])
 @pytest.mark.parametrize("N,M", [(300, 200), (1024, 128)])
 def test_every_tile_configuration_gives_the_same_bits(monkeypatch, prec, N, M):
     # every K-stage configuration, on single CTAs or on CTA pairs (256-row
