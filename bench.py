@@ -472,7 +472,7 @@ def run_ours(args, rank, world, dist):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": CFG["precision"], "data": "synthetic",
+            "dtype": "bf16" if CFG["precision"].startswith("bf16") else CFG["precision"], "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "M_per_gpu": M, "alpha": CFG["alpha"], "w": CFG["w"],
                        "Gamma": CFG["Gamma"], "dt": CFG["dt"], "precision": CFG["precision"],
                        "parallelism": "trajectory shards, no data-path collective" if world > 1 else "single GPU",
