@@ -416,6 +416,9 @@ __global__ void __launch_bounds__(RC_THREADS, 1) k_restc(const RcProblem* probs,
         }
         __syncthreads();
     }
+    // after a timed-out wait, the MMAs of the abandoned step finish before TMEM
+    // is freed (a bounded wait on the commit it would have waited for)
+    if (!ok && e == 0) rc_wait(&bar[0], phase ^ 1u, P.flags);
     // state and window sums back to global memory
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
