@@ -352,6 +352,10 @@ def run_ours(args, rank, world, dist):
     serial_ms = step_kernel_ms - (prof["noise"][0] / kp if noise_overlapped and prof.get("noise") else 0.0)
     share = prof[dominant][0] / kp / serial_ms
     launches_per_step = prof[dominant][1] / kp
+    # every launch of a step (the profiled pass counts them per kernel class):
+    # predictor and corrector launches and the closing kernel, plus the noise
+    # kernel where the draw does not ride in the two launches
+    launches_per_step_all = int(round(sum(v[1] for v in prof.values()) / kp))
     d_ms = (ms / K) * share / launches_per_step
     d_exec = prof[dominant][2] / n_dom
     d_algo = prof[dominant][3] / n_dom
@@ -497,7 +501,7 @@ def run_ours(args, rank, world, dist):
                     "note": "set_state_f32 from pinned host FP32 buffers (the mixed-precision state), K steps, "
                             "moments and observables to host",
                     "fp64_host_state": {"value": e2e64, "h2d_bytes_per_step": h2d64 / K}},
-            "gpu_launches": 4 * K,   # per step: noise, predictor launch, corrector launch, close
+            "gpu_launches": launches_per_step_all * K,
             "clocks": clocks.stats(c0, c1),
             "sustained": sustained,
             "precision_check": qualifier,

@@ -65,6 +65,7 @@ struct TcState {
     // the noise draw of step t + 2 on a second stream beside step t's launches
     // (TWA_NOISE_OVERLAP = 0: on the context's stream, before them)
     bool overlap_noise = true;
+    bool noise_epi = true;                       // dense step: the noise of t + 2 drawn inside the MIX launches
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float* part = nullptr;                                // [n_rt][M][4] sums of s

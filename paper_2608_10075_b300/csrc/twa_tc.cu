@@ -388,6 +388,16 @@ struct TcArgs {
     float* part_out;                  // sums of the output state
     float* field_out;                 // FIELD: [n_vec][N]
     unsigned long long* flags;
+    // launch argument of the dense step's MIX launches: the noise of step
+    // *nz_dt + nz_toff (BF16 images of eta into nz_E0 / nz_E1 and xi into
+    // nz_XI0 / nz_XI1 by the parity of that step), draws [nz_lo, nz_hi) of the
+    // M x (N + 1) in the order of k_noise_tc, drawn by the epilogue threads
+    // between tiles (nz_E0 = NULL: none)
+    __nv_bfloat16 *nz_E0, *nz_E1;
+    float *nz_XI0, *nz_XI1;
+    const int64_t* nz_dt;
+    int64_t nz_toff, nz_lo, nz_hi, nz_m0;
+    uint64_t nz_seed;
 };
 
 // A batch of problems in one launch: descriptor table (tensor maps in global
@@ -691,6 +701,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
         const int q = warp & 3;              // TMEM lane quadrant of this warp
         const int grp_e = (warp - 2) >> 2;   // which share of the accumulator columns
         const int et = threadIdx.x - 64;     // 0 .. EPI_THREADS - 1
+        // MIX launches of the dense step: this CTA's share of the noise draws of a
+        // later step, in `parts` pieces, one after each of its tiles (all of it
+        // at the end when the CTA has no tile)
+        const TcArgs& la = args;
+        auto draw_noise = [&](int64_t part, int64_t parts) {
+            const int64_t per = (la.nz_hi - la.nz_lo + gridDim.x - 1) / gridDim.x;
+            const int64_t c0 = la.nz_lo + (int64_t)blockIdx.x * per;
+            const int64_t c1 = c0 + per < la.nz_hi ? c0 + per : la.nz_hi;
+            const int64_t sub = (per + parts - 1) / parts;
+            const int64_t s0 = c0 + part * sub;
+            const int64_t s1 = s0 + sub < c1 ? s0 + sub : c1;
+            if (s0 >= s1) return;
+            const int64_t NP = la.N + 1;
+            const int64_t st = *la.nz_dt + la.nz_toff;
+            __nv_bfloat16* E = (st & 1) ? la.nz_E1 : la.nz_E0;
+            float* XI = (st & 1) ? la.nz_XI1 : la.nz_XI0;
+            for (int64_t e = s0 + et; e < s1; e += EPI_THREADS) {
+                const int64_t m = e / NP, i = e - m * NP;
+                float gx, gy;
+                normal2_f32(la.nz_seed, (uint32_t)(la.nz_m0 + m), (uint32_t)st, (uint32_t)i, gx, gy);
+                if (i < la.N) {
+                    E[(2 * m) * la.ldk + i] = __float2bfloat16_rn(gx);
+                    E[(2 * m + 1) * la.ldk + i] = __float2bfloat16_rn(gy);
+                } else {
+                    XI[2 * m] = gx;
+                    XI[2 * m + 1] = gy;
+                }
+            }
+        };
+        const bool nz = MODE == MODE_MIX && la.nz_E0 != nullptr;
+        if (nz && n_mine == 0) draw_noise(0, 1);
         int it = 0;
         for (int64_t k = 0; k < n_mine; ++k, ++it) {
             const int64_t t = tile_of(k);
@@ -904,6 +945,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ TcMa
                     *(float4*)(args.part_out + (rt * M + m) * 4) = o;
                 }
             }
+            if (nz) draw_noise(k, n_mine);
         }
     }
     __syncthreads();
@@ -1504,6 +1546,9 @@ int tc_prepare(twa_ctx* c) {
     // corrector launches instead of the two mixed launches (same results)
     t->separate_leta = env_int("TWA_SEPARATE_LETA", 0) != 0;
     t->overlap_noise = env_int("TWA_NOISE_OVERLAP", 1) != 0;
+    // TWA_NOISE_EPILOGUE=0: the dense step's noise draw as its own kernel (on a
+    // second stream unless TWA_NOISE_OVERLAP=0) instead of inside the MIX launches
+    t->noise_epi = env_int("TWA_NOISE_EPILOGUE", 1) != 0;
     if (!tf32 &&
         (!(t->bn == 128 || t->bn == 192 || t->bn == 256) || !(t->kc == 0 || t->kc == 1 || t->kc == 3 || t->kc == 4)))
         return set_error(c, TWA_EINVAL, "TWA_TC_BN must be 128, 192 or 256 and TWA_TC_KC 0, 1, 3 or 4");
@@ -2090,16 +2135,21 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         if (rc) return rc;
     } else {
         // the noise of step t + 2 (read by the L.eta tiles of step t + 1) into the
-        // buffers of t's parity, which step t's launches do not read: on a second
-        // stream beside them (joined before the closing kernel advances the step
-        // counter the draw reads), or before them on this stream when profiling
-        const bool side = ts->overlap_noise && !c->profiling;
+        // buffers of t's parity, which step t's launches do not read. By default
+        // the epilogue threads of the two MIX launches draw it between their
+        // tiles (half in each launch; the BF16 precisions, whose noise operand is
+        // one image), where they would otherwise wait for the next accumulator;
+        // else as its own kernel: on a second stream beside the launches (joined
+        // before the closing kernel advances the step counter the draw reads), or
+        // before them on this stream when profiling
+        const bool epi = ts->noise_epi && !ts->Elo && ts->kc != 2;
+        const bool side = !epi && ts->overlap_noise && !c->profiling;
         if (side) {
             if ((rc = side_stream(c))) return rc;
             TWA_CUDA(c, cudaEventRecord(ts->ev_fork, c->stream));
             TWA_CUDA(c, cudaStreamWaitEvent(ts->side, ts->ev_fork, 0));
         }
-        {
+        if (!epi) {
             ProfScope p(c, TWA_PROF_NOISE);
             k_noise_tc<<<nblk(M * (N + 1), 256), 256, 0, side ? ts->side : c->stream>>>(
                 ts->E, ts->Elo, ts->XI, ts->E1, ts->Elo1, ts->XI1, M, N, ts->ldk, c->seed, c->d_t, 2,
@@ -2107,10 +2157,23 @@ int tc_launch_step(twa_ctx* c, int64_t t) {
         }
         if (side) TWA_CUDA(c, cudaEventRecord(ts->ev_join, ts->side));
         const TcMaps none{};
-        const TcArgs fa = base_args(c);   // flags of the launch
+        TcArgs fa = base_args(c);   // flags of the launch, and the noise draws it carries
+        if (epi) {
+            fa.nz_E0 = ts->E;
+            fa.nz_E1 = ts->E1;
+            fa.nz_XI0 = ts->XI;
+            fa.nz_XI1 = ts->XI1;
+            fa.nz_dt = c->d_t;
+            fa.nz_toff = 2;
+            fa.nz_m0 = c->opts.traj_offset;
+            fa.nz_seed = c->seed;
+        }
+        const int64_t nz_total = M * (N + 1);
         const GroupDesc* dp = mp->desc + mp->nprob * (t & 1);
         for (int L = 0; L < 2; ++L) {
             const Group g{dp, mp->start, mp->nprob, mp->list[L], mp->first[L], mp->ctas[L]};
+            fa.nz_lo = L == 0 ? 0 : nz_total / 2;
+            fa.nz_hi = L == 0 ? nz_total / 2 : nz_total;
             ProfScope p(c, L == 0 ? TWA_PROF_PREDICT : TWA_PROF_CORRECT, mp->flops[L], mp->alg[L]);
             rc = ntw == 3   ? launch_cfg<MODE_MIX, 3>(c, none, fa, g, mp->tiles[L])
                  : ntw == 2 ? launch_cfg<MODE_MIX, 2>(c, none, fa, g, mp->tiles[L])

@@ -53,15 +53,18 @@ def test_graph_replay_is_bit_exact(prec):
 
 
 @pytest.mark.parametrize("graph", [True, False])
-@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3", "bf16b", "fp32"])
 def test_noise_draw_beside_the_launches_gives_the_same_bits(monkeypatch, prec, graph):
-    # the noise of step t + 2 drawn on a second stream while step t's launches
-    # run (default) versus on the context's stream before them; with a
-    # continuation and a set_state in between (the noise is primed again)
+    # the noise of step t + 2 drawn by the epilogue threads of step t's two
+    # launches (default for the BF16 precisions), on a second stream while they
+    # run ("1": the FP32 precision's default), or on the context's stream before
+    # them ("0"); with a continuation and a set_state in between (the noise is
+    # primed again)
     from paper_2608_10075_b300 import twa
     out = {}
-    for overlap in ("1", "0"):
-        monkeypatch.setenv("TWA_NOISE_OVERLAP", overlap)
+    for overlap in ("epi", "1", "0"):
+        monkeypatch.setenv("TWA_NOISE_EPILOGUE", "1" if overlap == "epi" else "0")
+        monkeypatch.setenv("TWA_NOISE_OVERLAP", "1" if overlap == "epi" else overlap)
         if not graph:
             monkeypatch.setenv("TWA_NO_GRAPH", "1")
         with twa.TWA(260, 1.0, 20.0, 1.0, 1e-3, seed=9, precision=prec, window_start=0.004) as g:
@@ -71,10 +74,11 @@ def test_noise_draw_beside_the_launches_gives_the_same_bits(monkeypatch, prec, g
             g.set_state(x, y, z)
             g.run(70, 5)
             out[overlap] = (g.get_state(), g.observables())
-    for u, v in zip(out["1"][0], out["0"][0]):
-        assert np.array_equal(u, v)
-    for k in ("Sz", "SpSm", "G2num", "g2"):
-        assert out["1"][1][k] == out["0"][1][k]
+    for mode in ("1", "0"):
+        for u, v in zip(out["epi"][0], out[mode][0]):
+            assert np.array_equal(u, v), mode
+        for k in ("Sz", "SpSm", "G2num", "g2"):
+            assert out["epi"][1][k] == out[mode][1][k], (mode, k)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
@@ -86,7 +90,9 @@ def test_trajectory_shards_reproduce_one_run(prec):
         assert np.array_equal(u[40:], v)
 
 
-def test_profile_counts_launches():
+def test_profile_counts_launches(monkeypatch):
+    # the noise draw as its own kernel (TWA_NOISE_EPILOGUE=0), serial when profiling
+    monkeypatch.setenv("TWA_NOISE_EPILOGUE", "0")
     from paper_2608_10075_b300 import twa
     with twa.TWA(300, 1.0, 20.0, 1.0, 1e-3, precision="bf16x3") as g:
         g.run(130, 1)
@@ -113,6 +119,21 @@ def test_profile_counts_launches():
     assert abs(alg - 4 * (2 * w / 3 + l_tri / 2)) <= 1e-9 * alg
 
 
+def test_noise_drawn_inside_the_launches():
+    # by default the BF16 precisions' dense step has no noise kernel: the two
+    # launches of step t draw the noise of step t + 2 (the prime of a run draws
+    # steps t and t + 1 as before)
+    from paper_2608_10075_b300 import twa
+    with twa.TWA(300, 1.0, 20.0, 1.0, 1e-3, precision="bf16b") as g:
+        g.run(130, 1)
+        g.profile(True)
+        g.run(130, 4)
+        p = g.profile_read()
+        g.profile(False)
+    assert p["noise"][1] == 0
+    assert p["predict"][1] == 4 and p["correct"][1] == 4 and p["close"][1] == 4
+
+
 def test_profile_counts_the_two_product_band():
     # BF16B at N = 1000 (four 256-row units): every W entry one product, plus a
     # second over the K columns [u - 64, u + 320) of each unit's rows; L the
@@ -137,8 +158,9 @@ def test_profile_counts_the_two_product_band():
     assert abs(issued - want) <= 1e-9 * issued, (issued, want)
 
 
-def test_profile_standalone_noise_factor_after_set_state():
+def test_profile_standalone_noise_factor_after_set_state(monkeypatch):
     # a new state drops the precomputed noise part: one standalone L.eta launch
+    monkeypatch.setenv("TWA_NOISE_EPILOGUE", "0")
     from paper_2608_10075_b300 import twa
     with twa.TWA(300, 1.0, 20.0, 1.0, 1e-3, precision="bf16x3") as g:
         g.run(130, 2)
